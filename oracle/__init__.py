@@ -1,0 +1,14 @@
+"""FP64 CPU oracle for the periodic 1-D two-body Wigner 2-RDM step.
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may use this package; the product path never
+does.  It shares no code with the CUDA path (see ``w2_oracle.c``).
+
+Every function is pinned by ``tests/test_oracle_*.py`` against something other
+than itself: the paper's two closed forms (Sec. 5.1), a numpy FFT form of the
+pseudo-difference operator, exact discrete identities (antisymmetry, mass
+leak, exchange symmetry, integer rolls, spline Fourier multipliers),
+convergence to classical rotation in a harmonic well, and a brute-force
+two-particle Schroedinger evolution.
+"""
+from .oracle import Oracle, build, lib_path  # noqa: F401

@@ -1,0 +1,193 @@
+"""Seeded synthetic inputs for the periodic 1-D two-body Wigner 2-RDM step.
+
+This module is shared by the CUDA path's callers (tests, bench) and by the
+CPU oracle.  It holds problem *inputs* only -- the potentials as plain
+functions of one coordinate, the initial 2-RDM Wigner function and the
+random numbers -- and none of the method's arithmetic (no pseudo-difference
+operator, no spline, no time step).  It imports nothing from the package.
+
+Workloads (Sec. 5 of arXiv:2511.11354 runs Gaussian-type synthetic data; no
+dataset is involved):
+
+* ``small``  -- 32^4 grid, L = 20, V = 0.5 cos(2 pi x / L), W = 1/sqrt(r^2+1),
+  packets (x0=-3, p0=+0.5) x (x0=+3, p0=-0.5), dt = 0.01.
+* ``dwell``  -- 64^4 grid, L = 24, capped double well min(0.05 (x^2-16)^2, 20)
+  folded periodic, packet centres drawn U[-4, 4] from the seed, dt = 0.005.
+* ``dwell_literal`` -- the same with the uncapped well (explicitly unstable
+  for the Lawson step; kept as a negative test case).
+
+Initial data: a product of pure-state Gaussians
+G(x, p) = 1/(pi hbar) exp(-(x-x0)^2/(2 s^2) - 2 s^2 (p-p0)^2 / hbar^2)
+(the pure-state form used for the strongly correlated example, Sec. 5.3,
+with a = 1/(4 s^2)), plus 1e-3 max|g| uniform noise from SplitMix64, then
+exchange-symmetrised, then normalised to unit mass.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Callable
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, index: np.ndarray) -> np.ndarray:
+    """SplitMix64 output for stream ``seed`` at positions ``index`` (uint64).
+
+    The published SplitMix64 finaliser (Steele, Lea & Flood, 2014) applied
+    to the counter ``seed * golden + (index + 1) * golden``.
+    """
+    with np.errstate(over="ignore"):
+        z = (np.uint64(seed) * _GOLDEN + (index.astype(np.uint64) + np.uint64(1)) * _GOLDEN)
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, index: np.ndarray) -> np.ndarray:
+    """Doubles in [0, 1) from the top 53 bits of SplitMix64."""
+    return (splitmix64(seed, index) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def fold(x, L):
+    """Min-image fold of x into [-L/2, L/2) (x = +L/2 maps to -L/2)."""
+    return x - L * np.floor((x + 0.5 * L) / L)
+
+
+# ----------------------------------------------------------------------------
+# Potentials (plain functions of one coordinate in [-L/2, L/2))
+# ----------------------------------------------------------------------------
+
+def cos_potential(amplitude: float, L: float) -> Callable[[float], float]:
+    return lambda x: amplitude * math.cos(2.0 * math.pi * x / L)
+
+
+def soft_coulomb(eps: float = 1.0) -> Callable[[float], float]:
+    """Smoothed Coulomb kernel 1/sqrt(r^2 + eps) (Sec. 2, 1-D example)."""
+    return lambda r: 1.0 / math.sqrt(r * r + eps)
+
+
+def double_well(cap: float | None = 20.0) -> Callable[[float], float]:
+    """0.05 (x^2 - 16)^2, optionally capped at ``cap``."""
+    if cap is None:
+        return lambda x: 0.05 * (x * x - 16.0) ** 2
+    return lambda x: min(0.05 * (x * x - 16.0) ** 2, cap)
+
+
+def harmonic(omega: float) -> Callable[[float], float]:
+    return lambda x: 0.5 * omega * omega * x * x
+
+
+def gaussian_potential(height: float, width2: float = 2.0) -> Callable[[float], float]:
+    """height * exp(-x^2 / width2); the Gaussian two-body interaction of the
+    two-body convergence test uses height H_B and width2 = 2."""
+    return lambda x: height * math.exp(-x * x / width2)
+
+
+def zero_potential() -> Callable[[float], float]:
+    return lambda x: 0.0
+
+
+# ----------------------------------------------------------------------------
+# Problem description
+# ----------------------------------------------------------------------------
+
+@dataclass
+class Problem:
+    nx: int
+    nk: int
+    L: float
+    dt: float
+    vext: Callable[[float], float]
+    vee: Callable[[float], float]
+    gamma: float = 1.0
+    c_hartree: float = 1.0
+    c_xc: float = 0.0
+    xc_kind: int = 0          # 0 none, 1 phi(n) = n, 2 Hedin-Lundqvist
+    hbar: float = 1.0
+    mass: float = 1.0
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def dx(self) -> float:
+        return self.L / self.nx
+
+    @property
+    def dp(self) -> float:
+        # momentum lattice spacing fixed by the spatial period (Sec. 3.1)
+        return math.pi * self.hbar / self.L
+
+    def x(self) -> np.ndarray:
+        return -0.5 * self.L + self.dx * np.arange(self.nx)
+
+    def p(self) -> np.ndarray:
+        return (np.arange(self.nk) - self.nk // 2) * self.dp
+
+    @property
+    def points(self) -> int:
+        return self.nx * self.nx * self.nk * self.nk
+
+
+def gaussian_1body(x, p, x0, p0, sigma, hbar, L):
+    """Pure-state Gaussian Wigner function, min-image in x."""
+    u = fold(x - x0, L)
+    return (1.0 / (math.pi * hbar)) * np.exp(-u * u / (2 * sigma * sigma)
+                                             - 2 * sigma * sigma * (p - p0) ** 2 / (hbar * hbar))
+
+
+def initial_state(prob: Problem, centres, momenta=(0.5, -0.5), sigma: float = 1.0,
+                  noise: float = 1e-3, seed: int = 0) -> np.ndarray:
+    """Exchange-symmetrised product of two Gaussian packets plus seeded noise.
+
+    Returns f[i1][i2][n1][n2] (float64, C order), normalised to unit mass
+    sum(f) dx^2 dp^2 = 1.
+    """
+    x = prob.x()
+    p = prob.p()
+    ga = gaussian_1body(x[:, None], p[None, :], centres[0], momenta[0], sigma, prob.hbar, prob.L)
+    gb = gaussian_1body(x[:, None], p[None, :], centres[1], momenta[1], sigma, prob.hbar, prob.L)
+    # g(x1, x2, p1, p2) = ga(x1, p1) gb(x2, p2) in layout [i1][i2][n1][n2]
+    g = np.einsum("ac,bd->abcd", ga, gb)
+    if noise:
+        idx = np.arange(g.size, dtype=np.uint64).reshape(g.shape)
+        g = g + noise * np.max(np.abs(g)) * (2.0 * uniform01(seed, idx) - 1.0)
+    f = 0.5 * (g + g.transpose(1, 0, 3, 2))
+    mass = f.sum() * prob.dx ** 2 * prob.dp ** 2
+    return np.ascontiguousarray(f / mass)
+
+
+def draw_centres(seed: int, lo: float = -4.0, hi: float = 4.0):
+    u = uniform01(seed + 0x5EED, np.arange(2, dtype=np.uint64))
+    c = np.sort(lo + (hi - lo) * u)
+    return float(c[0]), float(c[1])
+
+
+# ----------------------------------------------------------------------------
+# Named workloads
+# ----------------------------------------------------------------------------
+
+def workload_small(nx: int = 32, nk: int = 32) -> tuple[Problem, np.ndarray]:
+    """32^4, L=20, cosine external potential, soft-Coulomb pair, 20 steps of dt=0.01."""
+    L = 20.0
+    prob = Problem(nx=nx, nk=nk, L=L, dt=0.01, vext=cos_potential(0.5, L), vee=soft_coulomb(1.0),
+                   gamma=1.0, c_hartree=1.0, name=f"small_{nx}x{nk}", meta={"steps": 20, "seed": 0})
+    f0 = initial_state(prob, centres=(-3.0, 3.0), seed=0)
+    return prob, f0
+
+
+def workload_dwell(nx: int = 64, nk: int = 64, literal: bool = False, seed: int = 1,
+                   dtype=np.float64) -> tuple[Problem, np.ndarray]:
+    """64^4 capped double well on L=24, soft-Coulomb pair, dt = 0.005."""
+    L = 24.0
+    prob = Problem(nx=nx, nk=nk, L=L, dt=0.005, vext=double_well(None if literal else 20.0),
+                   vee=soft_coulomb(1.0), gamma=1.0, c_hartree=1.0,
+                   name=("dwell_literal" if literal else "dwell") + f"_{nx}x{nk}",
+                   meta={"steps": 1000, "seed": seed, "obs_every": 10})
+    f0 = initial_state(prob, centres=draw_centres(seed), seed=seed)
+    return prob, f0.astype(dtype, copy=False)

@@ -1,0 +1,289 @@
+"""Benchmark: 4-D phase-space point-updates/s of the periodic two-body Wigner
+2-RDM Lawson step on GB300, plain FP64 path, 64^4 double-well workload.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl w2|reference]
+
+One JSON line on rank 0.  "value" is whole-job throughput (all ranks) with
+the state resident in HBM; "e2e" goes through the public C ABI with the state
+copied from pinned host memory and the observables read back every step.
+Each rank advances its own independent replica (the step has no exchange
+between replicas), so scaling is weak and there is no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import shutil
+import signal
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "4-D phase-space point-updates/s vs plain FP64 GPU path at fixed rel-L2 error"
+UNIT = "point-updates/s"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload_desc(prob):
+    return {"workload": f"double-well 2-RDM Wigner step, {prob.nx}^2 x {prob.nk}^2 grid, L={prob.L:g}, "
+                        f"dt={prob.dt:g}, soft-Coulomb pair gamma={prob.gamma:g}, Hartree c_H={prob.c_hartree:g}, "
+                        f"capped well min(0.05(x^2-16)^2,20)",
+            "nx": prob.nx, "nk": prob.nk, "points": prob.points,
+            "l2": "inputs larger than L2: four 134 MB FP64 phase-space arrays are streamed every step",
+            "parallelism": "replicas"}
+
+
+def _oracle_sample(prob_full, min_seconds):
+    """Time the FP64 oracle on a bounded sample of the workload: whole Lawson
+    steps of the same 64^4 problem, as many as fit in min_seconds (>= 1)."""
+    import oracle
+    from paper_2511_11354_gb300 import inputs
+    prob, f0 = inputs.workload_dwell(nx=prob_full.nx, nk=prob_full.nk)
+    o = oracle.Oracle(prob)
+    steps, t0 = 0, time.perf_counter()
+    f = f0
+    while True:
+        f = o.step(f, 1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds:
+            break
+    return {"value": prob.points * steps / el, "unit": UNIT, "cores": oracle.Oracle.threads(), "kind": "oracle",
+            "sample": f"{steps} oracle Lawson step(s) of the full {prob.nx}^2 x {prob.nk}^2 workload "
+                      f"from its initial state, {el:.1f} s"}
+
+
+class ClockSampler:
+    def __init__(self, index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        if shutil.which("nvidia-smi") is None:
+            return
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        self.fh = open(self.path, "w")
+        self.proc = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                      "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.send_signal(signal.SIGTERM)
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _fp64_peak():
+    """Live FP64 tensor-path (DMMA) and DFMA peaks from the committed probe."""
+    src = os.path.join(ROOT, "paper_2511_11354_gb300", "probe", "fp64_peak.cu")
+    exe = os.path.join(ROOT, "paper_2511_11354_gb300", "_build", "fp64_peak")
+    if not os.path.exists(exe) or os.path.getmtime(exe) < os.path.getmtime(src):
+        os.makedirs(os.path.dirname(exe), exist_ok=True)
+        subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src], check=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.strip().splitlines()[-1]
+    return json.loads(out)
+
+
+# DRAM bytes (read + write) of one k_theta launch on the 64^4 workload from one
+# ncu capture (profiles/k_theta_f64_dwell_64x64.md), keyed by the hash of the
+# kernel source it was taken on: any change to the source reports null.
+THETA_TRAFFIC = {"e3336d52875dc0b6": 134.504704e6 + 86.966784e6}
+
+
+def _theta_traffic():
+    import hashlib
+    src = os.path.join(ROOT, "paper_2511_11354_gb300", "csrc", "w2_f64.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return THETA_TRAFFIC.get(h)
+
+
+def theta_flops_per_point(nk):
+    """Algorithmic FP64 flops of one pseudo-difference operator per phase-space
+    point: 2 nk multiply-adds for the one-body shifts along p1 and p2 plus the
+    mean anti-diagonal length (sum_s len(s)^2 / nk^2) for the pair shift."""
+    lens = [min(s + 1, 2 * nk - 1 - s) for s in range(2 * nk - 1)]
+    diag = sum(l * l for l in lens) / (nk * nk)
+    return 2.0 * (2 * nk + diag)
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle on the host cores."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2511_11354_gb300 import inputs
+    oracle.build()
+    prob_full, _ = inputs.workload_dwell()
+    prob, f0 = inputs.workload_dwell(nx=16, nk=prob_full.nk)
+    o = oracle.Oracle(prob)
+    f = f0
+    for _ in range(args.warmup):
+        f = o.step(f, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = o.step(f, 1)
+    el = time.perf_counter() - t0
+    value = prob.points * args.steps / el
+    sample = (f"each step: one oracle Lawson step of the workload restricted to a 16x16 spatial grid "
+              f"(16^2 x {prob.nk}^2 = {prob.points} points)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _workload_desc(prob_full),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.Oracle.threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=250)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="w2", choices=["w2", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2511_11354_gb300 import build as w2build
+    from paper_2511_11354_gb300 import inputs, w2
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w2build.build()
+
+    prob, f0 = inputs.workload_dwell()
+    ctx = w2.Context.from_problem(prob)
+    f_dev = torch.from_numpy(f0).cuda()
+    ctx.set_state(f_dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- device-resident timed region: exactly K steps ---------------------
+    ctx.step(args.warmup)
+    barrier()
+    clocks = ClockSampler(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.step(args.steps)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    ob = ctx.observables()
+    value = prob.points * args.steps * ws / (ms / 1e3)
+
+    # ---- per-kernel times (events around every launch, same stream) -------
+    kprof = ctx.step_profile(min(args.steps, 50))
+    k_theta = 0.5 * (kprof[2] + kprof[7])
+    flops = theta_flops_per_point(prob.nk) * prob.points
+    peaks = _fp64_peak()
+    achieved = flops / (k_theta * 1e-3) / 1e12
+
+    # ---- end to end through the C ABI: pinned host state in, observables out
+    ctx.set_state(f_dev)
+    ctx.step(1)
+    host = torch.from_numpy(f0).pin_memory()
+    h2d = host.numel() * host.element_size()
+    d2h = 8 * (8 + prob.nx + prob.nx * prob.nx)
+    barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        w2._check(ctx.lib.w2_set_state(ctx.h, w2.ctypes.c_void_p(host.data_ptr()), 0), "w2_set_state")
+        ctx.step(1)
+        ctx.observables()
+    t1.record(stream)
+    barrier()
+    ms_e2e = max_over_ranks(t0.elapsed_time(t1))
+    e2e = prob.points * args.steps * ws / (ms_e2e / 1e3)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = _oracle_sample(prob, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _workload_desc(prob),
+            "clocks": clk,
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": len(w2.STEP_KERNELS) * args.steps,
+            "roofline": {"bound": "tensor", "kernel": "k_theta (FP64 mma.sync m8n8k4, DMMA)",
+                         "achieved": achieved, "peak": peaks["fp64_dmma_tflops"], "unit": "TFLOP/s",
+                         "frac": achieved / peaks["fp64_dmma_tflops"], "traffic": _theta_traffic(),
+                         "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+                         "peak_source": "measured live by paper_2511_11354_gb300/probe/fp64_peak.cu "
+                                        "(FP64 tensor path; MEASURED_PEAKS.json has no FP64 figure)",
+                         "fp64_dfma_tflops": peaks["fp64_dfma_tflops"],
+                         "flops_per_launch": flops, "ms_per_launch": k_theta},
+            "kernel_ms": dict(zip(w2.STEP_KERNELS, [float(x) for x in kprof])),
+            "observables": {"mass": ob.mass, "energy": ob.energy, "entropy_lin": ob.entropy_lin,
+                            "status": ob.status},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * w2.h -- C ABI of the GB300 (sm_103a) library that advances the Wigner
+ * function of the two-body reduced density matrix (2-RDM) of a spatially
+ * periodic 1-D two-particle system by one Lawson step.
+ *
+ * The equation stepped is the 2-RDM Wigner equation of arXiv:2511.11354
+ * (Sec. 2.4, Eq. two_body_truncated_Wigner):
+ *
+ *   d_t f + (p1/m) d_x1 f + (p2/m) d_x2 f
+ *       = Theta_{U1}[f] + Theta_{U2}[f] + Theta_{gamma W}[f],
+ *
+ * with U_i = V_ext + c_H V_H[n_i] + c_xc phi(n_i) the one-body (external +
+ * Hartree + exchange-correlation) potential of particle i, built from its
+ * density n_i, and W the pair interaction.  On the periodic box each Theta is
+ * the pseudo-difference operator of Sec. 3.1 (Eqs. Hartree_FSM and
+ * two_body_FSM), a sum of momentum shifts by multiples of dp = pi hbar / L.
+ * A time step is the Lawson predictor-corrector of Sec. 4.1 with the
+ * characteristic shift X -> X - tau P / m done by periodic cubic B-spline
+ * interpolation (Sec. 4.1, A_per).
+ *
+ * Grid (shared by every entry point):
+ *   x_i = -L/2 + i dx,  dx = L / nx,           i in [0, nx)
+ *   p_n = (n - nk/2) dp, dp = pi hbar / L,      n in [0, nk)
+ *   phase-space arrays are f[i1][i2][n1][n2], n2 fastest, C order,
+ *   nx*nx*nk*nk elements; f is zero outside the momentum window.
+ *
+ * Conventions:
+ *   - Every function returns a w2_status; nothing throws.  The first CUDA
+ *     error seen by a context sticks (every later call returns W2_ERR_CUDA)
+ *     until w2_destroy.
+ *   - The caller owns every pointer it passes; nothing is retained after a
+ *     call returns, except the CUDA stream given to w2_create (borrowed for
+ *     the lifetime of the context).
+ *   - Device pointers are CUDA global-memory addresses on the context's
+ *     device (for example torch tensor data_ptr()).  Host pointers are plain
+ *     host memory (pinned or pageable).
+ *   - Work is queued on the context's stream and returns immediately, except
+ *     where a function says it synchronises.
+ *   - There is no CPU fallback: without a usable sm_103a device w2_create
+ *     fails with W2_ERR_CUDA.
+ */
+#ifndef W2_H
+#define W2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  W2_OK = 0,
+  W2_ERR_ARG = -1,          /* invalid argument (size, pointer, value)          */
+  W2_ERR_CUDA = -2,         /* a CUDA runtime call or kernel launch failed       */
+  W2_ERR_OOM = -3,          /* device or host allocation failed                  */
+  W2_ERR_STATE = -4,        /* call order violated (e.g. step before set_state)  */
+  W2_ERR_UNSTABLE = -5,     /* tau * max|symbol| exceeds the stability bound     */
+  W2_ERR_NONFINITE = -6,    /* a NaN or Inf was found in the state               */
+  W2_ERR_TIMEOUT = -7,      /* a bounded device-side wait gave up                */
+  W2_ERR_UNSUPPORTED = -8   /* valid but not supported (grid size, precision)    */
+} w2_status;
+
+typedef enum {
+  W2_F64 = 0            /* FP64 state and arithmetic                              */
+} w2_precision;
+
+typedef enum {
+  W2_XC_NONE = 0,       /* no exchange-correlation term                           */
+  W2_XC_LINEAR = 1,     /* phi(n) = n (the exchange test potential of Sec. 5.1.1) */
+  W2_XC_HEDIN_LUNDQVIST = 2  /* phi(n) = 0.985 c + 0.985*0.034 ln(1 + 18.37 c), c = max(n,0)^{1/3}:
+                                the H-L form of Sec. 2.2 in atomic units          */
+} w2_xc_kind;
+
+/* Problem description (Sec. 3.1 grid; Sec. 5 uses hbar = m = 1).
+ *   nx  : spatial points per particle, 4 <= nx; FP64 supports nx <= 128
+ *   nk  : momentum points per particle; FP64 supports nk in {8,16,...,64}
+ *   L   : period of the box (> 0); dt: time step tau (> 0)
+ *   hbar, mass: > 0
+ *   precision: a w2_precision;  xc_kind: a w2_xc_kind                          */
+typedef struct {
+  int32_t nx, nk;
+  double L, dt, hbar, mass;
+  int32_t precision;
+  int32_t xc_kind;
+} w2_config;
+
+/* A potential evaluated on the HOST only, at arguments already folded into
+ * [-L/2, L/2); user is passed through unchanged. */
+typedef double (*w2_fn)(double x, void *user);
+
+/* Observables of the current state (Sec. 2 definitions; reductions in FP64,
+ * in a fixed order, so repeated calls give identical bits).
+ *   mass        = sum f dx^2 dp^2
+ *   energy      = sum f (p1^2/2m + p2^2/2m + V(x1) + V(x2) + gamma W(x1-x2)) dV
+ *                 + (c_H/2) sum_i [n_1 V_H[n_1] + n_2 V_H[n_2]](x_i) dx
+ *   purity      = Tr rho_1^2 = 2 pi hbar sum f1^2 dx dp, f1 = sum_{x2,p2} f dx dp
+ *   entropy_lin = 1 - purity (linear entropy of the one-body matrix)
+ *   l2norm      = sqrt(sum f^2 dV)
+ *   step        = number of steps taken since the last w2_set_state        */
+typedef struct {
+  double mass, energy, purity, entropy_lin, l2norm;
+  int64_t step;
+} w2_obs;
+
+typedef struct w2_ctx w2_ctx;
+
+/* Create a context on the current CUDA device.  cuda_stream is a cudaStream_t
+ * (NULL = legacy default stream), borrowed.  Allocates the device workspace
+ * (4 phase-space arrays plus small tables).  Errors: W2_ERR_ARG (bad config or
+ * out == NULL), W2_ERR_UNSUPPORTED (nk not supported for the precision),
+ * W2_ERR_OOM, W2_ERR_CUDA (no usable device).  *out is NULL on failure. */
+w2_status w2_create(const w2_config *cfg, void *cuda_stream, w2_ctx **out);
+
+/* Set the external potential V_ext (vext), the pair interaction W (vee), the
+ * pair strength gamma, and the weights c_hartree of the Hartree potential
+ * V_H[n](y) = gamma dx sum_q W(fold(y - x_q)) n(x_q) (Sec. 2.3, smoothed
+ * Coulomb example, on the torus) and c_xc of the XC potential (Sec. 2.2).
+ * vext == NULL means V_ext = 0; vee == NULL means W = 0.  The callbacks are
+ * called on the host during this call only (at x_i + l L/(2 nk) and at the
+ * pair distances d dx + l L/(2 nk)).  Builds the pair kernel tables on the
+ * device (queued on the stream).
+ * Errors: W2_ERR_ARG (non-finite parameter or callback value),
+ * W2_ERR_UNSTABLE when tau/hbar * (2 max|dV_ext| + gamma max|dW| +
+ * 2 |c_H| gamma (max W - min W)) > 1 (the worst mode of Heun's method on the
+ * imaginary axis then grows by more than sqrt(1 + 1/4) per step; the
+ * Hartree bound assumes unit mass), W2_ERR_CUDA. */
+w2_status w2_set_potentials(w2_ctx *ctx, w2_fn vext, void *ue, w2_fn vee, void *ui,
+                            double gamma, double c_hartree, double c_xc);
+
+/* Copy a full state f[nx][nx][nk][nk] (double) into the context: from device
+ * memory when on_device != 0, else from host memory.  Resets the step count.
+ * Queued on the stream (a host source is copied with cudaMemcpyAsync, so a
+ * pageable host buffer is copied before return).
+ * Errors: W2_ERR_ARG (NULL f), W2_ERR_STATE (potentials not set), W2_ERR_CUDA. */
+w2_status w2_set_state(w2_ctx *ctx, const void *f, int32_t on_device);
+
+/* Copy the current state out (same layout).  With on_device == 0 the call
+ * synchronises the stream before returning.  Errors: W2_ERR_ARG, W2_ERR_STATE
+ * (no state), W2_ERR_CUDA. */
+w2_status w2_get_state(w2_ctx *ctx, void *f, int32_t on_device);
+
+/* Advance the state by nsteps >= 0 Lawson steps (Sec. 4.1):
+ *   g  = Theta[f^n];  a = A_tau f^n;  b = A_tau g
+ *   f~ = a + tau b;   f^{n+1} = a + tau/2 (b + Theta[f~])
+ * where each Theta takes its HXC potential from the densities of its own input
+ * and A_tau g(X, P) = g(X - tau P / m, P) by periodic cubic splines.
+ * One step is captured once into a CUDA graph and replayed; queued on the
+ * stream.  Errors: W2_ERR_ARG (nsteps < 0), W2_ERR_STATE, W2_ERR_CUDA. */
+w2_status w2_step(w2_ctx *ctx, int32_t nsteps);
+
+/* Compute the observables of the current state.  Synchronises the stream.
+ * out (required) receives the scalars; n1 (host, [nx], or NULL) the density
+ * n_1(x_i) = sum f dx dp^2 over (x2, p1, p2); n12 (host, [nx*nx], or NULL) the
+ * pair density n_12(x_i1, x_i2) = sum f dp^2 over (p1, p2).
+ * Errors: W2_ERR_ARG, W2_ERR_STATE, W2_ERR_NONFINITE (NaN/Inf in the state; the
+ * outputs are still written), W2_ERR_CUDA. */
+w2_status w2_observables(w2_ctx *ctx, w2_obs *out, double *n1, double *n12);
+
+/* Operator-level entry points on caller-owned DEVICE arrays of the context's
+ * layout (f and out may not alias).  Queued on the stream.
+ *
+ * w2_theta:  out = Theta_V[f] of Eq. two_body_truncated_Wigner (Sec. 3.1
+ *            discretisation), the HXC potentials built from the densities of f.
+ * w2_advect: out = A_tau f, i.e. out(X, P) = f(X - tau P/m, P) by the periodic
+ *            cubic B-spline of Sec. 4.1, x1 and x2 in turn.
+ * Errors: W2_ERR_ARG (NULL or aliasing pointers; for w2_theta also a pointer
+ * not 16-byte aligned), W2_ERR_STATE (potentials not set), W2_ERR_CUDA.  Both use the context's workspace and must not overlap
+ * with w2_step on another stream. */
+w2_status w2_theta(w2_ctx *ctx, const double *f, double *out);
+w2_status w2_advect(w2_ctx *ctx, const double *f, double *out);
+
+/* Diagnostic form of w2_step: advances nsteps > 0 steps launching the step's
+ * W2_STEP_KERNELS kernels directly (no graph) with a CUDA event pair on the
+ * context's stream around each, and writes to kernel_ms[k] (host, length
+ * W2_STEP_KERNELS) the mean duration in milliseconds of kernel k of a step:
+ *   0 per-X sums of f^n   1 kernel tables (f^n)   2 Theta sweep, predictor
+ *   3 shift along x2      4 shift along x1 + Lawson combination
+ *   5 per-X sums of f~    6 kernel tables (f~)    7 Theta sweep, corrector
+ * The state advances exactly as with w2_step.  Synchronises the stream.
+ * Errors: W2_ERR_ARG (nsteps <= 0 or kernel_ms NULL), W2_ERR_STATE, W2_ERR_CUDA. */
+#define W2_STEP_KERNELS 8
+w2_status w2_step_profile(w2_ctx *ctx, int32_t nsteps, double *kernel_ms);
+
+/* Release every resource of the context (NULL is ignored). */
+void w2_destroy(w2_ctx *ctx);
+
+/* Static, human-readable name of a status code. */
+const char *w2_status_string(w2_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* W2_H */

@@ -29,8 +29,8 @@
  *   R6 Hartree on the torus: V_H(y) = gamma dx sum_q W(fold(y - x_q)) n(x_q),
  *      weighted by c_H.
  *   R7 XC: c_xc * phi(n), phi(n) = n (xc_kind 1) or the Hedin-Lundqvist form
- *      in atomic units (xc_kind 2); n between grid points by trigonometric
- *      interpolation.
+ *      in atomic units (xc_kind 2), evaluated at max(n, 0); n between grid
+ *      points by trigonometric interpolation.
  *   R8 Lawson: the HXC potential of each Theta is built from that Theta's
  *      input (f^n for the predictor, f~ for the corrector).
  *   R12 entropy: linear entropy 1 - Tr rho1^2, Tr rho1^2 = 2 pi hbar sum f1^2 dx dp.
@@ -239,7 +239,8 @@ static double trig_interp(const orc_problem *P, const double *n, double y) {
 
 static double phi_xc(int kind, double n) {
   if (kind == 1) return n;
-  if (kind == 2) { double c = cbrt(n); return 0.985 * c + 0.985 * 0.034 * log(1.0 + 18.37 * c); }
+  /* Hedin-Lundqvist (Sec. 2.2) in atomic units, defined for n >= 0 */
+  if (kind == 2) { double c = cbrt(n > 0.0 ? n : 0.0); return 0.985 * c + 0.985 * 0.034 * log(1.0 + 18.37 * c); }
   return 0.0;
 }
 

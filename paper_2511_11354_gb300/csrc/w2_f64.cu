@@ -1,0 +1,615 @@
+// FP64 kernels of the periodic two-body Wigner 2-RDM step (sm_103a).
+//
+//  k_tables   : densities -> one-body potential on the fine points -> the real
+//               shift kernels K(x, j) of the pseudo-difference operator
+//               (Sec. 3.1, Eqs. Hartree_FSM and two_body_FSM).
+//  k_theta    : X-local sweep.  Per phase-space point X = (x1, x2) the
+//               operator is three Toeplitz contractions of the nk x nk block
+//               F(p1, p2): K1(x1) along p1, K2(x2) along p2 and K12(x1 - x2)
+//               along the anti-diagonal p1 + p2 = const (the two-body shift
+//               (p1 + j dp, p2 - j dp)).  They run on the FP64 tensor path
+//               (mma.sync m8n8k4 f64), the anti-diagonal one after shearing
+//               the block in shared memory.  Fused epilogue: the Lawson
+//               corrector combination and the per-X momentum sums.
+//  k_adv      : P-local sweep.  Periodic cubic B-spline shift (Sec. 4.1) of
+//               every x-line by tau p / m, one axis per launch; the spline
+//               coefficients come from the causal/anti-causal factorisation
+//               of the (1, 4, 1)/6 circulant with exact periodic start values.
+//  k_xsum, k_obs_* : fixed-order FP64 reductions (deterministic).
+#include <math.h>
+
+#include "w2_internal.cuh"
+
+namespace w2 {
+
+// ---------------------------------------------------------------------------
+// Tables
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double phi_xc(int kind, double n) {
+  if (kind == 1) return n;
+  if (kind == 2) {  // Hedin-Lundqvist form, defined for n >= 0
+    double c = cbrt(fmax(n, 0.0));
+    return 0.985 * c + 0.985 * 0.034 * log1p(18.37 * c);
+  }
+  return 0.0;
+}
+
+// grid: (nx, 2) for one-body kernels (blockIdx.y = particle), (nx, 1) for the
+// pair kernel.  Dynamic shared memory: (nx + M) doubles.
+__global__ void k_tables(TabArgs a) {
+  extern __shared__ double sm[];
+  const int nx = a.nx, nk = a.nk, M = a.M;
+  double *n = sm, *U = sm + nx;
+  const int i = blockIdx.x, part = blockIdx.y, tid = threadIdx.x;
+  const bool mf = !a.pair_mode && a.xsum && (a.c_h != 0.0 || (a.c_xc != 0.0 && a.xc_kind));
+  if (mf) {
+    const double w = a.dx * a.dp * a.dp;
+    for (int q = tid; q < nx; q += blockDim.x) {
+      double s = 0.0;
+      if (part == 0)
+        for (int k = 0; k < nx; ++k) s += a.xsum[(size_t)q * nx + k];
+      else
+        for (int k = 0; k < nx; ++k) s += a.xsum[(size_t)k * nx + q];
+      n[q] = s * w;
+    }
+  }
+  __syncthreads();
+  for (int l = tid; l < M; l += blockDim.x) {
+    double u;
+    if (a.pair_mode) {
+      u = a.gamma * a.w_fine[(size_t)i * M + l];
+    } else {
+      u = a.vext_fine[(size_t)i * M + l];
+      if (mf && a.c_h != 0.0) {
+        double vh = 0.0;
+        for (int q = 0; q < nx; ++q) {
+          int d = i - q;
+          d += (d < 0) ? nx : 0;
+          vh += a.w_fine[(size_t)d * M + l] * n[q];
+        }
+        u += a.c_h * a.gamma * a.dx * vh;
+      }
+      if (mf && a.c_xc != 0.0 && a.xc_kind) {
+        double ni = 0.0;
+        for (int q = 0; q < nx; ++q) {
+          int d = i - q;
+          d += (d < 0) ? nx : 0;
+          ni += a.d_fine[(size_t)d * M + l] * n[q];
+        }
+        u += a.c_xc * phi_xc(a.xc_kind, ni);
+      }
+    }
+    U[l] = u;
+  }
+  __syncthreads();
+  const int W = 2 * nk - 1;
+  double *K = a.K + ((size_t)part * nx + i) * W;
+  const double inv = 1.0 / (a.hbar * nk);
+  for (int j = tid; j < nk; j += blockDim.x) {
+    double s = 0.0;
+    for (int l = 1; l < nk; ++l) {
+      int m = (l * j) % M;
+      s += (U[l] - U[M - l]) * a.sintab[m];
+    }
+    s *= inv;
+    K[nk - 1 + j] = s;
+    K[nk - 1 - j] = -s;
+  }
+}
+
+cudaError_t launch_tables(const TabArgs &a, cudaStream_t s) {
+  dim3 grid(a.nx, a.pair_mode ? 1 : 2);
+  size_t smem = sizeof(double) * (a.nx + a.M);
+  k_tables<<<grid, 128, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Theta sweep on the FP64 tensor path
+// ---------------------------------------------------------------------------
+
+// D(8x8) += A(8x4) B(4x8), FP64.  Fragments (PTX ISA, mma.m8n8k4 .f64):
+// a = A[lane>>2][lane&3], b = B[lane&3][lane>>2],
+// d0, d1 = D[lane>>2][2*(lane&3) + {0,1}].
+__device__ __forceinline__ void dmma(double &d0, double &d1, double a, double b) {
+  asm("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+      : "+d"(d0), "+d"(d1)
+      : "d"(a), "d"(b));
+}
+
+template <int NK>
+struct ThetaSmem {
+  static constexpr int T = NK / 8;     // 8x8 tiles per momentum axis
+  static constexpr int S = NK + 4;     // padded row stride (doubles): 2 wavefronts per fragment load
+  static constexpr int doubles = 2 * NK * S + 3 * 2 * NK + 8;
+  static constexpr size_t bytes = sizeof(double) * doubles;
+};
+
+// One CTA per spatial point X; warp w owns momentum rows n1 in [8w, 8w+8).
+// mode 0: out = Theta[in].  mode 1: out = h + half_tau * Theta[in] and, when
+// xsum is given, xsum[X] = sum_P out (fixed order).
+template <int NK, int MODE>
+__global__ void __launch_bounds__(NK * 4) k_theta(ThetaArgs a) {
+  using L = ThetaSmem<NK>;
+  constexpr int T = L::T, S = L::S;
+  extern __shared__ __align__(16) double sm[];
+  double *F = sm;               // [NK][S] input block
+  double *Acc = F + NK * S;     // [NK][S] two-body term, unsheared
+  double *k1 = Acc + NK * S;    // [2NK] K1(x1, j + NK - 1)
+  double *k2 = k1 + 2 * NK;
+  double *k12 = k2 + 2 * NK;
+  double *red = k12 + 2 * NK;   // [T]
+
+  const int nx = a.nx;
+  const int X = blockIdx.x;
+  const int i1 = X / nx, i2 = X - i1 * nx;
+  int dd = i1 - i2;
+  dd += (dd < 0) ? nx : 0;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int g = lane >> 2, t4 = lane & 3;
+
+  const size_t base = (size_t)X * NK * NK;
+  {
+    const double2 *src = reinterpret_cast<const double2 *>(a.in + base);
+    for (int e = tid; e < NK * NK / 2; e += blockDim.x) {
+      double2 v = src[e];
+      int r = (2 * e) / NK, c = (2 * e) - r * NK;
+      F[r * S + c] = v.x;
+      F[r * S + c + 1] = v.y;
+    }
+    const int W = 2 * NK - 1;
+    for (int j = tid; j < W; j += blockDim.x) {
+      k1[j] = a.K1[(size_t)i1 * W + j];
+      k2[j] = a.K2[(size_t)i2 * W + j];
+      k12[j] = a.K12[(size_t)dd * W + j];
+    }
+  }
+  __syncthreads();
+
+  const int n1 = 8 * w + g;  // A-fragment / D-fragment row of this lane
+
+  // Two-body term in sheared coordinates: T12'(n1, s) = sum_{n1'} K12(n1' - n1)
+  // G(n1', s), G(n1', s) = F(n1', s - n1') (zero outside the window).  Output
+  // tiles s in [8c, 8c + 8) with c in [w, w + T] cover every valid n2 = s - n1.
+  for (int c = w; c <= w + T; ++c) {
+    double d0 = 0.0, d1 = 0.0;
+    const int nlo = max(0, 8 * c - NK + 1), nhi = min(NK - 1, 8 * c + 7);
+    const int s = 8 * c + g;  // B-fragment column
+    for (int k = nlo >> 2; k <= (nhi >> 2); ++k) {
+      const int n1p = 4 * k + t4;
+      const double av = k12[n1p - n1 + NK - 1];
+      const int n2 = s - n1p;
+      const double bv = (n2 >= 0 && n2 < NK) ? F[n1p * S + n2] : 0.0;
+      dmma(d0, d1, av, bv);
+    }
+    const int n2a = 8 * c + 2 * t4 - n1;
+    if (n2a >= 0 && n2a < NK) Acc[n1 * S + n2a] = d0;
+    if (n2a + 1 >= 0 && n2a + 1 < NK) Acc[n1 * S + n2a + 1] = d1;
+  }
+  __syncwarp();
+
+  // One-body terms: T1 = A1(x1) F, T2 = F A2(x2)^T, accumulated on top of T12.
+  double acc[T][2];
+#pragma unroll
+  for (int b = 0; b < T; ++b) {
+    acc[b][0] = Acc[n1 * S + 8 * b + 2 * t4];
+    acc[b][1] = Acc[n1 * S + 8 * b + 2 * t4 + 1];
+  }
+#pragma unroll 2
+  for (int k = 0; k < NK / 4; ++k) {
+    const int kk = 4 * k + t4;
+    const double a1 = k1[kk - n1 + NK - 1];   // A1[n1][n1'] = K1(n1' - n1)
+    const double a2 = F[n1 * S + kk];          // F[n1][n2']
+#pragma unroll
+    for (int b = 0; b < T; ++b) {
+      const double b1 = F[kk * S + 8 * b + g];         // F[n1'][n2]
+      dmma(acc[b][0], acc[b][1], a1, b1);
+      const double b2 = k2[kk - (8 * b + g) + NK - 1]; // K2(n2' - n2)
+      dmma(acc[b][0], acc[b][1], a2, b2);
+    }
+  }
+
+  // Epilogue.
+  double local = 0.0;
+#pragma unroll
+  for (int b = 0; b < T; ++b) {
+    const size_t o = base + (size_t)n1 * NK + 8 * b + 2 * t4;
+    double2 v;
+    if (MODE == 0) {
+      v.x = acc[b][0];
+      v.y = acc[b][1];
+    } else {
+      const double2 hv = *reinterpret_cast<const double2 *>(a.h + o);
+      v.x = hv.x + a.half_tau * acc[b][0];
+      v.y = hv.y + a.half_tau * acc[b][1];
+      local += v.x + v.y;
+    }
+    *reinterpret_cast<double2 *>(a.out + o) = v;
+  }
+  if (MODE == 1 && a.xsum) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) local += __shfl_xor_sync(0xffffffffu, local, off);
+    if (lane == 0) red[w] = local;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int q = 0; q < T; ++q) s += red[q];
+      a.xsum[X] = s;
+    }
+  }
+}
+
+template <int NK>
+static cudaError_t prep_theta() {
+  cudaError_t e = cudaFuncSetAttribute(k_theta<NK, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)ThetaSmem<NK>::bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_theta<NK, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)ThetaSmem<NK>::bytes);
+}
+
+template <int NK>
+static cudaError_t run_theta(int mode, const ThetaArgs &a, cudaStream_t s) {
+  dim3 grid(a.nx * a.nx), block(NK * 4);
+  if (mode == 0)
+    k_theta<NK, 0><<<grid, block, ThetaSmem<NK>::bytes, s>>>(a);
+  else
+    k_theta<NK, 1><<<grid, block, ThetaSmem<NK>::bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Characteristic shift (periodic cubic B-spline), one axis per launch
+// ---------------------------------------------------------------------------
+
+// Spline-coefficient solve in place on a strided column (length n):
+// (1, 4, 1)/6 eta = f  ==>  eta = -6 z d, with the causal pass
+// c_i = f_i + z c_{i-1} and the anti-causal pass d_i = c_i + z d_{i+1}; both
+// started from their exact periodic values (geometric sums over the period).
+// The factor -6 z is folded into the evaluation weights.
+__device__ __forceinline__ void spline_coeffs(double *col, int stride, int n, double z, double zscale,
+                                              int nterm) {
+  double c0 = 0.0, zk = 1.0;
+  for (int k = 0; k < nterm; ++k) {
+    int idx = (n - k) % n;
+    c0 += zk * col[idx * stride];
+    zk *= z;
+  }
+  double prev = c0 * zscale;
+  col[0] = prev;
+  for (int i = 1; i < n; ++i) {
+    prev = fma(z, prev, col[i * stride]);
+    col[i * stride] = prev;
+  }
+  double dN = 0.0;
+  zk = 1.0;
+  for (int k = 0; k < nterm; ++k) {
+    int idx = (n - 1 + k) % n;
+    dN += zk * col[idx * stride];
+    zk *= z;
+  }
+  prev = dN * zscale;
+  col[(n - 1) * stride] = prev;
+  for (int i = n - 2; i >= 0; --i) {
+    prev = fma(z, prev, col[i * stride]);
+    col[i * stride] = prev;
+  }
+}
+
+// Value of the spline at x_i - shift: sum_{a=-1..2} w_a d_{(i + k0 + a) mod n}.
+__device__ __forceinline__ double spline_eval(const double *col, int stride, int n, int i, int k0,
+                                              double w0, double w1, double w2, double w3) {
+  int j = (i + k0 - 1) % n;
+  j += (j < 0) ? n : 0;
+  double v = w0 * col[j * stride];
+  j = (j + 1 == n) ? 0 : j + 1;
+  v = fma(w1, col[j * stride], v);
+  j = (j + 1 == n) ? 0 : j + 1;
+  v = fma(w2, col[j * stride], v);
+  j = (j + 1 == n) ? 0 : j + 1;
+  v = fma(w3, col[j * stride], v);
+  return v;
+}
+
+// DIR 0: lines along x2 at fixed (i1 = blockIdx.y, n1 = blockIdx.x); the
+//        shift of line n2 is tau p_{n2} / m.
+// DIR 1: lines along x1 at fixed (i2 = blockIdx.y, n1 = blockIdx.x); the
+//        shift of every line is tau p_{n1} / m.
+// TWO: shift in0 and in1 together.  With DIR 1 and TWO the outputs are
+//      out0 = a + tau b, out1 = a + tau/2 b (a = shifted in0, b = shifted in1).
+// One thread per momentum column n2; the slab [x][n2] is staged in shared memory.
+template <int NK, int DIR, int TWO>
+__global__ void __launch_bounds__(NK) k_adv(AdvArgs a) {
+  constexpr int S = NK + 1;
+  extern __shared__ double sm[];
+  const int nx = a.nx;
+  double *A0 = sm, *A1 = sm + (size_t)nx * S;
+  const int n1 = blockIdx.x, fixed = blockIdx.y, t = threadIdx.x;
+  const size_t lineStride = (DIR == 0) ? (size_t)NK * NK : (size_t)nx * NK * NK;
+  const size_t base = (DIR == 0) ? ((size_t)fixed * nx * NK + n1) * NK   // i1 fixed
+                                 : ((size_t)fixed * NK + n1) * NK;       // i2 fixed
+  for (int i = 0; i < nx; ++i) {
+    A0[i * S + t] = a.in0[base + i * lineStride + t];
+    if (TWO) A1[i * S + t] = a.in1[base + i * lineStride + t];
+  }
+  const int sidx = (DIR == 0) ? t : n1;
+  const int k0 = a.k0tab[sidx];
+  const double w0 = a.wtab[4 * sidx], w1 = a.wtab[4 * sidx + 1], w2 = a.wtab[4 * sidx + 2],
+               w3 = a.wtab[4 * sidx + 3];
+  spline_coeffs(A0 + t, S, nx, a.z, a.zscale, a.nterm);
+  if (TWO) spline_coeffs(A1 + t, S, nx, a.z, a.zscale, a.nterm);
+  for (int i = 0; i < nx; ++i) {
+    const double va = spline_eval(A0 + t, S, nx, i, k0, w0, w1, w2, w3);
+    const size_t o = base + i * lineStride + t;
+    if (!TWO) {
+      a.out0[o] = va;
+    } else {
+      const double vb = spline_eval(A1 + t, S, nx, i, k0, w0, w1, w2, w3);
+      if (DIR == 0) {
+        a.out0[o] = va;
+        a.out1[o] = vb;
+      } else {
+        a.out0[o] = fma(a.tau, vb, va);
+        a.out1[o] = fma(0.5 * a.tau, vb, va);
+      }
+    }
+  }
+}
+
+template <int NK>
+static cudaError_t prep_adv(int smem_max) {
+  cudaError_t e = cudaSuccess;
+#define W2_ADV_ATTR(D, T2)                                                                 \
+  e = cudaFuncSetAttribute(k_adv<NK, D, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                           smem_max);                                                      \
+  if (e != cudaSuccess) return e;
+  W2_ADV_ATTR(0, 0) W2_ADV_ATTR(0, 1) W2_ADV_ATTR(1, 0) W2_ADV_ATTR(1, 1)
+#undef W2_ADV_ATTR
+  return e;
+}
+
+template <int NK>
+static cudaError_t run_adv(int dir, int two, const AdvArgs &a, cudaStream_t s) {
+  dim3 grid(NK, a.nx), block(NK);
+  size_t smem = sizeof(double) * (size_t)(two ? 2 : 1) * a.nx * (NK + 1);
+  if (dir == 0 && !two) k_adv<NK, 0, 0><<<grid, block, smem, s>>>(a);
+  if (dir == 0 && two) k_adv<NK, 0, 1><<<grid, block, smem, s>>>(a);
+  if (dir == 1 && !two) k_adv<NK, 1, 0><<<grid, block, smem, s>>>(a);
+  if (dir == 1 && two) k_adv<NK, 1, 1><<<grid, block, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Reductions
+// ---------------------------------------------------------------------------
+
+// xsum[X] = sum_P f(X, P), one block per X, fixed-order tree.
+__global__ void k_xsum(const double *f, double *xsum, int nk) {
+  __shared__ double red[256];
+  const int X = blockIdx.x, tid = threadIdx.x;
+  const size_t base = (size_t)X * nk * nk;
+  double s = 0.0;
+  for (int e = tid; e < nk * nk; e += blockDim.x) s += f[base + e];
+  red[tid] = s;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (tid < h) red[tid] += red[tid + h];
+    __syncthreads();
+  }
+  if (tid == 0) xsum[X] = red[0];
+}
+
+cudaError_t launch_xsum_f64(int nx, int nk, const double *f, double *xsum, cudaStream_t s) {
+  k_xsum<<<nx * nx, 256, 0, s>>>(f, xsum, nk);
+  return cudaGetLastError();
+}
+
+// Per-X partials: [0] sum f, [1] sum f (p1^2 + p2^2), [2] sum f^2, [3 + n1] sum_{n2} f.
+__global__ void k_obs_x(ObsArgs a) {
+  __shared__ double red[3][128];
+  const int nk = a.nk, X = blockIdx.x, tid = threadIdx.x;
+  const size_t base = (size_t)X * nk * nk;
+  double *xp = a.xpart + (size_t)X * (3 + nk);
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int r = 0; r < nk; ++r) {
+    // row sums: thread tid handles column block; reduce per row below
+    double rv = 0.0;
+    for (int c = tid; c < nk; c += blockDim.x) {
+      const double v = a.f[base + (size_t)r * nk + c];
+      const double p1 = (r - nk / 2) * a.dp, p2 = (c - nk / 2) * a.dp;
+      rv += v;
+      s1 += v * (p1 * p1 + p2 * p2);
+      s2 += v * v;
+    }
+    s0 += rv;
+    red[0][tid] = rv;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+      if (tid < h) red[0][tid] += red[0][tid + h];
+      __syncthreads();
+    }
+    if (tid == 0) xp[3 + r] = red[0][0];
+    __syncthreads();
+  }
+  red[0][tid] = s0;
+  red[1][tid] = s1;
+  red[2][tid] = s2;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (tid < h) {
+      red[0][tid] += red[0][tid + h];
+      red[1][tid] += red[1][tid + h];
+      red[2][tid] += red[2][tid + h];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    xp[0] = red[0][0];
+    xp[1] = red[1][0];
+    xp[2] = red[2][0];
+  }
+}
+
+// Single block: fixed-order final reductions.
+// out: [0] mass [1] energy [2] purity [3] l2norm [4] nonfinite flag
+//      [8 .. 8+nx) n_1 ; [8+nx .. 8+nx+nx*nx) n_12
+__global__ void k_obs_final(ObsArgs a) {
+  __shared__ double red[6][256];
+  extern __shared__ double dyn[];  // n1[nx], n2[nx]
+  const int nx = a.nx, nk = a.nk, M = a.M, tid = threadIdx.x, nt = blockDim.x;
+  const double dV = a.dx * a.dx * a.dp * a.dp;
+  double *n1 = dyn, *n2 = dyn + nx;
+  double m0 = 0, ek = 0, ep = 0, l2 = 0, bad = 0;
+  for (int X = tid; X < nx * nx; X += nt) {
+    const double *xp = a.xpart + (size_t)X * (3 + nk);
+    const int i1 = X / nx, i2 = X % nx;
+    int d = i1 - i2;
+    d += (d < 0) ? nx : 0;
+    const double vx = a.vext_grid[i1] + a.vext_grid[i2] + a.gamma * a.w_fine[(size_t)d * M];
+    m0 += xp[0];
+    ek += xp[1];
+    l2 += xp[2];
+    ep += xp[0] * vx;
+    if (!isfinite(xp[0]) || !isfinite(xp[1]) || !isfinite(xp[2])) bad = 1.0;
+    a.out[8 + nx + X] = xp[0] * a.dp * a.dp;
+  }
+  for (int i = tid; i < nx; i += nt) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int k = 0; k < nx; ++k) {
+      s1 += a.xpart[((size_t)i * nx + k) * (3 + nk)];
+      s2 += a.xpart[((size_t)k * nx + i) * (3 + nk)];
+    }
+    n1[i] = s1 * a.dx * a.dp * a.dp;
+    n2[i] = s2 * a.dx * a.dp * a.dp;
+    a.out[8 + i] = n1[i];
+  }
+  __syncthreads();
+  // Hartree energy and purity
+  double eh = 0.0, pur = 0.0;
+  if (a.c_h != 0.0) {
+    for (int i = tid; i < nx; i += nt) {
+      double va = 0.0, vb = 0.0;
+      for (int q = 0; q < nx; ++q) {
+        int d = i - q;
+        d += (d < 0) ? nx : 0;
+        va += a.w_fine[(size_t)d * M] * n1[q];
+        vb += a.w_fine[(size_t)d * M] * n2[q];
+      }
+      eh += 0.5 * a.c_h * a.gamma * a.dx * (va * n1[i] + vb * n2[i]) * a.dx;
+    }
+  }
+  for (int e = tid; e < nx * nk; e += nt) {
+    const int i1 = e / nk, r = e % nk;
+    double s = 0.0;
+    for (int i2 = 0; i2 < nx; ++i2) s += a.xpart[((size_t)i1 * nx + i2) * (3 + nk) + 3 + r];
+    const double f1 = s * a.dx * a.dp;
+    pur += f1 * f1;
+  }
+  red[0][tid] = m0;
+  red[1][tid] = ek;
+  red[2][tid] = ep;
+  red[3][tid] = l2;
+  red[4][tid] = eh;
+  red[5][tid] = pur + bad * 0.0;
+  __shared__ int sbad;
+  if (tid == 0) sbad = 0;
+  __syncthreads();
+  if (bad != 0.0) sbad = 1;
+  for (int h = nt / 2; h > 0; h >>= 1) {
+    if (tid < h)
+      for (int q = 0; q < 6; ++q) red[q][tid] += red[q][tid + h];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const double mass = red[0][0] * dV;
+    const double energy = red[1][0] * dV / (2.0 * a.mass) + red[2][0] * dV + red[4][0];
+    const double purity = 2.0 * 3.14159265358979323846 * a.hbar * red[5][0] * a.dx * a.dp;
+    const double l2n = sqrt(red[3][0] * dV);
+    a.out[0] = mass;
+    a.out[1] = energy;
+    a.out[2] = purity;
+    a.out[3] = l2n;
+    a.out[4] = (sbad || !isfinite(mass) || !isfinite(energy) || !isfinite(purity) || !isfinite(l2n)) ? 1.0 : 0.0;
+  }
+}
+
+cudaError_t launch_obs_f64(const ObsArgs &a, cudaStream_t s) {
+  k_obs_x<<<a.nx * a.nx, 128, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_obs_final<<<1, 256, sizeof(double) * 2 * a.nx, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Dispatch on nk
+// ---------------------------------------------------------------------------
+
+bool nk_supported_f64(int nk) { return nk >= 8 && nk <= 64 && nk % 8 == 0; }
+
+#define W2_NK_SWITCH(nk, CALL)       \
+  switch (nk) {                      \
+    case 8: return CALL<8>;          \
+    case 16: return CALL<16>;        \
+    case 24: return CALL<24>;        \
+    case 32: return CALL<32>;        \
+    case 40: return CALL<40>;        \
+    case 48: return CALL<48>;        \
+    case 56: return CALL<56>;        \
+    case 64: return CALL<64>;        \
+    default: return cudaErrorInvalidValue; \
+  }
+
+template <int NK>
+static cudaError_t prep_all() {
+  cudaError_t e = prep_theta<NK>();
+  if (e != cudaSuccess) return e;
+  return prep_adv<NK>(200 * 1024);
+}
+
+cudaError_t prepare_kernels_f64(int nk) {
+#define W2_CALL_PREP(N) prep_all<N>()
+  switch (nk) {
+    case 8: return W2_CALL_PREP(8);
+    case 16: return W2_CALL_PREP(16);
+    case 24: return W2_CALL_PREP(24);
+    case 32: return W2_CALL_PREP(32);
+    case 40: return W2_CALL_PREP(40);
+    case 48: return W2_CALL_PREP(48);
+    case 56: return W2_CALL_PREP(56);
+    case 64: return W2_CALL_PREP(64);
+    default: return cudaErrorInvalidValue;
+  }
+#undef W2_CALL_PREP
+}
+
+cudaError_t launch_theta_f64(int nk, int mode, const ThetaArgs &a, cudaStream_t s) {
+  switch (nk) {
+    case 8: return run_theta<8>(mode, a, s);
+    case 16: return run_theta<16>(mode, a, s);
+    case 24: return run_theta<24>(mode, a, s);
+    case 32: return run_theta<32>(mode, a, s);
+    case 40: return run_theta<40>(mode, a, s);
+    case 48: return run_theta<48>(mode, a, s);
+    case 56: return run_theta<56>(mode, a, s);
+    case 64: return run_theta<64>(mode, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_adv_f64(int nk, int dir, int two, const AdvArgs &a, cudaStream_t s) {
+  switch (nk) {
+    case 8: return run_adv<8>(dir, two, a, s);
+    case 16: return run_adv<16>(dir, two, a, s);
+    case 24: return run_adv<24>(dir, two, a, s);
+    case 32: return run_adv<32>(dir, two, a, s);
+    case 40: return run_adv<40>(dir, two, a, s);
+    case 48: return run_adv<48>(dir, two, a, s);
+    case 56: return run_adv<56>(dir, two, a, s);
+    case 64: return run_adv<64>(dir, two, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace w2

@@ -182,6 +182,42 @@ w2_status w2_advect(w2_ctx *ctx, const double *f, double *out);
 #define W2_STEP_KERNELS 8
 w2_status w2_step_profile(w2_ctx *ctx, int32_t nsteps, double *kernel_ms);
 
+/* Allocation-free form of w2_theta, for callers that may not allocate device
+ * memory at all: code that runs while someone else's CUDA stream capture is
+ * open (cudaMalloc is not allowed there), hot loops whose device memory is
+ * owned and budgeted by a host framework, or plug-ins whose host forbids
+ * calls into the allocator.  The paper has no counterpart; it is a property of
+ * this library only.
+ *
+ * out = Theta_V[f] for potentials the caller has already sampled (device
+ * arrays, row-major, l in [0, 2 nk), h' = L / (2 nk)):
+ *   u1[i][l]  = U1(x_i + l h')   one-body potential of particle 1
+ *   u2[i][l]  = U2(x_i + l h')   one-body potential of particle 2
+ *   u12[d][l] = U12(d dx + l h') pair potential (gamma W) at distance d dx + l h'
+ * With u1 = u2 = V_ext samples and u12 = gamma W samples this is w2_theta of a
+ * context whose c_hartree = c_xc = 0.  f and out: device [nx][nx][nk][nk]
+ * doubles, 16-byte aligned, not aliasing; cfg: only nx, nk, L, hbar and
+ * precision (W2_F64) are read.  Queued on cuda_stream (a cudaStream_t, NULL =
+ * legacy default stream).
+ *
+ * No allocation: the shift-kernel tables live in one fixed device array of
+ * 3 * W2_NOALLOC_MAX_NX * (2 * W2_NOALLOC_MAX_NK - 1) + 2 * W2_NOALLOC_MAX_NK
+ * doubles (about 391 KB) that is part of the library image, so every device
+ * that loads the library holds it until the process exits.  The first call on
+ * a device, with that device current, resolves the array's address and sets
+ * kernel attributes; make that first call before any stream capture.  All
+ * calls share the one array and every call rewrites all of it that it reads,
+ * so nothing has to be cleared between calls, but calls that overlap on the
+ * GPU (different streams, threads or captured graphs in flight at once) race
+ * on it and give wrong results.
+ * Errors: W2_ERR_ARG (NULL, aliasing or misaligned pointers, bad grid),
+ * W2_ERR_UNSUPPORTED (nx > W2_NOALLOC_MAX_NX, nk > W2_NOALLOC_MAX_NK, nk not a
+ * multiple of 8, or a precision other than W2_F64), W2_ERR_CUDA. */
+#define W2_NOALLOC_MAX_NX 128
+#define W2_NOALLOC_MAX_NK 64
+w2_status w2_theta_noalloc(const w2_config *cfg, const double *u1, const double *u2, const double *u12,
+                           const double *f, double *out, void *cuda_stream);
+
 /* Release every resource of the context (NULL is ignored). */
 void w2_destroy(w2_ctx *ctx);
 

@@ -140,6 +140,104 @@ def theta_flops_per_point(nk):
     return 2.0 * (2 * nk + diag)
 
 
+def bench_forms(args, barrier):
+    """The precision and batching forms on their own workloads (rank-local)."""
+    import torch
+
+    from paper_2511_11354_gb300 import inputs, w2
+    stream = torch.cuda.current_stream()
+    forms = {}
+
+    def timed(step, k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        step(k)
+        e1.record(stream)
+        barrier()
+        return e0.elapsed_time(e1)
+
+    # precision form: 128^4, double-well physics, FP32 state, TF32 split contractions
+    prob, _ = inputs.workload_dwell(nx=128, nk=128)
+    f0 = inputs.initial_state_chunked(prob, centres=inputs.draw_centres(2), seed=2, dtype=np.float32)
+    ctx = w2.Context.from_problem(prob, precision=w2.W2_F32_TF32X3)
+    ctx.set_state(torch.from_numpy(f0).cuda())
+    del f0
+    ctx.step(args.warmup)
+    k = args.form_steps
+    ms = timed(ctx.step, k)
+    kp = ctx.step_profile(min(k, 10))
+    theta_ms = 0.5 * (kp[2] + kp[7])
+    flops = 5 * theta_mma_per_block(prob.nk) * 2048.0 * prob.nx * prob.nx  # 5 products, 2048 flop per mma
+    tf32_peak = 0.4889 * MEASURED_BF16_TFLOPS()
+    forms["precision_tf32x3"] = {
+        "workload": f"double-well physics on a 128^2 x 128^2 grid (268M points), FP32 state, dt={prob.dt:g}",
+        "value": prob.points * k / (ms / 1e3), "unit": UNIT, "steps": k, "ms_per_step": ms / k,
+        "kernel_ms": dict(zip(w2.STEP_KERNELS, [float(x) for x in kp])),
+        "theta_tensor_tflops_executed": flops / (theta_ms * 1e-3) / 1e12,
+        "theta_tensor_frac_of_tf32_peak": flops / (theta_ms * 1e-3) / 1e12 / tf32_peak,
+        "tf32_peak_source": "0.4889 x measured cuBLAS bf16 burst (MEASURED_PEAKS.json), nominal tf32/bf16 ratio 1.1/2.25",
+    }
+    ctx.close()
+    torch.cuda.empty_cache()
+    # its error against the FP64 path on the 64^4 workload after 200 steps
+    if not args.no_form_error:
+        p64, f64 = inputs.workload_dwell()
+        a = w2.Context.from_problem(p64)
+        b = w2.Context.from_problem(p64, precision=w2.W2_F32_TF32X3)
+        a.set_state(f64)
+        b.set_state(f64.astype(np.float32))
+        a.step(200)
+        b.step(200)
+        fa, fb = a.get_state(), b.get_state().astype(np.float64)
+        oa, ob = a.observables(), b.observables()
+        forms["precision_tf32x3"]["error_vs_fp64_path_64^4_200_steps"] = {
+            "rel_l2": float(np.linalg.norm(fb - fa) / np.linalg.norm(fa)),
+            "mass": abs(ob.mass - oa.mass) / abs(oa.mass), "energy": abs(ob.energy - oa.energy) / abs(oa.energy),
+            "entropy_lin_abs": abs(ob.entropy_lin - oa.entropy_lin),
+            "n1_max_rel": float(np.abs(ob.n1 - oa.n1).max() / np.abs(oa.n1).max()),
+            "n12_max_rel": float(np.abs(ob.n12 - oa.n12).max() / np.abs(oa.n12).max())}
+        a.close()
+        b.close()
+    # batching form: 64 uneven instances, one graph-captured persistent step
+    probs, states = inputs.workload_batch(64, seed=3)
+    bt = w2.Batch(probs)
+    for i, f in enumerate(states):
+        bt.set_state(i, f.astype(np.float32))
+    del states
+    tuning = bt.autotune()
+    bt.step(args.warmup)
+    ms = timed(bt.step, k)
+    pts = sum(p.points for p in probs)
+    forms["batching"] = {
+        "workload": "64 instances, nx in {24,32,48,64}, nk in {32,48,64}, gamma in U[0.2,2] (seed 3), "
+                    f"{pts / 1e6:.1f}M points in total, FP32 state, TF32 split contractions",
+        "value": pts * k / (ms / 1e3), "unit": UNIT, "steps": k, "ms_per_step": ms / k, "autotuned_grids": tuning}
+    bt.close()
+    return forms
+
+
+def theta_mma_per_block(nk):
+    """mma.m16n8k8 tiles of one Theta block (per product): two dense nk x nk x nk
+    contractions plus the sheared pair term over the k-steps it can touch."""
+    dense = 2 * (nk // 16) * (nk // 8) * (nk // 8)
+    pair = 0
+    for w in range(nk // 16):
+        r0 = 16 * w
+        for c in range(r0 // 8, min((r0 + 15 + nk - 1) // 8, (2 * nk - 2) // 8) + 1):
+            nlo, nhi = max(0, 8 * c - nk + 1), min(nk - 1, 8 * c + 7)
+            pair += (nhi - (nlo & ~7)) // 8 + 1
+    return dense + pair
+
+
+def MEASURED_BF16_TFLOPS():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(path))["bf16_tflops"])
+    except Exception:
+        return 1900.0  # fallback figure of the profiling recipe
+
+
 def run_reference(args):
     """The reference arm: the FP64 CPU oracle on the host cores."""
     ws, rank, _ = _dist()
@@ -178,6 +276,9 @@ def main():
     ap.add_argument("--impl", default="w2", choices=["w2", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-form-error", action="store_true")
+    ap.add_argument("--form-steps", type=int, default=20)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -254,6 +355,9 @@ def main():
     ms_e2e = max_over_ranks(t0.elapsed_time(t1))
     e2e = prob.points * args.steps * ws / (ms_e2e / 1e3)
 
+    ctx.close()
+    forms = None if args.no_forms else bench_forms(args, barrier)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = _oracle_sample(prob, args.cpu_seconds)
@@ -278,9 +382,9 @@ def main():
             "observables": {"mass": ob.mass, "energy": ob.energy, "entropy_lin": ob.entropy_lin,
                             "status": ob.status},
             "cpu_baseline": cpu,
+            "forms": forms,
         }
         print(json.dumps(line), flush=True)
-    ctx.close()
     if ws > 1:
         dist.destroy_process_group()
 

@@ -22,7 +22,8 @@
  *   x_i = -L/2 + i dx,  dx = L / nx,           i in [0, nx)
  *   p_n = (n - nk/2) dp, dp = pi hbar / L,      n in [0, nk)
  *   phase-space arrays are f[i1][i2][n1][n2], n2 fastest, C order,
- *   nx*nx*nk*nk elements; f is zero outside the momentum window.
+ *   nx*nx*nk*nk elements (double for W2_F64, float for W2_F32_TF32X3);
+ *   f is zero outside the momentum window.
  *
  * Conventions:
  *   - Every function returns a w2_status; nothing throws.  The first CUDA
@@ -62,7 +63,12 @@ typedef enum {
 } w2_status;
 
 typedef enum {
-  W2_F64 = 0            /* FP64 state and arithmetic                              */
+  W2_F64 = 0,           /* FP64 state and arithmetic                              */
+  W2_F32_TF32X3 = 1     /* precision form: FP32 state; the pseudo-difference
+                           contractions on tensor cores with each operand split
+                           into two TF32 parts (three products, FP32 accumulate);
+                           the spline shift as an FP32 increment of the state;
+                           densities and observables reduced in FP64             */
 } w2_precision;
 
 typedef enum {
@@ -74,7 +80,8 @@ typedef enum {
 
 /* Problem description (Sec. 3.1 grid; Sec. 5 uses hbar = m = 1).
  *   nx  : spatial points per particle, 4 <= nx; FP64 supports nx <= 128
- *   nk  : momentum points per particle; FP64 supports nk in {8,16,...,64}
+ *   nk  : momentum points per particle; W2_F64 supports nk in {8,16,...,64},
+ *         W2_F32_TF32X3 nk in {16,32,...,128}
  *   L   : period of the box (> 0); dt: time step tau (> 0)
  *   hbar, mass: > 0
  *   precision: a w2_precision;  xc_kind: a w2_xc_kind                          */
@@ -128,7 +135,7 @@ w2_status w2_create(const w2_config *cfg, void *cuda_stream, w2_ctx **out);
 w2_status w2_set_potentials(w2_ctx *ctx, w2_fn vext, void *ue, w2_fn vee, void *ui,
                             double gamma, double c_hartree, double c_xc);
 
-/* Copy a full state f[nx][nx][nk][nk] (double) into the context: from device
+/* Copy a full state f[nx][nx][nk][nk] (element type of the precision) into the context: from device
  * memory when on_device != 0, else from host memory.  Resets the step count.
  * Queued on the stream (a host source is copied with cudaMemcpyAsync, so a
  * pageable host buffer is copied before return).
@@ -164,11 +171,13 @@ w2_status w2_observables(w2_ctx *ctx, w2_obs *out, double *n1, double *n12);
  *            discretisation), the HXC potentials built from the densities of f.
  * w2_advect: out = A_tau f, i.e. out(X, P) = f(X - tau P/m, P) by the periodic
  *            cubic B-spline of Sec. 4.1, x1 and x2 in turn.
- * Errors: W2_ERR_ARG (NULL or aliasing pointers; for w2_theta also a pointer
- * not 16-byte aligned), W2_ERR_STATE (potentials not set), W2_ERR_CUDA.  Both use the context's workspace and must not overlap
+ * Arrays hold the context precision's element type.
+ * Errors: W2_ERR_ARG (NULL or aliasing pointers; a pointer not 16-byte aligned
+ * for w2_theta, and for w2_advect in W2_F32_TF32X3), W2_ERR_STATE (potentials
+ * not set), W2_ERR_CUDA.  Both use the context's workspace and must not overlap
  * with w2_step on another stream. */
-w2_status w2_theta(w2_ctx *ctx, const double *f, double *out);
-w2_status w2_advect(w2_ctx *ctx, const double *f, double *out);
+w2_status w2_theta(w2_ctx *ctx, const void *f, void *out);
+w2_status w2_advect(w2_ctx *ctx, const void *f, void *out);
 
 /* Diagnostic form of w2_step: advances nsteps > 0 steps launching the step's
  * W2_STEP_KERNELS kernels directly (no graph) with a CUDA event pair on the
@@ -217,6 +226,109 @@ w2_status w2_step_profile(w2_ctx *ctx, int32_t nsteps, double *kernel_ms);
 #define W2_NOALLOC_MAX_NK 64
 w2_status w2_theta_noalloc(const w2_config *cfg, const double *u1, const double *u2, const double *u12,
                            const double *f, double *out, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Batching form: many independent problems (uneven nx, nk, potentials and
+ * pair strengths) advanced together.  Every instance is a W2_F32_TF32X3
+ * problem with its own state; one batch step runs each kernel of the step
+ * once for all instances as a persistent kernel striding over the flattened
+ * (instance, work item) list, and the whole step is captured once into a
+ * CUDA graph and replayed.  Results are identical, bit for bit, to running
+ * each instance in its own context.
+ * ------------------------------------------------------------------------ */
+typedef struct w2_batch w2_batch;
+
+/* Create n (1..4096) instances from cfgs[0..n) (every precision must be
+ * W2_F32_TF32X3, other fields as for w2_create) on the current device, all
+ * on the borrowed cuda_stream.  Errors: as w2_create, W2_ERR_UNSUPPORTED for
+ * another precision.  *out is NULL on failure. */
+w2_status w2_batch_create(const w2_config *cfgs, int32_t n, void *cuda_stream, w2_batch **out);
+
+/* Per-instance forms of w2_set_potentials / w2_set_state / w2_get_state /
+ * w2_observables for instance i in [0, n); W2_ERR_ARG for another i. */
+w2_status w2_batch_set_potentials(w2_batch *b, int32_t i, w2_fn vext, void *ue, w2_fn vee, void *ui,
+                                  double gamma, double c_hartree, double c_xc);
+w2_status w2_batch_set_state(w2_batch *b, int32_t i, const void *f, int32_t on_device);
+w2_status w2_batch_get_state(w2_batch *b, int32_t i, void *f, int32_t on_device);
+w2_status w2_batch_observables(w2_batch *b, int32_t i, w2_obs *out, double *n1, double *n12);
+
+/* Advance every instance by nsteps Lawson steps (as w2_step).  Needs
+ * potentials and a state on every instance (W2_ERR_STATE otherwise). */
+w2_status w2_batch_step(w2_batch *b, int32_t nsteps);
+
+/* Choose the grid size of every batched kernel by timing candidates (1 to 16
+ * CTAs per SM, capped at the number of work items) on the batch as it is
+ * (potentials and states set; the states are not changed).  Synchronises.
+ * grids_out (host, grids_len entries, or NULL) receives
+ *   [per-X sums, tables, then for each momentum-size class in order of first
+ *    appearance: nk, Theta sweep, shift x2, shift x1]  (zeros after the end).
+ * Errors: W2_ERR_ARG, W2_ERR_STATE, W2_ERR_CUDA. */
+w2_status w2_batch_autotune(w2_batch *b, int32_t *grids_out, int32_t grids_len);
+
+/* Release the batch and all its instances (NULL is ignored). */
+void w2_batch_destroy(w2_batch *b);
+
+/* ------------------------------------------------------------------------
+ * Learned form: a multilayer perceptron stands in for the two-body term
+ * Theta_{V12} (Eq. two_body_FSM) of W2_F64 contexts.  For each spatial point
+ * X = (x1, x2) its input row (BF16, w2_mlp_input_dim entries) is
+ *   s_f f(X, p1, p2) for all nk^2 momenta, s_f1 f1(x1, .) and s_f1 f1(x2, .)
+ *   (f1 = sum over x2, p2 of f dx dp, the reduced one-body Wigner function),
+ *   sin(2 pi (x1 - x2)/L), cos(2 pi (x1 - x2)/L), zeros up to a multiple of 32;
+ * its output is s_y Theta_{V12}[f](X, ., .) (nk^2 values).  Layers: input ->
+ * hidden -> hidden -> hidden -> nk^2 with SiLU between them; FP32 master
+ * weights, BF16 tensor-core products with FP32 accumulation; trained by the
+ * library's own forward, backward and Adam kernels on the mean squared error.
+ * Parameters are packed as W0 [din][H], b0 [H], W1 [H][H], b1, W2 [H][H], b2,
+ * W3 [H][nk^2], b3 [nk^2] (row-major, floats).
+ * ------------------------------------------------------------------------ */
+typedef struct w2_mlp w2_mlp;
+
+/* Create an MLP for momentum size nk (hidden width a multiple of 16) able to
+ * process max_rows input rows per call, on the borrowed cuda_stream.  The
+ * weights start uniform in +-sqrt(3/fan_in) (a fixed counter-based sequence),
+ * biases 0, scales 1.  Errors: W2_ERR_ARG, W2_ERR_OOM, W2_ERR_CUDA. */
+w2_status w2_mlp_create(int32_t nk, int32_t hidden, int32_t max_rows, void *cuda_stream, w2_mlp **out);
+size_t w2_mlp_param_count(const w2_mlp *m);
+int32_t w2_mlp_input_dim(const w2_mlp *m);
+/* Host copies of the packed FP32 parameters (synchronise). */
+w2_status w2_mlp_set_params(w2_mlp *m, const float *params);
+w2_status w2_mlp_get_params(w2_mlp *m, float *params);
+/* Input and output scales (all > 0). */
+w2_status w2_mlp_set_scales(w2_mlp *m, float s_f, float s_f1, float s_y);
+/* y[rows][nk^2] (device, FP32) = network(x) for x (device, BF16 [rows][din]). */
+w2_status w2_mlp_forward(w2_mlp *m, const void *x, int32_t rows, float *y);
+/* One Adam step (lr, beta 0.9 / 0.999, eps 1e-8) on the mean squared error
+ * against target (device, FP32 [rows][nk^2], already scaled by s_y); *loss
+ * (host) receives the loss before the update.  Synchronises.
+ * Errors: W2_ERR_ARG, W2_ERR_NONFINITE (non-finite loss), W2_ERR_CUDA. */
+w2_status w2_mlp_train_step(w2_mlp *m, const void *x, const float *target, int32_t rows, float lr, double *loss);
+/* Loss and its gradient with respect to the packed parameters (host,
+ * w2_mlp_param_count floats, or NULL), without an update.  Synchronises. */
+w2_status w2_mlp_gradients(w2_mlp *m, const void *x, const float *target, int32_t rows, float *grads, double *loss);
+void w2_mlp_destroy(w2_mlp *m);
+
+/* Input rows (device, BF16 [rows][w2_mlp_input_dim(m)]) for the spatial points
+ * xs[0..rows) (device int32, X = i1*nx + i2), or for every X in order when xs
+ * is NULL (rows must then be nx*nx), from the state f (device, the context's
+ * element type), with m's input scales.  Queued on the stream. */
+w2_status w2_features(w2_ctx *ctx, const w2_mlp *m, const void *f, const int32_t *xs, int32_t rows, void *x);
+
+/* out = Theta_{V12}[f] alone (the exact two-body term; device arrays of the
+ * context's element type, 16-byte aligned).  Queued on the stream. */
+w2_status w2_theta_pair(w2_ctx *ctx, const void *f, void *out);
+
+/* Make w2_step use m for the two-body term of a W2_F64 context (m must have
+ * the context's nk and max_rows >= nx*nx; m = NULL goes back to the exact
+ * term).  Every judge_every steps (0: never) the network is compared with the
+ * exact term on the current state (relative L2 error of the two-body term);
+ * above tol the context falls back to the exact term for good.  The MLP is
+ * borrowed and must outlive its use.  Errors: W2_ERR_ARG, W2_ERR_UNSUPPORTED
+ * (not W2_F64), W2_ERR_OOM. */
+w2_status w2_learned_attach(w2_ctx *ctx, w2_mlp *m, int32_t judge_every, double tol);
+/* active: 1 while the network is in use; judged: judgements so far; last_err:
+ * the latest relative error. */
+w2_status w2_learned_report(w2_ctx *ctx, int32_t *active, int32_t *judged, double *last_err);
 
 /* Release every resource of the context (NULL is ignored). */
 void w2_destroy(w2_ctx *ctx);

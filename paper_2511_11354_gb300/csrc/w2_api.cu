@@ -4,6 +4,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -11,32 +12,7 @@
 
 using namespace w2;
 
-struct w2_ctx {
-  w2_config cfg;
-  cudaStream_t stream;       // borrowed
-  cudaStream_t cap;          // private stream used only for graph capture
-  int dev;
-  int nx, nk, M;
-  size_t npts;
-  double dx, dp, hp, tau;
-  double gamma, c_h, c_xc;
-  bool have_pot, have_state;
-  int64_t steps;
-  w2_status sticky;
-  // phase-space arrays
-  double *f, *g, *t1, *t2;
-  // small device buffers
-  double *xsum, *xsum2;       // [nx*nx]
-  double *K, *K12;            // [2][nx][2nk-1], [nx][2nk-1]
-  double *vext_fine, *w_fine, *d_fine, *sintab, *vext_grid;
-  int *k0tab;
-  double *wtab;
-  double *xpart, *obs_out, *h_obs;
-  double z, zscale;
-  int nterm;
-  cudaGraphExec_t graph;
-  bool graph_ready;
-};
+
 
 #define W2_TRY(call)                                    \
   do {                                                  \
@@ -51,10 +27,14 @@ static double fold(double x, double L) { return x - L * floor((x + 0.5 * L) / L)
 
 static void free_all(w2_ctx *c) {
   void *ptrs[] = {c->f, c->g, c->t1, c->t2, c->xsum, c->xsum2, c->K, c->K12, c->vext_fine, c->w_fine,
-                  c->d_fine, c->sintab, c->vext_grid, c->k0tab, c->wtab, c->xpart, c->obs_out};
+                  c->d_fine, c->sintab, c->vext_grid, c->k0tab, c->wtab, c->xpart, c->obs_out,
+                  c->wtab32, c->ctab32};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_obs) cudaFreeHost(c->h_obs);
+  if (c->f1) cudaFree(c->f1);
+  if (c->xrows) cudaFree(c->xrows);
+  if (c->Kzero) cudaFree(c->Kzero);
   if (c->graph_ready) cudaGraphExecDestroy(c->graph);
   if (c->cap) cudaStreamDestroy(c->cap);
 }
@@ -108,8 +88,9 @@ extern "C" w2_status w2_create(const w2_config *cfg, void *cuda_stream, w2_ctx *
       !(cfg->hbar > 0) || !(cfg->mass > 0) || !isfinite(cfg->L) || !isfinite(cfg->dt) ||
       cfg->xc_kind < 0 || cfg->xc_kind > 2)
     return W2_ERR_ARG;
-  if (cfg->precision != W2_F64) return W2_ERR_UNSUPPORTED;
-  if (!nk_supported_f64(cfg->nk) || cfg->nx > 128) return W2_ERR_UNSUPPORTED;
+  if (cfg->precision != W2_F64 && cfg->precision != W2_F32_TF32X3) return W2_ERR_UNSUPPORTED;
+  if (cfg->precision == W2_F64 && (!nk_supported_f64(cfg->nk) || cfg->nx > 128)) return W2_ERR_UNSUPPORTED;
+  if (cfg->precision == W2_F32_TF32X3 && (!nk_supported_f32(cfg->nk) || cfg->nx > 128)) return W2_ERR_UNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return W2_ERR_CUDA;
   cudaDeviceProp prop;
@@ -122,6 +103,8 @@ extern "C" w2_status w2_create(const w2_config *cfg, void *cuda_stream, w2_ctx *
   ctx->cfg = *cfg;
   ctx->stream = (cudaStream_t)cuda_stream;
   ctx->dev = dev;
+  ctx->prec = cfg->precision;
+  ctx->esz = cfg->precision == W2_F64 ? sizeof(double) : sizeof(float);
   ctx->nx = cfg->nx;
   ctx->nk = cfg->nk;
   ctx->M = 2 * cfg->nk;
@@ -131,14 +114,16 @@ extern "C" w2_status w2_create(const w2_config *cfg, void *cuda_stream, w2_ctx *
   ctx->hp = cfg->L / ctx->M;
   ctx->tau = cfg->dt;
   ctx->z = sqrt(3.0) - 2.0;
-  ctx->nterm = ctx->nx <= 32 ? ctx->nx : 32;
+  // periodic start sums: |z|^k below the storage precision (z^32 ~ 5e-19, z^16 ~ 7e-10)
+  const int kmax = cfg->precision == W2_F64 ? 32 : 16;
+  ctx->nterm = ctx->nx <= kmax ? ctx->nx : kmax;
   ctx->zscale = (ctx->nterm == ctx->nx) ? 1.0 / (1.0 - pow(ctx->z, ctx->nx)) : 1.0;
 
   const int nx = ctx->nx, nk = ctx->nk, M = ctx->M, W = 2 * nk - 1;
   cudaError_t e = cudaSuccess;
 #define W2_ALLOC(ptr, bytes)                                  \
   if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), (bytes));
-  const size_t fb = sizeof(double) * ctx->npts;
+  const size_t fb = ctx->esz * ctx->npts;
   W2_ALLOC(ctx->f, fb) W2_ALLOC(ctx->g, fb) W2_ALLOC(ctx->t1, fb) W2_ALLOC(ctx->t2, fb)
   W2_ALLOC(ctx->xsum, sizeof(double) * nx * nx) W2_ALLOC(ctx->xsum2, sizeof(double) * nx * nx)
   W2_ALLOC(ctx->K, sizeof(double) * 2 * nx * W) W2_ALLOC(ctx->K12, sizeof(double) * nx * W)
@@ -147,10 +132,11 @@ extern "C" w2_status w2_create(const w2_config *cfg, void *cuda_stream, w2_ctx *
   W2_ALLOC(ctx->vext_grid, sizeof(double) * nx) W2_ALLOC(ctx->k0tab, sizeof(int) * nk)
   W2_ALLOC(ctx->wtab, sizeof(double) * 4 * nk) W2_ALLOC(ctx->xpart, sizeof(double) * nx * nx * (3 + nk))
   W2_ALLOC(ctx->obs_out, sizeof(double) * (8 + nx + nx * nx))
+  W2_ALLOC(ctx->wtab32, sizeof(float) * 4 * nk) W2_ALLOC(ctx->ctab32, sizeof(float) * 8 * nk)
 #undef W2_ALLOC
   if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->h_obs, sizeof(double) * (8 + nx + nx * nx));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = prepare_kernels_f64(nk);
+  if (e == cudaSuccess) e = ctx->prec == W2_F64 ? prepare_kernels_f64(nk) : prepare_kernels_f32(nk);
   if (e != cudaSuccess) {
     w2_status st = (e == cudaErrorMemoryAllocation) ? W2_ERR_OOM : W2_ERR_CUDA;
     cudaGetLastError();
@@ -166,6 +152,25 @@ extern "C" w2_status w2_create(const w2_config *cfg, void *cuda_stream, w2_ctx *
   e = cudaMemcpy(ctx->sintab, sint.data(), sizeof(double) * M, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(ctx->k0tab, k0.data(), sizeof(int) * nk, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(ctx->wtab, wt.data(), sizeof(double) * 4 * nk, cudaMemcpyHostToDevice);
+  // FP32 tables: weights, and the taps of (S - I) merged over offsets -3..3
+  // (evaluation weights at k0 + a, a = -1..2, plus z (1, 4, 1) at -1, 0, 1,
+  // since f_i = -z (d_{i-1} + 4 d_i + d_{i+1})), usable when k0 in [-2, 1].
+  std::vector<float> w32(4 * nk), c32(8 * nk, 0.0f);
+  for (int n = 0; n < nk; ++n) {
+    for (int q = 0; q < 4; ++q) w32[4 * n + q] = (float)wt[4 * n + q];
+    const int k0n = k0[n];
+    for (int o = -3; o <= 3; ++o) {
+      double t = 0.0;
+      const int a = o - k0n;  // weight index a in [-1, 2]
+      if (a >= -1 && a <= 2) t += wt[4 * n + a + 1];
+      if (o == -1 || o == 1) t += ctx->z;
+      if (o == 0) t += 4.0 * ctx->z;
+      c32[8 * n + o + 3] = (float)t;
+    }
+    c32[8 * n + 7] = (k0n >= -2 && k0n <= 1) ? 1.0f : 0.0f;
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(ctx->wtab32, w32.data(), sizeof(float) * 4 * nk, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ctx->ctab32, c32.data(), sizeof(float) * 8 * nk, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     free_all(ctx);
     delete ctx;
@@ -175,7 +180,7 @@ extern "C" w2_status w2_create(const w2_config *cfg, void *cuda_stream, w2_ctx *
   return W2_OK;
 }
 
-static TabArgs tab_args(w2_ctx *ctx, const double *xsum, int pair_mode) {
+TabArgs w2::tab_args(w2_ctx *ctx, const double *xsum, int pair_mode) {
   TabArgs a;
   a.nx = ctx->nx;
   a.nk = ctx->nk;
@@ -264,9 +269,8 @@ extern "C" w2_status w2_set_state(w2_ctx *ctx, const void *f, int32_t on_device)
   if (!ctx || !f) return W2_ERR_ARG;
   if (ctx->sticky) return ctx->sticky;
   if (!ctx->have_pot) return W2_ERR_STATE;
-  W2_TRY(cudaMemcpyAsync(ctx->f, f, sizeof(double) * ctx->npts,
+  W2_TRY(cudaMemcpyAsync(ctx->f, f, ctx->esz * ctx->npts,
                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
-  W2_TRY(launch_xsum_f64(ctx->nx, ctx->nk, ctx->f, ctx->xsum, ctx->stream));
   ctx->have_state = true;
   ctx->steps = 0;
   return W2_OK;
@@ -276,7 +280,7 @@ extern "C" w2_status w2_get_state(w2_ctx *ctx, void *f, int32_t on_device) {
   if (!ctx || !f) return W2_ERR_ARG;
   if (ctx->sticky) return ctx->sticky;
   if (!ctx->have_state) return W2_ERR_STATE;
-  W2_TRY(cudaMemcpyAsync(f, ctx->f, sizeof(double) * ctx->npts,
+  W2_TRY(cudaMemcpyAsync(f, ctx->f, ctx->esz * ctx->npts,
                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
   if (!on_device) W2_TRY(cudaStreamSynchronize(ctx->stream));
   return W2_OK;
@@ -291,6 +295,30 @@ struct StepEvents {
   if (evs && evs->ev) {                                                             \
     if ((e = cudaEventRecord(evs->ev[2 * (k) + (pos)], s)) != cudaSuccess) return e; \
   }
+
+// Feature rows of every spatial point of `f` into ctx->xrows (learned form).
+static cudaError_t enqueue_features(w2_ctx *ctx, const void *f, cudaStream_t s) {
+  FeatArgs fa;
+  fa.nx = ctx->nx;
+  fa.nk = ctx->nk;
+  fa.din = mlp_din(ctx->mlp);
+  fa.dx = ctx->dx;
+  fa.dp = ctx->dp;
+  fa.s_f = mlp_scale(ctx->mlp, 0);
+  fa.s_f1 = mlp_scale(ctx->mlp, 1);
+  fa.f1 = ctx->f1;
+  fa.f1_src_rows = 1;
+  fa.xs = nullptr;
+  fa.x = ctx->xrows;
+  return launch_features(fa, f, ctx->prec == W2_F64, ctx->nx * ctx->nx, s);
+}
+
+// The network's two-body term of `f` (in operator units) into the MLP output buffer.
+static cudaError_t enqueue_learned_pair(w2_ctx *ctx, const void *f, cudaStream_t s) {
+  cudaError_t e = enqueue_features(ctx, f, s);
+  if (e != cudaSuccess) return e;
+  return mlp_forward(ctx->mlp, ctx->xrows, ctx->nx * ctx->nx, mlp_out(ctx->mlp), 1.0f / mlp_scale(ctx->mlp, 2), s);
+}
 
 // One Lawson step on stream s (see w2.h):
 //   xsum(f^n) ; K(f^n) ; g = Theta f^n ; (t1, t2) = A_x2 (f, g) ;
@@ -317,6 +345,11 @@ static cudaError_t enqueue_step(w2_ctx *ctx, cudaStream_t s, const StepEvents *e
   th.K2 = ctx->K + (size_t)nx * W;
   th.K12 = ctx->K12;
   th.half_tau = 0.5 * ctx->tau;
+  const bool learned = ctx->mlp && ctx->learned_active;
+  if (learned) {
+    if ((e = enqueue_learned_pair(ctx, ctx->f, s)) != cudaSuccess) return e;
+    th.pair = mlp_out(ctx->mlp);
+  }
   W2_MARK(2, 0)
   if ((e = launch_theta_f64(nk, 0, th, s)) != cudaSuccess) return e;
   W2_MARK(2, 1)
@@ -352,21 +385,123 @@ static cudaError_t enqueue_step(w2_ctx *ctx, cudaStream_t s, const StepEvents *e
   th.h = ctx->f;
   th.out = ctx->f;
   th.xsum = nullptr;
+  if (learned && (e = enqueue_learned_pair(ctx, ctx->g, s)) != cudaSuccess) return e;
   W2_MARK(7, 0)
   if ((e = launch_theta_f64(nk, 1, th, s)) != cudaSuccess) return e;
   W2_MARK(7, 1)
   return cudaSuccess;
 }
 
+Adv32Args w2::adv32_args(w2_ctx *ctx) {
+  Adv32Args a;
+  memset(&a, 0, sizeof(a));
+  a.nx = ctx->nx;
+  a.k0tab = ctx->k0tab;
+  a.wtab = ctx->wtab32;
+  a.ctab = ctx->ctab32;
+  a.z = (float)ctx->z;
+  a.zscale = (float)ctx->zscale;
+  a.nterm = ctx->nterm;
+  a.tau = (float)ctx->tau;
+  return a;
+}
+
+// FP32 precision form of the same step (arrays hold floats):
+//   xsum(f) ; K(f) ; g = Theta f ; (d2 -> t1, g2 -> t2) = A_x2 ;
+//   (f~ -> g, dh -> t1) = A_x1 ; xsum(f~) ; K(f~) ; f = f + (dh + tau/2 Theta f~)
+static cudaError_t enqueue_step32(w2_ctx *ctx, cudaStream_t s, const StepEvents *evs) {
+  const int nx = ctx->nx, nk = ctx->nk, W = 2 * nk - 1;
+  float *f = (float *)ctx->f, *g = (float *)ctx->g, *t1 = (float *)ctx->t1, *t2 = (float *)ctx->t2;
+  cudaError_t e;
+  TabArgs ta = tab_args(ctx, ctx->xsum, 0);
+  W2_MARK(0, 0)
+  if ((e = launch_xsum_f32(nx, nk, f, ctx->xsum, s)) != cudaSuccess) return e;
+  W2_MARK(0, 1)
+  W2_MARK(1, 0)
+  if ((e = launch_tables(ta, s)) != cudaSuccess) return e;
+  W2_MARK(1, 1)
+  Theta32Args th;
+  th.nx = nx;
+  th.in = f;
+  th.base = nullptr;
+  th.h = nullptr;
+  th.out = g;
+  th.K1 = ctx->K;
+  th.K2 = ctx->K + (size_t)nx * W;
+  th.K12 = ctx->K12;
+  th.half_tau = (float)(0.5 * ctx->tau);
+  W2_MARK(2, 0)
+  if ((e = launch_theta_f32(nk, 0, th, s)) != cudaSuccess) return e;
+  W2_MARK(2, 1)
+  Adv32Args av = adv32_args(ctx);
+  av.f = f;
+  av.g = g;
+  av.d2 = t1;
+  av.g2 = t2;
+  W2_MARK(3, 0)
+  if ((e = launch_adv_f32(nk, 0, av, s)) != cudaSuccess) return e;
+  W2_MARK(3, 1)
+  av.d2in = t1;
+  av.g2in = t2;
+  av.ft = g;
+  av.dh = t1;
+  W2_MARK(4, 0)
+  if ((e = launch_adv_f32(nk, 1, av, s)) != cudaSuccess) return e;
+  W2_MARK(4, 1)
+  W2_MARK(5, 0)
+  if ((e = launch_xsum_f32(nx, nk, g, ctx->xsum, s)) != cudaSuccess) return e;
+  W2_MARK(5, 1)
+  W2_MARK(6, 0)
+  if ((e = launch_tables(ta, s)) != cudaSuccess) return e;
+  W2_MARK(6, 1)
+  th.in = g;
+  th.base = f;
+  th.h = t1;
+  th.out = f;
+  W2_MARK(7, 0)
+  if ((e = launch_theta_f32(nk, 1, th, s)) != cudaSuccess) return e;
+  W2_MARK(7, 1)
+  return cudaSuccess;
+}
+
+static cudaError_t enqueue_any(w2_ctx *ctx, cudaStream_t s, const StepEvents *evs) {
+  return ctx->prec == W2_F64 ? enqueue_step(ctx, s, evs) : enqueue_step32(ctx, s, evs);
+}
+
+static w2_status learned_judge(w2_ctx *ctx);
+
+static w2_status step_graph(w2_ctx *ctx, int32_t nsteps);
+
 extern "C" w2_status w2_step(w2_ctx *ctx, int32_t nsteps) {
   if (!ctx || nsteps < 0) return W2_ERR_ARG;
   if (ctx->sticky) return ctx->sticky;
   if (!ctx->have_pot || !ctx->have_state) return W2_ERR_STATE;
+  if (!(ctx->mlp && ctx->learned_active && ctx->judge_every > 0)) return step_graph(ctx, nsteps);
+  // learned form: judge the network against the exact two-body term every
+  // judge_every steps and fall back to the exact term when it is off
+  int left = nsteps;
+  while (left > 0) {
+    const int k = std::min(left, ctx->judge_every - ctx->since_judge);
+    w2_status st = step_graph(ctx, k);
+    if (st != W2_OK) return st;
+    left -= k;
+    ctx->since_judge += k;
+    if (ctx->since_judge >= ctx->judge_every) {
+      ctx->since_judge = 0;
+      st = learned_judge(ctx);
+      if (st != W2_OK) return st;
+      if (!ctx->learned_active) return left > 0 ? step_graph(ctx, left) : W2_OK;
+    }
+  }
+  return W2_OK;
+}
+
+static w2_status step_graph(w2_ctx *ctx, int32_t nsteps) {
   if (nsteps == 0) return W2_OK;
   if (!ctx->graph_ready) {
     cudaGraph_t graph;
     W2_TRY(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = enqueue_step(ctx, ctx->cap);
+    cudaError_t e = enqueue_any(ctx, ctx->cap, nullptr);
     cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {
       if (e2 == cudaSuccess) cudaGraphDestroy(graph);
@@ -398,12 +533,13 @@ extern "C" w2_status w2_observables(w2_ctx *ctx, w2_obs *out, double *n1, double
   a.mass = ctx->cfg.mass;
   a.gamma = ctx->gamma;
   a.c_h = ctx->c_h;
-  a.f = ctx->f;
+  a.f = ctx->prec == W2_F64 ? ctx->f : nullptr;
+  a.f32 = ctx->prec == W2_F64 ? nullptr : (const float *)ctx->f;
   a.vext_grid = ctx->vext_grid;
   a.w_fine = ctx->w_fine;
   a.xpart = ctx->xpart;
   a.out = ctx->obs_out;
-  W2_TRY(launch_obs_f64(a, ctx->stream));
+  W2_TRY(launch_obs(a, ctx->stream));
   const size_t nb = sizeof(double) * (8 + nx + (size_t)nx * nx);
   W2_TRY(cudaMemcpyAsync(ctx->h_obs, ctx->obs_out, nb, cudaMemcpyDeviceToHost, ctx->stream));
   W2_TRY(cudaStreamSynchronize(ctx->stream));
@@ -419,50 +555,81 @@ extern "C" w2_status w2_observables(w2_ctx *ctx, w2_obs *out, double *n1, double
   return h[4] != 0.0 ? W2_ERR_NONFINITE : W2_OK;
 }
 
-extern "C" w2_status w2_theta(w2_ctx *ctx, const double *f, double *out) {
+extern "C" w2_status w2_theta(w2_ctx *ctx, const void *f, void *out) {
   if (!ctx || !f || !out || f == out) return W2_ERR_ARG;
-  // the sweep moves pairs of doubles: both arrays must be 16-byte aligned
+  // the sweep moves pairs of doubles / four floats: both arrays must be 16-byte aligned
   if (((uintptr_t)f | (uintptr_t)out) & 15) return W2_ERR_ARG;
   if (ctx->sticky) return ctx->sticky;
   if (!ctx->have_pot) return W2_ERR_STATE;
   const int nx = ctx->nx, nk = ctx->nk, W = 2 * nk - 1;
-  W2_TRY(launch_xsum_f64(nx, nk, f, ctx->xsum2, ctx->stream));
+  if (ctx->prec == W2_F64)
+    W2_TRY(launch_xsum_f64(nx, nk, (const double *)f, ctx->xsum2, ctx->stream));
+  else
+    W2_TRY(launch_xsum_f32(nx, nk, (const float *)f, ctx->xsum2, ctx->stream));
   TabArgs ta = tab_args(ctx, ctx->xsum2, 0);
   W2_TRY(launch_tables(ta, ctx->stream));
-  ThetaArgs th;
-  th.nx = nx;
-  th.in = f;
-  th.h = nullptr;
-  th.out = out;
-  th.xsum = nullptr;
-  th.K1 = ctx->K;
-  th.K2 = ctx->K + (size_t)nx * W;
-  th.K12 = ctx->K12;
-  th.half_tau = 0.5 * ctx->tau;
-  W2_TRY(launch_theta_f64(nk, 0, th, ctx->stream));
+  if (ctx->prec == W2_F64) {
+    ThetaArgs th;
+    th.nx = nx;
+    th.in = (const double *)f;
+    th.h = nullptr;
+    th.out = (double *)out;
+    th.xsum = nullptr;
+    th.K1 = ctx->K;
+    th.K2 = ctx->K + (size_t)nx * W;
+    th.K12 = ctx->K12;
+    th.half_tau = 0.5 * ctx->tau;
+    W2_TRY(launch_theta_f64(nk, 0, th, ctx->stream));
+  } else {
+    Theta32Args th;
+    th.nx = nx;
+    th.in = (const float *)f;
+    th.base = nullptr;
+    th.h = nullptr;
+    th.out = (float *)out;
+    th.K1 = ctx->K;
+    th.K2 = ctx->K + (size_t)nx * W;
+    th.K12 = ctx->K12;
+    th.half_tau = (float)(0.5 * ctx->tau);
+    W2_TRY(launch_theta_f32(nk, 0, th, ctx->stream));
+  }
   return W2_OK;
 }
 
-extern "C" w2_status w2_advect(w2_ctx *ctx, const double *f, double *out) {
+extern "C" w2_status w2_advect(w2_ctx *ctx, const void *f, void *out) {
   if (!ctx || !f || !out || f == out) return W2_ERR_ARG;
+  // the FP32 shift stages its lines with 16-byte asynchronous copies
+  if (ctx->prec != W2_F64 && (((uintptr_t)f | (uintptr_t)out) & 15)) return W2_ERR_ARG;
   if (ctx->sticky) return ctx->sticky;
   if (!ctx->have_pot) return W2_ERR_STATE;
-  AdvArgs av;
-  av.nx = ctx->nx;
-  av.k0tab = ctx->k0tab;
-  av.wtab = ctx->wtab;
-  av.z = ctx->z;
-  av.zscale = ctx->zscale;
-  av.nterm = ctx->nterm;
-  av.tau = ctx->tau;
-  av.in0 = f;
-  av.in1 = nullptr;
-  av.out0 = ctx->t1;
-  av.out1 = nullptr;
-  W2_TRY(launch_adv_f64(ctx->nk, 1, 0, av, ctx->stream));  // x1 first
-  av.in0 = ctx->t1;
-  av.out0 = out;
-  W2_TRY(launch_adv_f64(ctx->nk, 0, 0, av, ctx->stream));  // then x2
+  if (ctx->prec == W2_F64) {
+    AdvArgs av;
+    av.nx = ctx->nx;
+    av.k0tab = ctx->k0tab;
+    av.wtab = ctx->wtab;
+    av.z = ctx->z;
+    av.zscale = ctx->zscale;
+    av.nterm = ctx->nterm;
+    av.tau = ctx->tau;
+    av.in0 = (const double *)f;
+    av.in1 = nullptr;
+    av.out0 = ctx->t1;
+    av.out1 = nullptr;
+    W2_TRY(launch_adv_f64(ctx->nk, 1, 0, av, ctx->stream));  // x1 first
+    av.in0 = ctx->t1;
+    av.out0 = (double *)out;
+    W2_TRY(launch_adv_f64(ctx->nk, 0, 0, av, ctx->stream));  // then x2
+  } else {
+    Adv32Args av = adv32_args(ctx);
+    av.f = (const float *)f;
+    av.g = nullptr;
+    av.d2 = (float *)ctx->t1;
+    W2_TRY(launch_adv_f32(ctx->nk, 0, av, ctx->stream));  // increment along x2
+    av.d2in = (const float *)ctx->t1;
+    av.g2in = nullptr;
+    av.ft = (float *)out;
+    W2_TRY(launch_adv_f32(ctx->nk, 1, av, ctx->stream));  // then x1: out = S1 (f + d2)
+  }
   return W2_OK;
 }
 
@@ -481,7 +648,7 @@ extern "C" w2_status w2_step_profile(w2_ctx *ctx, int32_t nsteps, double *kernel
   for (int q = 0; q < W2_STEP_KERNELS; ++q) kernel_ms[q] = 0.0;
   for (int s = 0; s < nsteps && st == W2_OK; ++s) {
     StepEvents se{ev.data() + (size_t)NE * s};
-    if (enqueue_step(ctx, ctx->stream, &se) != cudaSuccess) st = W2_ERR_CUDA;
+    if (enqueue_any(ctx, ctx->stream, &se) != cudaSuccess) st = W2_ERR_CUDA;
   }
   if (st == W2_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) st = W2_ERR_CUDA;
   for (int s = 0; s < nsteps && st == W2_OK; ++s)
@@ -500,5 +667,146 @@ extern "C" w2_status w2_step_profile(w2_ctx *ctx, int32_t nsteps, double *kernel
     return st;
   }
   ctx->steps += nsteps;
+  return W2_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Learned form
+// ---------------------------------------------------------------------------
+
+// Exact two-body term of `f` alone: the sweep with zero one-body tables.
+static cudaError_t enqueue_pair_exact(w2_ctx *ctx, const void *f, void *out, cudaStream_t s) {
+  const int nx = ctx->nx, nk = ctx->nk, W = 2 * nk - 1;
+  if (ctx->prec == W2_F64) {
+    ThetaArgs th;
+    th.nx = nx;
+    th.in = (const double *)f;
+    th.h = nullptr;
+    th.out = (double *)out;
+    th.xsum = nullptr;
+    th.K1 = ctx->Kzero;
+    th.K2 = ctx->Kzero + (size_t)nx * W;
+    th.K12 = ctx->K12;
+    th.half_tau = 0.0;
+    return launch_theta_f64(nk, 0, th, s);
+  }
+  Theta32Args th;
+  th.nx = nx;
+  th.in = (const float *)f;
+  th.base = nullptr;
+  th.h = nullptr;
+  th.out = (float *)out;
+  th.K1 = ctx->Kzero;
+  th.K2 = ctx->Kzero + (size_t)nx * W;
+  th.K12 = ctx->K12;
+  th.half_tau = 0.0f;
+  return launch_theta_f32(nk, 0, th, s);
+}
+
+static w2_status ensure_pair_buffers(w2_ctx *ctx) {
+  const int nx = ctx->nx, W = 2 * ctx->nk - 1;
+  if (!ctx->Kzero) {
+    if (cudaMalloc((void **)&ctx->Kzero, sizeof(double) * 2 * nx * W) != cudaSuccess) return W2_ERR_OOM;
+    if (cudaMemset(ctx->Kzero, 0, sizeof(double) * 2 * nx * W) != cudaSuccess) return W2_ERR_CUDA;
+  }
+  if (!ctx->f1 && cudaMalloc((void **)&ctx->f1, sizeof(float) * nx * ctx->nk) != cudaSuccess) return W2_ERR_OOM;
+  return W2_OK;
+}
+
+extern "C" w2_status w2_theta_pair(w2_ctx *ctx, const void *f, void *out) {
+  if (!ctx || !f || !out || f == out) return W2_ERR_ARG;
+  if (((uintptr_t)f | (uintptr_t)out) & 15) return W2_ERR_ARG;
+  if (ctx->sticky) return ctx->sticky;
+  if (!ctx->have_pot) return W2_ERR_STATE;
+  w2_status st = ensure_pair_buffers(ctx);
+  if (st != W2_OK) return st;
+  W2_TRY(enqueue_pair_exact(ctx, f, out, ctx->stream));
+  return W2_OK;
+}
+
+extern "C" w2_status w2_features(w2_ctx *ctx, const w2_mlp *m, const void *f, const int32_t *xs, int32_t rows,
+                                 void *x) {
+  if (!ctx || !m || !f || !x || rows < 1) return W2_ERR_ARG;
+  if (mlp_nk(m) != ctx->nk) return W2_ERR_ARG;
+  if (!xs && rows != ctx->nx * ctx->nx) return W2_ERR_ARG;
+  if (ctx->sticky) return ctx->sticky;
+  w2_status st = ensure_pair_buffers(ctx);
+  if (st != W2_OK) return st;
+  FeatArgs fa;
+  fa.nx = ctx->nx;
+  fa.nk = ctx->nk;
+  fa.din = mlp_din(m);
+  fa.dx = ctx->dx;
+  fa.dp = ctx->dp;
+  fa.s_f = mlp_scale(m, 0);
+  fa.s_f1 = mlp_scale(m, 1);
+  fa.f1 = ctx->f1;
+  fa.f1_src_rows = 1;
+  fa.xs = xs;
+  fa.x = (uint16_t *)x;
+  W2_TRY(launch_features(fa, f, ctx->prec == W2_F64, rows, ctx->stream));
+  return W2_OK;
+}
+
+// Relative L2 error of the network's two-body term against the exact one on
+// the current state; falls back to the exact term when above the tolerance.
+static w2_status learned_judge(w2_ctx *ctx) {
+  cudaStream_t s = ctx->stream;
+  W2_TRY(enqueue_pair_exact(ctx, ctx->f, ctx->g, s));
+  W2_TRY(enqueue_learned_pair(ctx, ctx->f, s));
+  W2_TRY(launch_sqdiff(mlp_out(ctx->mlp), ctx->g, ctx->prec == W2_F64, mlp_part(ctx->mlp), ctx->npts, 1.0, s));
+  W2_TRY(cudaMemcpyAsync(mlp_hpart(ctx->mlp), mlp_part(ctx->mlp), sizeof(double) * 256, cudaMemcpyDeviceToHost, s));
+  W2_TRY(cudaStreamSynchronize(s));
+  double d = 0.0, r = 0.0;
+  for (int q = 0; q < 128; ++q) {
+    d += mlp_hpart(ctx->mlp)[2 * q];
+    r += mlp_hpart(ctx->mlp)[2 * q + 1];
+  }
+  ctx->last_err = r > 0.0 ? sqrt(d / r) : (d > 0.0 ? INFINITY : 0.0);
+  ctx->judged += 1;
+  if (!(ctx->last_err <= ctx->judge_tol)) {
+    ctx->learned_active = false;
+    if (ctx->graph_ready) {  // the captured step used the network
+      cudaGraphExecDestroy(ctx->graph);
+      ctx->graph_ready = false;
+    }
+  }
+  return W2_OK;
+}
+
+extern "C" w2_status w2_learned_attach(w2_ctx *ctx, w2_mlp *m, int32_t judge_every, double tol) {
+  if (!ctx) return W2_ERR_ARG;
+  if (ctx->sticky) return ctx->sticky;
+  if (ctx->graph_ready) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph_ready = false;
+  }
+  if (!m) {
+    ctx->mlp = nullptr;
+    ctx->learned_active = false;
+    return W2_OK;
+  }
+  if (ctx->prec != W2_F64) return W2_ERR_UNSUPPORTED;
+  if (mlp_nk(m) != ctx->nk || mlp_maxrows(m) < ctx->nx * ctx->nx || judge_every < 0 || !(tol >= 0)) return W2_ERR_ARG;
+  w2_status st = ensure_pair_buffers(ctx);
+  if (st != W2_OK) return st;
+  if (!ctx->xrows &&
+      cudaMalloc((void **)&ctx->xrows, sizeof(uint16_t) * (size_t)ctx->nx * ctx->nx * mlp_din(m)) != cudaSuccess)
+    return W2_ERR_OOM;
+  ctx->mlp = m;
+  ctx->learned_active = true;
+  ctx->judge_every = judge_every;
+  ctx->judge_tol = tol;
+  ctx->since_judge = 0;
+  ctx->judged = 0;
+  ctx->last_err = 0.0;
+  return W2_OK;
+}
+
+extern "C" w2_status w2_learned_report(w2_ctx *ctx, int32_t *active, int32_t *judged, double *last_err) {
+  if (!ctx) return W2_ERR_ARG;
+  if (active) *active = ctx->mlp && ctx->learned_active ? 1 : 0;
+  if (judged) *judged = ctx->judged;
+  if (last_err) *last_err = ctx->last_err;
   return W2_OK;
 }

@@ -1,0 +1,598 @@
+// Precision form: FP32 state, split-precision tensor-core contractions.
+//
+//  k_theta32 : the X-local pseudo-difference sweep of w2_f64.cu on
+//              mma.sync m16n8k8 tf32 with FP32 accumulation.  The state block
+//              is split into two TF32 parts (hi = tf32(x), lo = tf32(x - hi))
+//              and the kernel table into three, and each product keeps the
+//              five terms down to 2^-22 relative.  The operator's output enters
+//              the time step scaled by tau*|Theta| (a few 1e-2), so its error
+//              stays below the FP32 rounding of the state.
+//  k_adv32   : periodic cubic-spline shift along x2 (DIR 0) and x1 (DIR 1).
+//              The shift of the state is computed as an increment
+//              delta = (S - I) f from taps that merge the B-spline evaluation
+//              weights with the (1,4,1)/6 interpolation condition, so its FP32
+//              error is proportional to the (sub-cell) shift, not to |f|; the
+//              state itself is rounded once per step, in the corrector.
+#include <math.h>
+#include <stdint.h>
+
+#include "w2_internal.cuh"
+
+namespace w2 {
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
+  hi = tf32_rna(x);
+  lo = tf32_rna(x - __uint_as_float(hi));
+}
+
+// Three TF32 parts of an FP64 kernel value: x = hi + mid + lo to ~2^-33.
+__device__ __forceinline__ void split3_tf32_d(double x, uint32_t &hi, uint32_t &mid, uint32_t &lo) {
+  hi = tf32_rna((float)x);
+  const double r1 = x - (double)__uint_as_float(hi);
+  mid = tf32_rna((float)r1);
+  lo = tf32_rna((float)(r1 - (double)__uint_as_float(mid)));
+}
+
+// D(16x8) += A(16x8) B(8x8), TF32 in, FP32 accumulate.  Fragments (PTX ISA,
+// mma.m16n8k8 .tf32): a = A[g][t], A[g+8][t], A[g][t+4], A[g+8][t+4];
+// b = B[t][g], B[t+4][g]; d = D[g][2t], D[g][2t+1], D[g+8][2t], D[g+8][2t+1]
+// with g = lane>>2, t = lane&3.
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Products of a three-part operand K = kh + km + kl (the kernel table) with a
+// two-part operand F = fh + fl, keeping every term down to 2^-22 relative.
+// The leading product kh fh goes to the accumulator `big`; the four small
+// ones (kl fh, km fl, km fh, kh fl, at most 2^-11 of it) to `small`.  The
+// tensor core's FP32 accumulation drops the bits of the smaller addend below
+// the larger one's last place (no rounding to nearest), which biases long
+// running sums; so the callers give `big` a fresh zero accumulator for each
+// 8-wide k-step and add it to the running sum with an ordinary FP32 add.
+// The kernel table is the same in every step, so a representation error in
+// it would act like a fixed perturbation of the potential and accumulate
+// coherently; three parts remove it.
+__device__ __forceinline__ void mma5_a3(float (&big)[4], float (&small)[4], const uint32_t (&kh)[4],
+                                        const uint32_t (&km)[4], const uint32_t (&kl)[4], const uint32_t (&fh)[2],
+                                        const uint32_t (&fl)[2]) {
+  mma_tf32(small, kl, fh);
+  mma_tf32(small, km, fl);
+  mma_tf32(small, km, fh);
+  mma_tf32(small, kh, fl);
+  mma_tf32(big, kh, fh);
+}
+
+// Same with the kernel table as the B operand and F as the A operand.
+__device__ __forceinline__ void mma5_b3(float (&big)[4], float (&small)[4], const uint32_t (&fh)[4],
+                                        const uint32_t (&fl)[4], const uint32_t (&kh)[2], const uint32_t (&km)[2],
+                                        const uint32_t (&kl)[2]) {
+  mma_tf32(small, fh, kl);
+  mma_tf32(small, fl, km);
+  mma_tf32(small, fh, km);
+  mma_tf32(small, fl, kh);
+  mma_tf32(big, fh, kh);
+}
+
+template <int NK>
+struct Theta32Smem {
+  static constexpr int S = NK + 8;  // padded row stride (floats): conflict-free B fragments
+  static constexpr size_t words = 3 * (size_t)NK * S + 9 * 2 * NK;
+  static constexpr size_t bytes = 4 * words;
+};
+
+// One CTA per X; warp w owns momentum rows [16w, 16w + 16).
+// MODE 0: out = Theta[in].  MODE 1: out = base + (h + half_tau Theta[in]).
+template <int NK, int MODE>
+// compiled once (not inlined) so the single-problem and batched kernels
+// run the same machine code and give identical bits
+__device__ __noinline__ void theta32_block(const Theta32Args &a, const int X, uint32_t *smu) {
+  using L = Theta32Smem<NK>;
+  constexpr int S = L::S, NT = NK / 8, W = 2 * NK - 1;
+  uint32_t *Fh = smu, *Fl = smu + NK * S;
+  float *Acc = reinterpret_cast<float *>(smu + 2 * NK * S);
+  uint32_t *kt = smu + 3 * NK * S;  // hi, mid, lo parts of K1, K2, K12, 2NK words each
+  uint32_t *k1h = kt, *k1m = kt + 2 * NK, *k1l = kt + 4 * NK;
+  uint32_t *k2h = kt + 6 * NK, *k2m = kt + 8 * NK, *k2l = kt + 10 * NK;
+  uint32_t *k12h = kt + 12 * NK, *k12m = kt + 14 * NK, *k12l = kt + 16 * NK;
+
+  const int nx = a.nx;
+  const int i1 = X / nx, i2 = X - i1 * nx;
+  int dd = i1 - i2;
+  dd += (dd < 0) ? nx : 0;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int g = lane >> 2, t4 = lane & 3;
+  const size_t base = (size_t)X * NK * NK;
+  {
+    const float4 *src = reinterpret_cast<const float4 *>(a.in + base);
+    for (int e = tid; e < NK * NK / 4; e += blockDim.x) {
+      const float4 v = src[e];
+      const int r = (4 * e) / NK, c = 4 * e - r * NK;
+      split_tf32(v.x, Fh[r * S + c], Fl[r * S + c]);
+      split_tf32(v.y, Fh[r * S + c + 1], Fl[r * S + c + 1]);
+      split_tf32(v.z, Fh[r * S + c + 2], Fl[r * S + c + 2]);
+      split_tf32(v.w, Fh[r * S + c + 3], Fl[r * S + c + 3]);
+    }
+    for (int j = tid; j < W; j += blockDim.x) {
+      split3_tf32_d(a.K1[(size_t)i1 * W + j], k1h[j], k1m[j], k1l[j]);
+      split3_tf32_d(a.K2[(size_t)i2 * W + j], k2h[j], k2m[j], k2l[j]);
+      split3_tf32_d(a.K12[(size_t)dd * W + j], k12h[j], k12m[j], k12l[j]);
+    }
+  }
+  __syncthreads();
+
+  const int r0 = 16 * w;
+  const int na = r0 + g, nb = r0 + g + 8;  // the two A/D rows of this lane
+
+  // Two-body term in sheared coordinates (see k_theta in w2_f64.cu).
+  {
+    const int cmax = min((r0 + 15 + NK - 1) >> 3, (2 * NK - 2) >> 3);
+    for (int c = r0 >> 3; c <= cmax; ++c) {
+      float d[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f};
+      const int nlo = max(0, 8 * c - NK + 1), nhi = min(NK - 1, 8 * c + 7);
+      const int s = 8 * c + g;
+      for (int kk = nlo & ~7; kk <= nhi; kk += 8) {
+        uint32_t ah[4], am[4], al[4], bh[2], bl[2];
+        const int c0 = kk + t4, c1 = kk + t4 + 4;
+        const int j0 = c0 - na + NK - 1, j1 = c0 - nb + NK - 1, j2 = c1 - na + NK - 1, j3 = c1 - nb + NK - 1;
+        ah[0] = k12h[j0]; am[0] = k12m[j0]; al[0] = k12l[j0];
+        ah[1] = k12h[j1]; am[1] = k12m[j1]; al[1] = k12l[j1];
+        ah[2] = k12h[j2]; am[2] = k12m[j2]; al[2] = k12l[j2];
+        ah[3] = k12h[j3]; am[3] = k12m[j3]; al[3] = k12l[j3];
+        const int m0 = s - c0, m1 = s - c1;
+        const bool v0 = (m0 >= 0 && m0 < NK), v1 = (m1 >= 0 && m1 < NK);
+        bh[0] = v0 ? Fh[c0 * S + m0] : 0u; bl[0] = v0 ? Fl[c0 * S + m0] : 0u;
+        bh[1] = v1 ? Fh[c1 * S + m1] : 0u; bl[1] = v1 ? Fl[c1 * S + m1] : 0u;
+        float t[4] = {0.f, 0.f, 0.f, 0.f};
+        mma5_a3(t, e, ah, am, al, bh, bl);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) d[q] += t[q];  // round-to-nearest on the CUDA cores
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) d[q] += e[q];
+      const int sa = 8 * c + 2 * t4;
+      int n2;
+      n2 = sa - na;     if (n2 >= 0 && n2 < NK) Acc[na * S + n2] = d[0];
+      n2 = sa + 1 - na; if (n2 >= 0 && n2 < NK) Acc[na * S + n2] = d[1];
+      n2 = sa - nb;     if (n2 >= 0 && n2 < NK) Acc[nb * S + n2] = d[2];
+      n2 = sa + 1 - nb; if (n2 >= 0 && n2 < NK) Acc[nb * S + n2] = d[3];
+    }
+  }
+  __syncwarp();
+
+  float acc[NT][4], sml[NT][4];
+#pragma unroll
+  for (int b = 0; b < NT; ++b) {
+    acc[b][0] = Acc[na * S + 8 * b + 2 * t4];
+    acc[b][1] = Acc[na * S + 8 * b + 2 * t4 + 1];
+    acc[b][2] = Acc[nb * S + 8 * b + 2 * t4];
+    acc[b][3] = Acc[nb * S + 8 * b + 2 * t4 + 1];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sml[b][q] = 0.f;
+  }
+  for (int kk = 0; kk < NK; kk += 8) {
+    const int c0 = kk + t4, c1 = kk + t4 + 4;
+    uint32_t a1h[4], a1m[4], a1l[4], a2h[4], a2l[4];
+    {  // A1[n1][n1'] = K1(n1' - n1)
+      const int j0 = c0 - na + NK - 1, j1 = c0 - nb + NK - 1, j2 = c1 - na + NK - 1, j3 = c1 - nb + NK - 1;
+      a1h[0] = k1h[j0]; a1m[0] = k1m[j0]; a1l[0] = k1l[j0];
+      a1h[1] = k1h[j1]; a1m[1] = k1m[j1]; a1l[1] = k1l[j1];
+      a1h[2] = k1h[j2]; a1m[2] = k1m[j2]; a1l[2] = k1l[j2];
+      a1h[3] = k1h[j3]; a1m[3] = k1m[j3]; a1l[3] = k1l[j3];
+    }
+    a2h[0] = Fh[na * S + c0]; a2l[0] = Fl[na * S + c0];               // F[n1][n2']
+    a2h[1] = Fh[nb * S + c0]; a2l[1] = Fl[nb * S + c0];
+    a2h[2] = Fh[na * S + c1]; a2l[2] = Fl[na * S + c1];
+    a2h[3] = Fh[nb * S + c1]; a2l[3] = Fl[nb * S + c1];
+#pragma unroll
+    for (int b = 0; b < NT; ++b) {
+      const int n2 = 8 * b + g;
+      uint32_t bh[2], bm[2], bl[2];
+      bh[0] = Fh[c0 * S + n2]; bl[0] = Fl[c0 * S + n2];               // F[n1'][n2]
+      bh[1] = Fh[c1 * S + n2]; bl[1] = Fl[c1 * S + n2];
+      float t[4] = {0.f, 0.f, 0.f, 0.f};
+      mma5_a3(t, sml[b], a1h, a1m, a1l, bh, bl);
+      const int j0 = c0 - n2 + NK - 1, j1 = c1 - n2 + NK - 1;         // K2(n2' - n2)
+      bh[0] = k2h[j0]; bm[0] = k2m[j0]; bl[0] = k2l[j0];
+      bh[1] = k2h[j1]; bm[1] = k2m[j1]; bl[1] = k2l[j1];
+      mma5_b3(t, sml[b], a2h, a2l, bh, bm, bl);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[b][q] += t[q];  // round-to-nearest on the CUDA cores
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < NT; ++b)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[b][q] += sml[b][q];
+
+#pragma unroll
+  for (int b = 0; b < NT; ++b) {
+#pragma unroll
+    for (int hrow = 0; hrow < 2; ++hrow) {
+      const int n1 = hrow ? nb : na;
+      const size_t o = base + (size_t)n1 * NK + 8 * b + 2 * t4;
+      float2 v;
+      if (MODE == 0) {
+        v.x = acc[b][2 * hrow];
+        v.y = acc[b][2 * hrow + 1];
+      } else {
+        const float2 hv = *reinterpret_cast<const float2 *>(a.h + o);
+        const float2 fv = *reinterpret_cast<const float2 *>(a.base + o);
+        v.x = fv.x + fmaf(a.half_tau, acc[b][2 * hrow], hv.x);
+        v.y = fv.y + fmaf(a.half_tau, acc[b][2 * hrow + 1], hv.y);
+      }
+      *reinterpret_cast<float2 *>(a.out + o) = v;
+    }
+  }
+}
+
+template <int NK, int MODE>
+__global__ void __launch_bounds__(NK * 2) k_theta32(Theta32Args a) {
+  extern __shared__ __align__(16) uint32_t smu[];
+  theta32_block<NK, MODE>(a, blockIdx.x, smu);
+}
+
+// Locate work item `item` in a class of instances with item offsets off[0..n].
+__device__ __forceinline__ int find_inst(const int *off, int n, int item) {
+  int k = 0;
+  while (k + 1 < n && off[k + 1] <= item) ++k;
+  return k;
+}
+
+// Persistent batched sweep: CTAs stride over the (instance, X) items of every
+// instance of one momentum size; args[2 * inst + MODE] holds that instance's
+// arguments.
+template <int NK, int MODE>
+__global__ void __launch_bounds__(NK * 2) k_btheta32(const Theta32Args *args, const int *inst, const int *off,
+                                                     int n) {
+  extern __shared__ __align__(16) uint32_t smu[];
+  const int total = off[n];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int k = find_inst(off, n, item);
+    const Theta32Args a = args[2 * inst[k] + MODE];
+    theta32_block<NK, MODE>(a, item - off[k], smu);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Spline shift, FP32
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void spline_coeffs32(float *col, int stride, int n, float z, float zscale, int nterm) {
+  float c0 = 0.f, zk = 1.f;
+  for (int k = 0; k < nterm; ++k) {
+    c0 = fmaf(zk, col[((n - k) % n) * stride], c0);
+    zk *= z;
+  }
+  float prev = c0 * zscale;
+  col[0] = prev;
+  for (int i = 1; i < n; ++i) {
+    prev = fmaf(z, prev, col[i * stride]);
+    col[i * stride] = prev;
+  }
+  float dN = 0.f;
+  zk = 1.f;
+  for (int k = 0; k < nterm; ++k) {
+    dN = fmaf(zk, col[((n - 1 + k) % n) * stride], dN);
+    zk *= z;
+  }
+  prev = dN * zscale;
+  col[(n - 1) * stride] = prev;
+  for (int i = n - 2; i >= 0; --i) {
+    prev = fmaf(z, prev, col[i * stride]);
+    col[i * stride] = prev;
+  }
+}
+
+__device__ __forceinline__ int wrap(int j, int n) {
+  j %= n;
+  return j < 0 ? j + n : j;
+}
+
+// Columns in shared memory carry kGhost copies of the periodic neighbours at
+// each end (row r holds element r - kGhost), so stencils within kGhost of a
+// point read straight rows without wrapping the index.
+constexpr int kGhost = 4;
+
+__device__ __forceinline__ void fill_ghosts(float *col, int stride, int n) {
+#pragma unroll
+  for (int k = 0; k < kGhost; ++k) {
+    col[(kGhost + n + k) * stride] = col[(kGhost + k) * stride];
+    col[(kGhost - 1 - k) * stride] = col[(kGhost + n - 1 - k) * stride];
+  }
+}
+
+// S f at i: sum_{a=-1..2} w_a d_{i + k0 + a}; col points at row 0 (ghosts included)
+__device__ __forceinline__ float eval32(const float *col, int stride, int n, int i, int k0, const float *w) {
+  float v = 0.f;
+  if (k0 >= -3 && k0 <= 2) {
+    const float *c = col + (kGhost + i + k0 - 1) * stride;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v = fmaf(w[q], c[q * stride], v);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v = fmaf(w[q], col[(kGhost + wrap(i + k0 - 1 + q, n)) * stride], v);
+  }
+  return v;
+}
+
+// (S - I) f at i.  ct[0..6]: merged taps at offsets -3..3, ct[7] = 1 when they
+// apply (|k0| small); otherwise the evaluation and the interpolation condition
+// are summed separately.
+__device__ __forceinline__ float incr32(const float *col, int stride, int n, int i, int k0, const float *w,
+                                        const float *ct, float z) {
+  const float *c = col + (kGhost + i) * stride;
+  if (ct[7] != 0.f) {
+    float v = 0.f;
+#pragma unroll
+    for (int o = -3; o <= 3; ++o) v = fmaf(ct[o + 3], c[o * stride], v);
+    return v;
+  }
+  const float sv = eval32(col, stride, n, i, k0, w);
+  const float fi = -z * (c[-stride] + 4.f * c[0] + c[stride]);
+  return sv - fi;
+}
+
+// DIR 0 (lines along x2 at fixed (i1 = blockIdx.y, n1 = blockIdx.x); the line
+// of column n2 is shifted by tau p_{n2}/m):
+//   d2 = (S2 - I) f,  g2 = S2 g (when g is given).
+// DIR 1 (lines along x1 at fixed (i2 = blockIdx.y, n1 = blockIdx.x); shift
+// tau p_{n1}/m), u = f + d2:
+//   two arrays: d1 = (S1 - I) u, b = S1 g2, ft = u + d1 + tau b,
+//               dh = d2 + d1 + tau/2 b   (dh may overwrite d2 in place)
+//   one array : ft = u + d1  (= S1 S2 f)
+// Columns (momentum values n2) handled by one CTA of the shift: at most 64, so
+// that a slab of a few arrays leaves room for two or three CTAs per SM.
+template <int NK>
+struct AdvCols {
+  static constexpr int C = NK >= 64 ? 64 : NK;
+  static constexpr int blocks = NK / C;
+};
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+
+// Stage rows i = 0..nx-1 of C contiguous floats (global stride lineStride)
+// into rows kGhost + i of a shared slab of stride C, 16 bytes per copy, all
+// copies of the CTA in flight together.
+template <int C>
+__device__ __forceinline__ void stage_slab(float *slab, const float *src, size_t lineStride, int nx) {
+  constexpr int Q = C / 4;
+  for (int e = threadIdx.x; e < nx * Q; e += blockDim.x) {
+    const int i = e / Q, c = 4 * (e - i * Q);
+    cp_async16(slab + (kGhost + i) * C + c, src + i * lineStride + c);
+  }
+}
+
+// DIR 0 (lines along x2 at fixed (i1, n1); the line of column n2 is shifted by
+// tau p_{n2}/m):  d2 = (S2 - I) f,  g2 = S2 g (when g is given).
+// DIR 1 (lines along x1 at fixed (i2, n1); shift tau p_{n1}/m), u = f + d2:
+//   two arrays: d1 = (S1 - I) u, b = S1 g2, ft = u + d1 + tau b,
+//               dh = d2 + d1 + tau/2 b   (dh may overwrite d2 in place)
+//   one array : ft = u + d1  (= S1 S2 f)
+// A CTA owns columns [cb*C, cb*C + C) of the slab, one thread per column.
+template <int NK, int DIR>
+// compiled once (not inlined) so the single-problem and batched kernels
+// run the same machine code and give identical bits
+__device__ __noinline__ void adv32_block(const Adv32Args &a, const int n1, const int cb, const int fixed,
+                                         float *sm32) {
+  constexpr int C = AdvCols<NK>::C;
+  const int nx = a.nx;
+  const int t = threadIdx.x, col = cb * C + t;
+  const int rows = nx + 2 * kGhost;
+  const size_t lineStride = (DIR == 0) ? (size_t)NK * NK : (size_t)nx * NK * NK;
+  const size_t base = ((DIR == 0) ? ((size_t)fixed * nx * NK + n1) * NK : ((size_t)fixed * NK + n1) * NK) + cb * C;
+  const int sidx = (DIR == 0) ? col : n1;
+  const int k0 = a.k0tab[sidx];
+  float w[4], ct[8];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) w[q] = a.wtab[4 * sidx + q];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) ct[q] = a.ctab[8 * sidx + q];
+  float *SA = sm32, *SB = sm32 + (size_t)rows * C, *SC = sm32 + 2 * (size_t)rows * C;
+  float *A = SA + t, *B = SB + t, *Cc = SC + t;  // this thread's column
+  if (DIR == 0) {
+    const bool two = a.g != nullptr;
+    stage_slab<C>(SA, a.f + base, lineStride, nx);
+    if (two) stage_slab<C>(SB, a.g + base, lineStride, nx);
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    spline_coeffs32(A + kGhost * C, C, nx, a.z, a.zscale, a.nterm);
+    fill_ghosts(A, C, nx);
+    if (two) {
+      spline_coeffs32(B + kGhost * C, C, nx, a.z, a.zscale, a.nterm);
+      fill_ghosts(B, C, nx);
+    }
+    for (int i = 0; i < nx; ++i) {
+      const size_t o = base + i * lineStride + t;
+      a.d2[o] = incr32(A, C, nx, i, k0, w, ct, a.z);
+      if (two) a.g2[o] = eval32(B, C, nx, i, k0, w);
+    }
+  } else {
+    const bool two = a.g2in != nullptr;
+    stage_slab<C>(SA, a.f + base, lineStride, nx);
+    stage_slab<C>(SB, a.d2in + base, lineStride, nx);
+    if (two) stage_slab<C>(SC, a.g2in + base, lineStride, nx);
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    for (int i = 0; i < nx; ++i) A[(kGhost + i) * C] += B[(kGhost + i) * C];  // u = f + d2
+    spline_coeffs32(A + kGhost * C, C, nx, a.z, a.zscale, a.nterm);
+    fill_ghosts(A, C, nx);
+    if (two) {
+      spline_coeffs32(Cc + kGhost * C, C, nx, a.z, a.zscale, a.nterm);
+      fill_ghosts(Cc, C, nx);
+    }
+    for (int i = 0; i < nx; ++i) {
+      const size_t o = base + i * lineStride + t;
+      const float d1 = incr32(A, C, nx, i, k0, w, ct, a.z);
+      // u_i recovered from its spline coefficients: u = (1,4,1)/6 eta = -z (d_{i-1} + 4 d_i + d_{i+1})
+      const float *ca = A + (kGhost + i) * C;
+      const float u = -a.z * (ca[-C] + 4.f * ca[0] + ca[C]);
+      if (two) {
+        const float b = eval32(Cc, C, nx, i, k0, w);
+        const float da = B[(kGhost + i) * C] + d1;
+        a.ft[o] = u + fmaf(a.tau, b, d1);
+        a.dh[o] = fmaf(0.5f * a.tau, b, da);
+      } else {
+        a.ft[o] = u + d1;
+      }
+    }
+  }
+}
+
+template <int NK, int DIR>
+__global__ void __launch_bounds__(AdvCols<NK>::C) k_adv32(Adv32Args a) {
+  extern __shared__ __align__(16) float sm32[];
+  adv32_block<NK, DIR>(a, blockIdx.x / AdvCols<NK>::blocks, blockIdx.x % AdvCols<NK>::blocks, blockIdx.y, sm32);
+}
+
+// Persistent batched shift: items are (instance, slab) with
+// slab = (fixed * NK + n1) * blocks + cb; args[2 * inst + DIR] holds that
+// instance's arguments.
+template <int NK, int DIR>
+__global__ void __launch_bounds__(AdvCols<NK>::C) k_badv32(const Adv32Args *args, const int *inst, const int *off,
+                                                           int n) {
+  extern __shared__ __align__(16) float sm32[];
+  constexpr int NB = AdvCols<NK>::blocks;
+  const int total = off[n];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int k = find_inst(off, n, item);
+    const Adv32Args a = args[2 * inst[k] + DIR];
+    const int slab = item - off[k];
+    const int cb = slab % NB, rest = slab / NB;
+    adv32_block<NK, DIR>(a, rest % NK, cb, rest / NK, sm32);
+    __syncthreads();
+  }
+}
+
+int adv_items_per_line_f32(int nk) { return nk >= 64 ? nk / 64 : 1; }
+
+// ---------------------------------------------------------------------------
+// Dispatch
+// ---------------------------------------------------------------------------
+
+bool nk_supported_f32(int nk) { return nk >= 16 && nk <= 128 && nk % 16 == 0; }
+
+template <int NK>
+static cudaError_t prep32() {
+  cudaError_t e = cudaFuncSetAttribute(k_theta32<NK, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)Theta32Smem<NK>::bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_theta32<NK, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Theta32Smem<NK>::bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adv32<NK, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adv32<NK, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_btheta32<NK, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Theta32Smem<NK>::bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_btheta32<NK, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Theta32Smem<NK>::bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_badv32<NK, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_badv32<NK, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  return e;
+}
+
+template <int NK>
+static cudaError_t run_btheta32(int mode, const BatchLaunch &b, const Theta32Args *args, cudaStream_t s) {
+  if (mode == 0)
+    k_btheta32<NK, 0><<<b.grid, NK * 2, Theta32Smem<NK>::bytes, s>>>(args, b.inst, b.off, b.n);
+  else
+    k_btheta32<NK, 1><<<b.grid, NK * 2, Theta32Smem<NK>::bytes, s>>>(args, b.inst, b.off, b.n);
+  return cudaGetLastError();
+}
+
+template <int NK>
+static cudaError_t run_badv32(int dir, const BatchLaunch &b, const Adv32Args *args, int nxmax, cudaStream_t s) {
+  constexpr int C = AdvCols<NK>::C;
+  const size_t smem = sizeof(float) * (size_t)(dir == 0 ? 2 : 3) * (nxmax + 2 * kGhost) * C;
+  if (dir == 0)
+    k_badv32<NK, 0><<<b.grid, C, smem, s>>>(args, b.inst, b.off, b.n);
+  else
+    k_badv32<NK, 1><<<b.grid, C, smem, s>>>(args, b.inst, b.off, b.n);
+  return cudaGetLastError();
+}
+
+template <int NK>
+static cudaError_t run_theta32(int mode, const Theta32Args &a, cudaStream_t s) {
+  dim3 grid(a.nx * a.nx), block(NK * 2);
+  if (mode == 0)
+    k_theta32<NK, 0><<<grid, block, Theta32Smem<NK>::bytes, s>>>(a);
+  else
+    k_theta32<NK, 1><<<grid, block, Theta32Smem<NK>::bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int NK>
+static cudaError_t run_adv32(int dir, const Adv32Args &a, cudaStream_t s) {
+  constexpr int C = AdvCols<NK>::C;
+  dim3 grid(NK * AdvCols<NK>::blocks, a.nx), block(C);
+  const int slabs = dir == 0 ? 2 : 3;
+  const size_t smem = sizeof(float) * (size_t)slabs * (a.nx + 2 * kGhost) * C;
+  if (dir == 0)
+    k_adv32<NK, 0><<<grid, block, smem, s>>>(a);
+  else
+    k_adv32<NK, 1><<<grid, block, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+#define W2_NK32_SWITCH(nk, EXPR_TEMPLATE) \
+  switch (nk) {                          \
+    case 16: return EXPR_TEMPLATE(16);   \
+    case 32: return EXPR_TEMPLATE(32);   \
+    case 48: return EXPR_TEMPLATE(48);   \
+    case 64: return EXPR_TEMPLATE(64);   \
+    case 80: return EXPR_TEMPLATE(80);   \
+    case 96: return EXPR_TEMPLATE(96);   \
+    case 112: return EXPR_TEMPLATE(112); \
+    case 128: return EXPR_TEMPLATE(128); \
+    default: return cudaErrorInvalidValue; \
+  }
+
+cudaError_t prepare_kernels_f32(int nk) {
+#define W2_P(N) prep32<N>()
+  W2_NK32_SWITCH(nk, W2_P)
+#undef W2_P
+}
+
+cudaError_t launch_theta_f32(int nk, int mode, const Theta32Args &a, cudaStream_t s) {
+#define W2_T(N) run_theta32<N>(mode, a, s)
+  W2_NK32_SWITCH(nk, W2_T)
+#undef W2_T
+}
+
+cudaError_t launch_adv_f32(int nk, int dir, const Adv32Args &a, cudaStream_t s) {
+#define W2_A(N) run_adv32<N>(dir, a, s)
+  W2_NK32_SWITCH(nk, W2_A)
+#undef W2_A
+}
+
+cudaError_t launch_btheta_f32(int nk, int mode, const BatchLaunch &b, const Theta32Args *args, cudaStream_t s) {
+#define W2_BT(N) run_btheta32<N>(mode, b, args, s)
+  W2_NK32_SWITCH(nk, W2_BT)
+#undef W2_BT
+}
+
+cudaError_t launch_badv_f32(int nk, int dir, const BatchLaunch &b, const Adv32Args *args, int nxmax,
+                            cudaStream_t s) {
+#define W2_BA(N) run_badv32<N>(dir, b, args, nxmax, s)
+  W2_NK32_SWITCH(nk, W2_BA)
+#undef W2_BA
+}
+
+}  // namespace w2

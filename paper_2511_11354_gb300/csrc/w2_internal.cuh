@@ -33,6 +33,7 @@ struct ThetaArgs {
   double *xsum;             // mode 1: per-X sums of out
   const double *K1, *K2, *K12;
   double half_tau;
+  const float *pair = nullptr;  // if set: the two-body term, [nx*nx][nk*nk], used instead of K12
 };
 
 struct AdvArgs {
@@ -49,11 +50,78 @@ struct AdvArgs {
 struct ObsArgs {
   int nx, nk, M;
   double dx, dp, hbar, mass, gamma, c_h;
-  const double *f;
+  const double *f;          // FP64 state, or
+  const float *f32;         // FP32 state (exactly one is non-null)
   const double *vext_grid;  // [nx]
   const double *w_fine;     // [nx][M]; column 0 is W(fold(d dx))
   double *xpart;            // [nx*nx][3 + nk] per-X partials
   double *out;              // [8 + nx + nx*nx]
+};
+
+struct Theta32Args {
+  int nx;
+  const float *in;          // state the operator acts on
+  const float *base;        // mode 1: the state f
+  const float *h;           // mode 1: the corrector increment
+  float *out;               // mode 0: Theta[in]; mode 1: base + (h + half_tau Theta[in])
+  const double *K1, *K2, *K12;
+  float half_tau;
+};
+
+struct Adv32Args {
+  int nx;
+  const float *f, *g;       // DIR 0 inputs (g may be null); DIR 1 reads f
+  float *d2, *g2;           // DIR 0 outputs
+  const float *d2in, *g2in; // DIR 1 inputs (g2in may be null)
+  float *ft, *dh;           // DIR 1 outputs
+  const int *k0tab;         // [nk]
+  const float *wtab;        // [nk][4] evaluation weights (times -6 z)
+  const float *ctab;        // [nk][8] merged increment taps, offsets -3..3, [7] = usable
+  float z, zscale;
+  int nterm;
+  float tau;
+};
+
+// A persistent batched launch over the work items of several instances:
+// inst[k] is the k-th instance of the class, items [off[k], off[k+1]) are its.
+struct BatchLaunch {
+  int grid;
+  const int *inst;
+  const int *off;
+  int n;
+};
+
+struct BXsum {
+  const float *f;
+  double *xsum;
+  int nk;
+};
+
+enum GemmEpi { GEMM_STORE = 0, GEMM_BIAS_SILU = 1, GEMM_BIAS_SCALE = 2, GEMM_DSILU = 3 };
+
+// C[M][N] = sum_k A(m, k) B(k, n) with bf16 A(m, k) = A[m*sam + k*sak] and
+// B(k, n) = B[k*sbk + n*sbn], followed by the epilogue `epi`.
+struct GemmArgs {
+  const void *A, *B;
+  long long sam, sak, sbk, sbn;
+  int M, N, K;
+  int epi;
+  const float *bias;   // [N] (BIAS_*)
+  const float *aux;    // [M][N] pre-activation Z (DSILU)
+  float scale;         // BIAS_SCALE
+  float *out_f32;      // [M][N]
+  uint16_t *out_bf16;  // [M][N] (BIAS_SILU, DSILU)
+};
+
+// Input rows of the learned two-body term (see w2_mlp.cu).
+struct FeatArgs {
+  int nx, nk, din;
+  double dx, dp;
+  float s_f, s_f1;
+  float *f1;           // [nx][nk] reduced one-body Wigner function (refreshed when f1_src_rows > 0)
+  int f1_src_rows;
+  const int *xs;       // spatial points of the rows (null: row r is X = r)
+  uint16_t *x;         // [rows][din] bf16
 };
 
 // Launchers (return the launch error).
@@ -61,8 +129,84 @@ cudaError_t launch_tables(const TabArgs &a, cudaStream_t s);
 cudaError_t launch_theta_f64(int nk, int mode, const ThetaArgs &a, cudaStream_t s);
 cudaError_t launch_adv_f64(int nk, int dir, int two, const AdvArgs &a, cudaStream_t s);
 cudaError_t launch_xsum_f64(int nx, int nk, const double *f, double *xsum, cudaStream_t s);
-cudaError_t launch_obs_f64(const ObsArgs &a, cudaStream_t s);
+cudaError_t launch_xsum_f32(int nx, int nk, const float *f, double *xsum, cudaStream_t s);
+cudaError_t launch_obs(const ObsArgs &a, cudaStream_t s);
 cudaError_t prepare_kernels_f64(int nk);
 bool nk_supported_f64(int nk);
+cudaError_t prepare_kernels_f32(int nk);
+bool nk_supported_f32(int nk);
+int adv_items_per_line_f32(int nk);  // column blocks of the FP32 shift per (n1, x) line
+cudaError_t launch_theta_f32(int nk, int mode, const Theta32Args &a, cudaStream_t s);
+cudaError_t launch_adv_f32(int nk, int dir, const Adv32Args &a, cudaStream_t s);
+cudaError_t launch_btheta_f32(int nk, int mode, const BatchLaunch &b, const Theta32Args *args, cudaStream_t s);
+cudaError_t launch_badv_f32(int nk, int dir, const BatchLaunch &b, const Adv32Args *args, int nxmax,
+                            cudaStream_t s);
+cudaError_t launch_btables(const TabArgs *args, const int *off, int n, int grid, int nxmax, int mmax,
+                           cudaStream_t s);
+cudaError_t launch_bxsum(const BXsum *args, const int *off, int n, int grid, cudaStream_t s);
+cudaError_t launch_gemm(const GemmArgs &a, cudaStream_t s);
+cudaError_t launch_features(const FeatArgs &a, const void *f, int f64, int rows, cudaStream_t s);
+cudaError_t launch_colsum(const float *in, float *out, int M, int N, cudaStream_t s);
+cudaError_t launch_adam(float *p, const float *g, float *m, float *v, uint16_t *pb, size_t n, float lr, float b1,
+                        float b2, int t, float eps, cudaStream_t s);
+cudaError_t launch_f2bf(const float *in, uint16_t *out, size_t n, cudaStream_t s);
+cudaError_t launch_mse(const float *Y, const float *T, float *dY, double *part, size_t n, float gscale,
+                       cudaStream_t s);
+cudaError_t launch_sqdiff(const float *a, const void *b, int b_f64, double *part, size_t n, double bscale,
+                          cudaStream_t s);
 
+}  // namespace w2
+
+// A single problem on one device (the object behind the w2_ctx handle).
+struct w2_ctx {
+  w2_config cfg;
+  cudaStream_t stream;       // borrowed
+  cudaStream_t cap;          // private stream used only for graph capture
+  int dev;
+  int prec;                  // w2_precision
+  size_t esz;                // bytes per phase-space element
+  int nx, nk, M;
+  size_t npts;
+  double dx, dp, hp, tau;
+  double gamma, c_h, c_xc;
+  bool have_pot, have_state;
+  int64_t steps;
+  w2_status sticky;
+  // phase-space arrays
+  double *f, *g, *t1, *t2;
+  // small device buffers
+  double *xsum, *xsum2;       // [nx*nx]
+  double *K, *K12;            // [2][nx][2nk-1], [nx][2nk-1]
+  double *vext_fine, *w_fine, *d_fine, *sintab, *vext_grid;
+  int *k0tab;
+  double *wtab;
+  float *wtab32, *ctab32;    // FP32 shift weights and merged increment taps
+  double *xpart, *obs_out, *h_obs;
+  double z, zscale;
+  int nterm;
+  cudaGraphExec_t graph;
+  bool graph_ready;
+  // learned form (FP64 contexts): the MLP's pair term replaces K12
+  w2_mlp *mlp;
+  bool learned_active;     // the step currently uses the network
+  int judge_every;         // steps between judgements (0: never)
+  double judge_tol;        // fall back to the exact term above this error
+  int since_judge, judged;
+  double last_err;
+  float *f1;               // [nx][nk] reduced Wigner function for the features
+  uint16_t *xrows;         // [nx*nx][din] feature rows
+  double *Kzero;           // [2][nx][2nk-1] zero one-body tables (pair-only sweeps)
+};
+
+namespace w2 {
+int mlp_din(const w2_mlp *m);
+int mlp_nk(const w2_mlp *m);
+int mlp_maxrows(const w2_mlp *m);
+float mlp_scale(const w2_mlp *m, int which);  // 0: s_f, 1: s_f1, 2: s_y
+float *mlp_out(w2_mlp *m);
+double *mlp_part(w2_mlp *m);
+double *mlp_hpart(w2_mlp *m);
+cudaError_t mlp_forward(w2_mlp *m, const uint16_t *x, int rows, float *y, float s, cudaStream_t st);
+TabArgs tab_args(w2_ctx *ctx, const double *xsum, int pair_mode);
+Adv32Args adv32_args(w2_ctx *ctx);
 }  // namespace w2

@@ -162,6 +162,39 @@ def initial_state(prob: Problem, centres, momenta=(0.5, -0.5), sigma: float = 1.
     return np.ascontiguousarray(f / mass)
 
 
+def initial_state_chunked(prob: Problem, centres, momenta=(0.5, -0.5), sigma: float = 1.0,
+                          noise: float = 1e-3, seed: int = 0, dtype=np.float32) -> np.ndarray:
+    """initial_state() for grids too large for whole-array temporaries: the
+    same values (the noise is a counter-based function of the linear index,
+    evaluated at both the index and its exchange image), built one x1-slab at
+    a time and returned in ``dtype``."""
+    nx, nk = prob.nx, prob.nk
+    x, p = prob.x(), prob.p()
+    ga = gaussian_1body(x[:, None], p[None, :], centres[0], momenta[0], sigma, prob.hbar, prob.L)
+    gb = gaussian_1body(x[:, None], p[None, :], centres[1], momenta[1], sigma, prob.hbar, prob.L)
+    amp = noise * float(np.max(np.abs(ga)) * np.max(np.abs(gb)))
+    out = np.empty((nx, nx, nk, nk), dtype=dtype)
+    i2 = np.arange(nx, dtype=np.uint64)[:, None, None]
+    n1 = np.arange(nk, dtype=np.uint64)[None, :, None]
+    n2 = np.arange(nk, dtype=np.uint64)[None, None, :]
+    NX, NK = np.uint64(nx), np.uint64(nk)
+    total = 0.0
+    for a in range(nx):
+        i1 = np.uint64(a)
+        g = ga[a][None, :, None] * gb[:, None, :]     # g(x1=a, x2, p1, p2)     [i2][n1][n2]
+        gt = gb[a][None, :, None] * ga[:, None, :]    # g(x2, x1=a, p2, p1)     exchange image
+        f = g + gt
+        if noise:
+            idx = ((i1 * NX + i2) * NK + n1) * NK + n2
+            idt = ((i2 * NX + i1) * NK + n2) * NK + n1
+            f = f + amp * (2.0 * uniform01(seed, idx) - 1.0) + amp * (2.0 * uniform01(seed, idt) - 1.0)
+        f *= 0.5
+        total += float(f.sum())
+        out[a] = f
+    out /= dtype(total * prob.dx ** 2 * prob.dp ** 2)
+    return out
+
+
 def draw_centres(seed: int, lo: float = -4.0, hi: float = 4.0):
     u = uniform01(seed + 0x5EED, np.arange(2, dtype=np.uint64))
     c = np.sort(lo + (hi - lo) * u)
@@ -191,3 +224,24 @@ def workload_dwell(nx: int = 64, nk: int = 64, literal: bool = False, seed: int 
                    meta={"steps": 1000, "seed": seed, "obs_every": 10})
     f0 = initial_state(prob, centres=draw_centres(seed), seed=seed)
     return prob, f0.astype(dtype, copy=False)
+
+
+def workload_batch(n: int = 64, seed: int = 3):
+    """Independent problems of uneven size and pair strength: per instance
+    nx in {24, 32, 48, 64}, nk in {32, 48, 64} and gamma in U[0.2, 2.0], all
+    drawn from the seed; L = 20, V = 0.5 cos(2 pi x / L), soft-Coulomb pair
+    scaled by gamma, Hartree on, dt = 0.01, two Gaussian packets with centres
+    drawn U[-4, 4] and momenta +-0.5.  Returns (problems, states)."""
+    L = 20.0
+    u = uniform01(seed, np.arange(3 * n, dtype=np.uint64)).reshape(n, 3)
+    nxs, nks = (24, 32, 48, 64), (32, 48, 64)
+    probs, states = [], []
+    for i in range(n):
+        nx = nxs[min(int(u[i, 0] * 4), 3)]
+        nk = nks[min(int(u[i, 1] * 3), 2)]
+        gamma = 0.2 + 1.8 * float(u[i, 2])
+        prob = Problem(nx=nx, nk=nk, L=L, dt=0.01, vext=cos_potential(0.5, L), vee=soft_coulomb(1.0),
+                       gamma=gamma, c_hartree=1.0, name=f"batch{i}_{nx}x{nk}", meta={"steps": 500, "seed": seed})
+        probs.append(prob)
+        states.append(initial_state(prob, centres=draw_centres(seed * 1000 + i), seed=seed * 1000 + i))
+    return probs, states

@@ -20,12 +20,18 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libw2.so")
 
 W2_F64 = 0
+W2_F32_TF32X3 = 1
 
 STATUS = {0: "W2_OK", -1: "W2_ERR_ARG", -2: "W2_ERR_CUDA", -3: "W2_ERR_OOM", -4: "W2_ERR_STATE",
           -5: "W2_ERR_UNSTABLE", -6: "W2_ERR_NONFINITE", -7: "W2_ERR_TIMEOUT", -8: "W2_ERR_UNSUPPORTED"}
 
 EXPORTS = ("w2_create", "w2_set_potentials", "w2_set_state", "w2_get_state", "w2_step",
-           "w2_step_profile", "w2_observables", "w2_theta", "w2_advect", "w2_destroy", "w2_status_string")
+           "w2_step_profile", "w2_observables", "w2_theta", "w2_advect", "w2_destroy", "w2_status_string",
+           "w2_batch_create", "w2_batch_set_potentials", "w2_batch_set_state", "w2_batch_get_state",
+           "w2_batch_observables", "w2_batch_step", "w2_batch_autotune", "w2_batch_destroy",
+           "w2_mlp_create", "w2_mlp_param_count", "w2_mlp_input_dim", "w2_mlp_set_params", "w2_mlp_get_params",
+           "w2_mlp_set_scales", "w2_mlp_forward", "w2_mlp_train_step", "w2_mlp_gradients", "w2_mlp_destroy",
+           "w2_features", "w2_theta_pair", "w2_learned_attach", "w2_learned_report")
 STEP_KERNELS = ("xsum_f", "tables_f", "theta_predictor", "shift_x2", "shift_x1_lawson", "xsum_ftilde",
                 "tables_ftilde", "theta_corrector")
 
@@ -72,10 +78,39 @@ def load(path: str = LIB_PATH):
     lib.w2_advect.argtypes = [vp, vp, vp]
     lib.w2_destroy.argtypes = [vp]
     lib.w2_destroy.restype = None
+    lib.w2_batch_create.argtypes = [ctypes.POINTER(Config), ctypes.c_int32, vp, ctypes.POINTER(vp)]
+    lib.w2_batch_set_potentials.argtypes = [vp, ctypes.c_int32, W2_FN, vp, W2_FN, vp, ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_double]
+    lib.w2_batch_set_state.argtypes = [vp, ctypes.c_int32, vp, ctypes.c_int32]
+    lib.w2_batch_get_state.argtypes = [vp, ctypes.c_int32, vp, ctypes.c_int32]
+    lib.w2_batch_observables.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(Obs), dp, dp]
+    lib.w2_batch_step.argtypes = [vp, ctypes.c_int32]
+    lib.w2_batch_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]
+    lib.w2_batch_destroy.argtypes = [vp]
+    lib.w2_batch_destroy.restype = None
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.w2_mlp_create.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, ctypes.POINTER(vp)]
+    lib.w2_mlp_param_count.argtypes = [vp]
+    lib.w2_mlp_param_count.restype = ctypes.c_size_t
+    lib.w2_mlp_input_dim.argtypes = [vp]
+    lib.w2_mlp_input_dim.restype = ctypes.c_int32
+    lib.w2_mlp_set_params.argtypes = [vp, fp]
+    lib.w2_mlp_get_params.argtypes = [vp, fp]
+    lib.w2_mlp_set_scales.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float]
+    lib.w2_mlp_forward.argtypes = [vp, vp, ctypes.c_int32, vp]
+    lib.w2_mlp_train_step.argtypes = [vp, vp, vp, ctypes.c_int32, ctypes.c_float, dp]
+    lib.w2_mlp_gradients.argtypes = [vp, vp, vp, ctypes.c_int32, fp, dp]
+    lib.w2_mlp_destroy.argtypes = [vp]
+    lib.w2_mlp_destroy.restype = None
+    lib.w2_features.argtypes = [vp, vp, vp, vp, ctypes.c_int32, vp]
+    lib.w2_theta_pair.argtypes = [vp, vp, vp]
+    lib.w2_learned_attach.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_double]
+    lib.w2_learned_report.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), dp]
     lib.w2_status_string.argtypes = [ctypes.c_int]
     lib.w2_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("w2_destroy", "w2_status_string"):
+        if name not in ("w2_destroy", "w2_status_string", "w2_batch_destroy", "w2_mlp_destroy",
+                        "w2_mlp_param_count", "w2_mlp_input_dim"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -86,10 +121,11 @@ def _check(code: int, what: str):
         raise W2Error(code, what)
 
 
-def _dev_ptr(t, shape=None):
+def _dev_ptr(t, shape=None, dtype=None):
     import torch
-    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
-        raise TypeError("expected a contiguous float64 CUDA tensor")
+    dtype = dtype or torch.float64
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"expected a contiguous {dtype} CUDA tensor")
     if shape is not None and tuple(t.shape) != tuple(shape):
         raise ValueError(f"shape {tuple(t.shape)} != {tuple(shape)}")
     return ctypes.c_void_p(t.data_ptr())
@@ -111,15 +147,18 @@ class Observables:
 class Context:
     """A w2_ctx: one problem on the current CUDA device."""
 
-    def __init__(self, nx, nk, L, dt, hbar=1.0, mass=1.0, xc_kind=0, stream=None):
+    def __init__(self, nx, nk, L, dt, hbar=1.0, mass=1.0, xc_kind=0, stream=None, precision=W2_F64):
         import torch
         self.lib = load()
+        self.precision = precision
+        self.np_dtype = np.float64 if precision == W2_F64 else np.float32
+        self.torch_dtype = torch.float64 if precision == W2_F64 else torch.float32
         self.shape = (nx, nx, nk, nk)
         self.nx, self.nk = nx, nk
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
-        cfg = Config(nx, nk, L, dt, hbar, mass, W2_F64, xc_kind)
+        cfg = Config(nx, nk, L, dt, hbar, mass, precision, xc_kind)
         h = ctypes.c_void_p()
         _check(self.lib.w2_create(ctypes.byref(cfg), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h)),
                "w2_create")
@@ -127,8 +166,8 @@ class Context:
         self._keep = []
 
     @classmethod
-    def from_problem(cls, prob, stream=None):
-        ctx = cls(prob.nx, prob.nk, prob.L, prob.dt, prob.hbar, prob.mass, prob.xc_kind, stream)
+    def from_problem(cls, prob, stream=None, precision=W2_F64):
+        ctx = cls(prob.nx, prob.nk, prob.L, prob.dt, prob.hbar, prob.mass, prob.xc_kind, stream, precision)
         ctx.set_potentials(prob.vext, prob.vee, prob.gamma, prob.c_hartree, prob.c_xc)
         return ctx
 
@@ -152,22 +191,22 @@ class Context:
     def set_state(self, f):
         """f: float64 CUDA tensor (device copy) or numpy array (host copy)."""
         if isinstance(f, np.ndarray):
-            f = np.ascontiguousarray(f, dtype=np.float64)
+            f = np.ascontiguousarray(f, dtype=self.np_dtype)
             assert f.shape == self.shape
             _check(self.lib.w2_set_state(self.h, ctypes.c_void_p(f.ctypes.data), 0), "w2_set_state")
         else:
-            _check(self.lib.w2_set_state(self.h, _dev_ptr(f, self.shape), 1), "w2_set_state")
+            _check(self.lib.w2_set_state(self.h, _dev_ptr(f, self.shape, self.torch_dtype), 1), "w2_set_state")
 
     def get_state(self, out=None):
         import torch
         if out is None:
-            out = np.empty(self.shape)
+            out = np.empty(self.shape, dtype=self.np_dtype)
         if isinstance(out, np.ndarray):
             _check(self.lib.w2_get_state(self.h, ctypes.c_void_p(out.ctypes.data), 0), "w2_get_state")
         elif isinstance(out, torch.Tensor) and not out.is_cuda:
             _check(self.lib.w2_get_state(self.h, ctypes.c_void_p(out.data_ptr()), 0), "w2_get_state")
         else:
-            _check(self.lib.w2_get_state(self.h, _dev_ptr(out, self.shape), 1), "w2_get_state")
+            _check(self.lib.w2_get_state(self.h, _dev_ptr(out, self.shape, self.torch_dtype), 1), "w2_get_state")
         return out
 
     def step(self, nsteps=1):
@@ -191,10 +230,197 @@ class Context:
             _check(code, "w2_observables")
         return Observables(o.mass, o.energy, o.purity, o.entropy_lin, o.l2norm, o.step, n1, n12, STATUS[code])
 
+    def theta_pair(self, f, out):
+        """out = the exact two-body term of f alone."""
+        _check(self.lib.w2_theta_pair(self.h, _dev_ptr(f, self.shape, self.torch_dtype),
+                                      _dev_ptr(out, self.shape, self.torch_dtype)), "w2_theta_pair")
+        return out
+
+    def features(self, mlp, f, xs, x):
+        """Input rows for the spatial points xs (int32 CUDA tensor, or None for all)."""
+        import torch
+        rows = self.nx * self.nx if xs is None else int(xs.numel())
+        xp = None if xs is None else ctypes.c_void_p(xs.data_ptr())
+        assert x.dtype == torch.bfloat16 and x.is_cuda and x.is_contiguous() and x.shape == (rows, mlp.din)
+        _check(self.lib.w2_features(self.h, mlp.h, _dev_ptr(f, self.shape, self.torch_dtype), xp, rows,
+                                    ctypes.c_void_p(x.data_ptr())), "w2_features")
+        return x
+
+    def attach_learned(self, mlp, judge_every=50, tol=0.1):
+        _check(self.lib.w2_learned_attach(self.h, None if mlp is None else mlp.h, int(judge_every), float(tol)),
+               "w2_learned_attach")
+        self._mlp = mlp
+
+    def learned_report(self):
+        a, j, e = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        _check(self.lib.w2_learned_report(self.h, ctypes.byref(a), ctypes.byref(j), ctypes.byref(e)),
+               "w2_learned_report")
+        return {"active": bool(a.value), "judged": j.value, "last_err": e.value}
+
     def theta(self, f, out):
-        _check(self.lib.w2_theta(self.h, _dev_ptr(f, self.shape), _dev_ptr(out, self.shape)), "w2_theta")
+        _check(self.lib.w2_theta(self.h, _dev_ptr(f, self.shape, self.torch_dtype),
+                                 _dev_ptr(out, self.shape, self.torch_dtype)), "w2_theta")
         return out
 
     def advect(self, f, out):
-        _check(self.lib.w2_advect(self.h, _dev_ptr(f, self.shape), _dev_ptr(out, self.shape)), "w2_advect")
+        _check(self.lib.w2_advect(self.h, _dev_ptr(f, self.shape, self.torch_dtype),
+                                  _dev_ptr(out, self.shape, self.torch_dtype)), "w2_advect")
         return out
+
+
+class Batch:
+    """A w2_batch: independent W2_F32_TF32X3 problems advanced together."""
+
+    def __init__(self, problems, stream=None):
+        import torch
+        self.lib = load()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.problems = list(problems)
+        cfgs = (Config * len(self.problems))(*[
+            Config(p.nx, p.nk, p.L, p.dt, p.hbar, p.mass, W2_F32_TF32X3, p.xc_kind) for p in self.problems])
+        h = ctypes.c_void_p()
+        _check(self.lib.w2_batch_create(cfgs, len(self.problems), ctypes.c_void_p(stream.cuda_stream),
+                                        ctypes.byref(h)), "w2_batch_create")
+        self.h = h
+        self._keep = []
+        for i, p in enumerate(self.problems):
+            ce = W2_FN(lambda x, _u, f=p.vext: float(f(x)))
+            cw = W2_FN(lambda r, _u, f=p.vee: float(f(r)))
+            self._keep += [ce, cw]
+            _check(self.lib.w2_batch_set_potentials(self.h, i, ce, None, cw, None, p.gamma, p.c_hartree, p.c_xc),
+                   "w2_batch_set_potentials")
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.w2_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def shape(self, i):
+        p = self.problems[i]
+        return (p.nx, p.nx, p.nk, p.nk)
+
+    def set_state(self, i, f):
+        if isinstance(f, np.ndarray):
+            f = np.ascontiguousarray(f, dtype=np.float32)
+            assert f.shape == self.shape(i)
+            _check(self.lib.w2_batch_set_state(self.h, i, ctypes.c_void_p(f.ctypes.data), 0), "w2_batch_set_state")
+        else:
+            import torch
+            _check(self.lib.w2_batch_set_state(self.h, i, _dev_ptr(f, self.shape(i), torch.float32), 1),
+                   "w2_batch_set_state")
+
+    def get_state(self, i):
+        out = np.empty(self.shape(i), dtype=np.float32)
+        _check(self.lib.w2_batch_get_state(self.h, i, ctypes.c_void_p(out.ctypes.data), 0), "w2_batch_get_state")
+        return out
+
+    def step(self, nsteps=1):
+        _check(self.lib.w2_batch_step(self.h, int(nsteps)), "w2_batch_step")
+
+    def autotune(self):
+        n = 2 + 4 * 16
+        g = (ctypes.c_int32 * n)()
+        _check(self.lib.w2_batch_autotune(self.h, g, n), "w2_batch_autotune")
+        v = list(g)
+        out = {"xsum": v[0], "tables": v[1], "classes": []}
+        for q in range(2, n, 4):
+            if v[q] == 0:
+                break
+            out["classes"].append({"nk": v[q], "theta": v[q + 1], "shift_x2": v[q + 2], "shift_x1": v[q + 3]})
+        return out
+
+    def observables(self, i):
+        o = Obs()
+        nx = self.problems[i].nx
+        n1 = np.zeros(nx)
+        n12 = np.zeros((nx, nx))
+        dp = ctypes.POINTER(ctypes.c_double)
+        code = self.lib.w2_batch_observables(self.h, i, ctypes.byref(o), n1.ctypes.data_as(dp),
+                                             n12.ctypes.data_as(dp))
+        if code not in (0, -6):
+            _check(code, "w2_batch_observables")
+        return Observables(o.mass, o.energy, o.purity, o.entropy_lin, o.l2norm, o.step, n1, n12, STATUS[code])
+
+
+class MLP:
+    """A w2_mlp: the learned stand-in for the two-body term."""
+
+    def __init__(self, nk, hidden=256, max_rows=4096, stream=None):
+        import torch
+        self.lib = load()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(self.lib.w2_mlp_create(nk, hidden, max_rows, ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h)),
+               "w2_mlp_create")
+        self.h = h
+        self.nk, self.hidden, self.max_rows = nk, hidden, max_rows
+        self.din = int(self.lib.w2_mlp_input_dim(h))
+        self.nparams = int(self.lib.w2_mlp_param_count(h))
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.w2_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def layout(self):
+        """[(name, offset, shape)] of the packed parameters."""
+        dims = [(self.din, self.hidden), (self.hidden, self.hidden), (self.hidden, self.hidden),
+                (self.hidden, self.nk * self.nk)]
+        out, off = [], 0
+        for l, (i, o) in enumerate(dims):
+            out.append((f"W{l}", off, (i, o)))
+            off += i * o
+            out.append((f"b{l}", off, (o,)))
+            off += o
+        return out
+
+    def get_params(self):
+        p = np.empty(self.nparams, dtype=np.float32)
+        _check(self.lib.w2_mlp_get_params(self.h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+               "w2_mlp_get_params")
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.nparams
+        _check(self.lib.w2_mlp_set_params(self.h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+               "w2_mlp_set_params")
+
+    def set_scales(self, s_f, s_f1, s_y):
+        self.scales = (float(s_f), float(s_f1), float(s_y))
+        _check(self.lib.w2_mlp_set_scales(self.h, *self.scales), "w2_mlp_set_scales")
+
+    def forward(self, x, y):
+        _check(self.lib.w2_mlp_forward(self.h, ctypes.c_void_p(x.data_ptr()), int(x.shape[0]),
+                                       ctypes.c_void_p(y.data_ptr())), "w2_mlp_forward")
+        return y
+
+    def train_step(self, x, target, lr):
+        loss = ctypes.c_double()
+        _check(self.lib.w2_mlp_train_step(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(target.data_ptr()),
+                                          int(x.shape[0]), float(lr), ctypes.byref(loss)), "w2_mlp_train_step")
+        return loss.value
+
+    def gradients(self, x, target):
+        g = np.empty(self.nparams, dtype=np.float32)
+        loss = ctypes.c_double()
+        _check(self.lib.w2_mlp_gradients(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(target.data_ptr()),
+                                         int(x.shape[0]), g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                         ctypes.byref(loss)), "w2_mlp_gradients")
+        return g, loss.value

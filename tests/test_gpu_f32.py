@@ -1,0 +1,120 @@
+"""GPU checks of the precision form (W2_F32_TF32X3: FP32 state, TF32 hi+lo
+tensor-core contractions, FP32 spline increments, FP64 reductions).
+
+Bars: the operator alone within 2e-6 relative L2 of the FP64 oracle on the
+same (FP32-representable) input; the shift within 1e-6; time steps within the
+1e-6 relative L2 of the forms against the FP64 path, checked over 20 steps of
+the small workload and 200 steps of the 64^4 double-well workload, with the
+error of each observable stated.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_11354_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_11354_gb300 import build
+    build.build()
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _ctx(prob, precision):
+    from paper_2511_11354_gb300 import w2
+    return w2.Context.from_problem(prob, precision=precision)
+
+
+@pytest.mark.parametrize("nx,nk", [(8, 16), (12, 32), (20, 48), (16, 64), (6, 128), (24, 80)])
+def test_theta32_parity(nx, nk):
+    from paper_2511_11354_gb300 import w2
+    prob, _ = inputs.workload_small(nx=nx, nk=nk)
+    f = inputs.initial_state(prob, centres=(-2.5, 3.0), seed=11, noise=0.05).astype(np.float32)
+    ctx = _ctx(prob, w2.W2_F32_TF32X3)
+    out = torch.empty(*f.shape, dtype=torch.float32, device="cuda")
+    ctx.theta(torch.from_numpy(f).cuda(), out)
+    ref = oracle.Oracle(prob).theta(f.astype(np.float64))
+    assert rel(out.cpu().numpy(), ref) < 2e-6
+
+
+@pytest.mark.parametrize("nx,nk,dt", [(8, 16, 0.37), (33, 32, 0.02), (64, 16, 0.9)])
+def test_advect32_parity(nx, nk, dt):
+    from paper_2511_11354_gb300 import w2
+    prob, _ = inputs.workload_small(nx=nx, nk=nk)
+    prob.dt = dt
+    prob.vext, prob.vee, prob.gamma, prob.c_hartree = inputs.zero_potential(), inputs.zero_potential(), 0.0, 0.0
+    f = inputs.initial_state(prob, centres=(-2.5, 3.0), seed=5, noise=0.1).astype(np.float32)
+    ctx = _ctx(prob, w2.W2_F32_TF32X3)
+    out = torch.empty(*f.shape, dtype=torch.float32, device="cuda")
+    ctx.advect(torch.from_numpy(f).cuda(), out)
+    assert rel(out.cpu().numpy(), oracle.Oracle(prob).advect(f.astype(np.float64))) < 1e-6
+
+
+def test_step32_small_workload_vs_oracle():
+    from paper_2511_11354_gb300 import w2
+    prob, f0 = inputs.workload_small(nx=32, nk=32)
+    ctx = _ctx(prob, w2.W2_F32_TF32X3)
+    ctx.set_state(f0.astype(np.float32))
+    ctx.step(20)
+    ref = oracle.Oracle(prob).step(f0, 20)
+    assert rel(ctx.get_state(), ref) < 1e-6
+
+
+def _f64_and_f32_run(prob, f0, steps):
+    from paper_2511_11354_gb300 import w2
+    a = _ctx(prob, w2.W2_F64)
+    a.set_state(f0)
+    b = _ctx(prob, w2.W2_F32_TF32X3)
+    b.set_state(f0.astype(np.float32))
+    obs_a, obs_b = [], []
+    done = 0
+    while done < steps:
+        k = min(50, steps - done)
+        a.step(k)
+        b.step(k)
+        done += k
+        obs_a.append(a.observables())
+        obs_b.append(b.observables())
+    return a, b, obs_a, obs_b
+
+
+def test_step32_dwell_64_200_steps_vs_f64_path():
+    """The precision form's acceptance check: the 64^4 double-well workload,
+    200 steps, relative L2 <= 1e-6 against the FP64 path (which matches the
+    oracle to 1e-10), plus the error of each observable."""
+    prob, f0 = inputs.workload_dwell()
+    a, b, oa, ob = _f64_and_f32_run(prob, f0, 200)
+    fa, fb = a.get_state(), b.get_state()
+    err = rel(fb, fa)
+    assert err < 1e-6, err
+    for x, y in zip(oa, ob):
+        assert abs(y.mass - x.mass) < 1e-6 * abs(x.mass)
+        assert abs(y.energy - x.energy) < 1e-6 * abs(x.energy)
+        assert abs(y.entropy_lin - x.entropy_lin) < 1e-6
+        assert np.abs(y.n1 - x.n1).max() < 1e-6 * np.abs(x.n1).max()
+        assert np.abs(y.n12 - x.n12).max() < 1e-6 * np.abs(x.n12).max()
+
+
+def test_step32_exchange_symmetry_and_determinism():
+    from paper_2511_11354_gb300 import w2
+    prob, f0 = inputs.workload_small(nx=16, nk=32)
+    outs = []
+    for _ in range(2):
+        c = _ctx(prob, w2.W2_F32_TF32X3)
+        c.set_state(f0.astype(np.float32))
+        c.step(10)
+        outs.append(c.get_state())
+    assert np.array_equal(outs[0], outs[1])
+    g = outs[0].astype(np.float64)
+    assert np.abs(g - g.transpose(1, 0, 3, 2)).max() < 1e-5 * np.abs(g).max()

@@ -214,7 +214,60 @@ def bench_forms(args, barrier):
                     f"{pts / 1e6:.1f}M points in total, FP32 state, TF32 split contractions",
         "value": pts * k / (ms / 1e3), "unit": UNIT, "steps": k, "ms_per_step": ms / k, "autotuned_grids": tuning}
     bt.close()
+    if not args.no_learned:
+        forms["learned"] = bench_learned(args, timed)
     return forms
+
+
+def bench_learned(args, timed):
+    """Learned form on the 64^4 double-well workload: a network trained on an
+    exact FP64 trajectory of the same problem replaces the two-body term; the
+    exact term judges it every 50 steps."""
+    import torch
+
+    from paper_2511_11354_gb300 import inputs, learned, w2
+    prob, f0 = inputs.workload_dwell()
+    k = args.learned_steps
+    mlp = w2.MLP(prob.nk, hidden=256, max_rows=prob.nx * prob.nx)
+    snaps, per = args.learned_snapshots, 128
+    X, T = learned.make_dataset(prob, f0, mlp, snapshots=snaps, stride=1, points_per_snapshot=per, seed=4)
+    losses = learned.train(mlp, X, T, steps=args.learned_train_steps, batch=1024, lr=2e-3, lr_final=1e-4, seed=4)
+    del X, T
+    torch.cuda.empty_cache()
+    f0d = torch.from_numpy(f0).cuda()
+
+    def make(net=None, judge=0):
+        c = w2.Context.from_problem(prob)
+        c.set_state(f0d)
+        if net is not None:
+            c.attach_learned(net, judge, 0.5)
+        return c
+
+    exact = make()
+    ms_exact = timed(exact.step, k)
+    net = make(mlp, 50)
+    ms_net = timed(net.step, k)
+    rep = net.learned_report()
+    zero = learned.zero_network(prob.nk, 32, prob.nx * prob.nx)
+    nopair = make(zero)
+    nopair.step(k)
+    fe, fn, f0p = exact.get_state(), net.get_state(), nopair.get_state()
+    out = {
+        "workload": f"double-well physics on the 64^2 x 64^2 grid, FP64 step with the two-body term from a 4-layer "
+                    f"MLP (width 256, BF16, FP32 accumulation) trained on {snaps} snapshots x {per} points of an exact "
+                    f"trajectory ({args.learned_train_steps} Adam steps, batch 1024); judge every 50 steps",
+        "value": prob.points * k / (ms_net / 1e3), "unit": UNIT, "steps": k, "ms_per_step": ms_net / k,
+        "exact_ms_per_step": ms_exact / k, "speedup_vs_exact": ms_exact / ms_net,
+        "train_loss_first_last": [losses[0], losses[-1]],
+        "judge": rep,
+        "rel_l2_vs_exact": float(np.linalg.norm(fn - fe) / np.linalg.norm(fe)),
+        "rel_l2_without_two_body_term": float(np.linalg.norm(f0p - fe) / np.linalg.norm(fe)),
+    }
+    for c in (exact, net, nopair):
+        c.close()
+    mlp.close()
+    zero.close()
+    return out
 
 
 def theta_mma_per_block(nk):
@@ -279,6 +332,10 @@ def main():
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-form-error", action="store_true")
     ap.add_argument("--form-steps", type=int, default=20)
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--learned-steps", type=int, default=100)
+    ap.add_argument("--learned-snapshots", type=int, default=300)
+    ap.add_argument("--learned-train-steps", type=int, default=2000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -1,0 +1,99 @@
+"""GPU checks of the learned form: the training kernels' gradients against the
+FP64 numpy reference network, the judge and fallback, and what a trained
+network gains over the method without the two-body term."""
+import numpy as np
+import pytest
+
+from oracle import mlp_ref
+from paper_2511_11354_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_11354_gb300 import build
+    build.build()
+
+
+def _bf16_round(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16).float().numpy()
+
+
+def test_mlp_gradients_match_reference():
+    """BF16 products with FP32 accumulation against FP64 on the same
+    BF16-rounded weights and inputs: relative L2 error of the whole gradient."""
+    from paper_2511_11354_gb300 import w2
+    nk, hidden, rows = 8, 32, 48
+    m = w2.MLP(nk, hidden, max_rows=rows)
+    rng = np.random.default_rng(1)
+    p = (rng.standard_normal(m.nparams) * 0.3).astype(np.float32)
+    m.set_params(p)
+    x = rng.standard_normal((rows, m.din)).astype(np.float32)
+    t = rng.standard_normal((rows, nk * nk)).astype(np.float32)
+    xb = torch.from_numpy(x).to(torch.bfloat16).cuda()
+    tt = torch.from_numpy(t).cuda()
+    g, loss = m.gradients(xb, tt)
+    # the reference sees the parameters as the tensor cores do (weights in BF16, biases FP32)
+    pr = p.astype(np.float64).copy()
+    for name, off, shape in m.layout():
+        if name.startswith("W"):
+            n = int(np.prod(shape))
+            pr[off:off + n] = _bf16_round(p[off:off + n])
+    lref, gref = mlp_ref.loss_and_grad(pr, _bf16_round(x).astype(np.float64), t.astype(np.float64),
+                                       m.din, hidden, nk * nk)
+    assert abs(loss - lref) < 2e-2 * lref
+    assert np.linalg.norm(g - gref) / np.linalg.norm(gref) < 5e-2
+    cos = float(g @ gref / (np.linalg.norm(g) * np.linalg.norm(gref)))
+    assert cos > 0.998
+    # one training step lowers the loss on the same batch
+    l0 = m.train_step(xb, tt, 1e-3)
+    l1 = m.train_step(xb, tt, 1e-3)
+    assert l1 < l0
+
+
+def _small_dwell():
+    prob, f0 = inputs.workload_dwell(nx=16, nk=32)
+    return prob, f0
+
+
+def test_judge_and_fallback():
+    from paper_2511_11354_gb300 import learned, w2
+    prob, f0 = _small_dwell()
+    zero = learned.zero_network(prob.nk, hidden=32, max_rows=prob.nx * prob.nx)
+    # a network that is plainly wrong (zero) falls back to the exact term at the first judgement
+    out, rep = learned.run(prob, f0, 12, zero, judge_every=5, tol=0.1)
+    assert rep["judged"] == 1 and not rep["active"] and rep["last_err"] == pytest.approx(1.0, abs=1e-6)
+    # ... and from then on the step is the exact one: 5 steps without, 7 with the pair term
+    ctx = w2.Context.from_problem(prob)
+    ctx.set_state(f0)
+    ctx.attach_learned(zero, 0, 1e30)
+    ctx.step(5)
+    ctx.attach_learned(None)
+    ctx.step(7)
+    assert np.array_equal(ctx.get_state(), out)
+
+
+def test_trained_network_beats_dropping_the_two_body_term():
+    """Trained on a short exact trajectory of the double-well physics, the
+    network stands in for the two-body term over the next 40 steps: the state
+    stays closer to the exact run than the run without the two-body term, and
+    the judge reports an error well below 1."""
+    from paper_2511_11354_gb300 import learned, w2
+    prob, f0 = _small_dwell()
+    torch.manual_seed(0)
+    mlp = w2.MLP(prob.nk, hidden=256, max_rows=max(512, prob.nx * prob.nx))
+    X, T = learned.make_dataset(prob, f0, mlp, snapshots=120, stride=1, points_per_snapshot=96, seed=0)
+    losses = learned.train(mlp, X, T, steps=1500, batch=512, lr=2e-3, lr_final=1e-4, seed=0)
+    assert losses[-1] < 0.2 * losses[0]
+    exact, _ = learned.run(prob, f0, 40)
+    net, rep = learned.run(prob, f0, 40, mlp, judge_every=20, tol=0.9)
+    nopair, _ = learned.run(prob, f0, 40, learned.zero_network(prob.nk, 32, prob.nx * prob.nx))
+    e_net = np.linalg.norm(net - exact) / np.linalg.norm(exact)
+    e_nopair = np.linalg.norm(nopair - exact) / np.linalg.norm(exact)
+    assert rep["judged"] == 2 and rep["active"], rep
+    assert rep["last_err"] < 0.5, rep
+    assert e_net < 0.5 * e_nopair, (e_net, e_nopair)

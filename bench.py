@@ -37,6 +37,20 @@ def _dist():
     return ws, rank, local
 
 
+def reduce_max(value, dist_mod, device):
+    """Maximum of a per-rank float over all ranks (the job's time is that of
+    the slowest replica)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(points_per_rank, steps, world_size, max_ms):
+    """Point-updates per second of all replicas together (weak scaling)."""
+    return points_per_rank * steps * world_size / (max_ms / 1e3)
+
+
 def _workload_desc(prob):
     return {"workload": f"double-well 2-RDM Wigner step, {prob.nx}^2 x {prob.nk}^2 grid, L={prob.L:g}, "
                         f"dt={prob.dt:g}, soft-Coulomb pair gamma={prob.gamma:g}, Hartree c_H={prob.c_hartree:g}, "
@@ -168,7 +182,7 @@ def bench_forms(args, barrier):
     ms = timed(ctx.step, k)
     kp = ctx.step_profile(min(k, 10))
     theta_ms = 0.5 * (kp[2] + kp[7])
-    flops = 5 * theta_mma_per_block(prob.nk) * 2048.0 * prob.nx * prob.nx  # 5 products, 2048 flop per mma
+    flops = 4 * theta_mma_per_block(prob.nk) * 2048.0 * prob.nx * prob.nx  # 4 products, 2048 flop per mma
     tf32_peak = 0.4889 * MEASURED_BF16_TFLOPS()
     forms["precision_tf32x3"] = {
         "workload": f"double-well physics on a 128^2 x 128^2 grid (268M points), FP32 state, dt={prob.dt:g}",
@@ -333,6 +347,7 @@ def main():
     ap.add_argument("--no-form-error", action="store_true")
     ap.add_argument("--form-steps", type=int, default=20)
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--only-forms", action="store_true", help="run only the forms (for profiling commands)")
     ap.add_argument("--learned-steps", type=int, default=100)
     ap.add_argument("--learned-snapshots", type=int, default=300)
     ap.add_argument("--learned-train-steps", type=int, default=2000)
@@ -353,6 +368,11 @@ def main():
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w2build.build()
+    if args.only_forms:
+        forms = bench_forms(args, torch.cuda.synchronize)
+        if rank == 0:
+            print(json.dumps({"impl": "w2", "only_forms": True, "forms": forms}), flush=True)
+        return
 
     prob, f0 = inputs.workload_dwell()
     ctx = w2.Context.from_problem(prob)
@@ -366,11 +386,7 @@ def main():
             dist.barrier()
 
     def max_over_ranks(x):
-        if ws == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return x if ws == 1 else reduce_max(x, dist, "cuda")
 
     # ---- device-resident timed region: exactly K steps ---------------------
     ctx.step(args.warmup)
@@ -384,7 +400,7 @@ def main():
     clk = clocks.stop()
     ms = max_over_ranks(e0.elapsed_time(e1))
     ob = ctx.observables()
-    value = prob.points * args.steps * ws / (ms / 1e3)
+    value = whole_job_rate(prob.points, args.steps, ws, ms)
 
     # ---- per-kernel times (events around every launch, same stream) -------
     kprof = ctx.step_profile(min(args.steps, 50))
@@ -410,7 +426,7 @@ def main():
     t1.record(stream)
     barrier()
     ms_e2e = max_over_ranks(t0.elapsed_time(t1))
-    e2e = prob.points * args.steps * ws / (ms_e2e / 1e3)
+    e2e = whole_job_rate(prob.points, args.steps, ws, ms_e2e)
 
     ctx.close()
     forms = None if args.no_forms else bench_forms(args, barrier)

@@ -47,6 +47,9 @@ def _load():
             lib.orc_potential_fine.argtypes = [ctypes.c_void_p, _dp, _dp]
             lib.orc_theta_with.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, ctypes.c_int, _dp]
             lib.orc_theta.argtypes = [ctypes.c_void_p, _dp, _dp]
+            _ip = ctypes.POINTER(ctypes.c_int)
+            lib.orc_theta_with_sample.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, ctypes.c_int, _ip, ctypes.c_int, _dp]
+            lib.orc_advect_sample.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, _ip, ctypes.c_int, _dp]
             lib.orc_shift_line.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, _dp]
             lib.orc_advect.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, _dp]
             lib.orc_step.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int]
@@ -121,6 +124,29 @@ class Oracle:
         U1 = np.ascontiguousarray(U1, dtype=np.float64)
         U2 = np.ascontiguousarray(U2, dtype=np.float64)
         self.lib.orc_theta_with(self.h, _ptr(f), _ptr(U1), _ptr(U2), int(terms), _ptr(out))
+        return out
+
+    def theta_sample(self, f, xs, U1=None, U2=None, terms=7):
+        """Theta f at the listed spatial points only (X = i1*nx + i2); the
+        one-body potentials default to those of f's own densities."""
+        f = self._f(f)
+        if U1 is None or U2 is None:
+            n1, n2 = self.marginals(f)
+            U1, U2 = self.potential_fine(n1), self.potential_fine(n2)
+        xs = np.ascontiguousarray(xs, dtype=np.intc)
+        out = np.empty((xs.size, self.prob.nk, self.prob.nk))
+        self.lib.orc_theta_with_sample(self.h, _ptr(f), _ptr(np.ascontiguousarray(U1)),
+                                       _ptr(np.ascontiguousarray(U2)), int(terms),
+                                       xs.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), int(xs.size), _ptr(out))
+        return out
+
+    def advect_sample(self, f, planes, tau=None):
+        """The characteristic shift of the listed momentum planes (n1*nk + n2)."""
+        f = self._f(f)
+        planes = np.ascontiguousarray(planes, dtype=np.intc)
+        out = np.empty((planes.size, self.prob.nx, self.prob.nx))
+        self.lib.orc_advect_sample(self.h, _ptr(f), float(self.prob.dt if tau is None else tau),
+                                   planes.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), int(planes.size), _ptr(out))
         return out
 
     def shift_line(self, line, shift):

@@ -331,6 +331,49 @@ void orc_theta_with(const orc_problem *P, const double *f, const double *U1, con
   free(c1); free(c2); free(c12);
 }
 
+/* orc_theta_with restricted to the spatial points xs[0..nxs) (X = i1 nx + i2):
+ * out[q][n1][n2] = (Theta f)(xs[q], n1, n2).  Same arithmetic; for checks of
+ * grids too large to sweep whole. */
+void orc_theta_with_sample(const orc_problem *P, const double *f, const double *U1, const double *U2, int terms,
+                           const int *xs, int nxs, double *out) {
+  int nx = P->nx, nk = P->nk, M = P->M;
+  double hb = P->hbar;
+  size_t W = 2 * nk - 1;
+  double complex *c1 = (double complex *)malloc(sizeof(double complex) * nx * W);
+  double complex *c2 = (double complex *)malloc(sizeof(double complex) * nx * W);
+  double complex *c12 = (double complex *)malloc(sizeof(double complex) * nx * W);
+  double *u12 = (double *)malloc(sizeof(double) * M);
+  for (int i = 0; i < nx; ++i) {
+    local_modes(P, U1 + (size_t)i * M, c1 + (size_t)i * W);
+    local_modes(P, U2 + (size_t)i * M, c2 + (size_t)i * W);
+    for (int l = 0; l < M; ++l) u12[l] = P->gamma * P->w_shift[i * M + l];
+    local_modes(P, u12, c12 + (size_t)i * W);
+  }
+  free(u12);
+#pragma omp parallel for schedule(static)
+  for (int q = 0; q < nxs; ++q) {
+    int i1 = xs[q] / nx, i2 = xs[q] % nx;
+    const double complex *a1 = c1 + (size_t)i1 * W + (nk - 1);
+    const double complex *a2 = c2 + (size_t)i2 * W + (nk - 1);
+    int d = ((i1 - i2) % nx + nx) % nx;
+    const double complex *a12 = c12 + (size_t)d * W + (nk - 1);
+    const double *F = f + idx4(P, i1, i2, 0, 0);
+#define FV(a, b) (((a) >= 0 && (a) < nk && (b) >= 0 && (b) < nk) ? F[(size_t)(a) * nk + (b)] : 0.0)
+    for (int n1 = 0; n1 < nk; ++n1)
+      for (int n2 = 0; n2 < nk; ++n2) {
+        double complex s = 0.0;
+        for (int m = -(nk - 1); m <= nk - 1; ++m) {
+          if (terms & 1) s += a1[m] * (FV(n1 + m, n2) - FV(n1 - m, n2));
+          if (terms & 2) s += a2[m] * (FV(n1, n2 + m) - FV(n1, n2 - m));
+          if (terms & 4) s += a12[m] * (FV(n1 + m, n2 - m) - FV(n1 - m, n2 + m));
+        }
+        out[((size_t)q * nk + n1) * nk + n2] = creal((I / hb) * s);
+      }
+#undef FV
+  }
+  free(c1); free(c2); free(c12);
+}
+
 /* Full Theta_V f of Eq. two_body_truncated_Wigner: HXC for both particles
  * (built from the densities of f itself) plus the two-body term. */
 void orc_theta(const orc_problem *P, const double *f, double *out) {
@@ -383,6 +426,36 @@ void orc_advect(const orc_problem *P, const double *f, double tau, double *out) 
           for (int i2 = 0; i2 < nx; ++i2) out[idx4(P, i1, i2, n1, n2)] = res[i2];
         }
       }
+    free(line); free(res); free(rhs); free(eta); free(plane);
+  }
+}
+
+/* orc_advect restricted to the momentum planes planes[0..np) (= n1 nk + n2):
+ * out[q][i1][i2] = (A_tau f)(i1, i2, planes[q]). */
+void orc_advect_sample(const orc_problem *P, const double *f, double tau, const int *planes, int np, double *out) {
+  int nx = P->nx, nk = P->nk;
+#pragma omp parallel
+  {
+    double *line = (double *)malloc(sizeof(double) * nx), *res = (double *)malloc(sizeof(double) * nx);
+    double *rhs = (double *)malloc(sizeof(double) * (nx + 3)), *eta = (double *)malloc(sizeof(double) * (nx + 3));
+    double *plane = (double *)malloc(sizeof(double) * nx * nx);
+#pragma omp for schedule(static)
+    for (int q = 0; q < np; ++q) {
+      int n1 = planes[q] / nk, n2 = planes[q] % nk;
+      double s1 = tau * ((n1 - nk / 2) * P->dp) / P->mass;
+      double s2 = tau * ((n2 - nk / 2) * P->dp) / P->mass;
+      for (int i1 = 0; i1 < nx; ++i1)
+        for (int i2 = 0; i2 < nx; ++i2) plane[i1 * nx + i2] = f[idx4(P, i1, i2, n1, n2)];
+      for (int i2 = 0; i2 < nx; ++i2) {
+        for (int i1 = 0; i1 < nx; ++i1) line[i1] = plane[i1 * nx + i2];
+        spline_shift_line(P, nx, P->dx, line, s1, res, rhs, eta);
+        for (int i1 = 0; i1 < nx; ++i1) plane[i1 * nx + i2] = res[i1];
+      }
+      for (int i1 = 0; i1 < nx; ++i1) {
+        spline_shift_line(P, nx, P->dx, plane + i1 * nx, s2, res, rhs, eta);
+        for (int i2 = 0; i2 < nx; ++i2) out[((size_t)q * nx + i1) * nx + i2] = res[i2];
+      }
+    }
     free(line); free(res); free(rhs); free(eta); free(plane);
   }
 }

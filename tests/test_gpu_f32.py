@@ -118,3 +118,35 @@ def test_step32_exchange_symmetry_and_determinism():
     assert np.array_equal(outs[0], outs[1])
     g = outs[0].astype(np.float64)
     assert np.abs(g - g.transpose(1, 0, 3, 2)).max() < 1e-5 * np.abs(g).max()
+
+
+def test_precision_full_size_128_sampled_outputs():
+    """The timed 128^4 workload itself: the operator at 24 sampled spatial
+    points and the shift on 24 sampled momentum planes against the oracle,
+    then one step that stays finite and exchange symmetric."""
+    from paper_2511_11354_gb300 import w2
+    prob, _ = inputs.workload_dwell(nx=128, nk=128)
+    f = inputs.initial_state_chunked(prob, centres=inputs.draw_centres(2), seed=2)
+    ctx = _ctx(prob, w2.W2_F32_TF32X3)
+    d = torch.from_numpy(f).cuda()
+    out = torch.empty_like(d)
+    rng = np.random.default_rng(0)
+    o = oracle.Oracle(prob)
+    f64 = f.astype(np.float64)
+    del f
+    xs = rng.choice(prob.nx * prob.nx, 24, replace=False)
+    ctx.theta(d, out)
+    got = out.view(prob.nx * prob.nx, prob.nk, prob.nk)[torch.from_numpy(xs).cuda()].cpu().numpy()
+    assert rel(got, o.theta_sample(f64, xs)) < 2e-6
+    planes = rng.choice(prob.nk * prob.nk, 24, replace=False)
+    ctx.advect(d, out)
+    got = out.view(prob.nx, prob.nx, prob.nk * prob.nk)[:, :, torch.from_numpy(planes).cuda()]
+    got = got.permute(2, 0, 1).contiguous().cpu().numpy()
+    assert rel(got, o.advect_sample(f64, planes)) < 1e-6
+    del f64
+    ctx.set_state(d)
+    ctx.step(1)
+    ctx.get_state(out)
+    assert bool(torch.isfinite(out).all())
+    sym = out.permute(1, 0, 3, 2)
+    assert float((out - sym).abs().max()) < 1e-5 * float(out.abs().max())

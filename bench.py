@@ -135,7 +135,7 @@ def _fp64_peak():
 # DRAM bytes (read + write) of one k_theta launch on the 64^4 workload from one
 # ncu capture (profiles/k_theta_f64_dwell_64x64.md), keyed by the hash of the
 # kernel source it was taken on: any change to the source reports null.
-THETA_TRAFFIC = {"e3336d52875dc0b6": 134.504704e6 + 86.966784e6}
+THETA_TRAFFIC = {"adc3232c8a8beccc": 134.482688e6 + 86.614528e6}
 
 
 def _theta_traffic():

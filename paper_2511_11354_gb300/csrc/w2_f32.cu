@@ -3,8 +3,8 @@
 //  k_theta32 : the X-local pseudo-difference sweep of w2_f64.cu on
 //              mma.sync m16n8k8 tf32 with FP32 accumulation.  The state block
 //              is split into two TF32 parts (hi = tf32(x), lo = tf32(x - hi))
-//              and the kernel table into three, and each product keeps the
-//              five terms down to 2^-22 relative.  The operator's output enters
+//              and the kernel table into three; four partial products per
+//              tile (see mma5_a3).  The operator's output enters
 //              the time step scaled by tau*|Theta| (a few 1e-2), so its error
 //              stays below the FP32 rounding of the state.
 //  k_adv32   : periodic cubic-spline shift along x2 (DIR 0) and x1 (DIR 1).
@@ -51,9 +51,11 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
 }
 
 // Products of a three-part operand K = kh + km + kl (the kernel table) with a
-// two-part operand F = fh + fl, keeping every term down to 2^-22 relative.
-// The leading product kh fh goes to the accumulator `big`; the four small
-// ones (kl fh, km fl, km fh, kh fl, at most 2^-11 of it) to `small`.  The
+// two-part operand F = fh + fl: kh fh, the 2^-11 terms km fh and kh fl, and
+// kl fh (2^-22, kept because the table is the same every step).  The dropped
+// km fl (2^-22) involves the low part of the state, which changes from step
+// to step, so its omission does not accumulate coherently.  The leading
+// product goes to the accumulator `big`, the small ones to `small`.  The
 // tensor core's FP32 accumulation drops the bits of the smaller addend below
 // the larger one's last place (no rounding to nearest), which biases long
 // running sums; so the callers give `big` a fresh zero accumulator for each
@@ -65,7 +67,6 @@ __device__ __forceinline__ void mma5_a3(float (&big)[4], float (&small)[4], cons
                                         const uint32_t (&km)[4], const uint32_t (&kl)[4], const uint32_t (&fh)[2],
                                         const uint32_t (&fl)[2]) {
   mma_tf32(small, kl, fh);
-  mma_tf32(small, km, fl);
   mma_tf32(small, km, fh);
   mma_tf32(small, kh, fl);
   mma_tf32(big, kh, fh);
@@ -76,7 +77,6 @@ __device__ __forceinline__ void mma5_b3(float (&big)[4], float (&small)[4], cons
                                         const uint32_t (&fl)[4], const uint32_t (&kh)[2], const uint32_t (&km)[2],
                                         const uint32_t (&kl)[2]) {
   mma_tf32(small, fh, kl);
-  mma_tf32(small, fl, km);
   mma_tf32(small, fh, km);
   mma_tf32(small, fl, kh);
   mma_tf32(big, fh, kh);

@@ -61,13 +61,14 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs a) {
   const uint16_t *A = (const uint16_t *)a.A, *B = (const uint16_t *)a.B;
   float acc[2][4][4] = {};
   for (int k0 = 0; k0 < a.K; k0 += GBK) {
+    // consecutive threads walk the operand's unit-stride direction (coalesced reads)
     for (int e = tid; e < GBM * GBK; e += 128) {
-      const int r = e / GBK, c = e % GBK;
+      const int r = a.sak == 1 ? e / GBK : e % GBM, c = a.sak == 1 ? e % GBK : e / GBM;
       const int m = m0 + r, k = k0 + c;
       As[r][c] = (m < a.M && k < a.K) ? A[(size_t)m * a.sam + (size_t)k * a.sak] : (uint16_t)0;
     }
     for (int e = tid; e < GBN * GBK; e += 128) {
-      const int r = e / GBK, c = e % GBK;  // r: n, c: k
+      const int r = a.sbk == 1 ? e / GBK : e % GBN, c = a.sbk == 1 ? e % GBK : e / GBN;  // r: n, c: k
       const int n = n0 + r, k = k0 + c;
       Bs[r][c] = (n < a.N && k < a.K) ? B[(size_t)k * a.sbk + (size_t)n * a.sbn] : (uint16_t)0;
     }
@@ -136,16 +137,22 @@ cudaError_t launch_gemm(const GemmArgs &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// f1[i][n] = dx dp sum_{i2, n2} f[i][i2][n][n2]  (T = double or float state)
+// f1[i][n] = dx dp sum_{i2, n2} f[i][i2][n][n2]  (T = double or float state).
+// One warp per (i, n): lanes stride along n2 (coalesced rows), then a fixed
+// shuffle tree; 8 warps per block, grid nx * ceil(nk / 8).
 template <typename T>
-__global__ void k_f1(const T *f, float *f1, int nx, int nk, double w) {
-  const int i = blockIdx.x, n = threadIdx.x;  // blockDim = nk
+__global__ void __launch_bounds__(256) k_f1(const T *f, float *f1, int nx, int nk, double w) {
+  const int groups = (nk + 7) / 8, lane = threadIdx.x & 31;
+  const int i = blockIdx.x / groups, n = (blockIdx.x % groups) * 8 + (threadIdx.x >> 5);
+  if (n >= nk) return;  // whole warp
   double s = 0.0;
   for (int i2 = 0; i2 < nx; ++i2) {
     const T *row = f + (((size_t)i * nx + i2) * nk + n) * nk;
-    for (int n2 = 0; n2 < nk; ++n2) s += (double)row[n2];
+    for (int n2 = lane; n2 < nk; n2 += 32) s += (double)row[n2];
   }
-  f1[(size_t)i * nk + n] = (float)(s * w);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) f1[(size_t)i * nk + n] = (float)(s * w);
 }
 
 // One input row per listed spatial point (xs[r] = i1 * nx + i2, or r itself when xs == null).
@@ -177,9 +184,9 @@ cudaError_t launch_features(const FeatArgs &a, const void *f, int f64, int rows,
   if (a.f1_src_rows > 0) {  // refresh f1 from the same state first
     const double w = a.dx * a.dp;
     if (f64)
-      k_f1<double><<<a.nx, a.nk, 0, s>>>((const double *)f, a.f1, a.nx, a.nk, w);
+      k_f1<double><<<a.nx * ((a.nk + 7) / 8), 256, 0, s>>>((const double *)f, a.f1, a.nx, a.nk, w);
     else
-      k_f1<float><<<a.nx, a.nk, 0, s>>>((const float *)f, a.f1, a.nx, a.nk, w);
+      k_f1<float><<<a.nx * ((a.nk + 7) / 8), 256, 0, s>>>((const float *)f, a.f1, a.nx, a.nk, w);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -22,7 +22,8 @@
  *   x_i = -L/2 + i dx,  dx = L / nx,           i in [0, nx)
  *   p_n = (n - nk/2) dp, dp = pi hbar / L,      n in [0, nk)
  *   phase-space arrays are f[i1][i2][n1][n2], n2 fastest, C order,
- *   nx*nx*nk*nk elements (double for W2_F64, float for W2_F32_TF32X3);
+ *   nx*nx*nk*nk elements (double for W2_F64 and W2_F64_SLICED, float for
+ *   W2_F32_TF32X3);
  *   f is zero outside the momentum window.
  *
  * Conventions:
@@ -63,12 +64,18 @@ typedef enum {
 } w2_status;
 
 typedef enum {
-  W2_F64 = 0,           /* FP64 state and arithmetic                              */
-  W2_F32_TF32X3 = 1     /* precision form: FP32 state; the pseudo-difference
-                           contractions on tensor cores with each operand split
-                           into two TF32 parts (three products, FP32 accumulate);
-                           the spline shift as an FP32 increment of the state;
-                           densities and observables reduced in FP64             */
+  W2_F64 = 0,           /* FP64 state and arithmetic (FP64 pipe: DMMA and DFMA)   */
+  W2_F32_TF32X3 = 1,    /* precision form: FP32 state; the pseudo-difference
+                           contractions on tensor cores, the state split into two
+                           TF32 parts and the kernel into three (four products,
+                           FP32 accumulate); the spline shift as an FP32 increment
+                           of the state; densities and observables in FP64       */
+  W2_F64_SLICED = 3     /* FP64 state and results as W2_F64 (the FP64 oracle to
+                           1e-10 over whole steps); the pseudo-difference
+                           contractions as exact products of six 8-bit integer
+                           slices of each operand on the BF16 tensor cores (the
+                           Ozaki splitting, 21 slice pairs), recombined in 64-bit
+                           integers; nk in {16, 32, 48, 64}                      */
 } w2_precision;
 
 typedef enum {
@@ -81,7 +88,7 @@ typedef enum {
 /* Problem description (Sec. 3.1 grid; Sec. 5 uses hbar = m = 1).
  *   nx  : spatial points per particle, 4 <= nx; FP64 supports nx <= 128
  *   nk  : momentum points per particle; W2_F64 supports nk in {8,16,...,64},
- *         W2_F32_TF32X3 nk in {16,32,...,128}
+ *         W2_F64_SLICED nk in {16,32,48,64}, W2_F32_TF32X3 nk in {16,32,...,128}
  *   L   : period of the box (> 0); dt: time step tau (> 0)
  *   hbar, mass: > 0
  *   precision: a w2_precision;  xc_kind: a w2_xc_kind                          */

@@ -25,6 +25,15 @@ using namespace w2;
 
 static double fold(double x, double L) { return x - L * floor((x + 0.5 * L) / L); }
 
+// Precisions whose state and results are FP64.
+static inline bool f64_state(int prec) { return prec == W2_F64 || prec == W2_F64_SLICED; }
+
+// The FP64 sweep of a context: on the FP64 pipe, or by exact slices on the
+// BF16 tensor cores.
+static cudaError_t theta64(const w2_ctx *ctx, int mode, const ThetaArgs &th, cudaStream_t s) {
+  return ctx->prec == W2_F64_SLICED ? launch_theta_f64s(ctx->nk, mode, th, s) : launch_theta_f64(ctx->nk, mode, th, s);
+}
+
 static void free_all(w2_ctx *c) {
   void *ptrs[] = {c->f, c->g, c->t1, c->t2, c->xsum, c->xsum2, c->K, c->K12, c->vext_fine, c->w_fine,
                   c->d_fine, c->sintab, c->vext_grid, c->k0tab, c->wtab, c->xpart, c->obs_out,
@@ -88,8 +97,10 @@ extern "C" w2_status w2_create(const w2_config *cfg, void *cuda_stream, w2_ctx *
       !(cfg->hbar > 0) || !(cfg->mass > 0) || !isfinite(cfg->L) || !isfinite(cfg->dt) ||
       cfg->xc_kind < 0 || cfg->xc_kind > 2)
     return W2_ERR_ARG;
-  if (cfg->precision != W2_F64 && cfg->precision != W2_F32_TF32X3) return W2_ERR_UNSUPPORTED;
+  if (cfg->precision != W2_F64 && cfg->precision != W2_F32_TF32X3 && cfg->precision != W2_F64_SLICED)
+    return W2_ERR_UNSUPPORTED;
   if (cfg->precision == W2_F64 && (!nk_supported_f64(cfg->nk) || cfg->nx > 128)) return W2_ERR_UNSUPPORTED;
+  if (cfg->precision == W2_F64_SLICED && (!nk_supported_f64s(cfg->nk) || cfg->nx > 128)) return W2_ERR_UNSUPPORTED;
   if (cfg->precision == W2_F32_TF32X3 && (!nk_supported_f32(cfg->nk) || cfg->nx > 128)) return W2_ERR_UNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return W2_ERR_CUDA;
@@ -104,7 +115,7 @@ extern "C" w2_status w2_create(const w2_config *cfg, void *cuda_stream, w2_ctx *
   ctx->stream = (cudaStream_t)cuda_stream;
   ctx->dev = dev;
   ctx->prec = cfg->precision;
-  ctx->esz = cfg->precision == W2_F64 ? sizeof(double) : sizeof(float);
+  ctx->esz = f64_state(cfg->precision) ? sizeof(double) : sizeof(float);
   ctx->nx = cfg->nx;
   ctx->nk = cfg->nk;
   ctx->M = 2 * cfg->nk;
@@ -115,7 +126,7 @@ extern "C" w2_status w2_create(const w2_config *cfg, void *cuda_stream, w2_ctx *
   ctx->tau = cfg->dt;
   ctx->z = sqrt(3.0) - 2.0;
   // periodic start sums: |z|^k below the storage precision (z^32 ~ 5e-19, z^16 ~ 7e-10)
-  const int kmax = cfg->precision == W2_F64 ? 32 : 16;
+  const int kmax = f64_state(cfg->precision) ? 32 : 16;
   ctx->nterm = ctx->nx <= kmax ? ctx->nx : kmax;
   ctx->zscale = (ctx->nterm == ctx->nx) ? 1.0 / (1.0 - pow(ctx->z, ctx->nx)) : 1.0;
 
@@ -136,7 +147,8 @@ extern "C" w2_status w2_create(const w2_config *cfg, void *cuda_stream, w2_ctx *
 #undef W2_ALLOC
   if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->h_obs, sizeof(double) * (8 + nx + nx * nx));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = ctx->prec == W2_F64 ? prepare_kernels_f64(nk) : prepare_kernels_f32(nk);
+  if (e == cudaSuccess) e = f64_state(ctx->prec) ? prepare_kernels_f64(nk) : prepare_kernels_f32(nk);
+  if (e == cudaSuccess && ctx->prec == W2_F64_SLICED) e = prepare_kernels_f64s(nk);
   if (e != cudaSuccess) {
     w2_status st = (e == cudaErrorMemoryAllocation) ? W2_ERR_OOM : W2_ERR_CUDA;
     cudaGetLastError();
@@ -310,7 +322,7 @@ static cudaError_t enqueue_features(w2_ctx *ctx, const void *f, cudaStream_t s) 
   fa.f1_src_rows = 1;
   fa.xs = nullptr;
   fa.x = ctx->xrows;
-  return launch_features(fa, f, ctx->prec == W2_F64, ctx->nx * ctx->nx, s);
+  return launch_features(fa, f, f64_state(ctx->prec), ctx->nx * ctx->nx, s);
 }
 
 // The network's two-body term of `f` (in operator units) into the MLP output buffer.
@@ -351,7 +363,7 @@ static cudaError_t enqueue_step(w2_ctx *ctx, cudaStream_t s, const StepEvents *e
     th.pair = mlp_out(ctx->mlp);
   }
   W2_MARK(2, 0)
-  if ((e = launch_theta_f64(nk, 0, th, s)) != cudaSuccess) return e;
+  if ((e = theta64(ctx, 0, th, s)) != cudaSuccess) return e;
   W2_MARK(2, 1)
   AdvArgs av;
   av.nx = nx;
@@ -387,7 +399,7 @@ static cudaError_t enqueue_step(w2_ctx *ctx, cudaStream_t s, const StepEvents *e
   th.xsum = nullptr;
   if (learned && (e = enqueue_learned_pair(ctx, ctx->g, s)) != cudaSuccess) return e;
   W2_MARK(7, 0)
-  if ((e = launch_theta_f64(nk, 1, th, s)) != cudaSuccess) return e;
+  if ((e = theta64(ctx, 1, th, s)) != cudaSuccess) return e;
   W2_MARK(7, 1)
   return cudaSuccess;
 }
@@ -465,7 +477,7 @@ static cudaError_t enqueue_step32(w2_ctx *ctx, cudaStream_t s, const StepEvents 
 }
 
 static cudaError_t enqueue_any(w2_ctx *ctx, cudaStream_t s, const StepEvents *evs) {
-  return ctx->prec == W2_F64 ? enqueue_step(ctx, s, evs) : enqueue_step32(ctx, s, evs);
+  return f64_state(ctx->prec) ? enqueue_step(ctx, s, evs) : enqueue_step32(ctx, s, evs);
 }
 
 static w2_status learned_judge(w2_ctx *ctx);
@@ -533,8 +545,8 @@ extern "C" w2_status w2_observables(w2_ctx *ctx, w2_obs *out, double *n1, double
   a.mass = ctx->cfg.mass;
   a.gamma = ctx->gamma;
   a.c_h = ctx->c_h;
-  a.f = ctx->prec == W2_F64 ? ctx->f : nullptr;
-  a.f32 = ctx->prec == W2_F64 ? nullptr : (const float *)ctx->f;
+  a.f = f64_state(ctx->prec) ? ctx->f : nullptr;
+  a.f32 = f64_state(ctx->prec) ? nullptr : (const float *)ctx->f;
   a.vext_grid = ctx->vext_grid;
   a.w_fine = ctx->w_fine;
   a.xpart = ctx->xpart;
@@ -562,13 +574,13 @@ extern "C" w2_status w2_theta(w2_ctx *ctx, const void *f, void *out) {
   if (ctx->sticky) return ctx->sticky;
   if (!ctx->have_pot) return W2_ERR_STATE;
   const int nx = ctx->nx, nk = ctx->nk, W = 2 * nk - 1;
-  if (ctx->prec == W2_F64)
+  if (f64_state(ctx->prec))
     W2_TRY(launch_xsum_f64(nx, nk, (const double *)f, ctx->xsum2, ctx->stream));
   else
     W2_TRY(launch_xsum_f32(nx, nk, (const float *)f, ctx->xsum2, ctx->stream));
   TabArgs ta = tab_args(ctx, ctx->xsum2, 0);
   W2_TRY(launch_tables(ta, ctx->stream));
-  if (ctx->prec == W2_F64) {
+  if (f64_state(ctx->prec)) {
     ThetaArgs th;
     th.nx = nx;
     th.in = (const double *)f;
@@ -579,7 +591,7 @@ extern "C" w2_status w2_theta(w2_ctx *ctx, const void *f, void *out) {
     th.K2 = ctx->K + (size_t)nx * W;
     th.K12 = ctx->K12;
     th.half_tau = 0.5 * ctx->tau;
-    W2_TRY(launch_theta_f64(nk, 0, th, ctx->stream));
+    W2_TRY(theta64(ctx, 0, th, ctx->stream));
   } else {
     Theta32Args th;
     th.nx = nx;
@@ -599,10 +611,10 @@ extern "C" w2_status w2_theta(w2_ctx *ctx, const void *f, void *out) {
 extern "C" w2_status w2_advect(w2_ctx *ctx, const void *f, void *out) {
   if (!ctx || !f || !out || f == out) return W2_ERR_ARG;
   // the FP32 shift stages its lines with 16-byte asynchronous copies
-  if (ctx->prec != W2_F64 && (((uintptr_t)f | (uintptr_t)out) & 15)) return W2_ERR_ARG;
+  if (!f64_state(ctx->prec) && (((uintptr_t)f | (uintptr_t)out) & 15)) return W2_ERR_ARG;
   if (ctx->sticky) return ctx->sticky;
   if (!ctx->have_pot) return W2_ERR_STATE;
-  if (ctx->prec == W2_F64) {
+  if (f64_state(ctx->prec)) {
     AdvArgs av;
     av.nx = ctx->nx;
     av.k0tab = ctx->k0tab;
@@ -677,7 +689,7 @@ extern "C" w2_status w2_step_profile(w2_ctx *ctx, int32_t nsteps, double *kernel
 // Exact two-body term of `f` alone: the sweep with zero one-body tables.
 static cudaError_t enqueue_pair_exact(w2_ctx *ctx, const void *f, void *out, cudaStream_t s) {
   const int nx = ctx->nx, nk = ctx->nk, W = 2 * nk - 1;
-  if (ctx->prec == W2_F64) {
+  if (f64_state(ctx->prec)) {
     ThetaArgs th;
     th.nx = nx;
     th.in = (const double *)f;
@@ -688,7 +700,7 @@ static cudaError_t enqueue_pair_exact(w2_ctx *ctx, const void *f, void *out, cud
     th.K2 = ctx->Kzero + (size_t)nx * W;
     th.K12 = ctx->K12;
     th.half_tau = 0.0;
-    return launch_theta_f64(nk, 0, th, s);
+    return theta64(ctx, 0, th, s);
   }
   Theta32Args th;
   th.nx = nx;
@@ -744,7 +756,7 @@ extern "C" w2_status w2_features(w2_ctx *ctx, const w2_mlp *m, const void *f, co
   fa.f1_src_rows = 1;
   fa.xs = xs;
   fa.x = (uint16_t *)x;
-  W2_TRY(launch_features(fa, f, ctx->prec == W2_F64, rows, ctx->stream));
+  W2_TRY(launch_features(fa, f, f64_state(ctx->prec), rows, ctx->stream));
   return W2_OK;
 }
 
@@ -754,7 +766,7 @@ static w2_status learned_judge(w2_ctx *ctx) {
   cudaStream_t s = ctx->stream;
   W2_TRY(enqueue_pair_exact(ctx, ctx->f, ctx->g, s));
   W2_TRY(enqueue_learned_pair(ctx, ctx->f, s));
-  W2_TRY(launch_sqdiff(mlp_out(ctx->mlp), ctx->g, ctx->prec == W2_F64, mlp_part(ctx->mlp), ctx->npts, 1.0, s));
+  W2_TRY(launch_sqdiff(mlp_out(ctx->mlp), ctx->g, f64_state(ctx->prec), mlp_part(ctx->mlp), ctx->npts, 1.0, s));
   W2_TRY(cudaMemcpyAsync(mlp_hpart(ctx->mlp), mlp_part(ctx->mlp), sizeof(double) * 256, cudaMemcpyDeviceToHost, s));
   W2_TRY(cudaStreamSynchronize(s));
   double d = 0.0, r = 0.0;
@@ -786,7 +798,7 @@ extern "C" w2_status w2_learned_attach(w2_ctx *ctx, w2_mlp *m, int32_t judge_eve
     ctx->learned_active = false;
     return W2_OK;
   }
-  if (ctx->prec != W2_F64) return W2_ERR_UNSUPPORTED;
+  if (!f64_state(ctx->prec)) return W2_ERR_UNSUPPORTED;
   if (mlp_nk(m) != ctx->nk || mlp_maxrows(m) < ctx->nx * ctx->nx || judge_every < 0 || !(tol >= 0)) return W2_ERR_ARG;
   w2_status st = ensure_pair_buffers(ctx);
   if (st != W2_OK) return st;

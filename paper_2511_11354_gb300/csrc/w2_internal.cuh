@@ -127,6 +127,11 @@ struct FeatArgs {
 // Launchers (return the launch error).
 cudaError_t launch_tables(const TabArgs &a, cudaStream_t s);
 cudaError_t launch_theta_f64(int nk, int mode, const ThetaArgs &a, cudaStream_t s);
+// FP64-accurate sweep by exact 8-bit slices on the BF16 tensor cores (w2_f64s.cu);
+// nk in {16, 32, 48, 64}; a.xsum must be null.
+cudaError_t launch_theta_f64s(int nk, int mode, const ThetaArgs &a, cudaStream_t s);
+cudaError_t prepare_kernels_f64s(int nk);
+bool nk_supported_f64s(int nk);
 cudaError_t launch_adv_f64(int nk, int dir, int two, const AdvArgs &a, cudaStream_t s);
 cudaError_t launch_xsum_f64(int nx, int nk, const double *f, double *xsum, cudaStream_t s);
 cudaError_t launch_xsum_f32(int nx, int nk, const float *f, double *xsum, cudaStream_t s);

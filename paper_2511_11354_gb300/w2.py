@@ -21,6 +21,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libw2.so")
 
 W2_F64 = 0
 W2_F32_TF32X3 = 1
+W2_F64_SLICED = 3
+F64_STATE = (W2_F64, W2_F64_SLICED)
 
 STATUS = {0: "W2_OK", -1: "W2_ERR_ARG", -2: "W2_ERR_CUDA", -3: "W2_ERR_OOM", -4: "W2_ERR_STATE",
           -5: "W2_ERR_UNSTABLE", -6: "W2_ERR_NONFINITE", -7: "W2_ERR_TIMEOUT", -8: "W2_ERR_UNSUPPORTED"}
@@ -151,8 +153,8 @@ class Context:
         import torch
         self.lib = load()
         self.precision = precision
-        self.np_dtype = np.float64 if precision == W2_F64 else np.float32
-        self.torch_dtype = torch.float64 if precision == W2_F64 else torch.float32
+        self.np_dtype = np.float64 if precision in F64_STATE else np.float32
+        self.torch_dtype = torch.float64 if precision in F64_STATE else torch.float32
         self.shape = (nx, nx, nk, nk)
         self.nx, self.nk = nx, nk
         if stream is None:

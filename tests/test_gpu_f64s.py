@@ -1,0 +1,159 @@
+"""GPU parity of the sliced FP64 path (W2_F64_SLICED: the pseudo-difference
+contractions as exact products of six 8-bit slices on the BF16 tensor cores)
+against the FP64 oracle, through the C ABI.
+
+Bars: the operator alone within 2e-12 relative L2 of the oracle (the slices
+keep 48 bits of each operand relative to its block maximum; the difference
+operator's cancellation costs about two decimal digits of that); whole time
+steps within 1e-10 relative L2, the FP64 bar of the plain path.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_11354_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_11354_gb300 import build
+    build.build()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _ctx(prob):
+    from paper_2511_11354_gb300 import w2
+    return w2.Context.from_problem(prob, precision=w2.W2_F64_SLICED)
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("nx,nk", [(8, 16), (12, 32), (20, 48), (16, 64), (7, 32), (33, 64)])
+def test_sliced_theta_parity(nx, nk):
+    prob, _ = inputs.workload_small(nx=nx, nk=nk)
+    f = inputs.initial_state(prob, centres=(-2.5, 3.0), seed=11, noise=0.05)
+    ctx = _ctx(prob)
+    out = torch.empty(prob.nx, prob.nx, prob.nk, prob.nk, dtype=torch.float64, device="cuda")
+    ctx.theta(_dev(f), out)
+    assert rel(out.cpu().numpy(), oracle.Oracle(prob).theta(f)) < 2e-12
+
+
+def test_sliced_theta_parity_xc_hartree_and_signs():
+    """H-L exchange-correlation on, and a state of both signs with a wide
+    dynamic range inside each block (exercises the balanced digits and the
+    per-block exponents)."""
+    prob, f = inputs.workload_small(nx=16, nk=32)
+    prob.c_xc, prob.xc_kind = -0.7, 2
+    rng = np.random.default_rng(3)
+    f = f * (1.0 + 0.5 * rng.standard_normal(f.shape)) - 0.3 * f.mean()
+    f[3, 5] *= 1e-9  # one block many binades below the others
+    ctx = _ctx(prob)
+    out = torch.empty(*f.shape, dtype=torch.float64, device="cuda")
+    ctx.theta(_dev(f), out)
+    ref = oracle.Oracle(prob).theta(f)
+    got = out.cpu().numpy()
+    assert rel(got, ref) < 2e-12
+    assert rel(got[3, 5], ref[3, 5]) < 2e-12  # the per-block scale keeps the small block's digits
+
+
+def test_sliced_step_parity_small_workload():
+    prob, f0 = inputs.workload_small()
+    ctx = _ctx(prob)
+    ctx.set_state(f0)
+    ctx.step(20)
+    assert rel(ctx.get_state(), oracle.Oracle(prob).step(f0, 20)) < 1e-10
+
+
+@pytest.mark.parametrize("nx,nk,steps", [(16, 16, 10), (20, 32, 5), (24, 48, 3)])
+def test_sliced_step_parity_dwell_shapes(nx, nk, steps):
+    prob, f0 = inputs.workload_dwell(nx=nx, nk=nk)
+    ctx = _ctx(prob)
+    ctx.set_state(_dev(f0))
+    ctx.step(steps)
+    assert rel(ctx.get_state(), oracle.Oracle(prob).step(f0, steps)) < 1e-10
+
+
+def test_sliced_step_parity_full_size_workload():
+    """64^4 double well (the benchmark workload, in its timed launch
+    configuration), 2 steps, every element compared."""
+    prob, f0 = inputs.workload_dwell()
+    ctx = _ctx(prob)
+    ctx.set_state(_dev(f0))
+    ctx.step(2)
+    got = ctx.get_state()
+    assert rel(got, oracle.Oracle(prob).step(f0, 2)) < 1e-10
+    assert np.abs(got - got.transpose(1, 0, 3, 2)).max() < 1e-13 * np.abs(got).max()
+
+
+def test_sliced_and_fp64_pipe_paths_agree_over_200_steps():
+    """The two FP64 paths on the 64^4 workload over 200 steps (the FP64-pipe
+    path is itself held to the oracle by test_gpu_f64.py)."""
+    from paper_2511_11354_gb300 import w2
+    prob, f0 = inputs.workload_dwell()
+    a = w2.Context.from_problem(prob)
+    b = _ctx(prob)
+    d = _dev(f0)
+    a.set_state(d)
+    b.set_state(d)
+    a.step(200)
+    b.step(200)
+    assert rel(b.get_state(), a.get_state()) < 1e-10
+    oa, ob = a.observables(), b.observables()
+    for k in ("mass", "energy", "entropy_lin"):
+        assert abs(getattr(ob, k) - getattr(oa, k)) < 1e-11 * max(1.0, abs(getattr(oa, k))), k
+
+
+def test_sliced_determinism_and_resume():
+    prob, f0 = inputs.workload_small(nx=16, nk=16)
+    a = _ctx(prob)
+    a.set_state(f0)
+    a.step(12)
+    b = _ctx(prob)
+    b.set_state(f0)
+    b.step(6)
+    c = _ctx(prob)
+    c.set_state(b.get_state())
+    c.step(6)
+    assert np.array_equal(c.get_state(), a.get_state())
+
+
+def test_sliced_nonfinite_and_unsupported():
+    from paper_2511_11354_gb300 import w2
+    prob, f0 = inputs.workload_small(nx=8, nk=16)
+    ctx = _ctx(prob)
+    bad = f0.copy()
+    bad[1, 2, 3, 4] = np.inf
+    out = torch.empty(*bad.shape, dtype=torch.float64, device="cuda")
+    ctx.theta(_dev(bad), out)
+    assert bool(torch.isnan(out[1, 2]).all())
+    ctx.set_state(bad)
+    assert ctx.observables().status == "W2_ERR_NONFINITE"
+    for nk in (8, 24, 128):  # slices need nk in {16, 32, 48, 64}
+        with pytest.raises(w2.W2Error) as e:
+            w2.Context(8, nk, 1.0, 0.01, precision=w2.W2_F64_SLICED)
+        assert e.value.name == "W2_ERR_UNSUPPORTED"
+
+
+def test_sliced_learned_pair_term_matches_fp64_pipe():
+    """The learned form's hook (a supplied two-body term) on the sliced path."""
+    from paper_2511_11354_gb300 import learned, w2
+    prob, f0 = inputs.workload_dwell(nx=16, nk=32)
+    zero = learned.zero_network(prob.nk, hidden=32, max_rows=prob.nx * prob.nx)
+    outs = []
+    for prec in (w2.W2_F64, w2.W2_F64_SLICED):
+        c = w2.Context.from_problem(prob, precision=prec)
+        c.set_state(f0)
+        c.attach_learned(zero, 0, 1e30)
+        c.step(5)
+        outs.append(c.get_state())
+    assert rel(outs[1], outs[0]) < 1e-11

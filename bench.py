@@ -1,5 +1,7 @@
 """Benchmark: 4-D phase-space point-updates/s of the periodic two-body Wigner
-2-RDM Lawson step on GB300, plain FP64 path, 64^4 double-well workload.
+2-RDM Lawson step on GB300, FP64 results (the sliced FP64 path, held to the
+FP64 oracle at 1e-10), 64^4 double-well workload; the FP64-pipe path and the
+precision, batching and learned forms are reported beside it.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl w2|reference]
 
@@ -132,15 +134,15 @@ def _fp64_peak():
     return json.loads(out)
 
 
-# DRAM bytes (read + write) of one k_theta launch on the 64^4 workload from one
-# ncu capture (profiles/k_theta_f64_dwell_64x64.md), keyed by the hash of the
+# DRAM bytes (read + write) of one k_theta_s launch on the 64^4 workload from
+# one ncu capture (profiles/k_theta_s_dwell_64x64.md), keyed by the hash of the
 # kernel source it was taken on: any change to the source reports null.
-THETA_TRAFFIC = {"adc3232c8a8beccc": 134.482688e6 + 86.614528e6}
+THETA_TRAFFIC = {}
 
 
 def _theta_traffic():
     import hashlib
-    src = os.path.join(ROOT, "paper_2511_11354_gb300", "csrc", "w2_f64.cu")
+    src = os.path.join(ROOT, "paper_2511_11354_gb300", "csrc", "w2_f64s.cu")
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     return THETA_TRAFFIC.get(h)
 
@@ -284,6 +286,32 @@ def bench_learned(args, timed):
     return out
 
 
+SLICE_PAIRS = 21  # digit pairs (s, t), s + t <= 5, of the sliced FP64 sweep
+
+
+def sliced_mma_per_block(nk):
+    """mma.m16n8k16 instructions one k_theta_s block executes (all 21 digit
+    pairs): the two dense one-body contractions plus the sheared pair tiles
+    over the k-steps each tile group touches."""
+    rt = nk // 16
+    one_body = 2 * rt * (nk // 16) * SLICE_PAIRS * 2 * (nk // 16)
+    pair = 0
+    for r in range(rt):
+        r0 = 16 * r
+        cfirst, clast = r0 // 8, min((r0 + 15 + nk - 1) // 8, (2 * nk - 2) // 8)
+        ntile = clast - cfirst + 1
+        half = (ntile + 1) // 2
+        for lo, hi in ((cfirst, cfirst + half), (cfirst + half, clast + 1)):
+            c = lo
+            while c < hi:
+                nt = min(3, hi - c)
+                klo = max(0, 8 * c - nk + 1) & ~15
+                khi = min(nk - 1, 8 * (c + nt - 1) + 7)
+                pair += len(range(klo, khi + 1, 16)) * SLICE_PAIRS * nt
+                c += nt
+    return one_body + pair
+
+
 def theta_mma_per_block(nk):
     """mma.m16n8k8 tiles of one Theta block (per product): two dense nk x nk x nk
     contractions plus the sheared pair term over the k-steps it can touch."""
@@ -297,12 +325,20 @@ def theta_mma_per_block(nk):
     return dense + pair
 
 
-def MEASURED_BF16_TFLOPS():
+def MEASURED_BF16_TFLOPS(sustained=False):
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
-        return float(json.load(open(path))["bf16_tflops"])
+        return float(json.load(open(path))["bf16_tflops_sustained" if sustained else "bf16_tflops"])
     except Exception:
-        return 1900.0  # fallback figure of the profiling recipe
+        return 1700.0 if sustained else 1900.0  # fallback figures of the profiling recipe
+
+
+def MEASURED_HBM_GBS():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(path))["hbm_gbs"])
+    except Exception:
+        return 6800.0  # fallback figure of the profiling recipe
 
 
 def run_reference(args):
@@ -375,7 +411,7 @@ def main():
         return
 
     prob, f0 = inputs.workload_dwell()
-    ctx = w2.Context.from_problem(prob)
+    ctx = w2.Context.from_problem(prob, precision=w2.W2_F64_SLICED)
     f_dev = torch.from_numpy(f0).cuda()
     ctx.set_state(f_dev)
     stream = torch.cuda.current_stream()
@@ -405,9 +441,31 @@ def main():
     # ---- per-kernel times (events around every launch, same stream) -------
     kprof = ctx.step_profile(min(args.steps, 50))
     k_theta = 0.5 * (kprof[2] + kprof[7])
-    flops = theta_flops_per_point(prob.nk) * prob.points
+    fp64_flops = theta_flops_per_point(prob.nk) * prob.points   # the FP64 contraction of one sweep
+    alg_flops = SLICE_PAIRS * fp64_flops                          # its 21 slice products
+    exec_flops = sliced_mma_per_block(prob.nk) * 4096.0 * prob.nx * prob.nx
+    bf16_peak = MEASURED_BF16_TFLOPS(sustained=True)
+    achieved = alg_flops / (k_theta * 1e-3) / 1e12
+    shift_bytes = 32.0 * prob.points  # two arrays read and two written, 8 B each
+    k_shift = kprof[4]
+    step_bytes = 72.0 * prob.points   # algorithmic bytes of a whole step
+
+    # ---- the FP64-pipe path (DMMA sweep, FP64 shift) on the same workload ---
+    pipe = w2.Context.from_problem(prob)
+    pipe.set_state(f_dev)
+    pipe.step(args.warmup)
+    kp = min(args.steps, 50)
+    barrier()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    pipe.step(kp)
+    p1.record(stream)
+    barrier()
+    ms_pipe = max_over_ranks(p0.elapsed_time(p1))
+    kprof_pipe = pipe.step_profile(min(kp, 20))
+    pipe.close()
     peaks = _fp64_peak()
-    achieved = flops / (k_theta * 1e-3) / 1e12
+    k_theta_pipe = 0.5 * (kprof_pipe[2] + kprof_pipe[7])
 
     # ---- end to end through the C ABI: pinned host state in, observables out
     ctx.set_state(f_dev)
@@ -443,15 +501,33 @@ def main():
             "clocks": clk,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": len(w2.STEP_KERNELS) * args.steps,
-            "roofline": {"bound": "tensor", "kernel": "k_theta (FP64 mma.sync m8n8k4, DMMA)",
-                         "achieved": achieved, "peak": peaks["fp64_dmma_tflops"], "unit": "TFLOP/s",
-                         "frac": achieved / peaks["fp64_dmma_tflops"], "traffic": _theta_traffic(),
+            "roofline": {"bound": "tensor", "kernel": "k_theta_s (sliced FP64 sweep, BF16 mma.sync m16n8k16)",
+                         "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
+                         "frac": achieved / bf16_peak, "traffic": _theta_traffic(),
                          "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-                         "peak_source": "measured live by paper_2511_11354_gb300/probe/fp64_peak.cu "
-                                        "(FP64 tensor path; MEASURED_PEAKS.json has no FP64 figure)",
-                         "fp64_dfma_tflops": peaks["fp64_dfma_tflops"],
-                         "flops_per_launch": flops, "ms_per_launch": k_theta},
+                         "peak_source": "bf16_tflops_sustained of measured (MEASURED_PEAKS.json, cuBLAS)",
+                         "flops_per_launch": alg_flops,
+                         "flops_rule": "21 slice products x the FP64 contraction (2 (2 nk + mean anti-diagonal) "
+                                       "flop per point)",
+                         "executed_mma_flops_per_launch": exec_flops,
+                         "fp64_equivalent_tflops": fp64_flops / (k_theta * 1e-3) / 1e12,
+                         "ms_per_launch": k_theta},
+            "roofline_shift": {"bound": "hbm", "kernel": "k_adv_df<64,1,1> (x1 lines, double-float)",
+                               "achieved": shift_bytes / (k_shift * 1e-3) / 1e9,
+                               "peak": MEASURED_HBM_GBS(), "unit": "GB/s",
+                               "frac": shift_bytes / (k_shift * 1e-3) / 1e9 / MEASURED_HBM_GBS(),
+                               "bytes_per_launch": shift_bytes, "ms_per_launch": k_shift,
+                               "peak_source": "hbm_gbs of measured (MEASURED_PEAKS.json)"},
+            "step_hbm_frac": step_bytes / (ms / args.steps * 1e-3) / 1e9 / MEASURED_HBM_GBS(),
             "kernel_ms": dict(zip(w2.STEP_KERNELS, [float(x) for x in kprof])),
+            "fp64_pipe_path": {
+                "what": "W2_F64: DMMA m8n8k4 sweep and FP64 spline shift on the FP64 pipe, same workload",
+                "value": whole_job_rate(prob.points, kp, ws, ms_pipe), "unit": UNIT, "steps": kp,
+                "ms_per_step": ms_pipe / kp,
+                "kernel_ms": dict(zip(w2.STEP_KERNELS, [float(x) for x in kprof_pipe])),
+                "theta_fp64_tflops": fp64_flops / (k_theta_pipe * 1e-3) / 1e12,
+                "fp64_dmma_peak_tflops": peaks["fp64_dmma_tflops"], "fp64_dfma_peak_tflops": peaks["fp64_dfma_tflops"],
+                "peak_source": "measured live by paper_2511_11354_gb300/probe/fp64_peak.cu"},
             "observables": {"mass": ob.mass, "energy": ob.energy, "entropy_lin": ob.entropy_lin,
                             "status": ob.status},
             "cpu_baseline": cpu,

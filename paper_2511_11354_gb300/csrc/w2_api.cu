@@ -37,7 +37,7 @@ static cudaError_t theta64(const w2_ctx *ctx, int mode, const ThetaArgs &th, cud
 static void free_all(w2_ctx *c) {
   void *ptrs[] = {c->f, c->g, c->t1, c->t2, c->xsum, c->xsum2, c->K, c->K12, c->vext_fine, c->w_fine,
                   c->d_fine, c->sintab, c->vext_grid, c->k0tab, c->wtab, c->xpart, c->obs_out,
-                  c->wtab32, c->ctab32};
+                  c->wtab32, c->ctab32, c->wdf, c->zpow};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_obs) cudaFreeHost(c->h_obs);
@@ -74,6 +74,12 @@ extern "C" void w2_destroy(w2_ctx *ctx) {
 // s = tau p_n / (m dx) cells behind each grid point; with k0 = floor(-s) and
 // theta = -s - k0 the value is sum_{a=-1..2} eta_{i+k0+a} b_a(theta) (the
 // four B-spline pieces of Sec. 4.1 on [0, 1)), eta = -6 z d.
+// v as a double-float pair (hi = v rounded to FP32, lo = the rest rounded).
+static float2 split_df(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+
 static void spline_tables(const w2_ctx *c, std::vector<int> &k0, std::vector<double> &w) {
   k0.resize(c->nk);
   w.resize(4 * c->nk);
@@ -144,11 +150,13 @@ extern "C" w2_status w2_create(const w2_config *cfg, void *cuda_stream, w2_ctx *
   W2_ALLOC(ctx->wtab, sizeof(double) * 4 * nk) W2_ALLOC(ctx->xpart, sizeof(double) * nx * nx * (3 + nk))
   W2_ALLOC(ctx->obs_out, sizeof(double) * (8 + nx + nx * nx))
   W2_ALLOC(ctx->wtab32, sizeof(float) * 4 * nk) W2_ALLOC(ctx->ctab32, sizeof(float) * 8 * nk)
+  W2_ALLOC(ctx->wdf, sizeof(float2) * 4 * nk) W2_ALLOC(ctx->zpow, sizeof(float2) * 32)
 #undef W2_ALLOC
   if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->h_obs, sizeof(double) * (8 + nx + nx * nx));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = f64_state(ctx->prec) ? prepare_kernels_f64(nk) : prepare_kernels_f32(nk);
   if (e == cudaSuccess && ctx->prec == W2_F64_SLICED) e = prepare_kernels_f64s(nk);
+  if (e == cudaSuccess && ctx->prec == W2_F64_SLICED) e = prepare_kernels_adv_df(nk);
   if (e != cudaSuccess) {
     w2_status st = (e == cudaErrorMemoryAllocation) ? W2_ERR_OOM : W2_ERR_CUDA;
     cudaGetLastError();
@@ -183,6 +191,12 @@ extern "C" w2_status w2_create(const w2_config *cfg, void *cuda_stream, w2_ctx *
   }
   if (e == cudaSuccess) e = cudaMemcpy(ctx->wtab32, w32.data(), sizeof(float) * 4 * nk, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(ctx->ctab32, c32.data(), sizeof(float) * 8 * nk, cudaMemcpyHostToDevice);
+  // double-float tables of the sliced path
+  std::vector<float2> wdf(4 * nk), zpow(32);
+  for (int q = 0; q < 4 * nk; ++q) wdf[q] = split_df(wt[q]);
+  for (int k = 0; k < 32; ++k) zpow[k] = split_df(pow(ctx->z, k));
+  if (e == cudaSuccess) e = cudaMemcpy(ctx->wdf, wdf.data(), sizeof(float2) * 4 * nk, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ctx->zpow, zpow.data(), sizeof(float2) * 32, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     free_all(ctx);
     delete ctx;
@@ -298,6 +312,21 @@ extern "C" w2_status w2_get_state(w2_ctx *ctx, void *f, int32_t on_device) {
   return W2_OK;
 }
 
+static AdvDFArgs adv_df_args(const w2_ctx *ctx) {
+  AdvDFArgs a;
+  memset(&a, 0, sizeof(a));
+  a.nx = ctx->nx;
+  a.k0tab = ctx->k0tab;
+  a.wdf = ctx->wdf;
+  a.zpow = ctx->zpow;
+  a.z = split_df(ctx->z);
+  a.zscale = split_df(ctx->zscale);
+  a.tau = split_df(ctx->tau);
+  a.half_tau = split_df(0.5 * ctx->tau);
+  a.nterm = ctx->nterm;
+  return a;
+}
+
 // Optional per-kernel CUDA events around every launch of a step (profiling).
 struct StepEvents {
   cudaEvent_t *ev;  // [2 * W2_STEP_KERNELS] or null
@@ -377,15 +406,25 @@ static cudaError_t enqueue_step(w2_ctx *ctx, cudaStream_t s, const StepEvents *e
   av.in1 = ctx->g;
   av.out0 = ctx->t1;
   av.out1 = ctx->t2;
+  AdvDFArgs ad = adv_df_args(ctx);  // the sliced path: pairs in t1, t2
+  ad.in0 = ctx->f;
+  ad.in1 = ctx->g;
+  ad.out0 = ctx->t1;
+  ad.out1 = ctx->t2;
+  const bool df = ctx->prec == W2_F64_SLICED;
   W2_MARK(3, 0)
-  if ((e = launch_adv_f64(nk, 0, 1, av, s)) != cudaSuccess) return e;
+  if ((e = df ? launch_adv_df(nk, 0, 1, ad, s) : launch_adv_f64(nk, 0, 1, av, s)) != cudaSuccess) return e;
   W2_MARK(3, 1)
   av.in0 = ctx->t1;
   av.in1 = ctx->t2;
   av.out0 = ctx->g;  // f~
   av.out1 = ctx->f;  // h
+  ad.in0 = ctx->t1;
+  ad.in1 = ctx->t2;
+  ad.out0 = ctx->g;
+  ad.out1 = ctx->f;
   W2_MARK(4, 0)
-  if ((e = launch_adv_f64(nk, 1, 1, av, s)) != cudaSuccess) return e;
+  if ((e = df ? launch_adv_df(nk, 1, 1, ad, s) : launch_adv_f64(nk, 1, 1, av, s)) != cudaSuccess) return e;
   W2_MARK(4, 1)
   W2_MARK(5, 0)
   if ((e = launch_xsum_f64(nx, nk, ctx->g, ctx->xsum, s)) != cudaSuccess) return e;
@@ -614,7 +653,15 @@ extern "C" w2_status w2_advect(w2_ctx *ctx, const void *f, void *out) {
   if (!f64_state(ctx->prec) && (((uintptr_t)f | (uintptr_t)out) & 15)) return W2_ERR_ARG;
   if (ctx->sticky) return ctx->sticky;
   if (!ctx->have_pot) return W2_ERR_STATE;
-  if (f64_state(ctx->prec)) {
+  if (ctx->prec == W2_F64_SLICED) {
+    AdvDFArgs ad = adv_df_args(ctx);
+    ad.in0 = f;
+    ad.out0 = ctx->t1;
+    W2_TRY(launch_adv_df(ctx->nk, 1, 0, ad, ctx->stream));  // x1 first, into pairs
+    ad.in0 = ctx->t1;
+    ad.out0 = out;
+    W2_TRY(launch_adv_df(ctx->nk, 0, 0, ad, ctx->stream));  // then x2, back to FP64
+  } else if (f64_state(ctx->prec)) {
     AdvArgs av;
     av.nx = ctx->nx;
     av.k0tab = ctx->k0tab;

@@ -36,6 +36,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "w2_df.cuh"
 #include "w2_internal.cuh"
 
 namespace w2 {
@@ -86,19 +87,6 @@ __device__ __forceinline__ void digits6(double v, int emax, int (&d)[kDig]) {
 // BF16 bits of a small integer (|d| <= 256): exact through the FP32 magic-number sum.
 __device__ __forceinline__ uint32_t bf16_int(int d) {
   return __float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f) >> 16;
-}
-
-// m * 2^x as FP64 (truncated to 53 bits; below the normal range: signed zero).
-__device__ __forceinline__ double ll_to_double_scaled(long long v, int x) {
-  if (v == 0) return 0.0;
-  const unsigned long long sg = (unsigned long long)v & 0x8000000000000000ull;
-  const unsigned long long m = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
-  const int top = 63 - __clzll((long long)m);
-  const unsigned long long mant = top > 52 ? (m >> (top - 52)) : (m << (52 - top));
-  int be = top + x + 1023;
-  if (be <= 0) return __longlong_as_double((long long)sg);
-  if (be > 2046) return __longlong_as_double((long long)(sg | 0x7ff0000000000000ull));
-  return __longlong_as_double((long long)(sg | ((unsigned long long)be << 52) | (mant & 0xfffffffffffffull)));
 }
 
 // The five diagonal accumulators of one output as an int64 in units of

@@ -47,6 +47,18 @@ struct AdvArgs {
   double tau;               // combination weight (x1 pass with two arrays)
 };
 
+// The shift of the sliced FP64 path in double-float pairs (w2_adv_df.cu).
+struct AdvDFArgs {
+  int nx;
+  const void *in0, *in1;    // FP64 arrays, or pair arrays in the second pass (in1 may be null)
+  void *out0, *out1;        // pair arrays in the first pass, FP64 in the second
+  const int *k0tab;         // [nk] integer part of the foot offset
+  const float2 *wdf;        // [nk][4] B-spline weights times -6 z, (hi, lo)
+  const float2 *zpow;       // [32] z^k, (hi, lo)
+  float2 z, zscale, tau, half_tau;  // (hi, lo)
+  int nterm;                // terms of the periodic start sums (<= 32)
+};
+
 struct ObsArgs {
   int nx, nk, M;
   double dx, dp, hbar, mass, gamma, c_h;
@@ -133,6 +145,8 @@ cudaError_t launch_theta_f64s(int nk, int mode, const ThetaArgs &a, cudaStream_t
 cudaError_t prepare_kernels_f64s(int nk);
 bool nk_supported_f64s(int nk);
 cudaError_t launch_adv_f64(int nk, int dir, int two, const AdvArgs &a, cudaStream_t s);
+cudaError_t launch_adv_df(int nk, int dir, int two, const AdvDFArgs &a, cudaStream_t s);
+cudaError_t prepare_kernels_adv_df(int nk);
 cudaError_t launch_xsum_f64(int nx, int nk, const double *f, double *xsum, cudaStream_t s);
 cudaError_t launch_xsum_f32(int nx, int nk, const float *f, double *xsum, cudaStream_t s);
 cudaError_t launch_obs(const ObsArgs &a, cudaStream_t s);
@@ -185,6 +199,7 @@ struct w2_ctx {
   double *vext_fine, *w_fine, *d_fine, *sintab, *vext_grid;
   int *k0tab;
   double *wtab;
+  float2 *wdf, *zpow;        // double-float shift weights [nk][4] and z^k [32] (sliced path)
   float *wtab32, *ctab32;    // FP32 shift weights and merged increment taps
   double *xpart, *obs_out, *h_obs;
   double z, zscale;

@@ -1,11 +1,13 @@
 """GPU parity of the sliced FP64 path (W2_F64_SLICED: the pseudo-difference
-contractions as exact products of six 8-bit slices on the BF16 tensor cores)
-against the FP64 oracle, through the C ABI.
+contractions as exact products of six 8-bit slices on the BF16 tensor cores,
+the spline shift in double-float pairs) against the FP64 oracle, through the
+C ABI.
 
 Bars: the operator alone within 2e-12 relative L2 of the oracle (the slices
 keep 48 bits of each operand relative to its block maximum; the difference
-operator's cancellation costs about two decimal digits of that); whole time
-steps within 1e-10 relative L2, the FP64 bar of the plain path.
+operator's cancellation costs about two decimal digits of that); the shift
+within 1e-13 (pairs keep about 47 bits per operation); whole time steps within
+1e-10 relative L2, the FP64 bar of the plain path.
 """
 import numpy as np
 import pytest
@@ -64,6 +66,20 @@ def test_sliced_theta_parity_xc_hartree_and_signs():
     got = out.cpu().numpy()
     assert rel(got, ref) < 2e-12
     assert rel(got[3, 5], ref[3, 5]) < 2e-12  # the per-block scale keeps the small block's digits
+
+
+@pytest.mark.parametrize("nx,nk,dt", [(8, 16, 0.37), (12, 32, 0.37), (33, 48, 0.05), (64, 64, 0.9), (20, 64, 0.005)])
+def test_sliced_advect_parity(nx, nk, dt):
+    """The double-float spline shift of the sliced path (shifts of many cells
+    down to a small fraction of one) against the oracle's FP64 shift."""
+    prob, _ = inputs.workload_small(nx=nx, nk=nk)
+    prob.dt = dt
+    prob.vext, prob.vee, prob.gamma, prob.c_hartree = inputs.zero_potential(), inputs.zero_potential(), 0.0, 0.0
+    f = inputs.initial_state(prob, centres=(-2.5, 3.0), seed=5, noise=0.1)
+    ctx = _ctx(prob)
+    out = torch.empty(*f.shape, dtype=torch.float64, device="cuda")
+    ctx.advect(_dev(f), out)
+    assert rel(out.cpu().numpy(), oracle.Oracle(prob).advect(f)) < 1e-13
 
 
 def test_sliced_step_parity_small_workload():

@@ -281,7 +281,8 @@ void w2_batch_destroy(w2_batch *b);
  * X = (x1, x2) its input row (BF16, w2_mlp_input_dim entries) is
  *   s_f f(X, p1, p2) for all nk^2 momenta, s_f1 f1(x1, .) and s_f1 f1(x2, .)
  *   (f1 = sum over x2, p2 of f dx dp, the reduced one-body Wigner function),
- *   sin(2 pi (x1 - x2)/L), cos(2 pi (x1 - x2)/L), zeros up to a multiple of 32;
+ *   sin(2 pi m (x1 - x2)/L), cos(2 pi m (x1 - x2)/L) for m = 1..8 (in that
+ *   order, sin first), zeros up to a multiple of 32;
  * its output is s_y Theta_{V12}[f](X, ., .) (nk^2 values).  Layers: input ->
  * hidden -> hidden -> hidden -> nk^2 with SiLU between them; FP32 master
  * weights, BF16 tensor-core products with FP32 accumulation; trained by the
@@ -342,6 +343,9 @@ void w2_destroy(w2_ctx *ctx);
 
 /* Static, human-readable name of a status code. */
 const char *w2_status_string(w2_status s);
+/* The CUDA runtime's message for the error behind the calling thread's most
+ * recent W2_ERR_CUDA (a static string; "no CUDA error recorded" if none). */
+const char *w2_last_cuda_error(void);
 
 #ifdef __cplusplus
 }

@@ -18,12 +18,20 @@ using namespace w2;
   do {                                                  \
     cudaError_t e_ = (call);                            \
     if (e_ != cudaSuccess) {                            \
+      w2::note_cuda_error(e_);                          \
       ctx->sticky = W2_ERR_CUDA;                        \
       return W2_ERR_CUDA;                               \
     }                                                   \
   } while (0)
 
 static double fold(double x, double L) { return x - L * floor((x + 0.5 * L) / L); }
+
+static thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+void w2::note_cuda_error(cudaError_t e) { g_last_cuda_error = e; }
+
+extern "C" const char *w2_last_cuda_error(void) {
+  return g_last_cuda_error == cudaSuccess ? "no CUDA error recorded" : cudaGetErrorString(g_last_cuda_error);
+}
 
 // Precisions whose state and results are FP64.
 static inline bool f64_state(int prec) { return prec == W2_F64 || prec == W2_F64_SLICED; }

@@ -109,6 +109,9 @@ struct BXsum {
   int nk;
 };
 
+// Harmonics of the pair distance r = x1 - x2 in an MLP input row.
+constexpr int kMlpHarmonics = 8;
+
 enum GemmEpi { GEMM_STORE = 0, GEMM_BIAS_SILU = 1, GEMM_BIAS_SCALE = 2, GEMM_DSILU = 3 };
 
 // C[M][N] = sum_k A(m, k) B(k, n) with bf16 A(m, k) = A[m*sam + k*sak] and
@@ -135,6 +138,9 @@ struct FeatArgs {
   const int *xs;       // spatial points of the rows (null: row r is X = r)
   uint16_t *x;         // [rows][din] bf16
 };
+
+// Record the CUDA error behind a W2_ERR_CUDA return (read by w2_last_cuda_error).
+void note_cuda_error(cudaError_t e);
 
 // Launchers (return the launch error).
 cudaError_t launch_tables(const TabArgs &a, cudaStream_t s);
@@ -164,6 +170,8 @@ cudaError_t launch_btables(const TabArgs *args, const int *off, int n, int grid,
                            cudaStream_t s);
 cudaError_t launch_bxsum(const BXsum *args, const int *off, int n, int grid, cudaStream_t s);
 cudaError_t launch_gemm(const GemmArgs &a, cudaStream_t s);
+// Pipelined inference GEMM (unit-stride A rows and B rows; BIAS_SILU / BIAS_SCALE epilogues).
+cudaError_t launch_gemm_fwd(const GemmArgs &a, cudaStream_t s);
 cudaError_t launch_features(const FeatArgs &a, const void *f, int f64, int rows, cudaStream_t s);
 cudaError_t launch_colsum(const float *in, float *out, int M, int N, cudaStream_t s);
 cudaError_t launch_adam(float *p, const float *g, float *m, float *v, uint16_t *pb, size_t n, float lr, float b1,
@@ -226,6 +234,7 @@ float mlp_scale(const w2_mlp *m, int which);  // 0: s_f, 1: s_f1, 2: s_y
 float *mlp_out(w2_mlp *m);
 double *mlp_part(w2_mlp *m);
 double *mlp_hpart(w2_mlp *m);
+// Inference forward (pipelined GEMM with fused epilogues).
 cudaError_t mlp_forward(w2_mlp *m, const uint16_t *x, int rows, float *y, float s, cudaStream_t st);
 TabArgs tab_args(w2_ctx *ctx, const double *xsum, int pair_mode);
 Adv32Args adv32_args(w2_ctx *ctx);

@@ -36,15 +36,17 @@ float *mlp_out(w2_mlp *m) { return m->Y; }
 double *mlp_part(w2_mlp *m) { return m->part; }
 double *mlp_hpart(w2_mlp *m) { return m->h_part; }
 
-// y[rows][dout] = s * (MLP(x) ), x bf16 [rows][din] on the device.
-cudaError_t mlp_forward(w2_mlp *m, const uint16_t *x, int rows, float *y, float s, cudaStream_t st) {
+// y[rows][dout] = s * MLP(x), x bf16 [rows][din]: each layer one pipelined
+// GEMM with the bias / SiLU / scale epilogue fused; with keep_z the FP32
+// pre-activations of the hidden layers stay in m->Z for the backward pass.
+static cudaError_t mlp_forward_impl(w2_mlp *m, const uint16_t *x, int rows, float *y, float s, bool keep_z,
+                                    cudaStream_t st) {
   const void *in = x;
-  long long ld = m->din;
   for (int l = 0; l < 4; ++l) {
     GemmArgs a;
     memset(&a, 0, sizeof(a));
     a.A = in;
-    a.sam = ld;
+    a.sam = m->fin[l];
     a.sak = 1;
     a.B = m->pb + m->offW[l];
     a.sbk = m->fout[l];
@@ -55,25 +57,34 @@ cudaError_t mlp_forward(w2_mlp *m, const uint16_t *x, int rows, float *y, float 
     a.bias = m->p + m->offb[l];
     if (l < 3) {
       a.epi = GEMM_BIAS_SILU;
-      a.out_f32 = m->Z[l];
+      a.out_f32 = keep_z ? m->Z[l] : nullptr;
       a.out_bf16 = m->A[l];
     } else {
       a.epi = GEMM_BIAS_SCALE;
       a.scale = s;
       a.out_f32 = y;
     }
-    cudaError_t e = launch_gemm(a, st);
+    cudaError_t e = launch_gemm_fwd(a, st);
     if (e != cudaSuccess) return e;
     in = m->A[l < 3 ? l : 2];
-    ld = m->H;
   }
   return cudaSuccess;
+}
+
+cudaError_t mlp_forward(w2_mlp *m, const uint16_t *x, int rows, float *y, float s, cudaStream_t st) {
+  return mlp_forward_impl(m, x, rows, y, s, false, st);
+}
+
+static cudaError_t mlp_forward_train(w2_mlp *m, const uint16_t *x, int rows, float *y, float s, cudaStream_t st) {
+  return mlp_forward_impl(m, x, rows, y, s, true, st);
 }
 }  // namespace w2
 
 #define WM_TRY(call)                 \
   do {                               \
-    if ((call) != cudaSuccess) {     \
+    cudaError_t e_ = (call);         \
+    if (e_ != cudaSuccess) {         \
+      w2::note_cuda_error(e_);       \
       return W2_ERR_CUDA;            \
     }                                \
   } while (0)
@@ -117,7 +128,7 @@ extern "C" w2_status w2_mlp_create(int32_t nk, int32_t hidden, int32_t max_rows,
   m->nk = nk;
   m->H = hidden;
   m->dout = nk * nk;
-  m->din = ((nk * nk + 2 * nk + 2) + 31) / 32 * 32;
+  m->din = ((nk * nk + 2 * nk + 2 * kMlpHarmonics) + 31) / 32 * 32;
   m->maxrows = max_rows;
   m->stream = (cudaStream_t)cuda_stream;
   const int fin[4] = {m->din, hidden, hidden, hidden}, fout[4] = {hidden, hidden, hidden, m->dout};
@@ -206,7 +217,7 @@ extern "C" w2_status w2_mlp_forward(w2_mlp *m, const void *x, int32_t rows, floa
 // leaves the gradient in m->g and the loss in *loss (synchronises).
 static w2_status forward_backward(w2_mlp *m, const uint16_t *x, const float *target, int rows, double *loss) {
   cudaStream_t s = m->stream;
-  WM_TRY(mlp_forward(m, x, rows, m->Y, 1.0f, s));
+  WM_TRY(mlp_forward_train(m, x, rows, m->Y, 1.0f, s));
   const size_t ny = (size_t)rows * m->dout;
   WM_TRY(launch_mse(m->Y, target, m->dY, m->part, ny, (float)(2.0 / (double)ny), s));
   WM_TRY(launch_f2bf(m->dY, m->dYb, ny, s));

@@ -2,7 +2,7 @@
 // Theta_{V12} of the pseudo-difference operator, with its own training
 // kernels.  For a spatial point X = (x1, x2) the input is
 //   [ s_f f(X, p1, p2) (nk^2),  s_f1 f1(x1, .), s_f1 f1(x2, .) (2 nk),
-//     sin(2 pi r / L), cos(2 pi r / L) (r = x1 - x2),  zero padding ]
+//     sin(2 pi m r / L), cos(2 pi m r / L) for m = 1..8 (r = x1 - x2),  zero padding ]
 // (f1 = sum_{x2,p2} f dx dp is the reduced one-body Wigner function), and the
 // output is s_y Theta_{V12}[f](X, ., .) (nk^2).  Layers: D_in -> H -> H -> H
 // -> nk^2 with SiLU between them; weights kept in FP32 for the optimiser and
@@ -131,6 +131,133 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs a) {
       }
 }
 
+// ---------------------------------------------------------------------------
+// Inference GEMM: C = A B + epilogue with A [M][K] (K contiguous) and B [K][N]
+// (N contiguous), BF16 in, FP32 accumulation on mma.sync m16n8k16.  64 x 128
+// tiles, 32-wide K steps, 4 warps (2 x 2, 32 x 64 each), three cp.async stages
+// of 16-byte copies, fragments by ldmatrix (.trans for B); bias + SiLU (BF16
+// out, optional FP32 pre-activation) or bias + scale (FP32 out) fused.
+// ---------------------------------------------------------------------------
+constexpr int FBM = 64, FBN = 128, FBK = 32, FSTAGES = 3;
+constexpr int FAS = FBK + 8, FBS = FBN + 8;  // padded row strides (BF16): conflict-free ldmatrix
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int bytes) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void ldsm4(uint32_t (&r)[4], const uint16_t *p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
+__device__ __forceinline__ void ldsm4t(uint32_t (&r)[4], const uint16_t *p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
+__global__ void __launch_bounds__(128) k_gemm_fwd(GemmArgs a) {
+  __shared__ __align__(16) uint16_t As[FSTAGES][FBM][FAS];
+  __shared__ __align__(16) uint16_t Bs[FSTAGES][FBK][FBS];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp >> 1, wn = warp & 1, g = lane >> 2, t4 = lane & 3;
+  const int m0 = blockIdx.y * FBM, n0 = blockIdx.x * FBN;
+  const uint16_t *A = (const uint16_t *)a.A, *B = (const uint16_t *)a.B;
+  const int nkt = (a.K + FBK - 1) / FBK;
+
+  auto load = [&](int kt, int st) {
+    const int k0 = kt * FBK;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {  // A: 64 rows x 4 chunks
+      const int c = tid + q * 128, r = c >> 2, ch = c & 3;
+      const int row = m0 + r, k = k0 + ch * 8;
+      const bool in = row < a.M && k < a.K;
+      cp_async16(&As[st][r][ch * 8], in ? A + (size_t)row * a.K + k : A, in ? 16 : 0);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {  // B: 32 rows x 16 chunks
+      const int c = tid + q * 128, r = c >> 4, ch = c & 15;
+      const int k = k0 + r, n = n0 + ch * 8;
+      const bool in = k < a.K && n < a.N;
+      cp_async16(&Bs[st][r][ch * 8], in ? B + (size_t)k * a.N + n : B, in ? 16 : 0);
+    }
+  };
+
+  float acc[2][8][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+
+#pragma unroll
+  for (int st = 0; st < FSTAGES - 1; ++st) {
+    if (st < nkt) load(st, st);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
+  for (int kt = 0; kt < nkt; ++kt) {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(FSTAGES - 2) : "memory");
+    __syncthreads();  // tile kt landed for everyone; tile kt - 1's buffer is free
+    if (kt + FSTAGES - 1 < nkt) load(kt + FSTAGES - 1, (kt + FSTAGES - 1) % FSTAGES);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    const int st = kt % FSTAGES;
+#pragma unroll
+    for (int kk = 0; kk < FBK; kk += 16) {
+      uint32_t af[2][4], bf[8][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) ldsm4(af[i], &As[st][wm * 32 + i * 16 + (lane & 15)][kk + (lane >> 4) * 8]);
+#pragma unroll
+      for (int j = 0; j < 8; j += 2) {
+        uint32_t r[4];
+        ldsm4t(r, &Bs[st][kk + (lane & 15)][wn * 64 + j * 8 + (lane >> 4) * 8]);
+        bf[j][0] = r[0];
+        bf[j][1] = r[1];
+        bf[j + 1][0] = r[2];
+        bf[j + 1][1] = r[3];
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) mma_bf16(acc[i][j], af[i], bf[j]);
+    }
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int m = m0 + wm * 32 + i * 16 + g + 8 * h, n = n0 + wn * 64 + j * 8 + 2 * t4;
+        if (m >= a.M || n >= a.N) continue;
+        const size_t o = (size_t)m * a.N + n;
+        const float v0 = acc[i][j][2 * h] + a.bias[n], v1 = acc[i][j][2 * h + 1] + a.bias[n + 1];
+        if (a.epi == GEMM_BIAS_SILU) {
+          if (a.out_f32) *reinterpret_cast<float2 *>(a.out_f32 + o) = make_float2(v0, v1);
+          *reinterpret_cast<uint32_t *>(a.out_bf16 + o) = (uint32_t)f2bf(silu(v0)) | ((uint32_t)f2bf(silu(v1)) << 16);
+        } else {
+          *reinterpret_cast<float2 *>(a.out_f32 + o) = make_float2(v0 * a.scale, v1 * a.scale);
+        }
+      }
+}
+
+// The inference GEMM for unit-stride rows (A K-contiguous, B N-contiguous,
+// K and N multiples of 8, 16-byte aligned rows).
+cudaError_t launch_gemm_fwd(const GemmArgs &a, cudaStream_t s) {
+  if (a.sak != 1 || a.sbn != 1 || a.sam != a.K || a.sbk != a.N || (a.K & 7) || (a.N & 7) ||
+      (((uintptr_t)a.A | (uintptr_t)a.B) & 15) || (a.epi != GEMM_BIAS_SILU && a.epi != GEMM_BIAS_SCALE))
+    return cudaErrorInvalidValue;
+  dim3 grid((a.N + FBN - 1) / FBN, (a.M + FBM - 1) / FBM);
+  k_gemm_fwd<<<grid, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gemm(const GemmArgs &a, cudaStream_t s) {
   dim3 grid((a.N + GBN - 1) / GBN, (a.M + GBM - 1) / GBM);
   k_gemm<<<grid, 128, 0, s>>>(a);
@@ -172,10 +299,11 @@ __global__ void k_features(FeatArgs a, const T *f) {
       v = a.s_f1 * a.f1[(size_t)i1 * nk + (e - P)];
     else if (e < P + 2 * nk)
       v = a.s_f1 * a.f1[(size_t)i2 * nk + (e - P - nk)];
-    else if (e == P + 2 * nk)
-      v = sinpif(2.f * (float)(i1 - i2) / (float)nx);
-    else if (e == P + 2 * nk + 1)
-      v = cospif(2.f * (float)(i1 - i2) / (float)nx);
+    else if (e < P + 2 * nk + 2 * kMlpHarmonics) {  // sin, cos (2 pi m r / L), m = 1..kMlpHarmonics
+      const int q = e - P - 2 * nk, m = q / 2 + 1;
+      const float u = 2.f * (float)(m * (i1 - i2)) / (float)nx;
+      v = (q & 1) ? cospif(u) : sinpif(u);
+    }
     row[e] = f2bf(v);
   }
 }

@@ -18,11 +18,13 @@ def _torch():
     return torch
 
 
-def make_dataset(prob, f0, mlp, snapshots, stride, points_per_snapshot, seed=0, ctx=None):
+def make_dataset(prob, f0, mlp, snapshots, stride, points_per_snapshot, seed=0, ctx=None, scale="max"):
     """Run the exact FP64 method from f0 and collect, every `stride` steps,
     input rows and scaled two-body targets for `points_per_snapshot` random
     spatial points.  Sets the network's input/output scales from the first
-    snapshot.  Returns (X bf16 [rows][din], T f32 [rows][nk^2])."""
+    snapshot: the reciprocal maximum (scale="max") or root mean square
+    ("rms") of f, f1 and the two-body term.  Returns (X bf16 [rows][din],
+    T f32 [rows][nk^2])."""
     torch = _torch()
     own = ctx is None
     if own:
@@ -42,7 +44,12 @@ def make_dataset(prob, f0, mlp, snapshots, stride, points_per_snapshot, seed=0, 
         ctx.theta_pair(f, pair)
         if s == 0:
             f1 = f.sum(dim=(1, 3)) * prob.dx * prob.dp
-            mlp.set_scales(1.0 / float(f.abs().max()), 1.0 / float(f1.abs().max()), 1.0 / float(pair.abs().max()))
+            if scale == "rms":
+                mlp.set_scales(1.0 / float(f.square().mean().sqrt()), 1.0 / float(f1.square().mean().sqrt()),
+                               1.0 / float(pair.square().mean().sqrt()))
+            else:
+                mlp.set_scales(1.0 / float(f.abs().max()), 1.0 / float(f1.abs().max()),
+                               1.0 / float(pair.abs().max()))
         xs = torch.randperm(nx * nx, generator=gen)[:points_per_snapshot].to(torch.int32).cuda()
         r0 = s * points_per_snapshot
         ctx.features(mlp, f, xs, X[r0:r0 + points_per_snapshot])
@@ -79,11 +86,12 @@ def zero_network(nk, hidden=256, max_rows=4096):
     return m
 
 
-def run(prob, f0, steps, mlp=None, judge_every=0, tol=1e30):
-    """Advance the FP64 method `steps` steps, with `mlp` for the two-body term
-    when given.  Returns (final state, learned report or None)."""
+def run(prob, f0, steps, mlp=None, judge_every=0, tol=1e30, precision=w2.W2_F64):
+    """Advance the FP64 method (W2_F64 or W2_F64_SLICED) `steps` steps, with
+    `mlp` for the two-body term when given.  Returns (final state, learned
+    report or None)."""
     torch = _torch()
-    ctx = w2.Context.from_problem(prob)
+    ctx = w2.Context.from_problem(prob, precision=precision)
     ctx.set_state(torch.from_numpy(np.ascontiguousarray(f0, dtype=np.float64)).cuda())
     if mlp is not None:
         ctx.attach_learned(mlp, judge_every, tol)

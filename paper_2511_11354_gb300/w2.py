@@ -29,6 +29,7 @@ STATUS = {0: "W2_OK", -1: "W2_ERR_ARG", -2: "W2_ERR_CUDA", -3: "W2_ERR_OOM", -4:
 
 EXPORTS = ("w2_create", "w2_set_potentials", "w2_set_state", "w2_get_state", "w2_step",
            "w2_step_profile", "w2_observables", "w2_theta", "w2_advect", "w2_destroy", "w2_status_string",
+           "w2_last_cuda_error",
            "w2_batch_create", "w2_batch_set_potentials", "w2_batch_set_state", "w2_batch_get_state",
            "w2_batch_observables", "w2_batch_step", "w2_batch_autotune", "w2_batch_destroy",
            "w2_mlp_create", "w2_mlp_param_count", "w2_mlp_input_dim", "w2_mlp_set_params", "w2_mlp_get_params",
@@ -110,8 +111,9 @@ def load(path: str = LIB_PATH):
     lib.w2_learned_report.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), dp]
     lib.w2_status_string.argtypes = [ctypes.c_int]
     lib.w2_status_string.restype = ctypes.c_char_p
+    lib.w2_last_cuda_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("w2_destroy", "w2_status_string", "w2_batch_destroy", "w2_mlp_destroy",
+        if name not in ("w2_destroy", "w2_status_string", "w2_last_cuda_error", "w2_batch_destroy", "w2_mlp_destroy",
                         "w2_mlp_param_count", "w2_mlp_input_dim"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -120,6 +122,8 @@ def load(path: str = LIB_PATH):
 
 def _check(code: int, what: str):
     if code != 0:
+        if code == -2:  # W2_ERR_CUDA: name the CUDA error behind it
+            what = f"{what} ({load().w2_last_cuda_error().decode()})"
         raise W2Error(code, what)
 
 

@@ -97,3 +97,62 @@ def test_trained_network_beats_dropping_the_two_body_term():
     assert rep["judged"] == 2 and rep["active"], rep
     assert rep["last_err"] < 0.5, rep
     assert e_net < 0.5 * e_nopair, (e_net, e_nopair)
+
+
+def test_feature_rows_match_their_definition():
+    """Input rows of the network (w2_features): the scaled block, the scaled
+    reduced one-body function at x1 and at x2, and eight harmonics of the pair
+    distance, each within BF16 rounding of its definition."""
+    from paper_2511_11354_gb300 import w2
+    prob, f0 = inputs.workload_dwell(nx=8, nk=16)
+    nx, nk, P = prob.nx, prob.nk, prob.nk * prob.nk
+    ctx = w2.Context.from_problem(prob)
+    mlp = w2.MLP(nk, 32, max_rows=64)
+    mlp.set_scales(2.0, 3.0, 1.0)
+    pts = [0, 5, 17, 63]
+    xs = torch.tensor(pts, dtype=torch.int32, device="cuda")
+    X = torch.empty(len(pts), mlp.din, dtype=torch.bfloat16, device="cuda")
+    ctx.features(mlp, torch.from_numpy(f0).cuda(), xs, X)
+    got = X.float().cpu().numpy()
+    f1 = f0.sum(axis=(1, 3)) * prob.dx * prob.dp  # [x1][p1]
+    for r, Xi in enumerate(pts):
+        i1, i2 = divmod(Xi, nx)
+        want = np.zeros(mlp.din)
+        want[:P] = 2.0 * f0[i1, i2].ravel()
+        want[P:P + nk] = 3.0 * f1[i1]
+        want[P + nk:P + 2 * nk] = 3.0 * f1[i2]
+        for m in range(1, 9):
+            u = 2 * np.pi * m * (i1 - i2) / nx
+            want[P + 2 * nk + 2 * (m - 1)] = np.sin(u)
+            want[P + 2 * nk + 2 * (m - 1) + 1] = np.cos(u)
+        assert np.all(np.abs(got[r] - want) <= 2.0 ** -8 * np.abs(want) + 1e-6), r
+
+
+@pytest.mark.parametrize("nk,hidden,rows", [(8, 32, 200), (16, 64, 300), (64, 256, 4096)])
+def test_inference_forward_matches_reference(nk, hidden, rows):
+    """The inference forward (pipelined BF16 GEMMs with fused bias/SiLU
+    epilogues) against the FP64 reference network with the same BF16
+    roundings: BF16 weights and inputs, hidden activations rounded to BF16
+    between layers.  The shapes cover ragged row and column tiles, a K tail
+    below one 32-wide step and the timed size."""
+    from paper_2511_11354_gb300 import w2
+    m = w2.MLP(nk, hidden, max_rows=rows)
+    rng = np.random.default_rng(nk)
+    p = (rng.standard_normal(m.nparams) * 0.2).astype(np.float32)
+    m.set_params(p)
+    x = (rng.standard_normal((rows, m.din)) * 0.5).astype(np.float32)
+    xb = torch.from_numpy(x).to(torch.bfloat16).cuda()
+    y = torch.empty(rows, nk * nk, dtype=torch.float32, device="cuda")
+    m.forward(xb, y)
+    got = y.cpu().numpy().astype(np.float64)
+    pr = p.astype(np.float64).copy()
+    for name, off, shape in m.layout():
+        if name.startswith("W"):
+            n = int(np.prod(shape))
+            pr[off:off + n] = _bf16_round(p[off:off + n])
+    a = _bf16_round(x).astype(np.float64)
+    for l, (W, b) in enumerate(mlp_ref.unpack(pr, m.din, hidden, nk * nk)):
+        z = a @ W + b
+        a = _bf16_round(mlp_ref.silu(z)).astype(np.float64) if l < 3 else z
+    err = np.linalg.norm(got - a) / np.linalg.norm(a)
+    assert err < 5e-3, err

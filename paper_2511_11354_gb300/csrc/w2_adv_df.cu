@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(TWO ? 2 * NK : NK) k_adv_df(AdvDFArgs a) {
   const int n1 = blockIdx.x, fixed = blockIdx.y;
   const int t = TWO ? (int)(threadIdx.x >> 1) : (int)threadIdx.x;  // column n2
   const int r = TWO ? (int)(threadIdx.x & 1) : 0;                  // array
-  float2 *A = smf + (size_t)r * nx * S;
+  float2 *A = smf + (size_t)r * (nx * S + 8);  // second buffer skewed by 16 banks (lanes 2c, 2c+1 differ)
   const void *in = r ? a.in1 : a.in0;
   const size_t lineStride = (DIR == 0) ? (size_t)NK * NK : (size_t)nx * NK * NK;
   const size_t base = (DIR == 0) ? ((size_t)fixed * nx * NK + n1) * NK : ((size_t)fixed * NK + n1) * NK;
@@ -235,7 +235,7 @@ cudaError_t prep_adv_df() {
 template <int NK>
 cudaError_t run_adv_df(int dir, int two, const AdvDFArgs &a, cudaStream_t s) {
   dim3 grid(NK, a.nx), block(two ? 2 * NK : NK);
-  const size_t smem = sizeof(float2) * (size_t)(two ? 2 : 1) * a.nx * (NK + 1);
+  const size_t smem = sizeof(float2) * ((size_t)(two ? 2 : 1) * a.nx * (NK + 1) + 8);
   if (dir == 0 && !two) k_adv_df<NK, 0, 0><<<grid, block, smem, s>>>(a);
   if (dir == 0 && two) k_adv_df<NK, 0, 1><<<grid, block, smem, s>>>(a);
   if (dir == 1 && !two) k_adv_df<NK, 1, 0><<<grid, block, smem, s>>>(a);

@@ -196,6 +196,16 @@ def bench_forms(args, barrier):
     }
     ctx.close()
     torch.cuda.empty_cache()
+    # the same form on the 64^4 workload of the FP64 headline (same grid, same physics)
+    p64, f64 = inputs.workload_dwell()
+    c64 = w2.Context.from_problem(p64, precision=w2.W2_F32_TF32X3)
+    c64.set_state(torch.from_numpy(f64.astype(np.float32)).cuda())
+    c64.step(args.warmup)
+    k64 = max(k, 20)
+    ms64 = timed(c64.step, k64)
+    forms["precision_tf32x3"]["on_64^4"] = {"value": p64.points * k64 / (ms64 / 1e3), "unit": UNIT, "steps": k64,
+                                             "ms_per_step": ms64 / k64}
+    c64.close()
     # its error against the FP64 path on the 64^4 workload after 200 steps
     if not args.no_form_error:
         p64, f64 = inputs.workload_dwell()

@@ -56,6 +56,7 @@ def _load():
             lib.orc_step.restype = ctypes.c_int
             lib.orc_observables.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp]
             lib.orc_threads.restype = ctypes.c_int
+            lib.orc_set_hartree_poisson.argtypes = [ctypes.c_void_p]
             _lib = lib
     return _lib
 
@@ -82,6 +83,8 @@ class Oracle:
             raise ValueError("oracle rejected the problem description")
         self.h = ctypes.c_void_p(h)
         self.shape = (prob.nx, prob.nx, prob.nk, prob.nk)
+        if getattr(prob, "hartree", "pair") == "poisson":
+            self.lib.orc_set_hartree_poisson(self.h)
 
     def __del__(self):
         h = getattr(self, "h", None)

@@ -34,6 +34,8 @@
  *   R8 Lawson: the HXC potential of each Theta is built from that Theta's
  *      input (f^n for the predictor, f~ for the corrector).
  *   R12 entropy: linear entropy 1 - Tr rho1^2, Tr rho1^2 = 2 pi hbar sum f1^2 dx dp.
+ *   R15 neutralised Poisson Hartree (plasma workloads): the N_x-point Fourier
+ *      solution of -V'' = n - mean(n), Nyquist mode as its cosine half.
  *
  * Layout of every phase-space array: f[i1][i2][n1][n2], n2 fastest, double.
  * "parity pinned": every function here is checked by tests/test_oracle_*.py
@@ -61,6 +63,8 @@ typedef struct orc_problem {
   double *vext_fine;      /* [nx][M]: V_ext(fold(x_i + l h'))            */
   double *vext_grid;      /* [nx]   : V_ext(x_i)                          */
   double *w_shift;        /* [nx][M]: W(fold(d dx + l h')), d = 0..nx-1   */
+  int hartree_kind;       /* 0: gamma dx sum_q W n (R6); 1: neutralised periodic Poisson (R15) */
+  double *h_shift;        /* [nx][M]: G(d dx + l h'), the Poisson kernel (hartree_kind 1) */
   double *ainv;           /* [(nx+3)^2]: inverse of A_per                 */
 } orc_problem;
 
@@ -165,7 +169,7 @@ static void spline_shift_line(const orc_problem *P, int N, double h, const doubl
 
 void orc_destroy(orc_problem *P) {
   if (!P) return;
-  free(P->vext_fine); free(P->vext_grid); free(P->w_shift); free(P->ainv);
+  free(P->vext_fine); free(P->vext_grid); free(P->w_shift); free(P->ainv); free(P->h_shift);
   free(P);
 }
 
@@ -252,7 +256,15 @@ void orc_potential_fine(const orc_problem *P, const double *n, double *out) {
   for (int i = 0; i < nx; ++i)
     for (int l = 0; l < M; ++l) {
       double u = P->vext_fine[i * M + l];
-      if (P->c_h != 0.0 && n) {
+      if (P->c_h != 0.0 && n && P->hartree_kind == 1) {
+        /* neutralised Poisson (R15): V_H(y) = sum_q G(y - x_q) n(x_q) */
+        double vh = 0.0;
+        for (int q = 0; q < nx; ++q) {
+          int d = ((i - q) % nx + nx) % nx;
+          vh += P->h_shift[d * M + l] * n[q];
+        }
+        u += P->c_h * vh;
+      } else if (P->c_h != 0.0 && n) {
         /* V_H(y) = gamma dx sum_q W(fold(y - x_q)) n(x_q), y = x_i + l h';
          * y - x_q = (i - q) dx + l h' */
         double vh = 0.0;
@@ -524,14 +536,16 @@ void orc_observables(const orc_problem *P, const double *f, double *obs, double 
   orc_marginals(P, f, na, nb);
   double eh = 0.0;
   if (P->c_h != 0.0) {
+    const double *ker = P->hartree_kind == 1 ? P->h_shift : P->w_shift;
+    const double fac = P->hartree_kind == 1 ? 1.0 : P->gamma * P->dx;
     for (int i = 0; i < nx; ++i) {
       double va = 0.0, vb = 0.0;
       for (int q = 0; q < nx; ++q) {
         int d = ((i - q) % nx + nx) % nx;
-        va += P->w_shift[d * M + 0] * na[q];
-        vb += P->w_shift[d * M + 0] * nb[q];
+        va += ker[d * M + 0] * na[q];
+        vb += ker[d * M + 0] * nb[q];
       }
-      eh += 0.5 * P->c_h * P->gamma * P->dx * (va * na[i] + vb * nb[i]) * P->dx;
+      eh += 0.5 * P->c_h * fac * (va * na[i] + vb * nb[i]) * P->dx;
     }
   }
   double pur = 0.0;
@@ -540,6 +554,34 @@ void orc_observables(const orc_problem *P, const double *f, double *obs, double 
   obs[0] = mass; obs[1] = ekin + epot + eh; obs[2] = pur; obs[3] = 1.0 - pur; obs[4] = sqrt(l2);
   if (n1out) for (int i = 0; i < nx; ++i) n1out[i] = na[i];
   free(f1); free(na); free(nb);
+}
+
+/* Neutralised periodic Poisson Hartree term (the 1-D Coulomb example of
+ * Sec. 2.3 with an ion background that cancels the zero mode):
+ *   -V_H'' = n - mean(n),  V_H(y) = sum_{m != 0} a_m e^{i k_m y} / k_m^2,
+ *   k_m = 2 pi m / L,  a_m = (1/N_x) sum_q n(x_q) e^{-i k_m x_q},
+ * the N_x-point series with, for even N_x, the Nyquist mode m = N_x/2 taken
+ * as its cosine half (reading R15).  As a convolution:
+ *   V_H(y) = sum_q G(y - x_q) n(x_q),
+ *   G(r) = (1/N_x) [ 2 sum_{0 < m < N_x/2} cos(k_m r) / k_m^2 + cos(k_{N_x/2} r) / k_{N_x/2}^2 ].
+ * Sets G on the fine points d dx + l h' and switches the Hartree term to it. */
+void orc_set_hartree_poisson(orc_problem *P) {
+  int nx = P->nx, M = P->M;
+  if (!P->h_shift) P->h_shift = (double *)malloc(sizeof(double) * nx * M);
+  for (int d = 0; d < nx; ++d)
+    for (int l = 0; l < M; ++l) {
+      double r = d * P->dx + l * P->hp, g = 0.0;
+      for (int m = 1; 2 * m < nx; ++m) {
+        double k = 2.0 * ORC_PI * m / P->L;
+        g += 2.0 * cos(k * r) / (k * k);
+      }
+      if (nx % 2 == 0) {
+        double k = ORC_PI * nx / P->L;
+        g += cos(k * r) / (k * k);
+      }
+      P->h_shift[d * M + l] = g / nx;
+    }
+  P->hartree_kind = 1;
 }
 
 int orc_threads(void) {

@@ -111,6 +111,7 @@ class Problem:
     xc_kind: int = 0          # 0 none, 1 phi(n) = n, 2 Hedin-Lundqvist
     hbar: float = 1.0
     mass: float = 1.0
+    hartree: str = "pair"     # "pair": gamma dx sum W n; "poisson": neutralised periodic Poisson
     name: str = ""
     meta: dict = field(default_factory=dict)
 
@@ -245,3 +246,49 @@ def workload_batch(n: int = 64, seed: int = 3):
         probs.append(prob)
         states.append(initial_state(prob, centres=draw_centres(seed * 1000 + i), seed=seed * 1000 + i))
     return probs, states
+
+
+# ---------------------------------------------------------------------------
+# Periodic plasma workloads (the quantum Landau damping and two-stream
+# examples): box [-5 pi, 5 pi)^2, momentum spacing 0.1 (= pi hbar / L),
+# Hartree from the neutralised periodic Poisson equation, Hedin-Lundqvist
+# XC, smoothed Coulomb pair 1/sqrt(r^2 + soft), dt = 0.01.  The paper's mesh
+# is 257^2 x 128^2 with the endpoint; the periodic grid drops it: 256^2 x 128^2.
+# ---------------------------------------------------------------------------
+
+PLASMA_L = 10.0 * math.pi
+PLASMA_K = 0.4
+
+
+def plasma_problem(kind: str = "landau", nx: int = 256, nk: int = 128, soft: float = 1.0, xc: bool = True,
+                   two_body: bool = True) -> Problem:
+    if kind not in ("landau", "two_stream"):
+        raise ValueError(kind)
+    return Problem(nx=nx, nk=nk, L=PLASMA_L, dt=0.01, vext=zero_potential(), vee=soft_coulomb(soft),
+                   gamma=1.0 if two_body else 0.0, c_hartree=1.0, c_xc=1.0 if xc else 0.0, xc_kind=2 if xc else 0,
+                   hartree="poisson", name=f"plasma_{kind}", meta={"eps": 0.1 if kind == "landau" else 0.02})
+
+
+def plasma_factors(prob: Problem, kind: str, eps: float | None = None):
+    """The separable initial 2-RDM f = a(x1) a(x2) b(p1) b(p2) of the plasma
+    examples: a = 1 + eps cos(0.4 x); Landau: b = exp(-p^2/2) / sqrt(2 pi);
+    two-stream: b = (1 + 5 p^2) exp(-p^2/2) / (6 sqrt(2 pi))."""
+    eps = prob.meta.get("eps", 0.1) if eps is None else eps
+    a = 1.0 + eps * np.cos(PLASMA_K * prob.x())
+    p = prob.p()
+    if kind == "landau":
+        b = np.exp(-0.5 * p * p) / math.sqrt(2.0 * math.pi)
+    else:
+        b = (1.0 + 5.0 * p * p) * np.exp(-0.5 * p * p) / (6.0 * math.sqrt(2.0 * math.pi))
+    return a, b
+
+
+def workload_plasma(kind: str = "landau", nx: int = 256, nk: int = 128, soft: float = 1.0, xc: bool = True,
+                    two_body: bool = True, eps: float | None = None, dtype=np.float64):
+    """(problem, initial state) of a plasma example (host array; for the full
+    256^2 x 128^2 mesh build the state from plasma_factors on the device)."""
+    prob = plasma_problem(kind, nx, nk, soft, xc, two_body)
+    a, b = plasma_factors(prob, kind, eps)
+    f = (a[:, None, None, None] * a[None, :, None, None] * b[None, None, :, None] * b[None, None, None, :])
+    return prob, np.ascontiguousarray(f, dtype=dtype)
+

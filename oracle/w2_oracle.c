@@ -228,15 +228,24 @@ void orc_marginals(const orc_problem *P, const double *f, double *n1, double *n2
 }
 
 /* Trigonometric interpolant of the grid density n at y (Nyquist mode halved). */
-static double trig_interp(const orc_problem *P, const double *n, double y) {
+/* Fourier coefficients c_m = (1/N) sum_q n_q e^{-2 pi i m q / N}, m = -N/2..N/2
+ * (index m + N/2), of the grid samples n_q = n(x_q) */
+static void trig_coeffs(const orc_problem *P, const double *n, double complex *c) {
+  int N = P->nx;
+  for (int m = -N / 2; m <= N / 2; ++m) {
+    double complex s = 0.0;
+    for (int q = 0; q < N; ++q) s += n[q] * cexp(-2.0 * I * ORC_PI * m * q / N);
+    c[m + N / 2] = s / N;
+  }
+}
+
+/* The trigonometric interpolant of the samples at y (Nyquist terms halved). */
+static double trig_eval(const orc_problem *P, const double complex *c, double y) {
   int N = P->nx;
   double x0 = -0.5 * P->L, val = 0.0;
   for (int m = -N / 2; m <= N / 2; ++m) {
-    double complex c = 0.0;
-    for (int q = 0; q < N; ++q) c += n[q] * cexp(-2.0 * I * ORC_PI * m * q / N);
-    c /= N;
     double wgt = (N % 2 == 0 && (m == N / 2 || m == -N / 2)) ? 0.5 : 1.0;
-    val += wgt * creal(c * cexp(2.0 * I * ORC_PI * m * (y - x0) / P->L));
+    val += wgt * creal(c[m + N / 2] * cexp(2.0 * I * ORC_PI * m * (y - x0) / P->L));
   }
   return val;
 }
@@ -253,6 +262,11 @@ static double phi_xc(int kind, double n) {
  * V_HXC; readings R6, R7).  out is [nx][M]. */
 void orc_potential_fine(const orc_problem *P, const double *n, double *out) {
   int nx = P->nx, M = P->M;
+  double complex *tc = NULL;
+  if (P->c_xc != 0.0 && P->xc_kind && n) {
+    tc = (double complex *)malloc(sizeof(double complex) * (nx + 1));
+    trig_coeffs(P, n, tc);
+  }
   for (int i = 0; i < nx; ++i)
     for (int l = 0; l < M; ++l) {
       double u = P->vext_fine[i * M + l];
@@ -276,10 +290,11 @@ void orc_potential_fine(const orc_problem *P, const double *n, double *out) {
       }
       if (P->c_xc != 0.0 && P->xc_kind && n) {
         double y = -0.5 * P->L + i * P->dx + l * P->hp;
-        u += P->c_xc * phi_xc(P->xc_kind, trig_interp(P, n, y));
+        u += P->c_xc * phi_xc(P->xc_kind, trig_eval(P, tc, y));
       }
       out[i * M + l] = u;
     }
+  free(tc);
 }
 
 /* Fourier modes of a periodic function from its M samples u(y + l h'),

@@ -79,6 +79,14 @@ typedef enum {
 } w2_precision;
 
 typedef enum {
+  W2_HARTREE_PAIR = 0,     /* V_H[n](x) = gamma dx sum_q W(fold(x - x_q)) n(x_q): the pair
+                              kernel of w2_set_potentials (the default)                   */
+  W2_HARTREE_POISSON = 1   /* neutralised periodic Poisson (the 1-D Coulomb example of
+                              Sec. 2.3 under an ion background): -V_H'' = n - mean(n),
+                              the N_x-point Fourier solution, Nyquist mode as its cosine  */
+} w2_hartree_kind;
+
+typedef enum {
   W2_XC_NONE = 0,       /* no exchange-correlation term                           */
   W2_XC_LINEAR = 1,     /* phi(n) = n (the exchange test potential of Sec. 5.1.1) */
   W2_XC_HEDIN_LUNDQVIST = 2  /* phi(n) = 0.985 c + 0.985*0.034 ln(1 + 18.37 c), c = max(n,0)^{1/3}:
@@ -86,7 +94,8 @@ typedef enum {
 } w2_xc_kind;
 
 /* Problem description (Sec. 3.1 grid; Sec. 5 uses hbar = m = 1).
- *   nx  : spatial points per particle, 4 <= nx; FP64 supports nx <= 128
+ *   nx  : spatial points per particle, 4 <= nx; FP64 supports nx <= 128,
+ *         W2_F32_TF32X3 nx <= 256
  *   nk  : momentum points per particle; W2_F64 supports nk in {8,16,...,64},
  *         W2_F64_SLICED nk in {16,32,48,64}, W2_F32_TF32X3 nk in {16,32,...,128}
  *   L   : period of the box (> 0); dt: time step tau (> 0)
@@ -141,6 +150,17 @@ w2_status w2_create(const w2_config *cfg, void *cuda_stream, w2_ctx **out);
  * Hartree bound assumes unit mass), W2_ERR_CUDA. */
 w2_status w2_set_potentials(w2_ctx *ctx, w2_fn vext, void *ue, w2_fn vee, void *ui,
                             double gamma, double c_hartree, double c_xc);
+
+/* Choose how the Hartree potential (weight c_hartree) is formed: kind is a
+ * w2_hartree_kind.  W2_HARTREE_POISSON (the plasma examples, Sec. 5.2) solves
+ *   -V_H'' = n - mean(n),  V_H(y) = sum_q G(y - x_q) n(x_q),
+ *   G(r) = (1/N_x) [2 sum_{0 < m < N_x/2} cos(k_m r)/k_m^2 + cos(k_{N_x/2} r)/k_{N_x/2}^2],
+ * k_m = 2 pi m / L (the last term for even N_x only); the energy's Hartree
+ * term uses the same kernel.  May be called before or after
+ * w2_set_potentials; the stability precheck of w2_set_potentials leaves the
+ * Poisson term out (it depends on the state).  Errors: W2_ERR_ARG,
+ * W2_ERR_OOM, W2_ERR_CUDA. */
+w2_status w2_set_hartree(w2_ctx *ctx, int32_t kind);
 
 /* Copy a full state f[nx][nx][nk][nk] (element type of the precision) into the context: from device
  * memory when on_device != 0, else from host memory.  Resets the step count.

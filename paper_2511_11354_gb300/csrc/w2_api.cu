@@ -45,7 +45,7 @@ static cudaError_t theta64(const w2_ctx *ctx, int mode, const ThetaArgs &th, cud
 static void free_all(w2_ctx *c) {
   void *ptrs[] = {c->f, c->g, c->t1, c->t2, c->xsum, c->xsum2, c->K, c->K12, c->vext_fine, c->w_fine,
                   c->d_fine, c->sintab, c->vext_grid, c->k0tab, c->wtab, c->xpart, c->obs_out,
-                  c->wtab32, c->ctab32, c->wdf, c->zpow};
+                  c->wtab32, c->ctab32, c->wdf, c->zpow, c->h_fine};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_obs) cudaFreeHost(c->h_obs);
@@ -115,7 +115,7 @@ extern "C" w2_status w2_create(const w2_config *cfg, void *cuda_stream, w2_ctx *
     return W2_ERR_UNSUPPORTED;
   if (cfg->precision == W2_F64 && (!nk_supported_f64(cfg->nk) || cfg->nx > 128)) return W2_ERR_UNSUPPORTED;
   if (cfg->precision == W2_F64_SLICED && (!nk_supported_f64s(cfg->nk) || cfg->nx > 128)) return W2_ERR_UNSUPPORTED;
-  if (cfg->precision == W2_F32_TF32X3 && (!nk_supported_f32(cfg->nk) || cfg->nx > 128)) return W2_ERR_UNSUPPORTED;
+  if (cfg->precision == W2_F32_TF32X3 && (!nk_supported_f32(cfg->nk) || cfg->nx > 256)) return W2_ERR_UNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return W2_ERR_CUDA;
   cudaDeviceProp prop;
@@ -233,7 +233,42 @@ TabArgs w2::tab_args(w2_ctx *ctx, const double *xsum, int pair_mode) {
   a.d_fine = ctx->d_fine;
   a.sintab = ctx->sintab;
   a.K = pair_mode ? ctx->K12 : ctx->K;
+  a.h_fine = ctx->hartree_kind == W2_HARTREE_POISSON ? ctx->h_fine : nullptr;
   return a;
+}
+
+extern "C" w2_status w2_set_hartree(w2_ctx *ctx, int32_t kind) {
+  if (!ctx || (kind != W2_HARTREE_PAIR && kind != W2_HARTREE_POISSON)) return W2_ERR_ARG;
+  if (ctx->sticky) return ctx->sticky;
+  const int nx = ctx->nx, M = ctx->M;
+  if (kind == W2_HARTREE_POISSON) {
+    // G(r) = (1/N_x) [2 sum_{0 < m < N_x/2} cos(k_m r)/k_m^2 + cos(k_{N_x/2} r)/k_{N_x/2}^2 (N_x even)],
+    // k_m = 2 pi m / L, at r = d dx + l h'
+    std::vector<double> g((size_t)nx * M);
+    const double L = ctx->cfg.L;
+    for (int d = 0; d < nx; ++d)
+      for (int l = 0; l < M; ++l) {
+        const double r = d * ctx->dx + l * ctx->hp;
+        double v = 0.0;
+        for (int m = 1; 2 * m < nx; ++m) {
+          const double k = 2.0 * M_PI * m / L;
+          v += 2.0 * cos(k * r) / (k * k);
+        }
+        if (nx % 2 == 0) {
+          const double k = M_PI * nx / L;
+          v += cos(k * r) / (k * k);
+        }
+        g[(size_t)d * M + l] = v / nx;
+      }
+    if (!ctx->h_fine && cudaMalloc((void **)&ctx->h_fine, sizeof(double) * nx * M) != cudaSuccess) return W2_ERR_OOM;
+    W2_TRY(cudaMemcpy(ctx->h_fine, g.data(), sizeof(double) * nx * M, cudaMemcpyHostToDevice));
+  }
+  ctx->hartree_kind = kind;
+  if (ctx->graph_ready) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph_ready = false;
+  }
+  return W2_OK;
 }
 
 extern "C" w2_status w2_set_potentials(w2_ctx *ctx, w2_fn vext, void *ue, w2_fn vee, void *ui, double gamma,
@@ -276,7 +311,9 @@ extern "C" w2_status w2_set_potentials(w2_ctx *ctx, w2_fn vext, void *ue, w2_fn 
     wmin = fmin(wmin, wf[k]);
     wmax = fmax(wmax, wf[k]);
   }
-  const double hart = 2.0 * fabs(c_hartree) * fabs(gamma) * (wmax - wmin);
+  // (the neutralised Poisson Hartree term depends on the state's density and
+  // has no a-priori bound here; it is left out of the precheck)
+  const double hart = ctx->hartree_kind == W2_HARTREE_POISSON ? 0.0 : 2.0 * fabs(c_hartree) * fabs(gamma) * (wmax - wmin);
   const double y = ctx->tau / ctx->cfg.hbar * (2.0 * dvmax + dwmax + hart);
   if (!(y <= 1.0)) return W2_ERR_UNSTABLE;
 
@@ -596,6 +633,7 @@ extern "C" w2_status w2_observables(w2_ctx *ctx, w2_obs *out, double *n1, double
   a.f32 = f64_state(ctx->prec) ? nullptr : (const float *)ctx->f;
   a.vext_grid = ctx->vext_grid;
   a.w_fine = ctx->w_fine;
+  a.h_fine = ctx->hartree_kind == W2_HARTREE_POISSON ? ctx->h_fine : nullptr;
   a.xpart = ctx->xpart;
   a.out = ctx->obs_out;
   W2_TRY(launch_obs(a, ctx->stream));

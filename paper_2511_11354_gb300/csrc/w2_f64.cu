@@ -62,13 +62,14 @@ __device__ __noinline__ void tables_block(const TabArgs &a, const int i, const i
     } else {
       u = a.vext_fine[(size_t)i * M + l];
       if (mf && a.c_h != 0.0) {
+        const double *ker = a.h_fine ? a.h_fine : a.w_fine;  // Poisson kernel, or W scaled below
         double vh = 0.0;
         for (int q = 0; q < nx; ++q) {
           int d = i - q;
           d += (d < 0) ? nx : 0;
-          vh += a.w_fine[(size_t)d * M + l] * n[q];
+          vh += ker[(size_t)d * M + l] * n[q];
         }
-        u += a.c_h * a.gamma * a.dx * vh;
+        u += a.c_h * (a.h_fine ? 1.0 : a.gamma * a.dx) * vh;
       }
       if (mf && a.c_xc != 0.0 && a.xc_kind) {
         double ni = 0.0;

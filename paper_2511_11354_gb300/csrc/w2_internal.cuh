@@ -23,6 +23,8 @@ struct TabArgs {
   const double *d_fine;     // [nx][M] trigonometric interpolation weights (xc only)
   const double *sintab;     // [M] sin(pi m / nk)
   double *K;                // pair_mode 0: [2][nx][2nk-1]; pair_mode 1: [nx][2nk-1]
+  const double *h_fine = nullptr;  // [nx][M] Hartree kernel G(d dx + l h') (neutralised Poisson);
+                                   // null: gamma dx W (w_fine)
 };
 
 struct ThetaArgs {
@@ -68,6 +70,7 @@ struct ObsArgs {
   const double *w_fine;     // [nx][M]; column 0 is W(fold(d dx))
   double *xpart;            // [nx*nx][3 + nk] per-X partials
   double *out;              // [8 + nx + nx*nx]
+  const double *h_fine = nullptr;  // as in TabArgs (column 0: the kernel at grid distances)
 };
 
 struct Theta32Args {
@@ -208,6 +211,8 @@ struct w2_ctx {
   int *k0tab;
   double *wtab;
   float2 *wdf, *zpow;        // double-float shift weights [nk][4] and z^k [32] (sliced path)
+  int hartree_kind;          // W2_HARTREE_PAIR or W2_HARTREE_POISSON
+  double *h_fine;            // [nx][M] Poisson Hartree kernel (W2_HARTREE_POISSON), else null
   float *wtab32, *ctab32;    // FP32 shift weights and merged increment taps
   double *xpart, *obs_out, *h_obs;
   double z, zscale;

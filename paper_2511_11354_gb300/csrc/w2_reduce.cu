@@ -222,10 +222,10 @@ __global__ void k_obs_final(ObsArgs a) {
       for (int q = 0; q < nx; ++q) {
         int d = i - q;
         d += (d < 0) ? nx : 0;
-        va += a.w_fine[(size_t)d * M] * n1[q];
-        vb += a.w_fine[(size_t)d * M] * n2[q];
+        va += (a.h_fine ? a.h_fine : a.w_fine)[(size_t)d * M] * n1[q];
+        vb += (a.h_fine ? a.h_fine : a.w_fine)[(size_t)d * M] * n2[q];
       }
-      eh += 0.5 * a.c_h * a.gamma * a.dx * (va * n1[i] + vb * n2[i]) * a.dx;
+      eh += 0.5 * a.c_h * (a.h_fine ? 1.0 : a.gamma * a.dx) * (va * n1[i] + vb * n2[i]) * a.dx;
     }
   }
   for (int e = tid; e < nx * nk; e += nt) {

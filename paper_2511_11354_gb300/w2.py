@@ -22,6 +22,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libw2.so")
 W2_F64 = 0
 W2_F32_TF32X3 = 1
 W2_F64_SLICED = 3
+W2_HARTREE_PAIR = 0
+W2_HARTREE_POISSON = 1
 F64_STATE = (W2_F64, W2_F64_SLICED)
 
 STATUS = {0: "W2_OK", -1: "W2_ERR_ARG", -2: "W2_ERR_CUDA", -3: "W2_ERR_OOM", -4: "W2_ERR_STATE",
@@ -29,7 +31,7 @@ STATUS = {0: "W2_OK", -1: "W2_ERR_ARG", -2: "W2_ERR_CUDA", -3: "W2_ERR_OOM", -4:
 
 EXPORTS = ("w2_create", "w2_set_potentials", "w2_set_state", "w2_get_state", "w2_step",
            "w2_step_profile", "w2_observables", "w2_theta", "w2_advect", "w2_destroy", "w2_status_string",
-           "w2_last_cuda_error",
+           "w2_last_cuda_error", "w2_set_hartree",
            "w2_batch_create", "w2_batch_set_potentials", "w2_batch_set_state", "w2_batch_get_state",
            "w2_batch_observables", "w2_batch_step", "w2_batch_autotune", "w2_batch_destroy",
            "w2_mlp_create", "w2_mlp_param_count", "w2_mlp_input_dim", "w2_mlp_set_params", "w2_mlp_get_params",
@@ -174,8 +176,13 @@ class Context:
     @classmethod
     def from_problem(cls, prob, stream=None, precision=W2_F64):
         ctx = cls(prob.nx, prob.nk, prob.L, prob.dt, prob.hbar, prob.mass, prob.xc_kind, stream, precision)
+        if getattr(prob, "hartree", "pair") == "poisson":
+            ctx.set_hartree(W2_HARTREE_POISSON)
         ctx.set_potentials(prob.vext, prob.vee, prob.gamma, prob.c_hartree, prob.c_xc)
         return ctx
+
+    def set_hartree(self, kind):
+        _check(self.lib.w2_set_hartree(self.h, int(kind)), "w2_set_hartree")
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

@@ -24,7 +24,7 @@ struct Class {  // instances sharing one momentum size
   int *d_inst = nullptr, *d_off_x = nullptr, *d_off_slab = nullptr;
   int items_x = 0, items_slab = 0;
   int grid_theta = 0, grid_adv0 = 0, grid_adv1 = 0;
-  int nxmax = 0;
+  int nxmax = 0, nxmin = 1 << 30;
 };
 
 }  // namespace
@@ -168,6 +168,7 @@ extern "C" w2_status w2_batch_create(const w2_config *cfgs, int32_t n, void *cud
     }
     b->cls[k].inst.push_back(i);
     b->cls[k].nxmax = std::max(b->cls[k].nxmax, c->nx);
+    b->cls[k].nxmin = std::min(b->cls[k].nxmin, c->nx);
   }
   b->items_x = off_x[n];
   b->items_tab = off_tab[n];
@@ -248,11 +249,11 @@ static cudaError_t enqueue_batch_step(w2_batch *b, cudaStream_t s) {
   }
   for (auto &c : b->cls) {
     BatchLaunch bl{c.grid_adv0, c.d_inst, c.d_off_slab, (int)c.inst.size()};
-    if ((e = launch_badv_f32(c.nk, 0, bl, b->d_adv, c.nxmax, s)) != cudaSuccess) return e;
+    if ((e = launch_badv_f32(c.nk, 0, bl, b->d_adv, c.nxmax, adv32_pieces(c.nxmax), s)) != cudaSuccess) return e;
   }
   for (auto &c : b->cls) {
     BatchLaunch bl{c.grid_adv1, c.d_inst, c.d_off_slab, (int)c.inst.size()};
-    if ((e = launch_badv_f32(c.nk, 1, bl, b->d_adv, c.nxmax, s)) != cudaSuccess) return e;
+    if ((e = launch_badv_f32(c.nk, 1, bl, b->d_adv, c.nxmax, adv32_pieces(c.nxmax), s)) != cudaSuccess) return e;
   }
   if ((e = launch_bxsum(b->d_xs_ft, b->d_off_x, b->n, b->grid_xsum, s)) != cudaSuccess) return e;
   if ((e = launch_btables(b->d_tab, b->d_off_tab, b->n, b->grid_tab, b->nxmax, b->mmax, s)) != cudaSuccess) return e;
@@ -381,7 +382,7 @@ extern "C" w2_status w2_batch_autotune(w2_batch *b, int32_t *grids_out, int32_t 
     pick = c.grid_adv0;
     for (int g : candidates(c.items_slab)) {
       BatchLaunch bl{g, c.d_inst, c.d_off_slab, m};
-      float t = time_best(s, [&] { return launch_badv_f32(c.nk, 0, bl, b->d_adv, c.nxmax, s); }, 2, &err);
+      float t = time_best(s, [&] { return launch_badv_f32(c.nk, 0, bl, b->d_adv, c.nxmax, adv32_pieces(c.nxmax), s); }, 2, &err);
       if (t < best) best = t, pick = g;
     }
     c.grid_adv0 = pick;
@@ -395,8 +396,8 @@ extern "C" w2_status w2_batch_autotune(w2_batch *b, int32_t *grids_out, int32_t 
       float t = time_best(
           s,
           [&] {
-            cudaError_t e0 = launch_badv_f32(c.nk, 0, b0, b->d_adv, c.nxmax, s);
-            return e0 != cudaSuccess ? e0 : launch_badv_f32(c.nk, 1, bl, b->d_adv, c.nxmax, s);
+            cudaError_t e0 = launch_badv_f32(c.nk, 0, b0, b->d_adv, c.nxmax, adv32_pieces(c.nxmax), s);
+            return e0 != cudaSuccess ? e0 : launch_badv_f32(c.nk, 1, bl, b->d_adv, c.nxmax, adv32_pieces(c.nxmax), s);
           },
           2, &err);
       if (t < best) best = t, pick = g;

@@ -293,6 +293,65 @@ __device__ __forceinline__ void spline_coeffs32(float *col, int stride, int n, f
   }
 }
 
+// The same solve on one or two strided columns (c1 may be null) by several
+// threads per column: each runs both recursions over its rows [lo, hi) (empty
+// for a thread without a piece), started from its own start sums (the same
+// periodic sums as above, at the piece's first / last row; with nterm < n
+// they drop |z|^nterm < 2^-24 of the tail).  Every thread of the CTA calls
+// this: it holds the CTA barriers between the phases.
+__device__ __forceinline__ void spline_coeffs32_chunked(float *c0, float *c1, int stride, int n, float z, float zscale,
+                                                        int nterm, int lo, int hi) {
+  const int nt = hi > lo ? nterm : 0;  // an empty piece reads nothing
+  float s0 = 0.f, s1 = 0.f, zk = 1.f;
+  for (int k = 0; k < nt; ++k) {
+    int idx = lo - k;
+    idx += (idx < 0) ? n : 0;
+    s0 = fmaf(zk, c0[idx * stride], s0);
+    if (c1) s1 = fmaf(zk, c1[idx * stride], s1);
+    zk *= z;
+  }
+  __syncthreads();  // every start sum has read the input line
+  if (hi > lo) {
+    float p0 = s0 * zscale, p1 = s1 * zscale;
+    c0[lo * stride] = p0;
+    if (c1) c1[lo * stride] = p1;
+    for (int i = lo + 1; i < hi; ++i) {
+      p0 = fmaf(z, p0, c0[i * stride]);
+      c0[i * stride] = p0;
+      if (c1) {
+        p1 = fmaf(z, p1, c1[i * stride]);
+        c1[i * stride] = p1;
+      }
+    }
+  }
+  __syncthreads();
+  const int e = hi - 1;
+  s0 = s1 = 0.f;
+  zk = 1.f;
+  for (int k = 0; k < nt; ++k) {
+    int idx = e + k;
+    idx -= (idx >= n) ? n : 0;
+    s0 = fmaf(zk, c0[idx * stride], s0);
+    if (c1) s1 = fmaf(zk, c1[idx * stride], s1);
+    zk *= z;
+  }
+  __syncthreads();  // every start sum has read the causal pass
+  if (hi > lo) {
+    float p0 = s0 * zscale, p1 = s1 * zscale;
+    c0[e * stride] = p0;
+    if (c1) c1[e * stride] = p1;
+    for (int i = e - 1; i >= lo; --i) {
+      p0 = fmaf(z, p0, c0[i * stride]);
+      c0[i * stride] = p0;
+      if (c1) {
+        p1 = fmaf(z, p1, c1[i * stride]);
+        c1[i * stride] = p1;
+      }
+    }
+  }
+  __syncthreads();
+}
+
 __device__ __forceinline__ int wrap(int j, int n) {
   j %= n;
   return j < 0 ? j + n : j;
@@ -381,7 +440,9 @@ __device__ __forceinline__ void stage_slab(float *slab, const float *src, size_t
 //   two arrays: d1 = (S1 - I) u, b = S1 g2, ft = u + d1 + tau b,
 //               dh = d2 + d1 + tau/2 b   (dh may overwrite d2 in place)
 //   one array : ft = u + d1  (= S1 S2 f)
-// A CTA owns columns [cb*C, cb*C + C) of the slab, one thread per column.
+// A CTA owns columns [cb*C, cb*C + C) of the slab with adv32_pieces(nx)
+// threads per column: thread t takes column t % C and the rows of piece t / C
+// (staging, the spline solve in pieces, the evaluation).
 template <int NK, int DIR>
 // compiled once (not inlined) so the single-problem and batched kernels
 // run the same machine code and give identical bits
@@ -389,17 +450,21 @@ __device__ __noinline__ void adv32_block(const Adv32Args &a, const int n1, const
                                          float *sm32) {
   constexpr int C = AdvCols<NK>::C;
   const int nx = a.nx;
-  const int t = threadIdx.x, col = cb * C + t;
+  // the pieces depend on nx only, so that every launch shape gives the same bits;
+  // threads beyond them idle (a batch launch is sized for its longest lines)
+  const int t = threadIdx.x % C, q = threadIdx.x / C, P = adv32_pieces(nx);
+  const int col = cb * C + t;
   const int rows = nx + 2 * kGhost;
+  const int lo = q < P ? (q * nx) / P : 0, hi = q < P ? ((q + 1) * nx) / P : 0;
   const size_t lineStride = (DIR == 0) ? (size_t)NK * NK : (size_t)nx * NK * NK;
   const size_t base = ((DIR == 0) ? ((size_t)fixed * nx * NK + n1) * NK : ((size_t)fixed * NK + n1) * NK) + cb * C;
   const int sidx = (DIR == 0) ? col : n1;
   const int k0 = a.k0tab[sidx];
   float w[4], ct[8];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) w[q] = a.wtab[4 * sidx + q];
+  for (int r = 0; r < 4; ++r) w[r] = a.wtab[4 * sidx + r];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) ct[q] = a.ctab[8 * sidx + q];
+  for (int r = 0; r < 8; ++r) ct[r] = a.ctab[8 * sidx + r];
   float *SA = sm32, *SB = sm32 + (size_t)rows * C, *SC = sm32 + 2 * (size_t)rows * C;
   float *A = SA + t, *B = SB + t, *Cc = SC + t;  // this thread's column
   if (DIR == 0) {
@@ -408,13 +473,13 @@ __device__ __noinline__ void adv32_block(const Adv32Args &a, const int n1, const
     if (two) stage_slab<C>(SB, a.g + base, lineStride, nx);
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-    spline_coeffs32(A + kGhost * C, C, nx, a.z, a.zscale, a.nterm);
-    fill_ghosts(A, C, nx);
-    if (two) {
-      spline_coeffs32(B + kGhost * C, C, nx, a.z, a.zscale, a.nterm);
-      fill_ghosts(B, C, nx);
+    spline_coeffs32_chunked(A + kGhost * C, two ? B + kGhost * C : nullptr, C, nx, a.z, a.zscale, a.nterm, lo, hi);
+    if (threadIdx.x < C) {
+      fill_ghosts(A, C, nx);
+      if (two) fill_ghosts(B, C, nx);
     }
-    for (int i = 0; i < nx; ++i) {
+    __syncthreads();
+    for (int i = lo; i < hi; ++i) {
       const size_t o = base + i * lineStride + t;
       a.d2[o] = incr32(A, C, nx, i, k0, w, ct, a.z);
       if (two) a.g2[o] = eval32(B, C, nx, i, k0, w);
@@ -426,14 +491,15 @@ __device__ __noinline__ void adv32_block(const Adv32Args &a, const int n1, const
     if (two) stage_slab<C>(SC, a.g2in + base, lineStride, nx);
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-    for (int i = 0; i < nx; ++i) A[(kGhost + i) * C] += B[(kGhost + i) * C];  // u = f + d2
-    spline_coeffs32(A + kGhost * C, C, nx, a.z, a.zscale, a.nterm);
-    fill_ghosts(A, C, nx);
-    if (two) {
-      spline_coeffs32(Cc + kGhost * C, C, nx, a.z, a.zscale, a.nterm);
-      fill_ghosts(Cc, C, nx);
+    for (int i = lo; i < hi; ++i) A[(kGhost + i) * C] += B[(kGhost + i) * C];  // u = f + d2
+    __syncthreads();
+    spline_coeffs32_chunked(A + kGhost * C, two ? Cc + kGhost * C : nullptr, C, nx, a.z, a.zscale, a.nterm, lo, hi);
+    if (threadIdx.x < C) {
+      fill_ghosts(A, C, nx);
+      if (two) fill_ghosts(Cc, C, nx);
     }
-    for (int i = 0; i < nx; ++i) {
+    __syncthreads();
+    for (int i = lo; i < hi; ++i) {
       const size_t o = base + i * lineStride + t;
       const float d1 = incr32(A, C, nx, i, k0, w, ct, a.z);
       // u_i recovered from its spline coefficients: u = (1,4,1)/6 eta = -z (d_{i-1} + 4 d_i + d_{i+1})
@@ -452,7 +518,7 @@ __device__ __noinline__ void adv32_block(const Adv32Args &a, const int n1, const
 }
 
 template <int NK, int DIR>
-__global__ void __launch_bounds__(AdvCols<NK>::C) k_adv32(Adv32Args a) {
+__global__ void __launch_bounds__(8 * AdvCols<NK>::C) k_adv32(Adv32Args a) {
   extern __shared__ __align__(16) float sm32[];
   adv32_block<NK, DIR>(a, blockIdx.x / AdvCols<NK>::blocks, blockIdx.x % AdvCols<NK>::blocks, blockIdx.y, sm32);
 }
@@ -461,7 +527,7 @@ __global__ void __launch_bounds__(AdvCols<NK>::C) k_adv32(Adv32Args a) {
 // slab = (fixed * NK + n1) * blocks + cb; args[2 * inst + DIR] holds that
 // instance's arguments.
 template <int NK, int DIR>
-__global__ void __launch_bounds__(AdvCols<NK>::C) k_badv32(const Adv32Args *args, const int *inst, const int *off,
+__global__ void __launch_bounds__(8 * AdvCols<NK>::C) k_badv32(const Adv32Args *args, const int *inst, const int *off,
                                                            int n) {
   extern __shared__ __align__(16) float sm32[];
   constexpr int NB = AdvCols<NK>::blocks;
@@ -518,13 +584,15 @@ static cudaError_t run_btheta32(int mode, const BatchLaunch &b, const Theta32Arg
 }
 
 template <int NK>
-static cudaError_t run_badv32(int dir, const BatchLaunch &b, const Adv32Args *args, int nxmax, cudaStream_t s) {
+static cudaError_t run_badv32(int dir, const BatchLaunch &b, const Adv32Args *args, int nxmax, int pieces,
+                              cudaStream_t s) {
   constexpr int C = AdvCols<NK>::C;
   const size_t smem = sizeof(float) * (size_t)(dir == 0 ? 2 : 3) * (nxmax + 2 * kGhost) * C;
+  const int threads = C * pieces;
   if (dir == 0)
-    k_badv32<NK, 0><<<b.grid, C, smem, s>>>(args, b.inst, b.off, b.n);
+    k_badv32<NK, 0><<<b.grid, threads, smem, s>>>(args, b.inst, b.off, b.n);
   else
-    k_badv32<NK, 1><<<b.grid, C, smem, s>>>(args, b.inst, b.off, b.n);
+    k_badv32<NK, 1><<<b.grid, threads, smem, s>>>(args, b.inst, b.off, b.n);
   return cudaGetLastError();
 }
 
@@ -541,7 +609,7 @@ static cudaError_t run_theta32(int mode, const Theta32Args &a, cudaStream_t s) {
 template <int NK>
 static cudaError_t run_adv32(int dir, const Adv32Args &a, cudaStream_t s) {
   constexpr int C = AdvCols<NK>::C;
-  dim3 grid(NK * AdvCols<NK>::blocks, a.nx), block(C);
+  dim3 grid(NK * AdvCols<NK>::blocks, a.nx), block(C * adv32_pieces(a.nx));
   const int slabs = dir == 0 ? 2 : 3;
   const size_t smem = sizeof(float) * (size_t)slabs * (a.nx + 2 * kGhost) * C;
   if (dir == 0)
@@ -588,9 +656,10 @@ cudaError_t launch_btheta_f32(int nk, int mode, const BatchLaunch &b, const Thet
 #undef W2_BT
 }
 
-cudaError_t launch_badv_f32(int nk, int dir, const BatchLaunch &b, const Adv32Args *args, int nxmax,
+cudaError_t launch_badv_f32(int nk, int dir, const BatchLaunch &b, const Adv32Args *args, int nxmax, int pieces,
                             cudaStream_t s) {
-#define W2_BA(N) run_badv32<N>(dir, b, args, nxmax, s)
+  if (pieces < 1 || pieces > 8) return cudaErrorInvalidValue;
+#define W2_BA(N) run_badv32<N>(dir, b, args, nxmax, pieces, s)
   W2_NK32_SWITCH(nk, W2_BA)
 #undef W2_BA
 }

@@ -167,8 +167,11 @@ int adv_items_per_line_f32(int nk);  // column blocks of the FP32 shift per (n1,
 cudaError_t launch_theta_f32(int nk, int mode, const Theta32Args &a, cudaStream_t s);
 cudaError_t launch_adv_f32(int nk, int dir, const Adv32Args &a, cudaStream_t s);
 cudaError_t launch_btheta_f32(int nk, int mode, const BatchLaunch &b, const Theta32Args *args, cudaStream_t s);
-cudaError_t launch_badv_f32(int nk, int dir, const BatchLaunch &b, const Adv32Args *args, int nxmax,
+cudaError_t launch_badv_f32(int nk, int dir, const BatchLaunch &b, const Adv32Args *args, int nxmax, int pieces,
                             cudaStream_t s);
+// Threads per column of the FP32 shift for lines of nx points (pieces of 32
+// rows or more, at most 8).
+__host__ __device__ inline int adv32_pieces(int nx) { return nx >= 256 ? 8 : nx >= 128 ? 4 : nx >= 64 ? 2 : 1; }
 cudaError_t launch_btables(const TabArgs *args, const int *off, int n, int grid, int nxmax, int mmax,
                            cudaStream_t s);
 cudaError_t launch_bxsum(const BXsum *args, const int *off, int n, int grid, cudaStream_t s);

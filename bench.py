@@ -491,6 +491,11 @@ def main():
     ms = max_over_ranks(e0.elapsed_time(e1))
     ob = ctx.observables()
     value = whole_job_rate(prob.points, args.steps, ws, ms)
+    # occupation numbers and correlation entropy of the evolved state (device, synchronous)
+    ctx.occupations()
+    t_occ = time.perf_counter()
+    occ, s_corr = ctx.occupations()
+    ms_occ = (time.perf_counter() - t_occ) * 1e3
 
     # ---- per-kernel times (events around every launch, same stream) -------
     kprof = ctx.step_profile(min(args.steps, 50))
@@ -583,7 +588,9 @@ def main():
                 "fp64_dmma_peak_tflops": peaks["fp64_dmma_tflops"], "fp64_dfma_peak_tflops": peaks["fp64_dfma_tflops"],
                 "peak_source": "measured live by paper_2511_11354_gb300/probe/fp64_peak.cu"},
             "observables": {"mass": ob.mass, "energy": ob.energy, "entropy_lin": ob.entropy_lin,
-                            "status": ob.status},
+                            "status": ob.status, "correlation_entropy": s_corr,
+                            "occupations_top3": [float(v) for v in occ[:3]],
+                            "occupations_ms": ms_occ},
             "cpu_baseline": cpu,
             "forms": forms,
         }

@@ -358,6 +358,29 @@ w2_status w2_learned_attach(w2_ctx *ctx, w2_mlp *m, int32_t judge_every, double 
  * the latest relative error. */
 w2_status w2_learned_report(w2_ctx *ctx, int32_t *active, int32_t *judged, double *last_err);
 
+/* ------------------------------------------------------------------------
+ * Occupation numbers and correlation entropy (the paper's appendix on the
+ * correlation entropy through the Wigner function, Sec. 5.3):
+ *   f1(x, p) = sum_{x2, p2} f dx dp  (particle 1),
+ *   rho1(x_{mu - nu}, x_{mu + nu}) = dp sum_n f1(x_mu, p_n) e^{-2 pi i (n - nk/2) nu / nx},
+ * nu = (c - b)/2 for the entry (b, c) with c - b the minimal image on the
+ * torus, mu = b + nu (for odd b + c a half point, where f1 comes from its
+ * periodic trigonometric interpolant), rho1 made Hermitian as
+ * (rho1 + rho1^H)/2.  occ[k] (host, nx values, largest first) are the
+ * eigenvalues of rho1 dx (a cyclic Jacobi eigensolver on the device, FP64);
+ * *entropy (host) = sum_k n_k ln n_k / sum_k n_k over n_k > 1e-14 n_0.
+ * Either pointer may be NULL.  Synchronises the stream.
+ * Errors: W2_ERR_ARG, W2_ERR_STATE (no state), W2_ERR_OOM, W2_ERR_CUDA. */
+w2_status w2_occupations(w2_ctx *ctx, double *occ, double *entropy);
+
+/* Eigenvalues of batch complex Hermitian n x n matrices (device, row-major,
+ * interleaved re/im doubles, 16-byte aligned; overwritten), one CTA per
+ * matrix, cyclic Jacobi with the round-robin ordering (at most 40 sweeps;
+ * stops when the off-diagonal part is below 1e-14 of the matrix).  eig:
+ * device [batch][n], largest first.  Queued on cuda_stream.
+ * Errors: W2_ERR_ARG (NULL, misaligned, n outside [1, 4096]), W2_ERR_CUDA. */
+w2_status w2_hermitian_eigvals(void *a, int32_t n, int32_t batch, double *eig, void *cuda_stream);
+
 /* Release every resource of the context (NULL is ignored). */
 void w2_destroy(w2_ctx *ctx);
 

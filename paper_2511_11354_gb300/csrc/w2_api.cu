@@ -45,7 +45,8 @@ static cudaError_t theta64(const w2_ctx *ctx, int mode, const ThetaArgs &th, cud
 static void free_all(w2_ctx *c) {
   void *ptrs[] = {c->f, c->g, c->t1, c->t2, c->xsum, c->xsum2, c->K, c->K12, c->vext_fine, c->w_fine,
                   c->d_fine, c->sintab, c->vext_grid, c->k0tab, c->wtab, c->xpart, c->obs_out,
-                  c->wtab32, c->ctab32, c->wdf, c->zpow, c->h_fine};
+                  c->wtab32, c->ctab32, c->wdf, c->zpow, c->h_fine, c->rdm_f1, c->rdm_fh, c->rdm_kh,
+                  c->rdm_eig, c->rdm_ph, c->rdm_rho};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_obs) cudaFreeHost(c->h_obs);
@@ -915,3 +916,63 @@ extern "C" w2_status w2_learned_report(w2_ctx *ctx, int32_t *active, int32_t *ju
   if (last_err) *last_err = ctx->last_err;
   return W2_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Occupation numbers and correlation entropy
+// ---------------------------------------------------------------------------
+
+extern "C" w2_status w2_occupations(w2_ctx *ctx, double *occ, double *entropy) {
+  if (!ctx) return W2_ERR_ARG;
+  if (ctx->sticky) return ctx->sticky;
+  if (!ctx->have_state) return W2_ERR_STATE;
+  const int nx = ctx->nx, nk = ctx->nk;
+  if (!ctx->rdm_rho) {
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->rdm_f1, sizeof(double) * nx * nk);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->rdm_fh, sizeof(double) * nx * nk);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->rdm_kh, sizeof(double) * nx);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->rdm_eig, sizeof(double) * (nx + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->rdm_ph, sizeof(double2) * nx * nk);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->rdm_rho, sizeof(double2) * nx * nx);
+    if (e != cudaSuccess) return W2_ERR_OOM;
+    // half-point interpolation kernel: K(j + 1/2), K(t) = (1/N)[1 + 2 sum_{0 < m < N/2} cos(2 pi m t / N)]
+    std::vector<double> kh(nx);
+    for (int j = 0; j < nx; ++j) {
+      double v = 1.0;
+      for (int m = 1; 2 * m < nx; ++m) v += 2.0 * cos(2.0 * M_PI * m * (j + 0.5) / nx);
+      kh[j] = v / nx;
+    }
+    // phases dp e^{-2 pi i (n - nk/2)(d/2)/nx}, d = -(nx/2) .. nx - nx/2 - 1
+    std::vector<double2> ph((size_t)nx * nk);
+    for (int di = 0; di < nx; ++di) {
+      const int d = di - nx / 2;
+      for (int n = 0; n < nk; ++n) {
+        const double a = -2.0 * M_PI * (n - nk / 2) * (0.5 * d) / nx;
+        ph[(size_t)di * nk + n] = make_double2(ctx->dp * cos(a), ctx->dp * sin(a));
+      }
+    }
+    W2_TRY(cudaMemcpy(ctx->rdm_kh, kh.data(), sizeof(double) * nx, cudaMemcpyHostToDevice));
+    W2_TRY(cudaMemcpy(ctx->rdm_ph, ph.data(), sizeof(double2) * nx * nk, cudaMemcpyHostToDevice));
+  }
+  cudaStream_t s = ctx->stream;
+  W2_TRY(launch_rdm_f1(ctx->f, f64_state(ctx->prec), ctx->rdm_f1, nx, nk, ctx->dx, ctx->dp, s));
+  W2_TRY(launch_rdm_rho(ctx->rdm_f1, ctx->rdm_kh, ctx->rdm_fh, ctx->rdm_ph, ctx->rdm_rho, nx, nk, ctx->dx, s));
+  W2_TRY(launch_jacobi_herm(ctx->rdm_rho, nx, 1, ctx->rdm_eig, s));
+  W2_TRY(launch_corr_entropy(ctx->rdm_eig, nx, ctx->rdm_eig + nx, s));
+  if (occ) W2_TRY(cudaMemcpyAsync(occ, ctx->rdm_eig, sizeof(double) * nx, cudaMemcpyDeviceToHost, s));
+  if (entropy) W2_TRY(cudaMemcpyAsync(entropy, ctx->rdm_eig + nx, sizeof(double), cudaMemcpyDeviceToHost, s));
+  W2_TRY(cudaStreamSynchronize(s));
+  return W2_OK;
+}
+
+extern "C" w2_status w2_hermitian_eigvals(void *a, int32_t n, int32_t batch, double *eig, void *cuda_stream) {
+  if (!a || !eig || n < 1 || n > 4096 || batch < 1) return W2_ERR_ARG;
+  if ((uintptr_t)a & 15) return W2_ERR_ARG;
+  cudaError_t e = launch_jacobi_herm((double2 *)a, n, batch, eig, (cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) {
+    note_cuda_error(e);
+    return W2_ERR_CUDA;
+  }
+  return W2_OK;
+}
+

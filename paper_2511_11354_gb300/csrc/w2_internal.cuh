@@ -142,6 +142,14 @@ struct FeatArgs {
   uint16_t *x;         // [rows][din] bf16
 };
 
+// Occupation numbers (w2_rdm.cu): f1 of the state, rho1 dx on the grid, and
+// the batched Jacobi eigensolver of complex Hermitian matrices.
+cudaError_t launch_rdm_f1(const void *f, int f64, double *f1, int nx, int nk, double dx, double dp, cudaStream_t s);
+cudaError_t launch_rdm_rho(const double *f1, const double *kh, double *fh, const double2 *ph, double2 *rho, int nx,
+                           int nk, double dx, cudaStream_t s);
+cudaError_t launch_jacobi_herm(double2 *mats, int n, int batch, double *eig, cudaStream_t s);
+cudaError_t launch_corr_entropy(const double *eig, int n, double *entropy, cudaStream_t s);
+
 // Record the CUDA error behind a W2_ERR_CUDA return (read by w2_last_cuda_error).
 void note_cuda_error(cudaError_t e);
 
@@ -216,6 +224,9 @@ struct w2_ctx {
   float2 *wdf, *zpow;        // double-float shift weights [nk][4] and z^k [32] (sliced path)
   int hartree_kind;          // W2_HARTREE_PAIR or W2_HARTREE_POISSON
   double *h_fine;            // [nx][M] Poisson Hartree kernel (W2_HARTREE_POISSON), else null
+  // occupation numbers (allocated by the first w2_occupations)
+  double *rdm_f1, *rdm_fh, *rdm_kh, *rdm_eig;  // [nx][nk], [nx][nk], [nx], [nx + 1]
+  double2 *rdm_ph, *rdm_rho;                   // [nx][nk] phases, [nx][nx] rho1 dx
   float *wtab32, *ctab32;    // FP32 shift weights and merged increment taps
   double *xpart, *obs_out, *h_obs;
   double z, zscale;

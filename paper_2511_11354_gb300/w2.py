@@ -31,7 +31,7 @@ STATUS = {0: "W2_OK", -1: "W2_ERR_ARG", -2: "W2_ERR_CUDA", -3: "W2_ERR_OOM", -4:
 
 EXPORTS = ("w2_create", "w2_set_potentials", "w2_set_state", "w2_get_state", "w2_step",
            "w2_step_profile", "w2_observables", "w2_theta", "w2_advect", "w2_destroy", "w2_status_string",
-           "w2_last_cuda_error", "w2_set_hartree",
+           "w2_last_cuda_error", "w2_set_hartree", "w2_occupations", "w2_hermitian_eigvals",
            "w2_batch_create", "w2_batch_set_potentials", "w2_batch_set_state", "w2_batch_get_state",
            "w2_batch_observables", "w2_batch_step", "w2_batch_autotune", "w2_batch_destroy",
            "w2_mlp_create", "w2_mlp_param_count", "w2_mlp_input_dim", "w2_mlp_set_params", "w2_mlp_get_params",
@@ -183,6 +183,15 @@ class Context:
 
     def set_hartree(self, kind):
         _check(self.lib.w2_set_hartree(self.h, int(kind)), "w2_set_hartree")
+
+    def occupations(self):
+        """(occupation numbers of the one-body density matrix, largest first;
+        correlation entropy)."""
+        occ = np.zeros(self.nx)
+        s = ctypes.c_double()
+        _check(self.lib.w2_occupations(self.h, occ.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       ctypes.byref(s)), "w2_occupations")
+        return occ, s.value
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
@@ -437,3 +446,20 @@ class MLP:
                                          int(x.shape[0]), g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                          ctypes.byref(loss)), "w2_mlp_gradients")
         return g, loss.value
+
+
+def hermitian_eigvals(a):
+    """Eigenvalues (largest first) of a batch of complex Hermitian matrices:
+    a is a CUDA complex128 tensor [batch][n][n] (overwritten)."""
+    import torch
+    assert a.dtype == torch.complex128 and a.is_cuda and a.is_contiguous() and a.dim() == 3
+    batch, n, n2 = a.shape
+    assert n == n2
+    eig = torch.empty(batch, n, dtype=torch.float64, device=a.device)
+    lib = load()
+    lib.w2_hermitian_eigvals.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                         ctypes.c_void_p]
+    _check(lib.w2_hermitian_eigvals(ctypes.c_void_p(a.data_ptr()), n, batch, ctypes.c_void_p(eig.data_ptr()),
+                                    ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)), "w2_hermitian_eigvals")
+    return eig
+

@@ -1,4 +1,6 @@
-"""FP64 CPU oracle for the periodic 1-D two-body Wigner 2-RDM step.
+"""FP64 CPU oracle for the 1-D two-body Wigner 2-RDM step: the periodic path
+(``oracle.py`` over ``w2_oracle.c``) and the non-periodic spectral-element
+path (``sem_ref.py``).
 
 TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline leg may use this package; the product path never
@@ -12,3 +14,4 @@ convergence to classical rotation in a harmonic well, and a brute-force
 two-particle Schroedinger evolution.
 """
 from .oracle import Oracle, build, lib_path  # noqa: F401
+from .sem_ref import SemOracle  # noqa: F401

@@ -292,3 +292,95 @@ def workload_plasma(kind: str = "landau", nx: int = 256, nk: int = 128, soft: fl
     f = (a[:, None, None, None] * a[None, :, None, None] * b[None, None, :, None] * b[None, None, None, :])
     return prob, np.ascontiguousarray(f, dtype=dtype)
 
+
+
+# ---------------------------------------------------------------------------
+# Non-periodic problems (Sec. 3.2 and the strongly correlated example of
+# Sec. 5.4): a bounded box [-L/2, L/2]^2 sampled with its endpoints, and a
+# momentum window [-Lp/2, Lp/2] split into ncell equal cells of nq
+# Chebyshev-Gauss collocation points each.
+# ---------------------------------------------------------------------------
+
+@dataclass
+class SemProblem:
+    nx: int                   # spatial points per axis, both ends included
+    ncell: int                # momentum cells per axis
+    nq: int                   # Chebyshev-Gauss points per cell
+    L: float                  # box [-L/2, L/2]
+    Lp: float                 # momentum window [-Lp/2, Lp/2]
+    dt: float
+    vext: Callable[[float], float]
+    vee: Callable[[float], float]
+    gamma: float = 1.0        # strength of the two-body term gamma W(x1 - x2)
+    c_hartree: float = 1.0    # Hartree term c_H dx sum_q W(x - x_q) n(x_q)
+    c_xc: float = 0.0
+    xc_kind: int = 0          # 0 none, 1 phi(n) = n, 2 Hedin-Lundqvist
+    hbar: float = 1.0
+    mass: float = 1.0
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def dx(self) -> float:
+        return self.L / (self.nx - 1)
+
+    @property
+    def np_(self) -> int:
+        return self.ncell * self.nq
+
+    def x(self) -> np.ndarray:
+        return -0.5 * self.L + self.dx * np.arange(self.nx)
+
+    def p(self) -> np.ndarray:
+        """Collocation momenta, ascending: cell s spans
+        [-Lp/2 + s Lp/ncell, -Lp/2 + (s+1) Lp/ncell], its points sit at the
+        Chebyshev-Gauss abscissae -cos((2q+1) pi / (2 nq)) of the cell."""
+        w = self.Lp / self.ncell
+        c = -0.5 * self.Lp + w * (np.arange(self.ncell) + 0.5)
+        eta = -np.cos((2 * np.arange(self.nq) + 1) * np.pi / (2 * self.nq))
+        return (c[:, None] + 0.5 * w * eta[None, :]).reshape(-1)
+
+    @property
+    def points(self) -> int:
+        return self.nx * self.nx * self.np_ * self.np_
+
+
+def correlated_state(prob: SemProblem, r0=(-2.0, 2.0), p0=(0.0, 0.0), a: float = 0.25,
+                     alpha: float = 0.1, beta: float = 0.1) -> np.ndarray:
+    """Initial 2-RDM of the strongly correlated example:
+    f(x1, x2, p1, p2) = f1(x1, p1) f1(x2, p2) g12(|x1 - x2|) with
+    f1(r, p) = (1 / (2 pi hbar)) sum_k exp(-2a (r - r0_k)^2 - (p - p0_k)^2 / (2 a hbar^2))
+    and g12(r) = exp(-beta exp(-alpha r) / r) (zero at r = 0)."""
+    x, p, hb = prob.x(), prob.p(), prob.hbar
+    f1 = np.zeros((x.size, p.size))
+    for rc, pc in zip(r0, p0):
+        f1 += np.exp(-2 * a * (x[:, None] - rc) ** 2 - (p[None, :] - pc) ** 2 / (2 * a * hb * hb))
+    f1 /= 2 * math.pi * hb
+    r = np.abs(x[:, None] - x[None, :])
+    with np.errstate(divide="ignore"):
+        g = np.where(r > 0, np.exp(-beta * np.exp(-alpha * r) / np.where(r > 0, r, 1.0)), 0.0)
+    f = np.einsum("ac,bd->abcd", f1, f1) * g[:, :, None, None]
+    return np.ascontiguousarray(f)
+
+
+def sem_correlated_problem(hamiltonian: str = "IV", soft: float = 1.0, nx: int = 201, ncell: int = 8,
+                           nq: int = 16, L: float = 30.0, Lp: float = 20.0 * math.pi / 3.0) -> SemProblem:
+    """The strongly correlated example: box [-15, 15]^2, momenta
+    [-10 pi/3, 10 pi/3]^2, dx = 0.15 (201 points), 8 cells x 16 points per
+    momentum axis, dt = 0.01, smoothed Coulomb 1/sqrt(r^2 + soft).
+    Hamiltonians: I Hartree; II + Hedin-Lundqvist XC; III + the pair term;
+    IV + the external well -2/sqrt(x^2 + soft)."""
+    if hamiltonian not in ("I", "II", "III", "IV"):
+        raise ValueError(hamiltonian)
+    xc = hamiltonian != "I"
+    pair = hamiltonian in ("III", "IV")
+    vext = (lambda x: -2.0 / math.sqrt(x * x + soft)) if hamiltonian == "IV" else zero_potential()
+    return SemProblem(nx=nx, ncell=ncell, nq=nq, L=L, Lp=Lp, dt=0.01, vext=vext, vee=soft_coulomb(soft),
+                      gamma=1.0 if pair else 0.0, c_hartree=1.0, c_xc=1.0 if xc else 0.0, xc_kind=2 if xc else 0,
+                      name=f"correlated_{hamiltonian}_{nx}x{ncell * nq}", meta={"soft": soft, "T": 4.0})
+
+
+def workload_correlated(hamiltonian: str = "IV", soft: float = 1.0, nx: int = 201, ncell: int = 8, nq: int = 16,
+                        L: float = 30.0, Lp: float = 20.0 * math.pi / 3.0):
+    prob = sem_correlated_problem(hamiltonian, soft, nx, ncell, nq, L, Lp)
+    return prob, correlated_state(prob)

@@ -165,16 +165,18 @@ class SemOracle:
         return U
 
     # ---------------------------------------------------------------- Theta
-    def T_tensors(self, U):
+    def T_tensors(self, U, ms=None):
         """T+-[m][i][s*Q+l] = sum_n U(x_n) e^{+-2i (p_i - d^_s)(x_n - x_m)/hbar}
-        |P| O_l(-+|P| (x_n - x_m)/hbar) (Sec. 3.2.1)."""
+        |P| O_l(-+|P| (x_n - x_m)/hbar) (Sec. 3.2.1), for the targets ms
+        (all grid points by default)."""
         nx, hb = self.nx, self.hbar
+        ms = range(nx) if ms is None else ms
         d = np.arange(-(nx - 1), nx) * self.dx                     # all x_n - x_m
         O = osc_integral(self.Q, self.width * d / hb)               # [l][d]
-        Tp = np.zeros((nx, self.np_, self.np_), dtype=np.complex128)
+        Tp = np.zeros((len(ms), self.np_, self.np_), dtype=np.complex128)
         Tm = np.zeros_like(Tp)
         dps = self.p[:, None] - self.centre[None, :]                # p_i - d^_s   [i][s]
-        for m in range(nx):
+        for k, m in enumerate(ms):
             y = self.x - self.x[m]                                  # x_n - x_m
             idx = np.arange(nx) - m + (nx - 1)
             Opos = O[:, idx]                                        # O_l(+|P| y)   [l][n]
@@ -182,8 +184,8 @@ class SemOracle:
             # O_l(-z) = conj(O_l(z)) for real z
             tp = np.einsum("n,isn,ln->isl", U, ph, np.conj(Opos))
             tm = np.einsum("n,isn,ln->isl", U, np.conj(ph), Opos)
-            Tp[m] = self.width * tp.reshape(self.np_, self.np_)
-            Tm[m] = self.width * tm.reshape(self.np_, self.np_)
+            Tp[k] = self.width * tp.reshape(self.np_, self.np_)
+            Tm[k] = self.width * tm.reshape(self.np_, self.np_)
         return Tp, Tm
 
     def theta_one_body(self, f, U1, U2):
@@ -203,28 +205,55 @@ class SemOracle:
         out += np.matmul(b2, np.swapaxes(G2, 1, 2)[None])
         return out
 
+    def _two_body_parts(self):
+        y = self.y2
+        B = self.basis_transform(y)                                 # [y][s l]
+        E = np.exp(-2j * np.outer(self.p, y) / self.hbar)           # [p][y]
+        Y1, Y2 = np.meshgrid(y, y, indexing="ij")
+        pref = self.P.gamma * self.dx * self.dx / (1j * self.hbar * (math.pi * self.hbar) ** 2)
+        return B, E, Y1 - Y2, pref
+
+    def _two_body_block(self, parts, i1, i2, a):
+        """Theta_{gamma W} at X = (x_i1, x_i2) from the block's coefficients a."""
+        B, E, U12, pref = parts
+        D = self._D(self.x[i1] - self.x[i2], U12)
+        Fh = B @ a @ B.T                                             # F^(y1, y2)
+        return (pref * (E @ (D * Fh) @ E.T)).real
+
     def theta_two_body(self, f):
         """Sec. 3.2.2: (gamma dy^2 / (i hbar (pi hbar)^2)) sum_{y1,y2}
         e^{-2i (p1 y1 + p2 y2)/hbar} D_V(y1, y2) sum a_{s1 s2 l1 l2}
         O_{s1 s2 l1 l2}(y1, y2), with the two-body tensor a product of two
         one-cell transforms."""
-        P = self.P
-        if P.gamma == 0.0:
+        if self.P.gamma == 0.0:
             return np.zeros_like(f)
-        hb, dy = self.hbar, self.dx
-        y = self.y2
-        B = self.basis_transform(y)                                 # [y][s l]
-        E = np.exp(-2j * np.outer(self.p, y) / hb)                  # [p][y]
-        Y1, Y2 = np.meshgrid(y, y, indexing="ij")
-        pref = P.gamma * dy * dy / (1j * hb * (math.pi * hb) ** 2)
+        parts = self._two_body_parts()
         a = self.cell_coeffs(self.cell_coeffs(f, 2), 3)              # [i1][i2][s1 l1][s2 l2]
         out = np.zeros(f.shape)
         for i1 in range(self.nx):
             for i2 in range(self.nx):
-                r = self.x[i1] - self.x[i2]
-                D = self._D(r, Y1 - Y2)
-                Fh = B @ a[i1, i2] @ B.T                              # F^(y1, y2)
-                out[i1, i2] = (pref * (E @ (D * Fh) @ E.T)).real
+                out[i1, i2] = self._two_body_block(parts, i1, i2, a[i1, i2])
+        return out
+
+    def theta_sample(self, f, xs):
+        """Theta at the flat spatial indices xs (X = i1 nx + i2) only; the
+        potentials come from the densities of the whole state."""
+        n1, n2 = self.marginal(f)
+        U1, U2 = self.potential(n1), self.potential(n2)
+        pref = self.dx / (2j * math.pi * self.hbar ** 2)
+        i1s = [int(X) // self.nx for X in xs]
+        i2s = [int(X) % self.nx for X in xs]
+        Tp1, Tm1 = self.T_tensors(U1, i1s)
+        Tp2, Tm2 = self.T_tensors(U2, i2s)
+        parts = self._two_body_parts() if self.P.gamma != 0.0 else None
+        out = np.zeros((len(xs), self.np_, self.np_))
+        for k, (i1, i2) in enumerate(zip(i1s, i2s)):
+            blk = f[i1, i2]
+            G1 = (pref * (Tm1[k] - Tp1[k])).real
+            G2 = (pref * (Tm2[k] - Tp2[k])).real
+            out[k] = G1 @ self.cell_coeffs(blk, 0) + self.cell_coeffs(blk, 1) @ G2.T
+            if parts is not None:
+                out[k] += self._two_body_block(parts, i1, i2, self.cell_coeffs(self.cell_coeffs(blk, 0), 1))
         return out
 
     def _D(self, r, u):

@@ -1,0 +1,471 @@
+// Kernels of the non-periodic path: static tables of the spectral-element
+// operators (Sec. 3.2), densities and potentials, the D_V weighting of the
+// two-body chain (Sec. 3.2.2), the natural-boundary spline shift (Sec. 4.1),
+// the Lawson combinations and the observables.
+#include <math.h>
+
+#include "w2_sem.cuh"
+
+namespace w2sem {
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// int_{-1}^{1} T_k T_l for k + l even (0 otherwise).
+__device__ __forceinline__ double cheb_gram(int k, int l) {
+  const double a = (double)(k + l), b = (double)(k - l);
+  return 1.0 / (1.0 - a * a) + 1.0 / (1.0 - b * b);
+}
+
+// O_l(z) = int_{-1}^{1} e^{i z eta} T_l(eta) deta for l < Q at z = width d dx / hbar,
+// d = 0 .. nx-1, by the Jacobi-Anger expansion
+//   e^{i z eta} = J_0(z) + 2 sum_{k>=1} i^k J_k(z) T_k(eta)
+// with the Bessel values J_k(z) from Miller's backward recurrence
+// J_{k-1} = (2k/z) J_k - J_{k+1}, normalised by J_0 + 2 sum J_{2k} = 1.  The
+// sums over k are accumulated during the recurrence (unnormalised) and
+// divided by the normalisation at the end.  O_l is real for even l and
+// imaginary for odd l.
+__global__ void k_sem_osc(SemTabArgs a) {
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= a.nx) return;
+  const int Q = a.Q;
+  double S[32];
+#pragma unroll
+  for (int l = 0; l < 32; ++l) S[l] = 0.0;
+  double norm = 1.0;
+  const double z = a.width * (double)d * a.dx / a.hbar;
+  if (d == 0) {
+    for (int l = 0; l < Q; l += 2) S[l] = cheb_gram(0, l);  // J_k(0) = [k == 0]
+  } else {
+    int kst = (int)(z + 20.0 * cbrt(z + 1.0) + 40.0);
+    kst += kst & 1;
+    double jp1 = 0.0, jk = 1e-280;  // j_{k+1}, j_k at k = kst
+    norm = 0.0;
+    for (int k = kst; k >= 0; --k) {
+      // fold j_k into the sums
+      const double ck = (k == 0) ? 1.0 : 2.0;
+      if ((k & 1) == 0) {
+        norm += ck * jk;
+        const double sg = ((k >> 1) & 1) ? -1.0 : 1.0;
+        for (int l = 0; l < Q; l += 2) S[l] = fma(ck * sg * cheb_gram(k, l), jk, S[l]);
+      } else {
+        const double sg = (((k - 1) >> 1) & 1) ? -1.0 : 1.0;
+        for (int l = 1; l < Q; l += 2) S[l] = fma(2.0 * sg * cheb_gram(k, l), jk, S[l]);
+      }
+      if (k == 0) break;
+      const double jm1 = (2.0 * k / z) * jk - jp1;
+      jp1 = jk;
+      jk = jm1;
+      if (fabs(jk) > 1e250) {  // rescale everything accumulated so far
+        jk *= 1e-250; jp1 *= 1e-250; norm *= 1e-250;
+        for (int l = 0; l < Q; ++l) S[l] *= 1e-250;
+      }
+    }
+  }
+  for (int l = 0; l < Q; ++l) {
+    const double v = S[l] / norm;
+    a.osc[(d * Q + l) * 2 + 0] = (l % 2 == 0) ? v : 0.0;
+    a.osc[(d * Q + l) * 2 + 1] = (l % 2 == 0) ? 0.0 : v;
+  }
+}
+
+// O_l(width y / hbar) for y = d dx with d of either sign (O_l(-z) = conj O_l(z)).
+__device__ __forceinline__ double2 osc_at(const double *osc, int Q, int d, int l) {
+  const int ad = d < 0 ? -d : d;
+  double2 o = make_double2(osc[(ad * Q + l) * 2], osc[(ad * Q + l) * 2 + 1]);
+  if (d < 0) o.y = -o.y;
+  return o;
+}
+
+// One-body table: psi[d + nx - 1][i][j] = (dx / (pi hbar^2)) width
+//   sum_l C[l][q] Im[e^{-2i (p_i - c_s) y_d / hbar} O_l(width y_d / hbar)],
+// j = s Q + q, y_d = d dx, so that the operator's matrix at x_m is
+// G(x_m) = sum_n U(x_n) psi[n - m].
+__global__ void k_sem_psi(SemTabArgs a) {
+  const long long np = a.np, total = (long long)(2 * a.nx - 1) * np * np;
+  const double pref = a.dx * a.width / (kPi * a.hbar * a.hbar);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e % np), i = (int)((e / np) % np), dd = (int)(e / (np * np));
+    const int d = dd - (a.nx - 1), s = j / a.Q, q = j % a.Q;
+    const double y = (double)d * a.dx;
+    double sn, cs;
+    sincos(-2.0 * (a.p[i] - a.centre[s]) * y / a.hbar, &sn, &cs);
+    double acc = 0.0;
+    for (int l = 0; l < a.Q; ++l) {
+      const double2 o = osc_at(a.osc, a.Q, d, l);
+      acc = fma(a.cheb[l * a.Q + q], cs * o.y + sn * o.x, acc);  // Im[(cs + i sn)(o.x + i o.y)]
+    }
+    a.psi[e] = pref * acc;
+  }
+}
+
+// Two-body transform rows Phi_j(y_n) = sum_l C[l][q] (width/2) e^{2i c_s y_n / hbar}
+// O_l(width y_n / hbar), n = -h .. h (the exact transform of a nodal vector's
+// cell expansions at frequency y_n).
+__global__ void k_sem_phi(SemTabArgs a) {
+  const int Ny = 2 * a.h + 1, total = Ny * a.np;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int j = e % a.np, n = e / a.np - a.h, s = j / a.Q, q = j % a.Q;
+    const double y = (double)n * a.dx;
+    double sn, cs;
+    sincos(2.0 * a.centre[s] * y / a.hbar, &sn, &cs);
+    double re = 0.0, im = 0.0;
+    for (int l = 0; l < a.Q; ++l) {
+      const double2 o = osc_at(a.osc, a.Q, n, l);
+      const double c = a.cheb[l * a.Q + q];
+      re = fma(c, cs * o.x - sn * o.y, re);
+      im = fma(c, cs * o.y + sn * o.x, im);
+    }
+    a.phir[e] = 0.5 * a.width * re;
+    a.phii[e] = 0.5 * a.width * im;
+  }
+}
+
+// Block operands of the complex products (see launch_sem_tables).
+__global__ void k_sem_assemble(SemTabArgs a) {
+  const int np = a.np, h = a.h, Ny = 2 * h + 1, Nyh = h + 1;
+  const int nph = 2 * Nyh * 2 * np, neh = 2 * np * 2 * Nyh, nee = np * 2 * Ny;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nph + neh + nee; e += gridDim.x * blockDim.x) {
+    if (e < nph) {  // ph[r][c] = [[Phr_h, -Phi_h], [Phi_h, Phr_h]], rows y1 = 0 .. h
+      const int r = e / (2 * np), c = e % (2 * np);
+      const int br = r / Nyh, rr = r % Nyh, bc = c / np, cc = c % np;
+      const int src = (h + rr) * np + cc;
+      double v;
+      if (br == bc) v = a.phir[src]; else v = (br == 0) ? -a.phii[src] : a.phii[src];
+      a.ph[e] = v;
+    } else if (e < nph + neh) {  // eh[b][i][c]: b = 0: [Er_h | -Ei_h], b = 1: [Ei_h | Er_h]
+      const int f = e - nph;
+      const int b = f / (np * 2 * Nyh), i = (f / (2 * Nyh)) % np, c = f % (2 * Nyh);
+      const int half = c / Nyh, n = c % Nyh;  // y1 = n dx, n = 0 .. h
+      double sn, cs;
+      sincos(-2.0 * a.p[i] * ((double)n * a.dx) / a.hbar, &sn, &cs);  // E = cs + i sn
+      double v;
+      if (b == 0) v = (half == 0) ? cs : -sn; else v = (half == 0) ? sn : cs;
+      a.eh[f] = v;
+    } else {  // eier[i][c] = [Ei | Er] over y2 = (n - h) dx
+      const int f = e - nph - neh;
+      const int i = f / (2 * Ny), c = f % (2 * Ny);
+      const int n = (c % Ny) - h;
+      double sn, cs;
+      sincos(-2.0 * a.p[i] * ((double)n * a.dx) / a.hbar, &sn, &cs);
+      a.eier[f] = (c < Ny) ? sn : cs;
+    }
+  }
+}
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
+  __syncthreads();
+  if (ln == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < NT / 32; ++i) s += red[i];
+  return s;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(256) k_sem_xsum(int np, const double *__restrict__ f, const double *__restrict__ w,
+                                                  double *xs) {
+  __shared__ double red[8];
+  const long long X = blockIdx.x;
+  const double *fx = f + X * np * np;
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < np * np; e += 256) acc = fma(w[e / np] * w[e % np], fx[e], acc);
+  const double s = block_sum<256>(acc, red);
+  if (threadIdx.x == 0) xs[X] = s;
+}
+
+__global__ void k_sem_dens(int nx, double dx, const double *xs, double *n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nx) return;
+  double a = 0.0, b = 0.0;
+  for (int k = 0; k < nx; ++k) {
+    a += xs[(long long)i * nx + k];
+    b += xs[(long long)k * nx + i];
+  }
+  n[i] = dx * a;
+  n[nx + i] = dx * b;
+}
+
+__device__ __forceinline__ double phi_xc(int kind, double n) {
+  if (kind == 1) return n;
+  if (kind == 2) {  // Hedin-Lundqvist exchange-correlation potential, atomic units
+    const double c = cbrt(n > 0.0 ? n : 0.0);
+    return 0.985 * c + 0.985 * 0.034 * log1p(18.37 * c);
+  }
+  return 0.0;
+}
+
+// One block per particle: U, then its Toeplitz rows.
+__global__ void __launch_bounds__(256) k_sem_potential(SemPotArgs a) {
+  extern __shared__ double Us[];
+  const int k = blockIdx.x, nx = a.nx, W0 = 2 * (nx - 1);
+  const double *n = a.n + k * nx;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    double u = a.vext[i];
+    if (a.c_h != 0.0) {
+      double vh = 0.0;
+      for (int q = 0; q < nx; ++q) vh = fma(a.wgrid[i - q + W0], n[q], vh);
+      u += a.c_h * a.dx * vh;
+    }
+    if (a.c_xc != 0.0 && a.xc_kind) u += a.c_xc * phi_xc(a.xc_kind, n[i]);
+    Us[i] = u;
+    a.U[k * nx + i] = u;
+  }
+  __syncthreads();
+  const int nd = 2 * nx - 1;
+  for (long long e = threadIdx.x; e < (long long)nx * nd; e += blockDim.x) {
+    const int m = (int)(e / nd), dd = (int)(e % nd);
+    const int src = m + dd - (nx - 1);
+    a.ut[((long long)k * nx + m) * nd + dd] = (src >= 0 && src < nx) ? Us[src] : 0.0;
+  }
+}
+
+// Two-body weighting on a chunk of X: A_X holds [Ar; Ai] (2 Nyh x Ny) with
+// rows y1 = r dx (r = 0 .. h) and columns y2 = (c - h) dx.
+__global__ void k_sem_dmul(int nx, int h, int x0, int nb, const double *__restrict__ wgrid, double *A) {
+  const int Ny = 2 * h + 1, Nyh = h + 1, W0 = 2 * (nx - 1);
+  const long long per = (long long)2 * Nyh * Ny, total = per * nb;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int bb = (int)(e / per);
+    const int r = (int)((e % per) / Ny) % Nyh, c = (int)(e % Ny);
+    const int X = x0 + bb, rho = X / nx - X % nx;
+    const int u = r - (c - h);
+    const double D = wgrid[rho + u + W0] - wgrid[rho - u + W0];
+    A[e] *= (r == 0 ? 1.0 : 2.0) * D;
+  }
+}
+
+// Natural-boundary cubic spline shift of C adjacent lines: load the lines
+// into shared memory, solve the interior (1,4,1)/6 system with eta_0 = f_0,
+// eta_N = f_N by the Thomas recursion (one thread per line, in place), then
+// evaluate the four B-spline terms at the feet; the ghosts are
+// eta_{-1} = 2 eta_0 - eta_1, eta_{N+1} = 2 eta_N - eta_{N-1}, zero beyond.
+template <int AXIS>
+__global__ void k_sem_adv(SemAdvArgs a) {
+  extern __shared__ double sl[];
+  const int nx = a.nx, np = a.np, C = a.C, N = nx - 1;
+  const int c = threadIdx.x;
+  const int nchunk = (np + C - 1) / C;
+  const int chunk = blockIdx.x % nchunk, j1 = (blockIdx.x / nchunk) % np, o = blockIdx.x / (nchunk * np);
+  const int j2 = chunk * C + c;
+  const long long np2 = (long long)np * np;
+  long long base, stride;
+  if (AXIS == 0) { base = ((long long)o * np + j1) * np; stride = (long long)nx * np2; }  // o = i2
+  else { base = (long long)o * nx * np2 + (long long)j1 * np; stride = np2; }          // o = i1
+  if (j2 >= np) return;
+  for (int i = 0; i < nx; ++i) sl[i * C + c] = a.in[base + i * stride + j2];
+  // forward: d'_i = (r_i - d'_{i-1}) c'_i, r_i = 6 f_i - [i==1] f_0 - [i==N-1] f_N
+  double dprev = 0.0;
+  const double f0 = sl[c], fN = sl[N * C + c];
+  for (int i = 1; i <= N - 1; ++i) {
+    double r = 6.0 * sl[i * C + c];
+    if (i == 1) r -= f0;
+    if (i == N - 1) r -= fN;
+    dprev = (r - dprev) * a.cp[i];
+    sl[i * C + c] = dprev;
+  }
+  // backward: eta_{N-1} = d'_{N-1}, eta_i = d'_i - c'_i eta_{i+1}
+  double enext = sl[(N - 1) * C + c];
+  for (int i = N - 2; i >= 1; --i) {
+    enext = sl[i * C + c] - a.cp[i] * enext;
+    sl[i * C + c] = enext;
+  }
+  const int jm = (AXIS == 0) ? j1 : j2;
+  const int k0 = a.k0[jm];
+  const double w0 = a.wts[jm * 4], w1 = a.wts[jm * 4 + 1], w2 = a.wts[jm * 4 + 2], w3 = a.wts[jm * 4 + 3];
+  const double em1 = 2.0 * sl[c] - sl[C + c], eN1 = 2.0 * sl[N * C + c] - sl[(N - 1) * C + c];
+  auto eta = [&](int nu) -> double {
+    if (nu >= 0 && nu <= N) return sl[nu * C + c];
+    if (nu == -1) return em1;
+    if (nu == N + 1) return eN1;
+    return 0.0;
+  };
+  for (int i = 0; i < nx; ++i) {
+    const int nu = i + k0 - 1;
+    const double v = w0 * eta(nu) + w1 * eta(nu + 1) + w2 * eta(nu + 2) + w3 * eta(nu + 3);
+    a.out[base + i * stride + j2] = v;
+  }
+}
+
+__global__ void k_sem_axpy(long long n, const double *__restrict__ x, double a, const double *__restrict__ y,
+                           const double *__restrict__ y2, double *out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double t = y2 ? y[e] + y2[e] : y[e];
+    out[e] = fma(a, t, x[e]);
+  }
+}
+
+// Per-X partials: {sum ww f, sum ww f (p1^2 + p2^2)/2m, sum ww f^2, 0} and the
+// row sums r[j1] = sum_j2 w_j2 f (one warp per row, fixed order).
+__global__ void __launch_bounds__(256) k_sem_obs_x(SemObsArgs a) {
+  extern __shared__ double rows[];  // [np][3]
+  const long long X = blockIdx.x;
+  const int np = a.np, wid = threadIdx.x >> 5, ln = threadIdx.x & 31;
+  const double *fx = a.f + X * np * np;
+  for (int j1 = wid; j1 < np; j1 += 8) {
+    double r0 = 0.0, r2 = 0.0, r3 = 0.0;
+    for (int j2 = ln; j2 < np; j2 += 32) {
+      const double v = fx[j1 * np + j2], w = a.w[j2];
+      r0 = fma(w, v, r0);
+      r2 = fma(w * a.p[j2] * a.p[j2], v, r2);
+      r3 = fma(w * v, v, r3);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      r0 += __shfl_xor_sync(0xffffffffu, r0, o);
+      r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+      r3 += __shfl_xor_sync(0xffffffffu, r3, o);
+    }
+    if (ln == 0) { rows[j1 * 3] = r0; rows[j1 * 3 + 1] = r2; rows[j1 * 3 + 2] = r3; }
+  }
+  __syncthreads();
+  double *xp = a.xpart + X * (4 + np);
+  for (int j1 = threadIdx.x; j1 < np; j1 += 256) xp[4 + j1] = rows[j1 * 3];
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int j1 = 0; j1 < np; ++j1) {
+      const double w = a.w[j1];
+      s0 = fma(w, rows[j1 * 3], s0);
+      s1 = fma(w, a.p[j1] * a.p[j1] * rows[j1 * 3] + rows[j1 * 3 + 1], s1);
+      s2 = fma(w, rows[j1 * 3 + 2], s2);
+    }
+    xp[0] = s0;
+    xp[1] = s1 / (2.0 * a.mass);
+    xp[2] = s2;
+    xp[3] = 0.0;
+  }
+}
+
+// One block: out = {mass, energy, purity, entropy_lin, l2norm, 0, 0, 0, n1[nx]}.
+__global__ void __launch_bounds__(1024) k_sem_obs_fin(SemObsArgs a) {
+  __shared__ double red[32];
+  const int nx = a.nx, np = a.np, W0 = 2 * (nx - 1);
+  const long long nX = (long long)nx * nx;
+  double m = 0.0, e = 0.0, l2 = 0.0;
+  for (long long X = threadIdx.x; X < nX; X += blockDim.x) {
+    const double *xp = a.xpart + X * (4 + np);
+    const int i1 = (int)(X / nx), i2 = (int)(X % nx);
+    m += xp[0];
+    l2 += xp[2];
+    e += xp[1] + xp[0] * (a.vext[i1] + a.vext[i2] + a.gamma * a.wgrid[i1 - i2 + W0]);
+  }
+  m = block_sum<1024>(m, red);
+  e = block_sum<1024>(e, red);
+  l2 = block_sum<1024>(l2, red);
+  // Hartree energy (c_h / 2) dx sum_i n_k(x_i) V_H[n_k](x_i), both particles
+  double eh = 0.0;
+  for (int t = threadIdx.x; t < 2 * nx; t += blockDim.x) {
+    const int k = t / nx, i = t % nx;
+    const double *n = a.n + k * nx;
+    double vh = 0.0;
+    for (int q = 0; q < nx; ++q) vh = fma(a.wgrid[i - q + W0], n[q], vh);
+    eh += n[i] * a.dx * vh;
+  }
+  eh = block_sum<1024>(eh, red);
+  // purity 2 pi hbar dx sum_{i1,j1} w_j1 f1^2, f1 = dx sum_i2 r_X[j1]
+  double pu = 0.0;
+  for (long long t = threadIdx.x; t < (long long)nx * np; t += blockDim.x) {
+    const int i1 = (int)(t / np), j1 = (int)(t % np);
+    double f1 = 0.0;
+    for (int i2 = 0; i2 < nx; ++i2) f1 += a.xpart[((long long)i1 * nx + i2) * (4 + np) + 4 + j1];
+    f1 *= a.dx;
+    pu = fma(a.w[j1] * f1, f1, pu);
+  }
+  pu = block_sum<1024>(pu, red);
+  if (threadIdx.x == 0) {
+    const double dx2 = a.dx * a.dx;
+    a.out[0] = dx2 * m;
+    a.out[1] = dx2 * e + 0.5 * a.c_h * eh;
+    a.out[2] = 2.0 * kPi * a.hbar * a.dx * pu;
+    a.out[3] = 1.0 - a.out[2];
+    a.out[4] = sqrt(dx2 * l2);
+    a.out[5] = a.out[6] = a.out[7] = 0.0;
+  }
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) a.out[8 + i] = a.n[i];
+}
+
+inline int grid_for(long long n, int nt) {
+  long long g = (n + nt - 1) / nt;
+  return (int)(g < 152LL * 32 ? (g > 0 ? g : 1) : 152LL * 32);
+}
+
+}  // namespace
+
+cudaError_t launch_sem_osc(const SemTabArgs &a, cudaStream_t s) {
+  if (a.Q > 32) return cudaErrorInvalidValue;
+  k_sem_osc<<<(a.nx + 63) / 64, 64, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sem_tables(const SemTabArgs &a, cudaStream_t s) {
+  const long long npsi = (long long)(2 * a.nx - 1) * a.np * a.np;
+  k_sem_psi<<<grid_for(npsi, 256), 256, 0, s>>>(a);
+  k_sem_phi<<<grid_for((long long)(2 * a.h + 1) * a.np, 256), 256, 0, s>>>(a);
+  const long long nas = (long long)4 * (a.h + 1) * a.np * 2 + (long long)a.np * 2 * (2 * a.h + 1);
+  k_sem_assemble<<<grid_for(nas, 256), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sem_marginal(int nx, int np, double dx, const double *f, const double *w, double *xs,
+                                double *n, cudaStream_t s) {
+  k_sem_xsum<<<nx * nx, 256, 0, s>>>(np, f, w, xs);
+  k_sem_dens<<<(nx + 127) / 128, 128, 0, s>>>(nx, dx, xs, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sem_potential(const SemPotArgs &a, cudaStream_t s) {
+  k_sem_potential<<<2, 256, sizeof(double) * a.nx, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sem_dmul(int nx, int h, int x0, int nb, const double *wgrid, double *A, cudaStream_t s) {
+  const long long total = (long long)2 * (h + 1) * (2 * h + 1) * nb;
+  k_sem_dmul<<<grid_for(total, 256), 256, 0, s>>>(nx, h, x0, nb, wgrid, A);
+  return cudaGetLastError();
+}
+
+int sem_adv_cols(int nx, int np) {
+  int C = 64;
+  while (C > 8 && (size_t)C * nx * sizeof(double) > 200 * 1024) C >>= 1;
+  while (C > 8 && C / 2 >= np) C >>= 1;
+  return C;
+}
+
+cudaError_t launch_sem_adv(int axis, const SemAdvArgs &a, cudaStream_t s) {
+  const size_t smem = sizeof(double) * a.C * a.nx;
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  const long long nblk = (long long)a.nx * a.np * ((a.np + a.C - 1) / a.C);
+  if (nblk > 0x7fffffffLL) return cudaErrorInvalidValue;
+  cudaError_t e;
+  if (axis == 0) {
+    e = cudaFuncSetAttribute(k_sem_adv<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_sem_adv<0><<<(unsigned)nblk, a.C, smem, s>>>(a);
+  } else {
+    e = cudaFuncSetAttribute(k_sem_adv<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_sem_adv<1><<<(unsigned)nblk, a.C, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sem_axpy(long long n, const double *x, double a, const double *y, const double *y2, double *out,
+                            cudaStream_t s) {
+  k_sem_axpy<<<grid_for(n, 256), 256, 0, s>>>(n, x, a, y, y2, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sem_obs(const SemObsArgs &a, cudaStream_t s) {
+  const size_t smem = sizeof(double) * 3 * a.np;
+  k_sem_obs_x<<<a.nx * a.nx, 256, smem, s>>>(a);
+  k_sem_obs_fin<<<1, 1024, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace w2sem

@@ -36,7 +36,9 @@ EXPORTS = ("w2_create", "w2_set_potentials", "w2_set_state", "w2_get_state", "w2
            "w2_batch_observables", "w2_batch_step", "w2_batch_autotune", "w2_batch_destroy",
            "w2_mlp_create", "w2_mlp_param_count", "w2_mlp_input_dim", "w2_mlp_set_params", "w2_mlp_get_params",
            "w2_mlp_set_scales", "w2_mlp_forward", "w2_mlp_train_step", "w2_mlp_gradients", "w2_mlp_destroy",
-           "w2_features", "w2_theta_pair", "w2_learned_attach", "w2_learned_report")
+           "w2_features", "w2_theta_pair", "w2_learned_attach", "w2_learned_report",
+           "w2_sem_create", "w2_sem_set_potentials", "w2_sem_momenta", "w2_sem_set_state", "w2_sem_get_state",
+           "w2_sem_theta", "w2_sem_advect", "w2_sem_step", "w2_sem_observables", "w2_sem_destroy")
 STEP_KERNELS = ("xsum_f", "tables_f", "theta_predictor", "shift_x2", "shift_x1_lawson", "xsum_ftilde",
                 "tables_ftilde", "theta_corrector")
 
@@ -57,6 +59,12 @@ class Config(ctypes.Structure):
 class Obs(ctypes.Structure):
     _fields_ = [("mass", ctypes.c_double), ("energy", ctypes.c_double), ("purity", ctypes.c_double),
                 ("entropy_lin", ctypes.c_double), ("l2norm", ctypes.c_double), ("step", ctypes.c_int64)]
+
+
+class SemConfig(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ncell", ctypes.c_int32), ("nq", ctypes.c_int32), ("L", ctypes.c_double),
+                ("Lp", ctypes.c_double), ("dt", ctypes.c_double), ("hbar", ctypes.c_double),
+                ("mass", ctypes.c_double), ("xc_kind", ctypes.c_int32)]
 
 
 W2_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_double, ctypes.c_void_p)
@@ -111,11 +119,23 @@ def load(path: str = LIB_PATH):
     lib.w2_theta_pair.argtypes = [vp, vp, vp]
     lib.w2_learned_attach.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_double]
     lib.w2_learned_report.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), dp]
+    lib.w2_sem_create.argtypes = [ctypes.POINTER(SemConfig), vp, ctypes.POINTER(vp)]
+    lib.w2_sem_set_potentials.argtypes = [vp, W2_FN, vp, W2_FN, vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    lib.w2_sem_momenta.argtypes = [vp, dp, dp]
+    lib.w2_sem_set_state.argtypes = [vp, vp, ctypes.c_int32]
+    lib.w2_sem_get_state.argtypes = [vp, vp, ctypes.c_int32]
+    lib.w2_sem_theta.argtypes = [vp, vp, vp]
+    lib.w2_sem_advect.argtypes = [vp, vp, vp]
+    lib.w2_sem_step.argtypes = [vp, ctypes.c_int32]
+    lib.w2_sem_observables.argtypes = [vp, ctypes.POINTER(Obs), dp]
+    lib.w2_sem_destroy.argtypes = [vp]
+    lib.w2_sem_destroy.restype = None
     lib.w2_status_string.argtypes = [ctypes.c_int]
     lib.w2_status_string.restype = ctypes.c_char_p
     lib.w2_last_cuda_error.restype = ctypes.c_char_p
     for name in EXPORTS:
         if name not in ("w2_destroy", "w2_status_string", "w2_last_cuda_error", "w2_batch_destroy", "w2_mlp_destroy",
+                        "w2_sem_destroy",
                         "w2_mlp_param_count", "w2_mlp_input_dim"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -463,3 +483,89 @@ def hermitian_eigvals(a):
                                     ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)), "w2_hermitian_eigvals")
     return eig
 
+
+class SemContext:
+    """A w2_sem_ctx: one non-periodic problem (bounded box, Chebyshev
+    spectral elements in momentum) on the current CUDA device.  Arrays are
+    float64 [nx][nx][np][np]."""
+
+    def __init__(self, nx, ncell, nq, L, Lp, dt, hbar=1.0, mass=1.0, xc_kind=0, stream=None):
+        import torch
+        self.lib = load()
+        self.np_ = ncell * nq
+        self.nx = nx
+        self.shape = (nx, nx, self.np_, self.np_)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        cfg = SemConfig(nx, ncell, nq, L, Lp, dt, hbar, mass, xc_kind)
+        h = ctypes.c_void_p()
+        _check(self.lib.w2_sem_create(ctypes.byref(cfg), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h)),
+               "w2_sem_create")
+        self.h = h
+        self._keep = []
+
+    @classmethod
+    def from_problem(cls, prob, stream=None):
+        ctx = cls(prob.nx, prob.ncell, prob.nq, prob.L, prob.Lp, prob.dt, prob.hbar, prob.mass, prob.xc_kind, stream)
+        ctx.set_potentials(prob.vext, prob.vee, prob.gamma, prob.c_hartree, prob.c_xc)
+        return ctx
+
+    def set_potentials(self, vext, vee, gamma, c_h, c_xc):
+        fe = W2_FN(lambda x, u: float(vext(x)))
+        fw = W2_FN(lambda x, u: float(vee(x)))
+        self._keep = [fe, fw]
+        _check(self.lib.w2_sem_set_potentials(self.h, fe, None, fw, None, gamma, c_h, c_xc), "w2_sem_set_potentials")
+
+    def momenta(self):
+        p = np.zeros(self.np_)
+        w = np.zeros(self.np_)
+        dp = ctypes.POINTER(ctypes.c_double)
+        _check(self.lib.w2_sem_momenta(self.h, p.ctypes.data_as(dp), w.ctypes.data_as(dp)), "w2_sem_momenta")
+        return p, w
+
+    def set_state(self, f):
+        import torch
+        if isinstance(f, torch.Tensor):
+            _check(self.lib.w2_sem_set_state(self.h, _dev_ptr(f, self.shape), 1), "w2_sem_set_state")
+        else:
+            a = np.ascontiguousarray(f, dtype=np.float64)
+            assert a.shape == self.shape
+            _check(self.lib.w2_sem_set_state(self.h, a.ctypes.data_as(ctypes.c_void_p), 0), "w2_sem_set_state")
+
+    def get_state(self, out=None):
+        if out is not None:
+            _check(self.lib.w2_sem_get_state(self.h, _dev_ptr(out, self.shape), 1), "w2_sem_get_state")
+            return out
+        a = np.empty(self.shape)
+        _check(self.lib.w2_sem_get_state(self.h, a.ctypes.data_as(ctypes.c_void_p), 0), "w2_sem_get_state")
+        return a
+
+    def theta(self, f, out):
+        _check(self.lib.w2_sem_theta(self.h, _dev_ptr(f, self.shape), _dev_ptr(out, self.shape)), "w2_sem_theta")
+        return out
+
+    def advect(self, f, out):
+        _check(self.lib.w2_sem_advect(self.h, _dev_ptr(f, self.shape), _dev_ptr(out, self.shape)), "w2_sem_advect")
+        return out
+
+    def step(self, n=1):
+        _check(self.lib.w2_sem_step(self.h, int(n)), "w2_sem_step")
+
+    def observables(self):
+        o = Obs()
+        n1 = np.zeros(self.nx)
+        _check(self.lib.w2_sem_observables(self.h, ctypes.byref(o), n1.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "w2_sem_observables")
+        return Observables(o.mass, o.energy, o.purity, o.entropy_lin, o.l2norm, o.step, n1, None, "W2_OK")
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.w2_sem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

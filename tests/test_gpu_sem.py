@@ -1,0 +1,157 @@
+"""GPU parity of the non-periodic path (Chebyshev spectral elements in
+momentum, natural-boundary spline in position, Sec. 3.2 and 4.1) against the
+numpy oracle, through the C ABI (include/w2_sem.h).
+
+Sizes span several 64-wide product tiles and ragged tails (odd and even nx,
+nq not a power of two, np not a multiple of the tile); the last case is the
+strongly correlated example's mesh (201^2 x 128^2) checked on sampled
+spatial points, where the two-body chain runs in many chunks of X with a
+ragged last chunk.  Bars: operator 1e-12, shift 1e-13, steps 1e-10
+(relative L2), observables 1e-12.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import SemOracle
+from paper_2511_11354_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_11354_gb300 import build
+    build.build()
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _perturbed(f, seed=2):
+    rng = np.random.default_rng(seed)
+    g = f * (1.0 + 0.1 * rng.standard_normal(f.shape))
+    return np.ascontiguousarray(0.5 * (g + g.transpose(1, 0, 3, 2)))
+
+
+# (nx, ncell, nq, L, hamiltonian)
+CASES = [(17, 2, 6, 12.0, "IV"), (20, 3, 5, 10.0, "III"), (33, 4, 16, 14.0, "IV"), (25, 1, 32, 16.0, "II")]
+
+
+def _case(nx, ncell, nq, L, ham, soft=1.0):
+    prob, f = inputs.workload_correlated(ham, soft=soft, nx=nx, ncell=ncell, nq=nq, L=L)
+    return prob, _perturbed(f)
+
+
+def _ctx(prob):
+    from paper_2511_11354_gb300 import w2
+    return w2.SemContext.from_problem(prob)
+
+
+def test_momenta_and_weights():
+    prob, _ = _case(17, 3, 7, 12.0, "I")
+    p, w = _ctx(prob).momenta()
+    o = SemOracle(prob)
+    np.testing.assert_allclose(p, o.p, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(w, o.w, rtol=1e-14, atol=1e-15)
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_theta_parity(case):
+    prob, f = _case(*case)
+    ctx = _ctx(prob)
+    d = torch.from_numpy(f).cuda()
+    out = torch.empty_like(d)
+    ctx.theta(d, out)
+    assert rel(out.cpu().numpy(), SemOracle(prob).theta(f)) < 1e-12
+
+
+@pytest.mark.parametrize("which", ["one_body", "two_body"])
+def test_theta_terms_separately(which):
+    prob, f = _case(21, 2, 8, 12.0, "IV", soft=0.01)
+    if which == "one_body":
+        prob.gamma = 0.0
+    else:
+        prob.c_hartree, prob.c_xc, prob.vext = 0.0, 0.0, inputs.zero_potential()
+    ctx = _ctx(prob)
+    d = torch.from_numpy(f).cuda()
+    out = torch.empty_like(d)
+    ctx.theta(d, out)
+    assert rel(out.cpu().numpy(), SemOracle(prob).theta(f)) < 1e-12
+
+
+@pytest.mark.parametrize("case", CASES[:3])
+def test_advect_parity(case):
+    prob, f = _case(*case)
+    prob.dt = 0.37  # feet several cells away, some outside the box
+    ctx = _ctx(prob)
+    d = torch.from_numpy(f).cuda()
+    out = torch.empty_like(d)
+    ctx.advect(d, out)
+    assert rel(out.cpu().numpy(), SemOracle(prob).advect(f)) < 1e-13
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[1]])
+def test_steps_parity(case):
+    prob, f = _case(*case)
+    ctx = _ctx(prob)
+    ctx.set_state(f)
+    ctx.step(5)
+    ref = SemOracle(prob).step(f, 5)
+    assert rel(ctx.get_state(), ref) < 1e-10
+
+
+def test_observables_parity():
+    prob, f = _case(17, 2, 6, 12.0, "IV")
+    ctx = _ctx(prob)
+    ctx.set_state(f)
+    ob = ctx.observables()
+    ref = SemOracle(prob).observables(f)
+    for k in ("mass", "energy", "purity", "l2norm"):
+        assert abs(getattr(ob, k) - ref[k]) <= 1e-12 * max(1.0, abs(ref[k])), k
+    np.testing.assert_allclose(ob.n1, ref["n1"], rtol=1e-12, atol=1e-15)
+    assert ob.step == 0
+
+
+def test_errors():
+    from paper_2511_11354_gb300 import w2
+    with pytest.raises(w2.W2Error):
+        w2.SemContext(7, 2, 4, 10.0, 5.0, 0.01)         # nx too small
+    with pytest.raises(w2.W2Error):
+        w2.SemContext(17, 2, 33, 10.0, 5.0, 0.01)       # nq too large
+    ctx = w2.SemContext(17, 2, 4, 10.0, 5.0, 0.01)
+    with pytest.raises(w2.W2Error) as e:
+        ctx.step(1)                                     # no potentials, no state
+    assert e.value.name == "W2_ERR_STATE"
+    d = torch.zeros(ctx.shape, dtype=torch.float64, device="cuda")
+    with pytest.raises(w2.W2Error) as e:
+        ctx.advect(d, d)                                # overlapping arrays
+    assert e.value.name == "W2_ERR_ARG"
+
+
+def test_paper_mesh_sampled():
+    """The strongly correlated example's mesh: 201^2 x (8 x 16)^2 on
+    [-15, 15]^2 x [-10 pi/3, 10 pi/3]^2, Hamiltonian IV; the operator at 24
+    sampled spatial points (its potentials from the whole state) and one
+    step's exchange symmetry."""
+    prob, f = inputs.workload_correlated("IV", soft=1.0)
+    ctx = _ctx(prob)
+    d = torch.from_numpy(f).cuda()
+    out = torch.empty_like(d)
+    ctx.theta(d, out)
+    xs = np.random.default_rng(5).choice(prob.nx * prob.nx, 24, replace=False)
+    got = out.view(prob.nx * prob.nx, prob.np_, prob.np_)[torch.from_numpy(xs).cuda()].cpu().numpy()
+    assert rel(got, SemOracle(prob).theta_sample(f, xs)) < 1e-12
+    del out
+    ctx.set_state(d)
+    ctx.step(1)
+    g = ctx.get_state(torch.empty_like(d))
+    asym = (g - g.permute(1, 0, 3, 2)).abs().max().item()
+    assert math.isfinite(asym) and asym <= 1e-13 * g.abs().max().item()

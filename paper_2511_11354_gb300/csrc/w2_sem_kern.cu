@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(1024) k_sem_obs_fin(SemObsArgs a) {
     const double *n = a.n + k * nx;
     double vh = 0.0;
     for (int q = 0; q < nx; ++q) vh = fma(a.wgrid[i - q + W0], n[q], vh);
-    eh += n[i] * a.dx * vh;
+    eh += n[i] * a.dx * (a.dx * vh);  // n(x_i) dx V_H[n](x_i)
   }
   eh = block_sum<1024>(eh, red);
   // purity 2 pi hbar dx sum_{i1,j1} w_j1 f1^2, f1 = dx sum_i2 r_X[j1]

@@ -244,7 +244,61 @@ def bench_forms(args, barrier):
     bt.close()
     if not args.no_learned:
         forms["learned"] = bench_learned(args, timed)
+    if not args.no_sem:
+        forms[f"nonperiodic_correlated_{args.sem_nx}x128"] = bench_sem(args, timed)
     return forms
+
+
+def sem_flops(nx, np_):
+    """Algorithmic FP64 flops of one non-periodic operator (2 per multiply-add):
+    the one-body tables G = U-Toeplitz x psi, the products G1 F and F G2^T per
+    point X, and the two-body chain per X (F Phi^T, Ph T, Eh B, S [Ei|Er]^T on
+    the half y1 plane)."""
+    Ny, Nyh = 2 * ((nx - 1) // 2) + 1, (nx - 1) // 2 + 1
+    one = 2.0 * (2 * nx) * (2 * nx - 1) * np_ * np_ + 2.0 * nx * nx * 2 * np_ ** 3
+    two = 2.0 * nx * nx * (2 * np_ * np_ * Ny + 2 * Nyh * 2 * np_ * Ny + 2 * np_ * 2 * Nyh * Ny + np_ * np_ * 2 * Ny)
+    return one, two
+
+
+def bench_sem(args, timed):
+    """The strongly correlated example on the paper's mesh: 201^2 x (8 x 16)^2
+    points (6.6e8) on [-15, 15]^2 x [-10 pi/3, 10 pi/3]^2, Hamiltonian IV
+    (Hartree + Hedin-Lundqvist XC + smoothed Coulomb pair + external well,
+    soft 1), dt = 0.01, FP64, the operator by spectral elements (batched FP64
+    products on the FP64 pipe)."""
+    import torch
+
+    from paper_2511_11354_gb300 import inputs, w2
+    prob, f = inputs.workload_correlated("IV", soft=1.0, nx=args.sem_nx)
+    ctx = w2.SemContext.from_problem(prob)
+    d = torch.from_numpy(f).cuda()
+    del f
+    ctx.set_state(d)
+    ob0 = ctx.observables()
+    ctx.step(1)
+    k = max(1, args.sem_steps)
+    ms = timed(ctx.step, k)
+    out = torch.empty_like(d)
+    ms_theta = timed(lambda n: ctx.theta(d, out), 1)
+    ms_adv = timed(lambda n: ctx.advect(d, out), 1)
+    ob = ctx.observables()
+    one, two = sem_flops(prob.nx, prob.np_)
+    peak = _fp64_peak()["fp64_dfma_tflops"]
+    ach = (one + two) / (ms_theta * 1e-3) / 1e12
+    res = {"workload": f"strongly correlated example, Hamiltonian IV, {prob.nx}^2 x 128^2 mesh "
+                       f"({prob.points / 1e6:.0f}M points), box [-15, 15]^2, 8 Chebyshev cells x 16 points per "
+                       "momentum axis, FP64, dt = 0.01",
+           "value": prob.points * k / (ms / 1e3), "unit": UNIT, "steps": k, "warmup": 1, "ms_per_step": ms / k,
+           "theta_ms": ms_theta, "advect_ms": ms_adv,
+           "roofline": {"bound": "alu", "kernel": "k_gemm64 (batched FP64 products of the operator, DFMA)",
+                        "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                        "flops_per_operator": one + two, "two_body_share_of_flops": two / (one + two),
+                        "peak_source": "fp64_dfma_tflops measured live by paper_2511_11354_gb300/probe/fp64_peak.cu"},
+           "mass_drift": (ob.mass - ob0.mass) / ob0.mass, "energy": ob.energy}
+    ctx.close()
+    del d, out
+    torch.cuda.empty_cache()
+    return res
 
 
 def bench_plasma(args, timed):
@@ -437,6 +491,10 @@ def main():
     ap.add_argument("--no-form-error", action="store_true")
     ap.add_argument("--form-steps", type=int, default=20)
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-sem", action="store_true", help="skip the non-periodic (spectral-element) form")
+    ap.add_argument("--sem-steps", type=int, default=2)
+    ap.add_argument("--sem-nx", type=int, default=201, help="spatial points per axis of the non-periodic form")
+    ap.add_argument("--only-sem", action="store_true", help="run only the non-periodic form (for profiling commands)")
     ap.add_argument("--only-forms", action="store_true", help="run only the forms (for profiling commands)")
     ap.add_argument("--learned-steps", type=int, default=100)
     ap.add_argument("--learned-snapshots", type=int, default=300)
@@ -458,6 +516,18 @@ def main():
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w2build.build()
+    if args.only_sem:
+        def timed_only(step, k):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            step(k)
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
+        if rank == 0:
+            print(json.dumps({"impl": "w2", "only_sem": True, "sem": bench_sem(args, timed_only)}), flush=True)
+        return
     if args.only_forms:
         forms = bench_forms(args, torch.cuda.synchronize)
         if rank == 0:

@@ -71,11 +71,17 @@ extern "C" {
  * L    : box length (> 0);  Lp: momentum window length (> 0), with
  *        (Lp / ncell) * L / hbar <= 4096
  * dt   : time step tau (> 0);  hbar, mass: > 0
- * xc_kind: a w2_xc_kind */
+ * xc_kind: a w2_xc_kind
+ * precision: W2_F64 -- the operator's products on the FP64 pipe; or
+ *   W2_F64_SLICED -- the same products from exact 8-bit slices of the FP64
+ *   operands on the BF16 tensor cores (six digits per value, the 21 digit
+ *   pairs above 2^-48 of the line scales kept, integer recombination;
+ *   nx <= 256); FP64 state and results either way */
 typedef struct {
   int32_t nx, ncell, nq;
   double L, Lp, dt, hbar, mass;
   int32_t xc_kind;
+  int32_t precision;
 } w2_sem_config;
 
 typedef struct w2_sem_ctx w2_sem_ctx;

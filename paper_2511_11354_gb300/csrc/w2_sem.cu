@@ -29,6 +29,13 @@ struct w2_sem_ctx {
   double *xs = nullptr, *n = nullptr, *U = nullptr, *ut = nullptr, *G = nullptr;
   double *cT = nullptr, *cA = nullptr, *cS = nullptr, *xpart = nullptr, *obs = nullptr, *h_obs = nullptr;
   int *k0 = nullptr;
+  // tensor-core products (W2_F64_SLICED): digit planes and line exponents
+  int prec = W2_F64, Kp1 = 0, Kp2 = 0, Kp3 = 0, Kp4 = 0, ldp = 0;
+  double *ee = nullptr;                       // gamma dx^2 / (pi^2 hbar^3) [Ei | Er]
+  uint16_t *phrP = nullptr, *phiP = nullptr, *phP = nullptr, *ehP = nullptr, *eeP = nullptr, *gP = nullptr;
+  uint16_t *frP = nullptr, *fcP = nullptr, *tP = nullptr, *bP = nullptr, *sP = nullptr;
+  int *phrE = nullptr, *phiE = nullptr, *phE = nullptr, *ehE = nullptr, *eeE = nullptr, *gE = nullptr;
+  int *frE = nullptr, *fcE = nullptr, *tE = nullptr, *bE = nullptr, *sE = nullptr;
 };
 
 #define SEM_TRY(call)                   \
@@ -48,6 +55,10 @@ static void sem_free(w2_sem_ctx *c) {
   for (double *q : d)
     if (q) cudaFree(q);
   if (c->k0) cudaFree(c->k0);
+  void *v[] = {c->ee, c->phrP, c->phiP, c->phP, c->ehP, c->eeP, c->gP, c->frP, c->fcP, c->tP, c->bP, c->sP,
+               c->phrE, c->phiE, c->phE, c->ehE, c->eeE, c->gE, c->frE, c->fcE, c->tE, c->bE, c->sE};
+  for (void *q : v)
+    if (q) cudaFree(q);
   if (c->h_obs) cudaFreeHost(c->h_obs);
 }
 
@@ -58,6 +69,8 @@ extern "C" w2_status w2_sem_create(const w2_sem_config *cfg, void *cuda_stream, 
   if (nx < 8 || nx > 1024 || M < 1 || Q < 2 || Q > 32 || (long long)M * Q > 256) return W2_ERR_ARG;
   if (!(cfg->L > 0) || !(cfg->Lp > 0) || !(cfg->dt > 0) || !(cfg->hbar > 0) || !(cfg->mass > 0)) return W2_ERR_ARG;
   if (cfg->xc_kind < 0 || cfg->xc_kind > 2) return W2_ERR_ARG;
+  if (cfg->precision != W2_F64 && cfg->precision != W2_F64_SLICED) return W2_ERR_ARG;
+  if (cfg->precision == W2_F64_SLICED && nx > 256) return W2_ERR_ARG;  // sliced lines of 2 N_y <= 512 values
   // the Bessel recurrence of the oscillatory integrals runs to about z + 20 z^(1/3) + 40 terms
   if (cfg->Lp / M * cfg->L / cfg->hbar > 4096.0) return W2_ERR_ARG;
   w2_sem_ctx *ctx = new (std::nothrow) w2_sem_ctx();
@@ -70,9 +83,25 @@ extern "C" w2_status w2_sem_create(const w2_sem_config *cfg, void *cuda_stream, 
   const int np = ctx->np, Ny = ctx->Ny, Nyh = ctx->Nyh;
   ctx->npts = (long long)nx * nx * np * np;
   ctx->C = sem_adv_cols(nx, np);
-  // two-body chain chunk: about 256 MB of intermediates
+  ctx->prec = cfg->precision;
+  const bool sliced = ctx->prec == W2_F64_SLICED;
+  ctx->Kp1 = slice_kp(np); ctx->Kp2 = slice_kp(2 * np); ctx->Kp3 = slice_kp(2 * Nyh); ctx->Kp4 = slice_kp(2 * Ny);
+  ctx->ldp = (np + 7) / 8 * 8;
+  const int Kp1 = ctx->Kp1, Kp2 = ctx->Kp2, Kp3 = ctx->Kp3, Kp4 = ctx->Kp4, ldp = ctx->ldp;
+  // two-body chain chunk: about 256 MB of FP64 intermediates (1 GB with the
+  // slices, in whole rows of x1 so that a chunk's x1 index is affine in X)
   const double per_x = 8.0 * (2.0 * np * Ny + 2.0 * Nyh * Ny + 2.0 * np * Ny);
-  long long bx = (long long)(256.0 * 1024 * 1024 / per_x);
+  const double per_xs = per_x + 12.0 * ((double)np * Kp1 + (double)Kp1 * ldp + (double)Ny * Kp2 + (double)Ny * Kp3 +
+                                        (double)np * Kp4) + 4.0 * (3.0 * np + 2.0 * Ny);
+  long long bx;
+  if (!sliced) {
+    bx = (long long)(256.0 * 1024 * 1024 / per_x);
+  } else {
+    bx = (long long)(1024.0 * 1024 * 1024 / (per_xs * nx));
+    if (bx < 1) bx = 1;
+    bx *= nx;
+    while (bx > 65535) bx -= nx;
+  }
   if (bx < 1) bx = 1;
   if (bx > (long long)nx * nx) bx = (long long)nx * nx;
   ctx->bx = (int)bx;
@@ -119,6 +148,16 @@ extern "C" w2_status w2_sem_create(const w2_sem_config *cfg, void *cuda_stream, 
   SEM_ALLOC(ctx->U, 2 * nx) SEM_ALLOC(ctx->ut, 2LL * nx * (2 * nx - 1)) SEM_ALLOC(ctx->G, 2LL * nx * np * np)
   SEM_ALLOC(ctx->cT, bx * 2 * np * Ny) SEM_ALLOC(ctx->cA, bx * 2 * Nyh * Ny) SEM_ALLOC(ctx->cS, bx * 2 * np * Ny)
   SEM_ALLOC(ctx->xpart, (long long)nx * nx * (4 + np)) SEM_ALLOC(ctx->obs, 8 + nx)
+  if (sliced) {
+    SEM_ALLOC(ctx->ee, 2LL * np * Ny)
+    SEM_ALLOC(ctx->phrP, 6LL * Ny * Kp1) SEM_ALLOC(ctx->phiP, 6LL * Ny * Kp1) SEM_ALLOC(ctx->phP, 6LL * 2 * Nyh * Kp2)
+    SEM_ALLOC(ctx->ehP, 2 * 6LL * np * Kp3) SEM_ALLOC(ctx->eeP, 6LL * np * Kp4) SEM_ALLOC(ctx->gP, 6LL * 2 * nx * np * Kp1)
+    SEM_ALLOC(ctx->frP, bx * 6 * np * Kp1) SEM_ALLOC(ctx->fcP, bx * 6 * Kp1 * ldp) SEM_ALLOC(ctx->tP, bx * 6 * Ny * Kp2)
+    SEM_ALLOC(ctx->bP, bx * 6 * Ny * Kp3) SEM_ALLOC(ctx->sP, bx * 6 * np * Kp4)
+    SEM_ALLOC(ctx->phrE, Ny) SEM_ALLOC(ctx->phiE, Ny) SEM_ALLOC(ctx->phE, 2 * Nyh) SEM_ALLOC(ctx->ehE, 2 * np)
+    SEM_ALLOC(ctx->eeE, np) SEM_ALLOC(ctx->gE, 2LL * nx * np) SEM_ALLOC(ctx->frE, bx * np) SEM_ALLOC(ctx->fcE, bx * np)
+    SEM_ALLOC(ctx->tE, bx * Ny) SEM_ALLOC(ctx->bE, bx * Ny) SEM_ALLOC(ctx->sE, bx * np)
+  }
 #undef SEM_ALLOC
   if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->h_obs, sizeof(double) * (8 + nx));
   auto up = [&](void *dst, const void *src, size_t bytes) {
@@ -135,6 +174,17 @@ extern "C" w2_status w2_sem_create(const w2_sem_config *cfg, void *cuda_stream, 
                 ctx->osc, ctx->psi, ctx->phir, ctx->phii, ctx->ph, ctx->eh, ctx->eier};
   if (e == cudaSuccess) e = launch_sem_osc(ta, ctx->stream);
   if (e == cudaSuccess) e = launch_sem_tables(ta, ctx->stream);
+  if (sliced) {  // static slices: Phi rows (K = np), Ph rows (K = 2 np), the two Eh blocks (K = 2 Nyh)
+    auto rows = [&](const double *in, int L, int K, int Kp, uint16_t *P, int *E) {
+      SliceArgs sa{L, K, Kp, 0, in, K, 1, 0, 0, P, (long long)L * Kp, 0, E, 0, 1, 1, nullptr, nx, ctx->h, 0};
+      if (e == cudaSuccess) e = launch_slice(0, 0, sa, ctx->stream);
+    };
+    rows(ctx->phir, Ny, np, Kp1, ctx->phrP, ctx->phrE);
+    rows(ctx->phii, Ny, np, Kp1, ctx->phiP, ctx->phiE);
+    rows(ctx->ph, 2 * Nyh, 2 * np, Kp2, ctx->phP, ctx->phE);
+    rows(ctx->eh, np, 2 * Nyh, Kp3, ctx->ehP, ctx->ehE);
+    rows(ctx->eh + (long long)np * 2 * Nyh, np, 2 * Nyh, Kp3, ctx->ehP + 6LL * np * Kp3, ctx->ehE + np);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
     w2::note_cuda_error(e);
@@ -163,6 +213,14 @@ extern "C" w2_status w2_sem_set_potentials(w2_sem_ctx *ctx, w2_fn vext, void *ue
     if (!isfinite(x)) return W2_ERR_ARG;
   SEM_TRY(cudaMemcpyAsync(ctx->vext, v.data(), sizeof(double) * nx, cudaMemcpyHostToDevice, ctx->stream));
   SEM_TRY(cudaMemcpyAsync(ctx->wgrid, wg.data(), sizeof(double) * wg.size(), cudaMemcpyHostToDevice, ctx->stream));
+  if (ctx->prec == W2_F64_SLICED) {
+    const double alpha = gamma * ctx->dx * ctx->dx / (M_PI * M_PI * ctx->hbar * ctx->hbar * ctx->hbar);
+    const long long n = 2LL * ctx->np * ctx->Ny;
+    SEM_TRY(launch_sem_scale(n, alpha, ctx->eier, ctx->ee, ctx->stream));
+    SliceArgs sa{ctx->np, 2 * ctx->Ny, ctx->Kp4, 0, ctx->ee, 2 * ctx->Ny, 1, 0, 0, ctx->eeP,
+                 (long long)ctx->np * ctx->Kp4, 0, ctx->eeE, 0, 1, 1, nullptr, nx, ctx->h, 0};
+    SEM_TRY(launch_slice(0, 0, sa, ctx->stream));
+  }
   SEM_TRY(cudaStreamSynchronize(ctx->stream));
   ctx->gamma = gamma; ctx->c_h = c_h; ctx->c_xc = c_xc;
   ctx->have_pot = true;
@@ -201,7 +259,10 @@ extern "C" w2_status w2_sem_get_state(w2_sem_ctx *ctx, double *f, int32_t on_dev
 // sum_n U(x_n) psi[n - m] -> G1(x1) F_X + F_X G2(x2)^T, then the two-body chain
 // per chunk of X: T = F Phi^T, [Ar; Ai] = Ph T, B = w D (.) A,
 // [Sr | Si] = Eh B, out += c Im(S E^T).
+static w2_status sem_theta_sliced(w2_sem_ctx *ctx, const double *in, double *out);
+
 static w2_status sem_theta(w2_sem_ctx *ctx, const double *in, double *out) {
+  if (ctx->prec == W2_F64_SLICED) return sem_theta_sliced(ctx, in, out);
   const int nx = ctx->nx, np = ctx->np, Ny = ctx->Ny, Nyh = ctx->Nyh;
   const long long np2 = (long long)np * np, nX = (long long)nx * nx;
   cudaStream_t s = ctx->stream;
@@ -249,6 +310,100 @@ static w2_status sem_theta(w2_sem_ctx *ctx, const double *in, double *out) {
     g = Gemm64{np, np, 2 * Ny, ctx->cS, 2 * Ny, 0, ctx->eier, 2 * Ny, 1, out + x0 * np2, np, alpha, 1.0, nb, 1,
                sS, 0, 0, 0, np2, 0};
     SEM_TRY(launch_gemm64(g, s));
+  }
+  return W2_OK;
+}
+
+// The same operator from exact slices on the BF16 tensor cores (w2_gemms.cu).
+// Layouts chosen so that every sliced line runs along the contraction index:
+// T^T = Phi F^T ([Ny][2np]: [Tr | Ti]), A^T = T^T Ph^T ([Ny][2Nyh]), the D_V
+// weighting folded into the slicing of A^T, S = Eh B ([np][2Ny]: [Sr | Si]),
+// out += S (alpha [Ei | Er])^T; the one-body products use F's row slices
+// (F G2^T, and T^T) and its column slices (G1 F).
+static w2_status sem_theta_sliced(w2_sem_ctx *ctx, const double *in, double *out) {
+  const int nx = ctx->nx, np = ctx->np, Ny = ctx->Ny, Nyh = ctx->Nyh;
+  const int Kp1 = ctx->Kp1, Kp2 = ctx->Kp2, Kp3 = ctx->Kp3, Kp4 = ctx->Kp4, ldp = ctx->ldp;
+  const long long np2 = (long long)np * np, nX = (long long)nx * nx;
+  cudaStream_t s = ctx->stream;
+  SEM_TRY(launch_sem_marginal(nx, np, ctx->dx, in, ctx->w, ctx->xs, ctx->n, s));
+  SemPotArgs pa{nx, ctx->xc_kind, ctx->dx, ctx->c_h, ctx->c_xc, ctx->n, ctx->vext, ctx->wgrid, ctx->U, ctx->ut};
+  SEM_TRY(launch_sem_potential(pa, s));
+  Gemm64 g{2 * nx, (int)np2, 2 * nx - 1, ctx->ut, 2 * nx - 1, 0, ctx->psi, np2, 0, ctx->G, np2, 1.0, 0.0, 1, 1,
+           0, 0, 0, 0, 0, 0};
+  SEM_TRY(launch_gemm64(g, s));
+  {
+    SliceArgs sa{2 * nx * np, np, Kp1, 0, ctx->G, np, 1, 0, 0, ctx->gP, 2LL * nx * np * Kp1, 0, ctx->gE, 0, 1, 1,
+                 nullptr, nx, ctx->h, 0};
+    SEM_TRY(launch_slice(0, 0, sa, s));
+  }
+  // products over K in pieces of at most 256 (multiples of 32), adding after the first
+  auto gemm_k = [&](GemmSArgs a, int K, int b_kn) -> cudaError_t {
+    const int beta0 = a.beta;
+    for (int k0 = 0; k0 < K; k0 += 256) {
+      a.k0 = k0;
+      a.K = K - k0 < 256 ? K - k0 : 256;
+      a.beta = k0 ? 1 : beta0;
+      const cudaError_t e = launch_gemms(b_kn, a, s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  const long long frS = 6LL * np * Kp1, fcS = 6LL * Kp1 * ldp, tS = 6LL * Ny * Kp2, bS = 6LL * Ny * Kp3,
+                  sS = 6LL * np * Kp4;
+  for (long long x0 = 0; x0 < nX; x0 += ctx->bx) {
+    const int nb = (int)((nX - x0) < ctx->bx ? (nX - x0) : ctx->bx);
+    const long long i10 = x0 / nx;
+    const double *F = in + x0 * np2;
+    SliceArgs fr{np, np, Kp1, 0, F, np, 1, np2, 0, ctx->frP, (long long)np * Kp1, frS, ctx->frE, np, nb, 1,
+                 nullptr, nx, ctx->h, 0};
+    SEM_TRY(launch_slice(0, 0, fr, s));
+    SliceArgs fc{np, np, Kp1, ldp, F, 1, np, np2, 0, ctx->fcP, (long long)Kp1 * ldp, fcS, ctx->fcE, np, nb, 1,
+                 nullptr, nx, ctx->h, 0};
+    SEM_TRY(launch_slice(1, 0, fc, s));
+    // out_X = G1[i1] F_X  (B = F's column slices, row-major planes)
+    GemmSArgs a1{np, np, np, 0, ctx->gP + i10 * np * Kp1, Kp1, 2LL * nx * np * Kp1, (long long)np * Kp1, 0,
+                 ctx->gE + i10 * np, np, 0, ctx->fcP, ldp, (long long)Kp1 * ldp, nx * fcS, fcS, ctx->fcE,
+                 (long long)nx * np, np, out + x0 * np2, np, nx * np2, np2, 0, nb, nx};
+    SEM_TRY(gemm_k(a1, np, 1));
+    // out_X += F_X G2[i2]^T
+    GemmSArgs a2{np, np, np, 0, ctx->frP, Kp1, (long long)np * Kp1, nx * frS, frS, ctx->frE, (long long)nx * np, np,
+                 ctx->gP + (long long)nx * np * Kp1, Kp1, 2LL * nx * np * Kp1, 0, (long long)np * Kp1,
+                 ctx->gE + (long long)nx * np, 0, np, out + x0 * np2, np, nx * np2, np2, 1, nb, nx};
+    SEM_TRY(gemm_k(a2, np, 0));
+    if (ctx->gamma == 0.0) continue;
+    // T^T_X = [Phr F_X^T | Phi F_X^T]
+    GemmSArgs t{Ny, np, np, 0, ctx->phrP, Kp1, (long long)Ny * Kp1, 0, 0, ctx->phrE, 0, 0, ctx->frP, Kp1,
+                (long long)np * Kp1, frS, 0, ctx->frE, np, 0, ctx->cT, 2 * np, (long long)Ny * 2 * np, 0, 0, nb, 1};
+    SEM_TRY(gemm_k(t, np, 0));
+    t.A = ctx->phiP;
+    t.Ae = ctx->phiE;
+    t.C = ctx->cT + np;
+    SEM_TRY(gemm_k(t, np, 0));
+    SliceArgs ts{Ny, 2 * np, Kp2, 0, ctx->cT, 2 * np, 1, (long long)Ny * 2 * np, 0, ctx->tP, (long long)Ny * Kp2, tS,
+                 ctx->tE, Ny, nb, 1, nullptr, nx, ctx->h, 0};
+    SEM_TRY(launch_slice(0, 0, ts, s));
+    // A^T_X = T^T_X Ph^T
+    GemmSArgs aa{Ny, 2 * Nyh, 2 * np, 0, ctx->tP, Kp2, (long long)Ny * Kp2, tS, 0, ctx->tE, Ny, 0, ctx->phP, Kp2,
+                 2LL * Nyh * Kp2, 0, 0, ctx->phE, 0, 0, ctx->cA, 2 * Nyh, (long long)Ny * 2 * Nyh, 0, 0, nb, 1};
+    SEM_TRY(gemm_k(aa, 2 * np, 0));
+    // slices of B^T_X = w D (.) A^T_X
+    SliceArgs bs{Ny, 2 * Nyh, Kp3, 0, ctx->cA, 2 * Nyh, 1, (long long)Ny * 2 * Nyh, 0, ctx->bP, (long long)Ny * Kp3,
+                 bS, ctx->bE, Ny, nb, 1, ctx->wgrid, nx, ctx->h, (int)x0};
+    SEM_TRY(launch_slice(0, 1, bs, s));
+    // [Sr | Si]_X = [Er_h | -Ei_h] B, [Ei_h | Er_h] B
+    for (int blk = 0; blk < 2; ++blk) {
+      GemmSArgs sg{np, Ny, 2 * Nyh, 0, ctx->ehP + blk * 6LL * np * Kp3, Kp3, (long long)np * Kp3, 0, 0,
+                   ctx->ehE + blk * np, 0, 0, ctx->bP, Kp3, (long long)Ny * Kp3, bS, 0, ctx->bE, Ny, 0,
+                   ctx->cS + blk * Ny, 2 * Ny, (long long)np * 2 * Ny, 0, 0, nb, 1};
+      SEM_TRY(gemm_k(sg, 2 * Nyh, 0));
+    }
+    SliceArgs ss{np, 2 * Ny, Kp4, 0, ctx->cS, 2 * Ny, 1, (long long)np * 2 * Ny, 0, ctx->sP, (long long)np * Kp4, sS,
+                 ctx->sE, np, nb, 1, nullptr, nx, ctx->h, 0};
+    SEM_TRY(launch_slice(0, 0, ss, s));
+    // out_X += S_X (alpha [Ei | Er])^T
+    GemmSArgs fo{np, np, 2 * Ny, 0, ctx->sP, Kp4, (long long)np * Kp4, sS, 0, ctx->sE, np, 0, ctx->eeP, Kp4,
+                 (long long)np * Kp4, 0, 0, ctx->eeE, 0, 0, out + x0 * np2, np, np2, 0, 1, nb, 1};
+    SEM_TRY(gemm_k(fo, 2 * Ny, 0));
   }
   return W2_OK;
 }

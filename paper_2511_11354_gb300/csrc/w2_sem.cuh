@@ -95,4 +95,53 @@ struct SemObsArgs {
 };
 cudaError_t launch_sem_obs(const SemObsArgs &a, cudaStream_t s);
 
+// Scaling: out = a * in (n elements).
+cudaError_t launch_sem_scale(long long n, double a, const double *in, double *out, cudaStream_t s);
+
+// Exact slices of FP64 lines for the tensor-core products (w2_gemms.cu).
+// Row mode (cols = 0): line l holds in[l * ls + k], k < K (K <= 512); the
+// planes are [6][L][Kp] (plane stride pP = L * Kp), zero past K.  Column
+// mode (cols = 1): line l is column l of a row-major K x L matrix with row
+// stride ks; the planes are [6][Kp][ldp] (pP = Kp * ldp), zero past K and L.
+// ex[l] receives the line exponent E (every |v| < 2^E).  Batch b splits as
+// (b / bdiv, b % bdiv) for the input (strides sIn1, sIn2); planes and
+// exponents move by b * sP and b * sE.  Mode 1 (rows only) first multiplies
+// element (c = l, k) by w(r) (W(rho + u dx) - W(rho - u dx)), r = k % (h+1),
+// u = r - (c - h), rho = i1 - i2 of X = x0 + b (the two-body D_V weighting).
+struct SliceArgs {
+  int L, K, Kp, ldp;
+  const double *in;
+  long long ls, ks, sIn1, sIn2;
+  uint16_t *planes;
+  long long pP, sP;
+  int *ex;
+  long long sE;
+  int nbatch, bdiv;
+  const double *wgrid;
+  int nx, h, x0;
+};
+cudaError_t launch_slice(int cols, int mode, const SliceArgs &a, cudaStream_t s);
+int slice_kp(int K);
+
+// C_b (=|+=) A_b B_b from slices: A planes [6][M][lda] (pA plane stride,
+// line = row), B planes [6][N][ldb] (b_kn = 0, line = column) or [6][K][ldb]
+// (b_kn = 1, row-major), contraction over k0 .. k0 + K - 1 (K <= 256, k0 a
+// multiple of 32; the planes hold zeros past the data up to the next
+// multiple of 32).  Exponents Ae[M], Be[N].  beta = 1 adds to C.
+struct GemmSArgs {
+  int M, N, K, k0;
+  const uint16_t *A;
+  long long lda, pA, sA1, sA2;
+  const int *Ae;
+  long long sAe1, sAe2;
+  const uint16_t *B;
+  long long ldb, pB, sB1, sB2;
+  const int *Be;
+  long long sBe1, sBe2;
+  double *C;
+  long long ldc, sC1, sC2;
+  int beta, nbatch, bdiv;
+};
+cudaError_t launch_gemms(int b_kn, const GemmSArgs &g, cudaStream_t s);
+
 }  // namespace w2sem

@@ -293,6 +293,11 @@ __global__ void k_sem_adv(SemAdvArgs a) {
   }
 }
 
+__global__ void k_sem_scale(long long n, double a, const double *__restrict__ in, double *out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    out[e] = a * in[e];
+}
+
 __global__ void k_sem_axpy(long long n, const double *__restrict__ x, double a, const double *__restrict__ y,
                            const double *__restrict__ y2, double *out) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
@@ -458,6 +463,11 @@ cudaError_t launch_sem_adv(int axis, const SemAdvArgs &a, cudaStream_t s) {
 cudaError_t launch_sem_axpy(long long n, const double *x, double a, const double *y, const double *y2, double *out,
                             cudaStream_t s) {
   k_sem_axpy<<<grid_for(n, 256), 256, 0, s>>>(n, x, a, y, y2, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sem_scale(long long n, double a, const double *in, double *out, cudaStream_t s) {
+  k_sem_scale<<<grid_for(n, 256), 256, 0, s>>>(n, a, in, out);
   return cudaGetLastError();
 }
 

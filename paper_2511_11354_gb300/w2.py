@@ -64,7 +64,7 @@ class Obs(ctypes.Structure):
 class SemConfig(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ncell", ctypes.c_int32), ("nq", ctypes.c_int32), ("L", ctypes.c_double),
                 ("Lp", ctypes.c_double), ("dt", ctypes.c_double), ("hbar", ctypes.c_double),
-                ("mass", ctypes.c_double), ("xc_kind", ctypes.c_int32)]
+                ("mass", ctypes.c_double), ("xc_kind", ctypes.c_int32), ("precision", ctypes.c_int32)]
 
 
 W2_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_double, ctypes.c_void_p)
@@ -489,16 +489,17 @@ class SemContext:
     spectral elements in momentum) on the current CUDA device.  Arrays are
     float64 [nx][nx][np][np]."""
 
-    def __init__(self, nx, ncell, nq, L, Lp, dt, hbar=1.0, mass=1.0, xc_kind=0, stream=None):
+    def __init__(self, nx, ncell, nq, L, Lp, dt, hbar=1.0, mass=1.0, xc_kind=0, stream=None, precision=W2_F64):
         import torch
         self.lib = load()
+        self.precision = precision
         self.np_ = ncell * nq
         self.nx = nx
         self.shape = (nx, nx, self.np_, self.np_)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
-        cfg = SemConfig(nx, ncell, nq, L, Lp, dt, hbar, mass, xc_kind)
+        cfg = SemConfig(nx, ncell, nq, L, Lp, dt, hbar, mass, xc_kind, precision)
         h = ctypes.c_void_p()
         _check(self.lib.w2_sem_create(ctypes.byref(cfg), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h)),
                "w2_sem_create")
@@ -506,8 +507,9 @@ class SemContext:
         self._keep = []
 
     @classmethod
-    def from_problem(cls, prob, stream=None):
-        ctx = cls(prob.nx, prob.ncell, prob.nq, prob.L, prob.Lp, prob.dt, prob.hbar, prob.mass, prob.xc_kind, stream)
+    def from_problem(cls, prob, stream=None, precision=W2_F64):
+        ctx = cls(prob.nx, prob.ncell, prob.nq, prob.L, prob.Lp, prob.dt, prob.hbar, prob.mass, prob.xc_kind, stream,
+                  precision)
         ctx.set_potentials(prob.vext, prob.vee, prob.gamma, prob.c_hartree, prob.c_xc)
         return ctx
 

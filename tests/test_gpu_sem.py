@@ -50,9 +50,15 @@ def _case(nx, ncell, nq, L, ham, soft=1.0):
     return prob, _perturbed(f)
 
 
-def _ctx(prob):
+def _ctx(prob, prec="W2_F64"):
     from paper_2511_11354_gb300 import w2
-    return w2.SemContext.from_problem(prob)
+    return w2.SemContext.from_problem(prob, precision=getattr(w2, prec))
+
+
+# operator bars: FP64 pipe, and the tensor-core products from 47-bit slices
+# (each product of the chain rounds near 2^-47 of its line scales; measured
+# at the level of the FP64 pipe, about 1e-13)
+THETA_BAR = {"W2_F64": 1e-12, "W2_F64_SLICED": 1e-12}
 
 
 def test_momenta_and_weights():
@@ -63,28 +69,34 @@ def test_momenta_and_weights():
     np.testing.assert_allclose(w, o.w, rtol=1e-14, atol=1e-15)
 
 
+@pytest.mark.parametrize("prec", ["W2_F64", "W2_F64_SLICED"])
 @pytest.mark.parametrize("case", CASES)
-def test_theta_parity(case):
+def test_theta_parity(case, prec):
     prob, f = _case(*case)
-    ctx = _ctx(prob)
+    ctx = _ctx(prob, prec)
     d = torch.from_numpy(f).cuda()
     out = torch.empty_like(d)
     ctx.theta(d, out)
-    assert rel(out.cpu().numpy(), SemOracle(prob).theta(f)) < 1e-12
+    err = rel(out.cpu().numpy(), SemOracle(prob).theta(f))
+    print(f"theta {case} {prec}: {err:.3e}")
+    assert err < THETA_BAR[prec]
 
 
+@pytest.mark.parametrize("prec", ["W2_F64", "W2_F64_SLICED"])
 @pytest.mark.parametrize("which", ["one_body", "two_body"])
-def test_theta_terms_separately(which):
+def test_theta_terms_separately(which, prec):
     prob, f = _case(21, 2, 8, 12.0, "IV", soft=0.01)
     if which == "one_body":
         prob.gamma = 0.0
     else:
         prob.c_hartree, prob.c_xc, prob.vext = 0.0, 0.0, inputs.zero_potential()
-    ctx = _ctx(prob)
+    ctx = _ctx(prob, prec)
     d = torch.from_numpy(f).cuda()
     out = torch.empty_like(d)
     ctx.theta(d, out)
-    assert rel(out.cpu().numpy(), SemOracle(prob).theta(f)) < 1e-12
+    err = rel(out.cpu().numpy(), SemOracle(prob).theta(f))
+    print(f"theta {which} {prec}: {err:.3e}")
+    assert err < THETA_BAR[prec]
 
 
 @pytest.mark.parametrize("case", CASES[:3])
@@ -98,14 +110,17 @@ def test_advect_parity(case):
     assert rel(out.cpu().numpy(), SemOracle(prob).advect(f)) < 1e-13
 
 
+@pytest.mark.parametrize("prec", ["W2_F64", "W2_F64_SLICED"])
 @pytest.mark.parametrize("case", [CASES[0], CASES[1]])
-def test_steps_parity(case):
+def test_steps_parity(case, prec):
     prob, f = _case(*case)
-    ctx = _ctx(prob)
+    ctx = _ctx(prob, prec)
     ctx.set_state(f)
     ctx.step(5)
     ref = SemOracle(prob).step(f, 5)
-    assert rel(ctx.get_state(), ref) < 1e-10
+    err = rel(ctx.get_state(), ref)
+    print(f"steps {case} {prec}: {err:.3e}")
+    assert err < 1e-10
 
 
 def test_observables_parity():
@@ -126,6 +141,8 @@ def test_errors():
         w2.SemContext(7, 2, 4, 10.0, 5.0, 0.01)         # nx too small
     with pytest.raises(w2.W2Error):
         w2.SemContext(17, 2, 33, 10.0, 5.0, 0.01)       # nq too large
+    with pytest.raises(w2.W2Error):
+        w2.SemContext(257, 2, 4, 10.0, 5.0, 0.01, precision=w2.W2_F64_SLICED)  # sliced lines too long
     ctx = w2.SemContext(17, 2, 4, 10.0, 5.0, 0.01)
     with pytest.raises(w2.W2Error) as e:
         ctx.step(1)                                     # no potentials, no state
@@ -136,22 +153,25 @@ def test_errors():
     assert e.value.name == "W2_ERR_ARG"
 
 
-def test_paper_mesh_sampled():
+@pytest.mark.parametrize("prec", ["W2_F64", "W2_F64_SLICED"])
+def test_paper_mesh_sampled(prec):
     """The strongly correlated example's mesh: 201^2 x (8 x 16)^2 on
     [-15, 15]^2 x [-10 pi/3, 10 pi/3]^2, Hamiltonian IV; the operator at 24
     sampled spatial points (its potentials from the whole state) and one
     step's exchange symmetry."""
     prob, f = inputs.workload_correlated("IV", soft=1.0)
-    ctx = _ctx(prob)
+    ctx = _ctx(prob, prec)
     d = torch.from_numpy(f).cuda()
     out = torch.empty_like(d)
     ctx.theta(d, out)
     xs = np.random.default_rng(5).choice(prob.nx * prob.nx, 24, replace=False)
     got = out.view(prob.nx * prob.nx, prob.np_, prob.np_)[torch.from_numpy(xs).cuda()].cpu().numpy()
-    assert rel(got, SemOracle(prob).theta_sample(f, xs)) < 1e-12
+    err = rel(got, SemOracle(prob).theta_sample(f, xs))
+    print(f"paper mesh {prec}: {err:.3e}")
+    assert err < THETA_BAR[prec]
     del out
     ctx.set_state(d)
     ctx.step(1)
     g = ctx.get_state(torch.empty_like(d))
     asym = (g - g.permute(1, 0, 3, 2)).abs().max().item()
-    assert math.isfinite(asym) and asym <= 1e-13 * g.abs().max().item()
+    assert math.isfinite(asym) and asym <= (1e-13 if prec == "W2_F64" else 1e-11) * g.abs().max().item()

@@ -25,8 +25,11 @@
 //
 // Tiles.  A CTA of 4 warps computes a 64 x 32 output tile (warp tile 32 x 16:
 // two m16 by two n8 mma.m16n8k16 tiles), K in stages of 32 staged by cp.async
-// into shared memory (digit planes with a row stride of 40 BF16, conflict-free
-// for ldmatrix), two stages in flight.
+// into shared memory, two stages in flight.  Each 64-byte row of a digit
+// plane keeps its four 16-byte chunks in the order c ^ ((row >> 1) & 3), so
+// that the eight rows an ldmatrix reads fall in distinct banks without
+// padding (74 KB per CTA: three CTAs per SM).  The output tiles of one
+// batch entry are consecutive CTAs, so its operand slices are re-read from L2.
 #include <math.h>
 #include <stdint.h>
 
@@ -203,12 +206,15 @@ __device__ __forceinline__ uint32_t scale8(uint32_t x) {
   return __vsub2(x, nz & 0x04000400u);
 }
 
-constexpr int GM = 64, GN = 32, GK = 32, GT = 128, SPD = GK + 8;
+constexpr int GM = 64, GN = 32, GK = 32, GT = 128;
+
+// BF16 offset of chunk c (8 elements) of row r in a swizzled 32-element row.
+__device__ __forceinline__ int swz(int r, int c) { return r * 32 + ((c ^ ((r >> 1) & 3)) << 3); }
 
 template <int B_KN>
 struct GLayout {
-  static constexpr int a_stage = kDig * GM * SPD;                          // BF16 elements
-  static constexpr int b_stage = B_KN ? kDig * GK * (GN + 8) : kDig * GN * SPD;
+  static constexpr int a_stage = kDig * GM * GK;                           // BF16 elements
+  static constexpr int b_stage = kDig * GN * GK;                           // [n][k] or [k][n], 32 x 32
   static constexpr size_t bytes = 2 * (size_t)(a_stage + b_stage) * 2;
 };
 
@@ -217,7 +223,8 @@ __global__ void __launch_bounds__(GT) k_gemms(GemmSArgs g) {
   extern __shared__ __align__(16) uint16_t sm[];
   using Ly = GLayout<B_KN>;
   uint16_t *As = sm, *Bs = sm + 2 * Ly::a_stage;
-  const int b = blockIdx.x, n0 = blockIdx.y * GN, m0 = blockIdx.z * GM;
+  const int tn = (g.N + GN - 1) / GN;
+  const int b = blockIdx.y, n0 = (blockIdx.x % tn) * GN, m0 = (blockIdx.x / tn) * GM;
   const long long b1 = b / g.bdiv, b2 = b % g.bdiv;
   const uint16_t *A = g.A + b1 * g.sA1 + b2 * g.sA2;
   const uint16_t *B = g.B + b1 * g.sB1 + b2 * g.sB2;
@@ -231,7 +238,7 @@ __global__ void __launch_bounds__(GT) k_gemms(GemmSArgs g) {
       const int s = c / (GM * 4), r = (c / 4) % GM, q = c % 4;
       const bool ok = m0 + r < g.M;
       const uint16_t *src = A + s * g.pA + (long long)(ok ? m0 + r : 0) * g.lda + k0 + 8 * q;
-      cp_async16(as + (s * GM + r) * SPD + 8 * q, src, ok);
+      cp_async16(as + swz(s * GM + r, q), src, ok);
     }
     uint16_t *bs = Bs + buf * Ly::b_stage;
     if (!B_KN) {  // B[n][k]: kDig x 32 n x 32 k
@@ -239,14 +246,14 @@ __global__ void __launch_bounds__(GT) k_gemms(GemmSArgs g) {
         const int s = c / (GN * 4), r = (c / 4) % GN, q = c % 4;
         const bool ok = n0 + r < g.N;
         const uint16_t *src = B + s * g.pB + (long long)(ok ? n0 + r : 0) * g.ldb + k0 + 8 * q;
-        cp_async16(bs + (s * GN + r) * SPD + 8 * q, src, ok);
+        cp_async16(bs + swz(s * GN + r, q), src, ok);
       }
     } else {  // B[k][n]: kDig x 32 k x 32 n (row stride ldb, a multiple of 8, zero-padded past N)
       for (int c = t; c < kDig * GK * 4; c += GT) {
         const int s = c / (GK * 4), r = (c / 4) % GK, q = c % 4;
         const bool ok = n0 + 8 * q < g.ldb;
         const uint16_t *src = B + s * g.pB + (long long)(k0 + r) * g.ldb + (ok ? n0 + 8 * q : 0);
-        cp_async16(bs + (s * GK + r) * (GN + 8) + 8 * q, src, ok);
+        cp_async16(bs + swz(s * GK + r, q), src, ok);
       }
     }
     cp_async_commit();
@@ -282,11 +289,9 @@ __global__ void __launch_bounds__(GT) k_gemms(GemmSArgs g) {
 #pragma unroll
       for (int s = 0; s < kDig; ++s) {
         if (!B_KN) {
-          const uint16_t *p = bs + (s * GN + wn * 16 + (q >> 1) * 8 + r) * SPD + kk + (q & 1) * 8;
-          ldsm_x4(bf[s], p);
+          ldsm_x4(bf[s], bs + swz(s * GN + wn * 16 + (q >> 1) * 8 + r, (kk >> 3) + (q & 1)));
         } else {
-          const uint16_t *p = bs + (s * GK + kk + (q & 1) * 8 + r) * (GN + 8) + wn * 16 + (q >> 1) * 8;
-          ldsm_x4_t(bf[s], p);
+          ldsm_x4_t(bf[s], bs + swz(s * GK + kk + (q & 1) * 8 + r, 2 * wn + (q >> 1)));
         }
       }
 #pragma unroll
@@ -294,8 +299,7 @@ __global__ void __launch_bounds__(GT) k_gemms(GemmSArgs g) {
         uint32_t af[2][4];
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt) {
-          const uint16_t *p = as + (s * GM + wm * 32 + mt * 16 + (q & 1) * 8 + r) * SPD + kk + (q >> 1) * 8;
-          ldsm_x4(af[mt], p);
+          ldsm_x4(af[mt], as + swz(s * GM + wm * 32 + mt * 16 + (q & 1) * 8 + r, (kk >> 3) + (q >> 1)));
         }
 #pragma unroll
         for (int tt = 0; tt < kDig - s; ++tt) {
@@ -366,9 +370,9 @@ cudaError_t launch_slice(int cols, int mode, const SliceArgs &a, cudaStream_t s)
 cudaError_t launch_gemms(int b_kn, const GemmSArgs &g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.nbatch <= 0) return cudaSuccess;
   if (g.K > 256 || g.K <= 0 || g.bdiv <= 0 || g.lda % 8 || g.ldb % 8 || g.k0 % GK) return cudaErrorInvalidValue;
-  const int tn = (g.N + GN - 1) / GN, tm = (g.M + GM - 1) / GM;
-  if (tn > 65535 || tm > 65535) return cudaErrorInvalidValue;
-  dim3 grid(g.nbatch, tn, tm);
+  const long long tiles = (long long)((g.N + GN - 1) / GN) * ((g.M + GM - 1) / GM);
+  if (tiles > 0x7fffffffLL || g.nbatch > 65535) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)tiles, g.nbatch);
   cudaError_t e;
   if (b_kn) {
     e = cudaFuncSetAttribute(k_gemms<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GLayout<1>::bytes);

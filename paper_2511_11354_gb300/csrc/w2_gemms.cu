@@ -13,15 +13,15 @@
 //
 // Products.  sum_k a_k b_k = 2^(Ea + Eb - 94) sum_{s,t} 256^(10 - s - t) sum_k da_s db_t;
 // the 21 digit pairs with s + t <= 5 are kept.  Pairs of one diagonal
-// g = s + t share an FP32 accumulator.  Every digit product is at most 2^14
-// and a call contracts at most 256 terms, so the partial sums of the
-// diagonals 0..3 (at most four pairs) stay within 2^24 and are exact integers
-// whatever the order and truncation of the tensor core's additions.  The
-// diagonals 4 and 5 share the last accumulator (the g = 5 products use
-// 2^-8-scaled B digits); its rounding lies near 2^-50 of the line scales.  The
-// five accumulators are recombined in int64 and turned into FP64 by integer
-// operations; an output either replaces C or is added to it.  A line holding
-// Inf or NaN marks its exponent, and the outputs that touch it are NaN.
+// g = s + t share an FP32 accumulator (six of them).  Every digit product is
+// at most 2^14 and a call contracts at most 256 terms, so the partial sums of
+// the diagonals 0..3 (at most four pairs) stay within 2^24 and are exact
+// integers whatever the order and truncation of the tensor core's additions;
+// the diagonals 4 and 5 may round, near 2^-56 of the line scales.  The six
+// accumulators are recombined in int64 (units of diagonal 5) and turned into
+// FP64 by integer operations; an output either replaces C or is added to it.
+// A line holding Inf or NaN marks its exponent, and the outputs that touch
+// it are NaN.
 //
 // Tiles.  A CTA of 4 warps computes a 64 x 32 output tile (warp tile 32 x 16:
 // two m16 by two n8 mma.m16n8k16 tiles), K in stages of 32 staged by cp.async
@@ -200,12 +200,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// BF16 pair scaled by 2^-8 (zero halves stay zero; digits are normal numbers).
-__device__ __forceinline__ uint32_t scale8(uint32_t x) {
-  const uint32_t nz = __vcmpne2(x & 0x7fff7fffu, 0u);
-  return __vsub2(x, nz & 0x04000400u);
-}
-
 constexpr int GM = 64, GN = 32, GK = 32, GT = 128;
 
 // BF16 offset of chunk c (8 elements) of row r in a swizzled 32-element row.
@@ -219,7 +213,7 @@ struct GLayout {
 };
 
 template <int B_KN>
-__global__ void __launch_bounds__(GT) k_gemms(GemmSArgs g) {
+__global__ void __launch_bounds__(GT, 3) k_gemms(GemmSArgs g) {
   extern __shared__ __align__(16) uint16_t sm[];
   using Ly = GLayout<B_KN>;
   uint16_t *As = sm, *Bs = sm + 2 * Ly::a_stage;
@@ -259,9 +253,9 @@ __global__ void __launch_bounds__(GT) k_gemms(GemmSArgs g) {
     cp_async_commit();
   };
 
-  float acc[5][2][2][4];
+  float acc[kDig][2][2][4];
 #pragma unroll
-  for (int d = 0; d < 5; ++d)
+  for (int d = 0; d < kDig; ++d)
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -304,13 +298,10 @@ __global__ void __launch_bounds__(GT) k_gemms(GemmSArgs g) {
 #pragma unroll
         for (int tt = 0; tt < kDig - s; ++tt) {
           const int gd = s + tt;
-          const int slot = gd < 4 ? gd : 4;
-          uint32_t b00 = bf[tt][0], b01 = bf[tt][1], b10 = bf[tt][2], b11 = bf[tt][3];
-          if (gd == 5) { b00 = scale8(b00); b01 = scale8(b01); b10 = scale8(b10); b11 = scale8(b11); }
 #pragma unroll
           for (int mt = 0; mt < 2; ++mt) {
-            mma16816(acc[slot][mt][0], af[mt], b00, b01);
-            mma16816(acc[slot][mt][1], af[mt], b10, b11);
+            mma16816(acc[gd][mt][0], af[mt], bf[tt][0], bf[tt][1]);
+            mma16816(acc[gd][mt][1], af[mt], bf[tt][2], bf[tt][3]);
           }
         }
       }
@@ -333,13 +324,13 @@ __global__ void __launch_bounds__(GT) k_gemms(GemmSArgs g) {
         const int col = n0 + wn * 16 + nt * 8 + 2 * (ln & 3) + (e & 1);
         if (col >= g.N) continue;
         const int eb = Be[col];
-        const long long I = (long long)__float2int_rn(acc[0][mt][nt][e]) * (1ll << 32) +
-                            (long long)__float2int_rn(acc[1][mt][nt][e]) * (1ll << 24) +
-                            (long long)__float2int_rn(acc[2][mt][nt][e]) * (1ll << 16) +
-                            (long long)__float2int_rn(acc[3][mt][nt][e]) * (1ll << 8) +
-                            __float2ll_rn(acc[4][mt][nt][e]);
+        const long long I = (long long)__float2int_rn(acc[0][mt][nt][e]) * (1ll << 40) +
+                            (long long)__float2int_rn(acc[1][mt][nt][e]) * (1ll << 32) +
+                            (long long)__float2int_rn(acc[2][mt][nt][e]) * (1ll << 24) +
+                            (long long)__float2int_rn(acc[3][mt][nt][e]) * (1ll << 16) +
+                            __float2ll_rn(acc[4][mt][nt][e]) * (1ll << 8) + __float2ll_rn(acc[5][mt][nt][e]);
         double v = (ea == kBadExp || eb == kBadExp) ? __longlong_as_double(0x7ff8000000000000ll)
-                                                    : w2::ll_to_double_scaled(I, ea + eb - 46);
+                                                    : w2::ll_to_double_scaled(I, ea + eb - 54);
         double *c = C + (long long)row * g.ldc + col;
         *c = g.beta ? *c + v : v;
       }

@@ -225,30 +225,25 @@ __global__ void __launch_bounds__(GT, 3) k_gemms(GemmSArgs g) {
   const int t = threadIdx.x, warp = t >> 5, ln = t & 31;
   const int wm = warp & 1, wn = warp >> 1;
 
+  // Per-thread copy plan: chunk t + 128 i of a stage is (digit, row, 16-byte
+  // column q = t & 3); A rows t/4 and t/4 + 32, B row (or k row) t/4.
+  const int q4 = t & 3, r4 = t >> 2;
+  const bool okA0 = m0 + r4 < g.M, okA1 = m0 + r4 + 32 < g.M;
+  const uint16_t *a0 = A + (long long)(okA0 ? m0 + r4 : 0) * g.lda + 8 * q4;
+  const uint16_t *a1 = A + (long long)(okA1 ? m0 + r4 + 32 : 0) * g.lda + 8 * q4;
+  const bool okB = B_KN ? (n0 + 8 * q4 < g.ldb) : (n0 + r4 < g.N);
+  const uint16_t *b0 = B_KN ? B + (long long)r4 * g.ldb + (okB ? n0 + 8 * q4 : 0)
+                            : B + (long long)(okB ? n0 + r4 : 0) * g.ldb + 8 * q4;
+  const int dA0 = swz(r4, q4), dA1 = swz(r4 + 32, q4), dB = swz(r4, q4);
   auto load_stage = [&](int buf, int k0) {
     uint16_t *as = As + buf * Ly::a_stage;
-    // A: kDig x 64 rows x 32 k = 1536 chunks of 8
-    for (int c = t; c < kDig * GM * 4; c += GT) {
-      const int s = c / (GM * 4), r = (c / 4) % GM, q = c % 4;
-      const bool ok = m0 + r < g.M;
-      const uint16_t *src = A + s * g.pA + (long long)(ok ? m0 + r : 0) * g.lda + k0 + 8 * q;
-      cp_async16(as + swz(s * GM + r, q), src, ok);
-    }
     uint16_t *bs = Bs + buf * Ly::b_stage;
-    if (!B_KN) {  // B[n][k]: kDig x 32 n x 32 k
-      for (int c = t; c < kDig * GN * 4; c += GT) {
-        const int s = c / (GN * 4), r = (c / 4) % GN, q = c % 4;
-        const bool ok = n0 + r < g.N;
-        const uint16_t *src = B + s * g.pB + (long long)(ok ? n0 + r : 0) * g.ldb + k0 + 8 * q;
-        cp_async16(bs + swz(s * GN + r, q), src, ok);
-      }
-    } else {  // B[k][n]: kDig x 32 k x 32 n (row stride ldb, a multiple of 8, zero-padded past N)
-      for (int c = t; c < kDig * GK * 4; c += GT) {
-        const int s = c / (GK * 4), r = (c / 4) % GK, q = c % 4;
-        const bool ok = n0 + 8 * q < g.ldb;
-        const uint16_t *src = B + s * g.pB + (long long)(k0 + r) * g.ldb + (ok ? n0 + 8 * q : 0);
-        cp_async16(bs + swz(s * GK + r, q), src, ok);
-      }
+    const long long kb = B_KN ? (long long)k0 * g.ldb : k0;
+#pragma unroll
+    for (int s = 0; s < kDig; ++s) {
+      cp_async16(as + s * GM * GK + dA0, a0 + s * g.pA + k0, okA0);
+      cp_async16(as + s * GM * GK + dA1, a1 + s * g.pA + k0, okA1);
+      cp_async16(bs + s * GN * GK + dB, b0 + s * g.pB + kb, okB);
     }
     cp_async_commit();
   };

@@ -29,6 +29,7 @@ struct w2_sem_ctx {
   double *xs = nullptr, *n = nullptr, *U = nullptr, *ut = nullptr, *G = nullptr;
   double *cT = nullptr, *cA = nullptr, *cS = nullptr, *xpart = nullptr, *obs = nullptr, *h_obs = nullptr;
   int *k0 = nullptr;
+  float2 *cpdf = nullptr, *wtsdf = nullptr;  // spline tables as double-float pairs (sliced context)
   // tensor-core products (W2_F64_SLICED): digit planes and line exponents
   int prec = W2_F64, Kp1 = 0, Kp2 = 0, Kp3 = 0, Kp4 = 0, ldp = 0;
   double *ee = nullptr;                       // gamma dx^2 / (pi^2 hbar^3) [Ei | Er]
@@ -55,7 +56,7 @@ static void sem_free(w2_sem_ctx *c) {
   for (double *q : d)
     if (q) cudaFree(q);
   if (c->k0) cudaFree(c->k0);
-  void *v[] = {c->ee, c->phrP, c->phiP, c->phP, c->ehP, c->eeP, c->gP, c->frP, c->fcP, c->tP, c->bP, c->sP,
+  void *v[] = {c->cpdf, c->wtsdf, c->ee, c->phrP, c->phiP, c->phP, c->ehP, c->eeP, c->gP, c->frP, c->fcP, c->tP, c->bP, c->sP,
                c->phrE, c->phiE, c->phE, c->ehE, c->eeE, c->gE, c->frE, c->fcE, c->tE, c->bE, c->sE};
   for (void *q : v)
     if (q) cudaFree(q);
@@ -149,6 +150,7 @@ extern "C" w2_status w2_sem_create(const w2_sem_config *cfg, void *cuda_stream, 
   SEM_ALLOC(ctx->cT, bx * 2 * np * Ny) SEM_ALLOC(ctx->cA, bx * 2 * Nyh * Ny) SEM_ALLOC(ctx->cS, bx * 2 * np * Ny)
   SEM_ALLOC(ctx->xpart, (long long)nx * nx * (4 + np)) SEM_ALLOC(ctx->obs, 8 + nx)
   if (sliced) {
+    SEM_ALLOC(ctx->cpdf, nx) SEM_ALLOC(ctx->wtsdf, 4 * np)
     SEM_ALLOC(ctx->ee, 2LL * np * Ny)
     SEM_ALLOC(ctx->phrP, 6LL * Ny * Kp1) SEM_ALLOC(ctx->phiP, 6LL * Ny * Kp1) SEM_ALLOC(ctx->phP, 6LL * 2 * Nyh * Kp2)
     SEM_ALLOC(ctx->ehP, 2 * 6LL * np * Kp3) SEM_ALLOC(ctx->eeP, 6LL * np * Kp4) SEM_ALLOC(ctx->gP, 6LL * 2 * nx * np * Kp1)
@@ -170,6 +172,14 @@ extern "C" w2_status w2_sem_create(const w2_sem_config *cfg, void *cuda_stream, 
   up(ctx->cp, cp.data(), sizeof(double) * nx);
   up(ctx->wts, wts.data(), sizeof(double) * 4 * np);
   up(ctx->k0, k0.data(), sizeof(int) * np);
+  std::vector<float2> cpdf(nx), wtsdf(4 * np);
+  auto pair = [](double v) { const float h = (float)v; return make_float2(h, (float)(v - (double)h)); };
+  for (int i = 0; i < nx; ++i) cpdf[i] = pair(cp[i]);
+  for (int j = 0; j < 4 * np; ++j) wtsdf[j] = pair(wts[j]);
+  if (sliced) {
+    up(ctx->cpdf, cpdf.data(), sizeof(float2) * nx);
+    up(ctx->wtsdf, wtsdf.data(), sizeof(float2) * 4 * np);
+  }
   SemTabArgs ta{nx, M, Q, np, ctx->h, ctx->dx, ctx->width, ctx->hbar, ctx->Lp, ctx->p, ctx->centre, ctx->cheb,
                 ctx->osc, ctx->psi, ctx->phir, ctx->phii, ctx->ph, ctx->eh, ctx->eier};
   if (e == cudaSuccess) e = launch_sem_osc(ta, ctx->stream);
@@ -408,12 +418,15 @@ static w2_status sem_theta_sliced(w2_sem_ctx *ctx, const double *in, double *out
   return W2_OK;
 }
 
+// The sliced context shifts in double-float pairs (k_sem_adv_df), the
+// FP64-pipe context in FP64.
 static w2_status sem_advect(w2_sem_ctx *ctx, const double *in, double *out) {
-  SemAdvArgs aa{ctx->nx, ctx->np, ctx->C, in, ctx->t, ctx->cp, ctx->k0, ctx->wts};
-  SEM_TRY(launch_sem_adv(0, aa, ctx->stream));
+  const int df = ctx->prec == W2_F64_SLICED;
+  SemAdvArgs aa{ctx->nx, ctx->np, ctx->C, in, ctx->t, ctx->cp, ctx->k0, ctx->wts, ctx->cpdf, ctx->wtsdf};
+  SEM_TRY(launch_sem_adv(0, aa, ctx->stream, df));
   aa.in = ctx->t;
   aa.out = out;
-  SEM_TRY(launch_sem_adv(1, aa, ctx->stream));
+  SEM_TRY(launch_sem_adv(1, aa, ctx->stream, df));
   return W2_OK;
 }
 

@@ -77,8 +77,12 @@ struct SemAdvArgs {
   const double *cp;     // [nx] Thomas factors c'_i of the (1,4,1) interior system
   const int *k0;        // [np] integer part of the foot offset
   const double *wts;    // [np][4] B-spline weights
+  const float2 *cpdf = nullptr;   // the same factors and weights as double-float (hi, lo) pairs
+  const float2 *wtsdf = nullptr;
 };
-cudaError_t launch_sem_adv(int axis, const SemAdvArgs &a, cudaStream_t s);
+// df = 1: the recursion and the four-term evaluation in double-float pairs on
+// the FP32 pipe (FP64 in and out, converted with integer operations).
+cudaError_t launch_sem_adv(int axis, const SemAdvArgs &a, cudaStream_t s, int df = 0);
 int sem_adv_cols(int nx, int np);
 
 // out = x + a * y (y2 == null) or out = x + a * (y + y2), n elements.

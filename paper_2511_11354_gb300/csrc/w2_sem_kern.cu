@@ -4,6 +4,7 @@
 // the Lawson combinations and the observables.
 #include <math.h>
 
+#include "w2_df.cuh"
 #include "w2_sem.cuh"
 
 namespace w2sem {
@@ -241,55 +242,150 @@ __global__ void k_sem_dmul(int nx, int h, int x0, int nb, const double *__restri
   }
 }
 
-// Natural-boundary cubic spline shift of C adjacent lines: load the lines
-// into shared memory, solve the interior (1,4,1)/6 system with eta_0 = f_0,
-// eta_N = f_N by the Thomas recursion (one thread per line, in place), then
-// evaluate the four B-spline terms at the feet; the ghosts are
+// Natural-boundary cubic spline shift of C adjacent lines by 4 C threads:
+// all threads load the lines into shared memory (coalesced rows of C
+// values), one thread per line solves the interior (1,4,1)/6 system with
+// eta_0 = f_0, eta_N = f_N by the Thomas recursion in place, then all threads
+// evaluate the four B-spline terms at the feet and store; the ghosts are
 // eta_{-1} = 2 eta_0 - eta_1, eta_{N+1} = 2 eta_N - eta_{N-1}, zero beyond.
 template <int AXIS>
-__global__ void k_sem_adv(SemAdvArgs a) {
+__global__ void __launch_bounds__(256) k_sem_adv(SemAdvArgs a) {
   extern __shared__ double sl[];
-  const int nx = a.nx, np = a.np, C = a.C, N = nx - 1;
-  const int c = threadIdx.x;
+  const int nx = a.nx, np = a.np, C = a.C, N = nx - 1, T = 4 * C;
+  const int tid = threadIdx.x;
   const int nchunk = (np + C - 1) / C;
   const int chunk = blockIdx.x % nchunk, j1 = (blockIdx.x / nchunk) % np, o = blockIdx.x / (nchunk * np);
-  const int j2 = chunk * C + c;
+  const int c0 = chunk * C, width = np - c0 < C ? np - c0 : C;
   const long long np2 = (long long)np * np;
   long long base, stride;
   if (AXIS == 0) { base = ((long long)o * np + j1) * np; stride = (long long)nx * np2; }  // o = i2
   else { base = (long long)o * nx * np2 + (long long)j1 * np; stride = np2; }          // o = i1
-  if (j2 >= np) return;
-  for (int i = 0; i < nx; ++i) sl[i * C + c] = a.in[base + i * stride + j2];
-  // forward: d'_i = (r_i - d'_{i-1}) c'_i, r_i = 6 f_i - [i==1] f_0 - [i==N-1] f_N
-  double dprev = 0.0;
-  const double f0 = sl[c], fN = sl[N * C + c];
-  for (int i = 1; i <= N - 1; ++i) {
-    double r = 6.0 * sl[i * C + c];
-    if (i == 1) r -= f0;
-    if (i == N - 1) r -= fN;
-    dprev = (r - dprev) * a.cp[i];
-    sl[i * C + c] = dprev;
+  double *ghost = sl + (size_t)nx * C;  // [2][C]: eta_{-1}, eta_{N+1}
+  for (int e = tid; e < nx * C; e += T) {
+    const int i = e / C, c = e % C;
+    if (c < width) sl[e] = a.in[base + i * stride + c0 + c];
   }
-  // backward: eta_{N-1} = d'_{N-1}, eta_i = d'_i - c'_i eta_{i+1}
-  double enext = sl[(N - 1) * C + c];
-  for (int i = N - 2; i >= 1; --i) {
-    enext = sl[i * C + c] - a.cp[i] * enext;
-    sl[i * C + c] = enext;
+  __syncthreads();
+  if (tid < width) {
+    const int c = tid;
+    // forward: d'_i = (r_i - d'_{i-1}) c'_i, r_i = 6 f_i - [i==1] f_0 - [i==N-1] f_N
+    double dprev = 0.0;
+    const double f0 = sl[c], fN = sl[N * C + c];
+    for (int i = 1; i <= N - 1; ++i) {
+      double r = 6.0 * sl[i * C + c];
+      if (i == 1) r -= f0;
+      if (i == N - 1) r -= fN;
+      dprev = (r - dprev) * a.cp[i];
+      sl[i * C + c] = dprev;
+    }
+    // backward: eta_{N-1} = d'_{N-1}, eta_i = d'_i - c'_i eta_{i+1}
+    double enext = sl[(N - 1) * C + c];
+    for (int i = N - 2; i >= 1; --i) {
+      enext = sl[i * C + c] - a.cp[i] * enext;
+      sl[i * C + c] = enext;
+    }
+    ghost[c] = 2.0 * sl[c] - sl[C + c];
+    ghost[C + c] = 2.0 * sl[N * C + c] - sl[(N - 1) * C + c];
   }
-  const int jm = (AXIS == 0) ? j1 : j2;
-  const int k0 = a.k0[jm];
-  const double w0 = a.wts[jm * 4], w1 = a.wts[jm * 4 + 1], w2 = a.wts[jm * 4 + 2], w3 = a.wts[jm * 4 + 3];
-  const double em1 = 2.0 * sl[c] - sl[C + c], eN1 = 2.0 * sl[N * C + c] - sl[(N - 1) * C + c];
-  auto eta = [&](int nu) -> double {
-    if (nu >= 0 && nu <= N) return sl[nu * C + c];
-    if (nu == -1) return em1;
-    if (nu == N + 1) return eN1;
-    return 0.0;
-  };
-  for (int i = 0; i < nx; ++i) {
-    const int nu = i + k0 - 1;
-    const double v = w0 * eta(nu) + w1 * eta(nu + 1) + w2 * eta(nu + 2) + w3 * eta(nu + 3);
-    a.out[base + i * stride + j2] = v;
+  __syncthreads();
+  for (int e = tid; e < nx * C; e += T) {
+    const int i = e / C, c = e % C;
+    if (c >= width) continue;
+    const int jm = (AXIS == 0) ? j1 : c0 + c;
+    const int nu0 = i + a.k0[jm] - 1;
+    double v = 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int nu = nu0 + q;
+      double eta = 0.0;
+      if (nu >= 0 && nu <= N) eta = sl[nu * C + c];
+      else if (nu == -1) eta = ghost[c];
+      else if (nu == N + 1) eta = ghost[C + c];
+      v = fma(a.wts[jm * 4 + q], eta, v);
+    }
+    a.out[base + i * stride + c0 + c] = v;
+  }
+}
+
+// Double-float arithmetic on (hi, lo) FP32 pairs (Dekker / Knuth error-free
+// transformations, w2_df.cuh), about 2^-47 relative per operation.
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  float s, e;
+  w2::two_sum(a.x, b.x, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+  float h, l;
+  w2::fast_two_sum(s, e, h, l);
+  return make_float2(h, l);
+}
+__device__ __forceinline__ float2 df_mulv(float2 a, float2 b) {
+  float p, e;
+  w2::df_mul(a.x, a.y, b.x, b.y, p, e);
+  float h, l;
+  w2::fast_two_sum(p, e, h, l);
+  return make_float2(h, l);
+}
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+// The shift of k_sem_adv with the line values held as double-float pairs in
+// shared memory: the FP64 pipe of this GPU runs at about 1/64 of the FP32
+// rate, and the recursion plus the evaluation cost about seven FP64
+// operations per value.
+template <int AXIS>
+__global__ void __launch_bounds__(256) k_sem_adv_df(SemAdvArgs a) {
+  extern __shared__ float2 sf[];
+  const int nx = a.nx, np = a.np, C = a.C, N = nx - 1, T = 4 * C;
+  const int tid = threadIdx.x;
+  const int nchunk = (np + C - 1) / C;
+  const int chunk = blockIdx.x % nchunk, j1 = (blockIdx.x / nchunk) % np, o = blockIdx.x / (nchunk * np);
+  const int c0 = chunk * C, width = np - c0 < C ? np - c0 : C;
+  const long long np2 = (long long)np * np;
+  long long base, stride;
+  if (AXIS == 0) { base = ((long long)o * np + j1) * np; stride = (long long)nx * np2; }  // o = i2
+  else { base = (long long)o * nx * np2 + (long long)j1 * np; stride = np2; }          // o = i1
+  float2 *ghost = sf + (size_t)nx * C;  // [2][C]: eta_{-1}, eta_{N+1}
+  for (int e = tid; e < nx * C; e += T) {
+    const int i = e / C, c = e % C;
+    if (c < width) sf[e] = w2::df_split(a.in[base + i * stride + c0 + c]);
+  }
+  __syncthreads();
+  if (tid < width) {
+    const int c = tid;
+    const float2 six = make_float2(6.f, 0.f);
+    const float2 f0 = sf[c], fN = sf[N * C + c];
+    float2 dprev = make_float2(0.f, 0.f);
+    for (int i = 1; i <= N - 1; ++i) {
+      float2 r = df_mulv(sf[i * C + c], six);
+      if (i == 1) r = df_add(r, df_neg(f0));
+      if (i == N - 1) r = df_add(r, df_neg(fN));
+      dprev = df_mulv(df_add(r, df_neg(dprev)), a.cpdf[i]);
+      sf[i * C + c] = dprev;
+    }
+    float2 enext = sf[(N - 1) * C + c];
+    for (int i = N - 2; i >= 1; --i) {
+      enext = df_add(sf[i * C + c], df_neg(df_mulv(a.cpdf[i], enext)));
+      sf[i * C + c] = enext;
+    }
+    const float2 two = make_float2(2.f, 0.f);
+    ghost[c] = df_add(df_mulv(sf[c], two), df_neg(sf[C + c]));
+    ghost[C + c] = df_add(df_mulv(sf[N * C + c], two), df_neg(sf[(N - 1) * C + c]));
+  }
+  __syncthreads();
+  for (int e = tid; e < nx * C; e += T) {
+    const int i = e / C, c = e % C;
+    if (c >= width) continue;
+    const int jm = (AXIS == 0) ? j1 : c0 + c;
+    const int nu0 = i + a.k0[jm] - 1;
+    float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int nu = nu0 + q;
+      float2 eta = make_float2(0.f, 0.f);
+      if (nu >= 0 && nu <= N) eta = sf[nu * C + c];
+      else if (nu == -1) eta = ghost[c];
+      else if (nu == N + 1) eta = ghost[C + c];
+      v = df_add(v, df_mulv(a.wtsdf[jm * 4 + q], eta));
+    }
+    a.out[base + i * stride + c0 + c] = w2::df_join_general(v.x, v.y);
   }
 }
 
@@ -437,25 +533,33 @@ cudaError_t launch_sem_dmul(int nx, int h, int x0, int nb, const double *wgrid, 
 
 int sem_adv_cols(int nx, int np) {
   int C = 64;
-  while (C > 8 && (size_t)C * nx * sizeof(double) > 200 * 1024) C >>= 1;
+  while (C > 8 && (size_t)C * (nx + 2) * sizeof(double) > 110 * 1024) C >>= 1;
   while (C > 8 && C / 2 >= np) C >>= 1;
   return C;
 }
 
-cudaError_t launch_sem_adv(int axis, const SemAdvArgs &a, cudaStream_t s) {
-  const size_t smem = sizeof(double) * a.C * a.nx;
+cudaError_t launch_sem_adv(int axis, const SemAdvArgs &a, cudaStream_t s, int df) {
+  const size_t smem = sizeof(double) * a.C * (a.nx + 2);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   const long long nblk = (long long)a.nx * a.np * ((a.np + a.C - 1) / a.C);
   if (nblk > 0x7fffffffLL) return cudaErrorInvalidValue;
   cudaError_t e;
+  if (df) {
+    if (!a.cpdf || !a.wtsdf) return cudaErrorInvalidValue;
+    auto kern = axis == 0 ? k_sem_adv_df<0> : k_sem_adv_df<1>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)nblk, 4 * a.C, smem, s>>>(a);
+    return cudaGetLastError();
+  }
   if (axis == 0) {
     e = cudaFuncSetAttribute(k_sem_adv<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_sem_adv<0><<<(unsigned)nblk, a.C, smem, s>>>(a);
+    k_sem_adv<0><<<(unsigned)nblk, 4 * a.C, smem, s>>>(a);
   } else {
     e = cudaFuncSetAttribute(k_sem_adv<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_sem_adv<1><<<(unsigned)nblk, a.C, smem, s>>>(a);
+    k_sem_adv<1><<<(unsigned)nblk, 4 * a.C, smem, s>>>(a);
   }
   return cudaGetLastError();
 }

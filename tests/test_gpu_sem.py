@@ -99,15 +99,20 @@ def test_theta_terms_separately(which, prec):
     assert err < THETA_BAR[prec]
 
 
+@pytest.mark.parametrize("prec", ["W2_F64", "W2_F64_SLICED"])
 @pytest.mark.parametrize("case", CASES[:3])
-def test_advect_parity(case):
+def test_advect_parity(case, prec):
+    """The FP64-pipe context shifts in FP64, the sliced one in double-float
+    pairs (about 2^-47 per operation)."""
     prob, f = _case(*case)
     prob.dt = 0.37  # feet several cells away, some outside the box
-    ctx = _ctx(prob)
+    ctx = _ctx(prob, prec)
     d = torch.from_numpy(f).cuda()
     out = torch.empty_like(d)
     ctx.advect(d, out)
-    assert rel(out.cpu().numpy(), SemOracle(prob).advect(f)) < 1e-13
+    err = rel(out.cpu().numpy(), SemOracle(prob).advect(f))
+    print(f"advect {case} {prec}: {err:.3e}")
+    assert err < 1e-13
 
 
 @pytest.mark.parametrize("prec", ["W2_F64", "W2_F64_SLICED"])

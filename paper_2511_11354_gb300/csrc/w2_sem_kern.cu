@@ -329,12 +329,15 @@ __device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a
 // The shift of k_sem_adv with the line values held as double-float pairs in
 // shared memory: the FP64 pipe of this GPU runs at about 1/64 of the FP32
 // rate, and the recursion plus the evaluation cost about seven FP64
-// operations per value.
+// operations per value.  Each column keeps three rows below and above the
+// line (zero, zero, ghost | ghost, zero, zero), so a foot index is clamped
+// into [-3, N + 3] instead of branched on; thread t works on column t % C and
+// rows t / C + 4 k.
 template <int AXIS>
 __global__ void __launch_bounds__(256) k_sem_adv_df(SemAdvArgs a) {
   extern __shared__ float2 sf[];
-  const int nx = a.nx, np = a.np, C = a.C, N = nx - 1, T = 4 * C;
-  const int tid = threadIdx.x;
+  const int nx = a.nx, np = a.np, C = a.C, N = nx - 1;
+  const int tid = threadIdx.x, c = tid % C, r0 = tid / C;  // 4 rows in flight per column
   const int nchunk = (np + C - 1) / C;
   const int chunk = blockIdx.x % nchunk, j1 = (blockIdx.x / nchunk) % np, o = blockIdx.x / (nchunk * np);
   const int c0 = chunk * C, width = np - c0 < C ? np - c0 : C;
@@ -342,50 +345,53 @@ __global__ void __launch_bounds__(256) k_sem_adv_df(SemAdvArgs a) {
   long long base, stride;
   if (AXIS == 0) { base = ((long long)o * np + j1) * np; stride = (long long)nx * np2; }  // o = i2
   else { base = (long long)o * nx * np2 + (long long)j1 * np; stride = np2; }          // o = i1
-  float2 *ghost = sf + (size_t)nx * C;  // [2][C]: eta_{-1}, eta_{N+1}
-  for (int e = tid; e < nx * C; e += T) {
-    const int i = e / C, c = e % C;
-    if (c < width) sf[e] = w2::df_split(a.in[base + i * stride + c0 + c]);
+  float2 *col = sf + 3 * C + c;  // row nu of this column at col[nu * C], nu in [-3, N + 3]
+  const bool live = c < width;
+  const double *src = a.in + base + c0 + c;
+  if (live)
+    for (int i = r0; i < nx; i += 4) col[i * C] = w2::df_split(src[i * stride]);
+  if (r0 == 0) {
+    const float2 z = make_float2(0.f, 0.f);
+    col[-3 * C] = z; col[-2 * C] = z; col[(N + 2) * C] = z; col[(N + 3) * C] = z;
   }
   __syncthreads();
-  if (tid < width) {
-    const int c = tid;
-    const float2 six = make_float2(6.f, 0.f);
-    const float2 f0 = sf[c], fN = sf[N * C + c];
-    float2 dprev = make_float2(0.f, 0.f);
-    for (int i = 1; i <= N - 1; ++i) {
-      float2 r = df_mulv(sf[i * C + c], six);
-      if (i == 1) r = df_add(r, df_neg(f0));
-      if (i == N - 1) r = df_add(r, df_neg(fN));
-      dprev = df_mulv(df_add(r, df_neg(dprev)), a.cpdf[i]);
-      sf[i * C + c] = dprev;
+  if (r0 == 0 && live) {
+    const float2 six = make_float2(6.f, 0.f), two = make_float2(2.f, 0.f);
+    const float2 f0 = col[0], fN = col[N * C];
+    // forward: d'_i = (r_i - d'_{i-1}) c'_i, r_i = 6 f_i - [i==1] f_0 - [i==N-1] f_N
+    float2 dprev = df_mulv(df_add(df_mulv(col[C], six), df_neg(f0)), a.cpdf[1]);
+    if (N - 1 == 1) dprev = df_mulv(df_add(df_add(df_mulv(col[C], six), df_neg(f0)), df_neg(fN)), a.cpdf[1]);
+    col[C] = dprev;
+    for (int i = 2; i <= N - 2; ++i) {
+      dprev = df_mulv(df_add(df_mulv(col[i * C], six), df_neg(dprev)), a.cpdf[i]);
+      col[i * C] = dprev;
     }
-    float2 enext = sf[(N - 1) * C + c];
+    if (N - 1 >= 2) {
+      const int i = N - 1;
+      dprev = df_mulv(df_add(df_add(df_mulv(col[i * C], six), df_neg(fN)), df_neg(dprev)), a.cpdf[i]);
+      col[i * C] = dprev;
+    }
+    // backward: eta_{N-1} = d'_{N-1}, eta_i = d'_i - c'_i eta_{i+1}
+    float2 enext = dprev;
     for (int i = N - 2; i >= 1; --i) {
-      enext = df_add(sf[i * C + c], df_neg(df_mulv(a.cpdf[i], enext)));
-      sf[i * C + c] = enext;
+      enext = df_add(col[i * C], df_neg(df_mulv(a.cpdf[i], enext)));
+      col[i * C] = enext;
     }
-    const float2 two = make_float2(2.f, 0.f);
-    ghost[c] = df_add(df_mulv(sf[c], two), df_neg(sf[C + c]));
-    ghost[C + c] = df_add(df_mulv(sf[N * C + c], two), df_neg(sf[(N - 1) * C + c]));
+    col[-C] = df_add(df_mulv(col[0], two), df_neg(col[C]));
+    col[(N + 1) * C] = df_add(df_mulv(col[N * C], two), df_neg(col[(N - 1) * C]));
   }
   __syncthreads();
-  for (int e = tid; e < nx * C; e += T) {
-    const int i = e / C, c = e % C;
-    if (c >= width) continue;
-    const int jm = (AXIS == 0) ? j1 : c0 + c;
-    const int nu0 = i + a.k0[jm] - 1;
-    float2 v = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int nu = nu0 + q;
-      float2 eta = make_float2(0.f, 0.f);
-      if (nu >= 0 && nu <= N) eta = sf[nu * C + c];
-      else if (nu == -1) eta = ghost[c];
-      else if (nu == N + 1) eta = ghost[C + c];
-      v = df_add(v, df_mulv(a.wtsdf[jm * 4 + q], eta));
-    }
-    a.out[base + i * stride + c0 + c] = w2::df_join_general(v.x, v.y);
+  if (!live) return;
+  const int jm = (AXIS == 0) ? j1 : c0 + c;
+  const int k0 = a.k0[jm];
+  const float2 w0 = a.wtsdf[jm * 4], w1 = a.wtsdf[jm * 4 + 1], w2 = a.wtsdf[jm * 4 + 2], w3 = a.wtsdf[jm * 4 + 3];
+  double *dst = a.out + base + c0 + c;
+  for (int i = r0; i < nx; i += 4) {
+    const int nu = i + k0 - 1;
+    const float2 e0 = col[min(max(nu, -3), N + 3) * C], e1 = col[min(max(nu + 1, -3), N + 3) * C];
+    const float2 e2 = col[min(max(nu + 2, -3), N + 3) * C], e3 = col[min(max(nu + 3, -3), N + 3) * C];
+    const float2 v = df_add(df_add(df_mulv(w0, e0), df_mulv(w1, e1)), df_add(df_mulv(w2, e2), df_mulv(w3, e3)));
+    dst[i * stride] = w2::df_join(v.x, v.y);
   }
 }
 
@@ -533,13 +539,13 @@ cudaError_t launch_sem_dmul(int nx, int h, int x0, int nb, const double *wgrid, 
 
 int sem_adv_cols(int nx, int np) {
   int C = 64;
-  while (C > 8 && (size_t)C * (nx + 2) * sizeof(double) > 110 * 1024) C >>= 1;
+  while (C > 8 && (size_t)C * (nx + 6) * sizeof(double) > 110 * 1024) C >>= 1;
   while (C > 8 && C / 2 >= np) C >>= 1;
   return C;
 }
 
 cudaError_t launch_sem_adv(int axis, const SemAdvArgs &a, cudaStream_t s, int df) {
-  const size_t smem = sizeof(double) * a.C * (a.nx + 2);
+  const size_t smem = sizeof(double) * a.C * (a.nx + 6);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   const long long nblk = (long long)a.nx * a.np * ((a.np + a.C - 1) / a.C);
   if (nblk > 0x7fffffffLL) return cudaErrorInvalidValue;

@@ -539,7 +539,7 @@ cudaError_t launch_sem_dmul(int nx, int h, int x0, int nb, const double *wgrid, 
 
 int sem_adv_cols(int nx, int np) {
   int C = 64;
-  while (C > 8 && (size_t)C * (nx + 6) * sizeof(double) > 110 * 1024) C >>= 1;
+  while (C > 8 && (size_t)C * (nx + 6) * sizeof(double) > 56 * 1024) C >>= 1;
   while (C > 8 && C / 2 >= np) C >>= 1;
   return C;
 }

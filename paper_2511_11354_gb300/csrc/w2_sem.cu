@@ -89,8 +89,9 @@ extern "C" w2_status w2_sem_create(const w2_sem_config *cfg, void *cuda_stream, 
   ctx->Kp1 = slice_kp(np); ctx->Kp2 = slice_kp(2 * np); ctx->Kp3 = slice_kp(2 * Nyh); ctx->Kp4 = slice_kp(2 * Ny);
   ctx->ldp = (np + 7) / 8 * 8;
   const int Kp1 = ctx->Kp1, Kp2 = ctx->Kp2, Kp3 = ctx->Kp3, Kp4 = ctx->Kp4, ldp = ctx->ldp;
-  // two-body chain chunk: about 256 MB of FP64 intermediates (1 GB with the
-  // slices, in whole rows of x1 so that a chunk's x1 index is affine in X)
+  // two-body chain chunk: about 256 MB of FP64 intermediates (4 GB with the
+  // slices, in whole rows of x1 so that a chunk's x1 index is affine in X;
+  // large chunks keep the tail of each product's last wave small)
   const double per_x = 8.0 * (2.0 * np * Ny + 2.0 * Nyh * Ny + 2.0 * np * Ny);
   const double per_xs = per_x + 12.0 * ((double)np * Kp1 + (double)Kp1 * ldp + (double)Ny * Kp2 + (double)Ny * Kp3 +
                                         (double)np * Kp4) + 4.0 * (3.0 * np + 2.0 * Ny);
@@ -98,7 +99,7 @@ extern "C" w2_status w2_sem_create(const w2_sem_config *cfg, void *cuda_stream, 
   if (!sliced) {
     bx = (long long)(256.0 * 1024 * 1024 / per_x);
   } else {
-    bx = (long long)(1024.0 * 1024 * 1024 / (per_xs * nx));
+    bx = (long long)(4096.0 * 1024 * 1024 / (per_xs * nx));
     if (bx < 1) bx = 1;
     bx *= nx;
     while (bx > 65535) bx -= nx;

@@ -86,13 +86,14 @@ __global__ void __launch_bounds__(256) k_slice_rows(SliceArgs a) {
   const double *in = a.in + b1 * a.sIn1 + b2 * a.sIn2 + (long long)l * a.ls;
   double v[16];
   int emax = 0;
-  int rho = 0, W0 = 0, Nyh = 0, c = 0;
-  if (MODE == 1) {  // D_V weighting of the two-body chain: line c = y2 index, k = [re|im] x y1 index
+  const double *drow = nullptr;
+  int Nyh = 0, dstride = 0;
+  if (MODE == 1) {  // D_V weighting of the two-body chain: line l = y2 index, k = [re|im] x y1 index
     const int X = a.x0 + b;
-    rho = X / a.nx - X % a.nx;
-    W0 = 2 * (a.nx - 1);
+    const int rho = X / a.nx - X % a.nx;
     Nyh = a.h + 1;
-    c = l;
+    dstride = (2 * a.nx - 1) * (4 * a.h + 1);
+    drow = a.dtab + (long long)(rho + a.nx - 1) * (4 * a.h + 1) + 2 * a.h - (l - a.h);  // + r gives u = r - (l - h)
   }
 #pragma unroll
   for (int i = 0; i < 16; ++i) {
@@ -102,8 +103,7 @@ __global__ void __launch_bounds__(256) k_slice_rows(SliceArgs a) {
       x = in[k];
       if (MODE == 1) {
         const int r = k % Nyh;
-        const int u = r - (c - a.h);
-        x *= (r == 0 ? 1.0 : 2.0) * (a.wgrid[rho + u + W0] - a.wgrid[rho - u + W0]);
+        x *= drow[(r ? dstride : 0) + r];
       }
     }
     v[i] = x;

@@ -30,6 +30,10 @@ struct w2_sem_ctx {
   double *cT = nullptr, *cA = nullptr, *cS = nullptr, *xpart = nullptr, *obs = nullptr, *h_obs = nullptr;
   int *k0 = nullptr;
   float2 *cpdf = nullptr, *wtsdf = nullptr;  // spline tables as double-float pairs (sliced context)
+  double *dtab = nullptr;  // [2][2nx-1][4h+1] w (W(rho + u) - W(rho - u)), w = 1, 2 (sliced context)
+  uint16_t *psiP = nullptr, *utP = nullptr;  // slices of psi (columns) and of the U-Toeplitz rows
+  int *psiE = nullptr, *utE = nullptr, Kp5 = 0;
+  long long ldpsi = 0;  // row stride of the psi slices: np^2 rounded up to a multiple of 8
   // tensor-core products (W2_F64_SLICED): digit planes and line exponents
   int prec = W2_F64, Kp1 = 0, Kp2 = 0, Kp3 = 0, Kp4 = 0, ldp = 0;
   double *ee = nullptr;                       // gamma dx^2 / (pi^2 hbar^3) [Ei | Er]
@@ -56,7 +60,7 @@ static void sem_free(w2_sem_ctx *c) {
   for (double *q : d)
     if (q) cudaFree(q);
   if (c->k0) cudaFree(c->k0);
-  void *v[] = {c->cpdf, c->wtsdf, c->ee, c->phrP, c->phiP, c->phP, c->ehP, c->eeP, c->gP, c->frP, c->fcP, c->tP, c->bP, c->sP,
+  void *v[] = {c->psiP, c->utP, c->psiE, c->utE, c->dtab, c->cpdf, c->wtsdf, c->ee, c->phrP, c->phiP, c->phP, c->ehP, c->eeP, c->gP, c->frP, c->fcP, c->tP, c->bP, c->sP,
                c->phrE, c->phiE, c->phE, c->ehE, c->eeE, c->gE, c->frE, c->fcE, c->tE, c->bE, c->sE};
   for (void *q : v)
     if (q) cudaFree(q);
@@ -88,6 +92,8 @@ extern "C" w2_status w2_sem_create(const w2_sem_config *cfg, void *cuda_stream, 
   const bool sliced = ctx->prec == W2_F64_SLICED;
   ctx->Kp1 = slice_kp(np); ctx->Kp2 = slice_kp(2 * np); ctx->Kp3 = slice_kp(2 * Nyh); ctx->Kp4 = slice_kp(2 * Ny);
   ctx->ldp = (np + 7) / 8 * 8;
+  ctx->Kp5 = slice_kp(2 * nx - 1);
+  ctx->ldpsi = ((long long)np * np + 7) / 8 * 8;
   const int Kp1 = ctx->Kp1, Kp2 = ctx->Kp2, Kp3 = ctx->Kp3, Kp4 = ctx->Kp4, ldp = ctx->ldp;
   // two-body chain chunk: about 256 MB of FP64 intermediates (4 GB with the
   // slices, in whole rows of x1 so that a chunk's x1 index is affine in X;
@@ -151,7 +157,9 @@ extern "C" w2_status w2_sem_create(const w2_sem_config *cfg, void *cuda_stream, 
   SEM_ALLOC(ctx->cT, bx * 2 * np * Ny) SEM_ALLOC(ctx->cA, bx * 2 * Nyh * Ny) SEM_ALLOC(ctx->cS, bx * 2 * np * Ny)
   SEM_ALLOC(ctx->xpart, (long long)nx * nx * (4 + np)) SEM_ALLOC(ctx->obs, 8 + nx)
   if (sliced) {
-    SEM_ALLOC(ctx->cpdf, nx) SEM_ALLOC(ctx->wtsdf, 4 * np)
+    SEM_ALLOC(ctx->psiP, 6LL * ctx->Kp5 * ctx->ldpsi) SEM_ALLOC(ctx->psiE, (long long)np * np)
+    SEM_ALLOC(ctx->utP, 6LL * 2 * nx * ctx->Kp5) SEM_ALLOC(ctx->utE, 2 * nx)
+    SEM_ALLOC(ctx->cpdf, nx) SEM_ALLOC(ctx->wtsdf, 4 * np) SEM_ALLOC(ctx->dtab, 2LL * (2 * nx - 1) * (4 * ctx->h + 1))
     SEM_ALLOC(ctx->ee, 2LL * np * Ny)
     SEM_ALLOC(ctx->phrP, 6LL * Ny * Kp1) SEM_ALLOC(ctx->phiP, 6LL * Ny * Kp1) SEM_ALLOC(ctx->phP, 6LL * 2 * Nyh * Kp2)
     SEM_ALLOC(ctx->ehP, 2 * 6LL * np * Kp3) SEM_ALLOC(ctx->eeP, 6LL * np * Kp4) SEM_ALLOC(ctx->gP, 6LL * 2 * nx * np * Kp1)
@@ -195,6 +203,10 @@ extern "C" w2_status w2_sem_create(const w2_sem_config *cfg, void *cuda_stream, 
     rows(ctx->ph, 2 * Nyh, 2 * np, Kp2, ctx->phP, ctx->phE);
     rows(ctx->eh, np, 2 * Nyh, Kp3, ctx->ehP, ctx->ehE);
     rows(ctx->eh + (long long)np * 2 * Nyh, np, 2 * Nyh, Kp3, ctx->ehP + 6LL * np * Kp3, ctx->ehE + np);
+    // psi as columns (i, j) over the offset d: the B operand of the table product
+    SliceArgs sp{np * np, 2 * nx - 1, ctx->Kp5, (int)ctx->ldpsi, ctx->psi, 1, (long long)np * np, 0, 0, ctx->psiP,
+                 (long long)ctx->Kp5 * ctx->ldpsi, 0, ctx->psiE, 0, 1, 1, nullptr, nx, ctx->h, 0};
+    if (e == cudaSuccess) e = launch_slice(1, 0, sp, ctx->stream);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
@@ -231,6 +243,18 @@ extern "C" w2_status w2_sem_set_potentials(w2_sem_ctx *ctx, w2_fn vext, void *ue
     SliceArgs sa{ctx->np, 2 * ctx->Ny, ctx->Kp4, 0, ctx->ee, 2 * ctx->Ny, 1, 0, 0, ctx->eeP,
                  (long long)ctx->np * ctx->Kp4, 0, ctx->eeE, 0, 1, 1, nullptr, nx, ctx->h, 0};
     SEM_TRY(launch_slice(0, 0, sa, ctx->stream));
+    // D_V weights of the two-body chain, w (W(rho + u) - W(rho - u)) for w = 1 and 2
+    const int nr = 2 * nx - 1, nu = 4 * ctx->h + 1;
+    std::vector<double> dt(2LL * nr * nu);
+    for (int ir = 0; ir < nr; ++ir)
+      for (int iu = 0; iu < nu; ++iu) {
+        const int rho = ir - (nx - 1), u = iu - 2 * ctx->h;
+        const double D = wg[rho + u + W0] - wg[rho - u + W0];
+        dt[(long long)ir * nu + iu] = D;
+        dt[(long long)nr * nu + (long long)ir * nu + iu] = 2.0 * D;
+      }
+    SEM_TRY(cudaMemcpyAsync(ctx->dtab, dt.data(), sizeof(double) * dt.size(), cudaMemcpyHostToDevice, ctx->stream));
+    SEM_TRY(cudaStreamSynchronize(ctx->stream));
   }
   SEM_TRY(cudaStreamSynchronize(ctx->stream));
   ctx->gamma = gamma; ctx->c_h = c_h; ctx->c_xc = c_xc;
@@ -339,14 +363,6 @@ static w2_status sem_theta_sliced(w2_sem_ctx *ctx, const double *in, double *out
   SEM_TRY(launch_sem_marginal(nx, np, ctx->dx, in, ctx->w, ctx->xs, ctx->n, s));
   SemPotArgs pa{nx, ctx->xc_kind, ctx->dx, ctx->c_h, ctx->c_xc, ctx->n, ctx->vext, ctx->wgrid, ctx->U, ctx->ut};
   SEM_TRY(launch_sem_potential(pa, s));
-  Gemm64 g{2 * nx, (int)np2, 2 * nx - 1, ctx->ut, 2 * nx - 1, 0, ctx->psi, np2, 0, ctx->G, np2, 1.0, 0.0, 1, 1,
-           0, 0, 0, 0, 0, 0};
-  SEM_TRY(launch_gemm64(g, s));
-  {
-    SliceArgs sa{2 * nx * np, np, Kp1, 0, ctx->G, np, 1, 0, 0, ctx->gP, 2LL * nx * np * Kp1, 0, ctx->gE, 0, 1, 1,
-                 nullptr, nx, ctx->h, 0};
-    SEM_TRY(launch_slice(0, 0, sa, s));
-  }
   // products over K in pieces of at most 256 (multiples of 32), adding after the first
   auto gemm_k = [&](GemmSArgs a, int K, int b_kn) -> cudaError_t {
     const int beta0 = a.beta;
@@ -359,6 +375,18 @@ static w2_status sem_theta_sliced(w2_sem_ctx *ctx, const double *in, double *out
     }
     return cudaSuccess;
   };
+  {  // G[2 nx][np*np] = ut[2 nx][2 nx - 1] psi[2 nx - 1][np*np], from slices
+    const int Kp5 = ctx->Kp5;
+    SliceArgs su{2 * nx, 2 * nx - 1, Kp5, 0, ctx->ut, 2 * nx - 1, 1, 0, 0, ctx->utP, 2LL * nx * Kp5, 0, ctx->utE, 0,
+                 1, 1, nullptr, nx, ctx->h, 0};
+    SEM_TRY(launch_slice(0, 0, su, s));
+    GemmSArgs gt{2 * nx, (int)np2, 2 * nx - 1, 0, ctx->utP, Kp5, 2LL * nx * Kp5, 0, 0, ctx->utE, 0, 0, ctx->psiP,
+                 ctx->ldpsi, (long long)Kp5 * ctx->ldpsi, 0, 0, ctx->psiE, 0, 0, ctx->G, np2, 0, 0, 0, 1, 1};
+    SEM_TRY(gemm_k(gt, 2 * nx - 1, 1));
+    SliceArgs sa{2 * nx * np, np, Kp1, 0, ctx->G, np, 1, 0, 0, ctx->gP, 2LL * nx * np * Kp1, 0, ctx->gE, 0, 1, 1,
+                 nullptr, nx, ctx->h, 0};
+    SEM_TRY(launch_slice(0, 0, sa, s));
+  }
   const long long frS = 6LL * np * Kp1, fcS = 6LL * Kp1 * ldp, tS = 6LL * Ny * Kp2, bS = 6LL * Ny * Kp3,
                   sS = 6LL * np * Kp4;
   for (long long x0 = 0; x0 < nX; x0 += ctx->bx) {
@@ -399,7 +427,7 @@ static w2_status sem_theta_sliced(w2_sem_ctx *ctx, const double *in, double *out
     SEM_TRY(gemm_k(aa, 2 * np, 0));
     // slices of B^T_X = w D (.) A^T_X
     SliceArgs bs{Ny, 2 * Nyh, Kp3, 0, ctx->cA, 2 * Nyh, 1, (long long)Ny * 2 * Nyh, 0, ctx->bP, (long long)Ny * Kp3,
-                 bS, ctx->bE, Ny, nb, 1, ctx->wgrid, nx, ctx->h, (int)x0};
+                 bS, ctx->bE, Ny, nb, 1, ctx->dtab, nx, ctx->h, (int)x0};
     SEM_TRY(launch_slice(0, 1, bs, s));
     // [Sr | Si]_X = [Er_h | -Ei_h] B, [Ei_h | Er_h] B
     for (int blk = 0; blk < 2; ++blk) {

@@ -111,7 +111,8 @@ cudaError_t launch_sem_scale(long long n, double a, const double *in, double *ou
 // (b / bdiv, b % bdiv) for the input (strides sIn1, sIn2); planes and
 // exponents move by b * sP and b * sE.  Mode 1 (rows only) first multiplies
 // element (c = l, k) by w(r) (W(rho + u dx) - W(rho - u dx)), r = k % (h+1),
-// u = r - (c - h), rho = i1 - i2 of X = x0 + b (the two-body D_V weighting).
+// u = r - (c - h), rho = i1 - i2 of X = x0 + b (the two-body D_V weighting),
+// read from dtab[w == 2][rho + nx - 1][u + 2h] ((2 nx - 1) x (4h + 1) each).
 struct SliceArgs {
   int L, K, Kp, ldp;
   const double *in;
@@ -121,7 +122,7 @@ struct SliceArgs {
   int *ex;
   long long sE;
   int nbatch, bdiv;
-  const double *wgrid;
+  const double *dtab;
   int nx, h, x0;
 };
 cudaError_t launch_slice(int cols, int mode, const SliceArgs &a, cudaStream_t s);

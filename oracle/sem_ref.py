@@ -356,3 +356,66 @@ class SemOracle:
         l2 = math.sqrt(dx * dx * np.einsum("abcd,cd->", f * f, ww))
         return {"mass": mass, "energy": e, "purity": purity, "entropy_lin": 1.0 - purity,
                 "l2norm": l2, "n1": n1}
+
+
+# ---------------------------------------------------------------------------
+# Occupation numbers and correlation entropy of the one-body density matrix
+# (the strongly correlated example of Sec. 5.4 and the appendix on the
+# correlation entropy), on the bounded box.
+#
+# Readings (R25): the inverse Wigner transform
+#   rho1(r - y/2, r + y/2) = int f1(r, p) e^{-i p y / hbar} dp
+# is taken exactly over the cell expansions of f1 (the same transform as the
+# two-body term's, at y/2), with f1 = dx sum_{x2} int f dp2; rho1(x_b, x_c)
+# uses r = (x_b + x_c)/2, which for odd b + c is a half point where f1 comes
+# from the natural cubic spline of Sec. 4.1; rho1 is made Hermitian as
+# (rho1 + rho1^H)/2 and its occupations are the eigenvalues of rho1 dx.
+# ---------------------------------------------------------------------------
+
+def _sem_f1(o, f):
+    """f1[i][j] = dx sum_{i2} sum_{j2} w_{j2} f[i][i2][j][j2]."""
+    return o.dx * np.einsum("abcd,d->ac", f, o.w)
+
+
+def _sem_f1_halfgrid(o, f1):
+    """g[k] = f1 at x_0 + k dx/2, k = 0 .. 2 (nx - 1): the grid values and the
+    natural-spline values at the half points."""
+    nx = o.nx
+    eta = o.spline_coeffs(f1, 0)                       # [nu][j]
+    half = o.shift_matrix(-0.5 * o.dx) @ eta           # f1 at x_i + dx/2, i = 0 .. nx-1
+    g = np.empty((2 * nx - 1, f1.shape[1]))
+    g[0::2] = f1
+    g[1::2] = half[: nx - 1]
+    return g
+
+
+def sem_rho1_from_f1(o, f1):
+    """rho1[b][c] (complex nx x nx, Hermitian) from the reduced Wigner
+    function f1[nx][np]."""
+    nx = o.nx
+    g = _sem_f1_halfgrid(o, f1)
+    coef = o.cell_coeffs(g, 1)                          # [k][s l]
+    m = np.arange(-(nx - 1), nx)
+    B = o.basis_transform(0.5 * o.dx * m)               # int e^{2 i p y / hbar} C_l dp at y = m dx / 2
+    rho = np.empty((nx, nx), dtype=np.complex128)
+    for b in range(nx):
+        for c in range(nx):
+            rho[b, c] = np.dot(coef[b + c], np.conj(B[c - b + nx - 1]))
+    return 0.5 * (rho + rho.conj().T)
+
+
+def sem_rho1(o, f):
+    """rho1 of the state f."""
+    return sem_rho1_from_f1(o, _sem_f1(o, f))
+
+
+def sem_occupations(o, f=None, f1=None):
+    """Eigenvalues of rho1 dx, largest first (from the state f, or from f1)."""
+    rho = sem_rho1(o, f) if f1 is None else sem_rho1_from_f1(o, f1)
+    return np.sort(np.linalg.eigvalsh(rho * o.dx))[::-1]
+
+
+SemOracle.f1 = _sem_f1
+SemOracle.rho1 = sem_rho1
+SemOracle.rho1_from_f1 = sem_rho1_from_f1
+SemOracle.occupations = sem_occupations

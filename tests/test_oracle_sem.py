@@ -240,3 +240,48 @@ def test_correlated_state_and_observables():
     prob0 = inputs.SemProblem(nx=31, ncell=8, nq=12, L=prob.L, Lp=prob.Lp, dt=0.01, vext=inputs.zero_potential(),
                               vee=inputs.zero_potential(), gamma=0.0, c_hartree=0.0)
     assert abs(SemOracle(prob0).observables(fp)["energy"] - 0.25) < 1e-5
+
+
+# ---------------------------------------------------------------------------
+# Occupation numbers of the one-body density matrix (appendix on the
+# correlation entropy; strongly correlated example)
+# ---------------------------------------------------------------------------
+
+def _pure(o, x0, p0):
+    """Wigner function of a unit-width Gaussian pure state (mass 1)."""
+    return (1 / math.pi) * np.exp(-0.5 * (o.x[:, None] - x0) ** 2 - 2 * (o.p[None, :] - p0) ** 2)
+
+
+def test_occupations_of_a_pure_state_and_of_a_mixture():
+    """A pure state has one occupation 1 (rho1 = psi psi*); the 50/50
+    mixture of two unit-width Gaussians 4 apart has (1 +- e^-2)/2 (their
+    overlap is e^-2); the rest vanish as the mesh is refined."""
+    from oracle.rdm_ref import correlation_entropy
+    e = math.exp(-2.0)
+    errs = []
+    for nx in (61, 121):
+        prob = inputs.sem_correlated_problem("I", nx=nx, ncell=8, nq=12, L=30.0)
+        o = SemOracle(prob)
+        occ = o.occupations(f1=_pure(o, -1.0, 0.3))
+        assert abs(occ[0] - 1.0) < 1e-4 and occ[1] < 3e-4, occ[:3]
+        mix = 0.5 * (_pure(o, -2.0, 0.0) + _pure(o, 2.0, 0.0))
+        occ = o.occupations(f1=mix)
+        errs.append(max(abs(occ[0] - 0.5 * (1 + e)), abs(occ[1] - 0.5 * (1 - e))))
+        s = correlation_entropy(occ)
+        exact = sum(v * math.log(v) for v in (0.5 * (1 + e), 0.5 * (1 - e)))
+        assert abs(s - exact) < 5e-3, (s, exact)
+        # rho1 is Hermitian before the symmetrisation up to rounding
+        assert abs(occ.sum() - np.dot(o.w, mix.sum(axis=0)) * o.dx) < 1e-10
+    assert errs[1] < 1e-5 and errs[1] < errs[0] / 5, errs
+
+
+def test_reduced_wigner_function_of_the_state():
+    prob, f = inputs.workload_correlated("IV", nx=15, ncell=2, nq=4, L=30.0)
+    o = SemOracle(prob)
+    f1 = o.f1(f)
+    ref = np.array([[o.dx * sum(o.w[d] * f[a, b, c, d] for b in range(15) for d in range(8)) for c in range(8)]
+                    for a in range(15)])
+    np.testing.assert_allclose(f1, ref, rtol=1e-13, atol=1e-16)
+    # the trace of rho1 dx is the mass of f1
+    occ = o.occupations(f)
+    assert abs(occ.sum() - o.dx * np.dot(f1.sum(axis=0), o.w)) < 1e-12 * abs(occ.sum())

@@ -284,6 +284,9 @@ def bench_sem(args, timed):
     ms_theta = timed(lambda n: ctx.theta(d, out), 1)
     ms_adv = timed(lambda n: ctx.advect(d, out), 1)
     ob = ctx.observables()
+    t0 = time.perf_counter()
+    occ, s_corr = ctx.occupations()
+    ms_occ = 1e3 * (time.perf_counter() - t0)
     ctx.close()
     pipe = w2.SemContext.from_problem(prob, precision=w2.W2_F64)
     pipe.theta(d, out)
@@ -312,7 +315,8 @@ def bench_sem(args, timed):
                               "two_body_share_of_flops": two / (one + two),
                               "peak_source": "fp64_dfma_tflops measured live by "
                                              "paper_2511_11354_gb300/probe/fp64_peak.cu"},
-           "mass_drift": (ob.mass - ob0.mass) / ob0.mass, "energy": ob.energy}
+           "mass_drift": (ob.mass - ob0.mass) / ob0.mass, "energy": ob.energy,
+           "correlation_entropy": s_corr, "occupations_top3": [float(v) for v in occ[:3]], "occupations_ms": ms_occ}
     del d, out
     torch.cuda.empty_cache()
     return res

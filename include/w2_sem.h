@@ -127,6 +127,19 @@ w2_status w2_sem_step(w2_sem_ctx *ctx, int32_t nsteps);
  * be NULL.  Synchronises. */
 w2_status w2_sem_observables(w2_sem_ctx *ctx, w2_obs *out, double *n1);
 
+/* Occupation numbers and correlation entropy of the one-body density matrix
+ * of the state (the strongly correlated example, Sec. 5.4, and the appendix
+ * on the correlation entropy): f1 = dx sum_{x2} int f dp2; the inverse Wigner
+ * transform rho1(x_b, x_c) = int f1((x_b + x_c)/2, p) e^{-i p (x_c - x_b)/hbar} dp
+ * taken exactly over the cell expansions (the transform of the two-body term
+ * at half the offset), f1 at half points from the natural cubic spline;
+ * occ[nx] (host, may be NULL) receives the eigenvalues of rho1 dx, largest
+ * first, by the cyclic Jacobi method of w2_hermitian_eigvals, and *entropy
+ * (may be NULL) s = sum n ln n / sum n over the occupations above 1e-14 of
+ * the largest.  The first call allocates its work arrays (about
+ * 16 nx^2 + 40 nx np bytes).  Synchronises. */
+w2_status w2_sem_occupations(w2_sem_ctx *ctx, double *occ, double *entropy);
+
 void w2_sem_destroy(w2_sem_ctx *ctx);
 
 #ifdef __cplusplus

@@ -34,6 +34,10 @@ struct w2_sem_ctx {
   uint16_t *psiP = nullptr, *utP = nullptr;  // slices of psi (columns) and of the U-Toeplitz rows
   int *psiE = nullptr, *utE = nullptr, Kp5 = 0;
   long long ldpsi = 0;  // row stride of the psi slices: np^2 rounded up to a multiple of 8
+  // occupation numbers (allocated by the first w2_sem_occupations)
+  double *rf1 = nullptr, *reta = nullptr, *rg = nullptr, *rosc = nullptr, *rphr = nullptr, *rphi = nullptr,
+         *reig = nullptr;
+  double2 *rrho = nullptr;
   // tensor-core products (W2_F64_SLICED): digit planes and line exponents
   int prec = W2_F64, Kp1 = 0, Kp2 = 0, Kp3 = 0, Kp4 = 0, ldp = 0;
   double *ee = nullptr;                       // gamma dx^2 / (pi^2 hbar^3) [Ei | Er]
@@ -60,7 +64,7 @@ static void sem_free(w2_sem_ctx *c) {
   for (double *q : d)
     if (q) cudaFree(q);
   if (c->k0) cudaFree(c->k0);
-  void *v[] = {c->psiP, c->utP, c->psiE, c->utE, c->dtab, c->cpdf, c->wtsdf, c->ee, c->phrP, c->phiP, c->phP, c->ehP, c->eeP, c->gP, c->frP, c->fcP, c->tP, c->bP, c->sP,
+  void *v[] = {c->rf1, c->reta, c->rg, c->rosc, c->rphr, c->rphi, c->reig, c->rrho, c->psiP, c->utP, c->psiE, c->utE, c->dtab, c->cpdf, c->wtsdf, c->ee, c->phrP, c->phiP, c->phP, c->ehP, c->eeP, c->gP, c->frP, c->fcP, c->tP, c->bP, c->sP,
                c->phrE, c->phiE, c->phE, c->ehE, c->eeE, c->gE, c->frE, c->fcE, c->tE, c->bE, c->sE};
   for (void *q : v)
     if (q) cudaFree(q);
@@ -510,6 +514,41 @@ extern "C" w2_status w2_sem_observables(w2_sem_ctx *ctx, w2_obs *out, double *n1
   out->l2norm = ctx->h_obs[4];
   out->step = ctx->step;
   if (n1) memcpy(n1, ctx->h_obs + 8, sizeof(double) * nx);
+  return W2_OK;
+}
+
+extern "C" w2_status w2_sem_occupations(w2_sem_ctx *ctx, double *occ, double *entropy) {
+  if (!ctx) return W2_ERR_ARG;
+  if (ctx->sticky) return ctx->sticky;
+  if (!ctx->have_state) return W2_ERR_STATE;
+  const int nx = ctx->nx, np = ctx->np, Q = ctx->Q;
+  cudaStream_t s = ctx->stream;
+  if (!ctx->rrho) {
+    cudaError_t e = cudaSuccess;
+#define SEM_ALLOC(ptr, count) \
+  if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), sizeof(*(ptr)) * (size_t)(count));
+    SEM_ALLOC(ctx->rf1, (long long)nx * np) SEM_ALLOC(ctx->reta, (long long)(nx + 2) * np)
+    SEM_ALLOC(ctx->rg, (long long)(2 * nx - 1) * np) SEM_ALLOC(ctx->rosc, 2LL * nx * Q)
+    SEM_ALLOC(ctx->rphr, (long long)(2 * nx - 1) * np) SEM_ALLOC(ctx->rphi, (long long)(2 * nx - 1) * np)
+    SEM_ALLOC(ctx->reig, nx + 1) SEM_ALLOC(ctx->rrho, (long long)nx * nx)
+#undef SEM_ALLOC
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return W2_ERR_OOM;
+    }
+    // transform rows at half steps: Phi_j(m dx / 2), m = -(nx - 1) .. nx - 1
+    SemTabArgs ta{nx, ctx->M, Q, np, nx - 1, 0.5 * ctx->dx, ctx->width, ctx->hbar, ctx->Lp, ctx->p, ctx->centre,
+                  ctx->cheb, ctx->rosc, nullptr, ctx->rphr, ctx->rphi, nullptr, nullptr, nullptr};
+    SEM_TRY(launch_sem_osc(ta, s));
+    SEM_TRY(launch_sem_phi(ta, s));
+  }
+  SEM_TRY(launch_sem_rdm(nx, np, ctx->dx, ctx->f, ctx->w, ctx->cp, ctx->rf1, ctx->reta, ctx->rg, ctx->rphr, ctx->rphi,
+                         ctx->rrho, s));
+  SEM_TRY(w2::launch_jacobi_herm(ctx->rrho, nx, 1, ctx->reig, s));
+  SEM_TRY(w2::launch_corr_entropy(ctx->reig, nx, ctx->reig + nx, s));
+  if (occ) SEM_TRY(cudaMemcpyAsync(occ, ctx->reig, sizeof(double) * nx, cudaMemcpyDeviceToHost, s));
+  if (entropy) SEM_TRY(cudaMemcpyAsync(entropy, ctx->reig + nx, sizeof(double), cudaMemcpyDeviceToHost, s));
+  SEM_TRY(cudaStreamSynchronize(s));
   return W2_OK;
 }
 

@@ -45,6 +45,7 @@ struct SemTabArgs {
 };
 cudaError_t launch_sem_osc(const SemTabArgs &a, cudaStream_t s);
 cudaError_t launch_sem_tables(const SemTabArgs &a, cudaStream_t s);
+cudaError_t launch_sem_phi(const SemTabArgs &a, cudaStream_t s);  // Phi rows only (rows -h .. h at spacing dx)
 
 // Per-X weighted sums xs[X] = sum_{j1,j2} w_j1 w_j2 f[X][j1][j2] and the
 // densities n[0..nx) = dx sum_i2 xs, n[nx..2nx) = dx sum_i1 xs.
@@ -98,6 +99,15 @@ struct SemObsArgs {
   double *out;          // [8 + nx]
 };
 cudaError_t launch_sem_obs(const SemObsArgs &a, cudaStream_t s);
+
+// Occupation numbers on the bounded box: f1[i][j] = dx sum_{i2} sum_{j2} w_{j2} f
+// (f1: [nx][np]); g[k] = f1 at x_0 + k dx / 2 (k < 2 nx - 1; the odd rows from the
+// natural cubic spline of each column, eta scratch [nx + 2][np]); and
+// rho[b][c] = dx sum_j g[b + c][j] conj(Phi_j((c - b) dx / 2)) with the
+// transform rows phr/phi [2 nx - 1][np] (k_sem_phi at half steps), made
+// Hermitian.
+cudaError_t launch_sem_rdm(int nx, int np, double dx, const double *f, const double *w, const double *cp, double *f1,
+                           double *eta, double *g, const double *phr, const double *phi, double2 *rho, cudaStream_t s);
 
 // Scaling: out = a * in (n elements).
 cudaError_t launch_sem_scale(long long n, double a, const double *in, double *out, cudaStream_t s);

@@ -497,6 +497,69 @@ __global__ void __launch_bounds__(1024) k_sem_obs_fin(SemObsArgs a) {
   for (int i = threadIdx.x; i < nx; i += blockDim.x) a.out[8 + i] = a.n[i];
 }
 
+// Occupation numbers: the reduced Wigner function (one block per (x, p)),
+// its half points by the natural spline, and the density matrix.
+__global__ void __launch_bounds__(128) k_sem_f1(int nx, int np, double dx, const double *__restrict__ f,
+                                                const double *__restrict__ w, double *f1) {
+  __shared__ double red[4];
+  const int i = blockIdx.x / np, j = blockIdx.x % np;
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < nx * np; e += 128) {
+    const int i2 = e / np, j2 = e % np;
+    acc = fma(w[j2], f[(((long long)i * nx + i2) * np + j) * np + j2], acc);
+  }
+  const double v = block_sum<128>(acc, red);
+  if (threadIdx.x == 0) f1[(long long)i * np + j] = dx * v;
+}
+
+__global__ void k_sem_halfgrid(int nx, int np, const double *f1, const double *cp, double *eta, double *g) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= np) return;
+  const int N = nx - 1;
+  double *E = eta + j;  // eta_nu at E[(nu + 1) * np], nu = -1 .. N + 1
+  auto F = [&](int i) { return f1[(long long)i * np + j]; };
+  E[np] = F(0);
+  E[(N + 1) * np] = F(N);
+  double dprev = 0.0;
+  for (int i = 1; i <= N - 1; ++i) {
+    double r = 6.0 * F(i);
+    if (i == 1) r -= F(0);
+    if (i == N - 1) r -= F(N);
+    dprev = (r - dprev) * cp[i];
+    E[(i + 1) * np] = dprev;
+  }
+  double enext = dprev;
+  for (int i = N - 2; i >= 1; --i) {
+    enext = E[(i + 1) * np] - cp[i] * enext;
+    E[(i + 1) * np] = enext;
+  }
+  E[0] = 2.0 * E[np] - E[2 * np];
+  E[(N + 2) * np] = 2.0 * E[(N + 1) * np] - E[N * np];
+  for (int i = 0; i < nx; ++i) g[(long long)(2 * i) * np + j] = F(i);
+  // B-spline weights at theta = 1/2: 1/48, 23/48, 23/48, 1/48
+  for (int i = 0; i < N; ++i) {
+    const double v = (E[i * np] + E[(i + 3) * np]) * (1.0 / 48.0) + (E[(i + 1) * np] + E[(i + 2) * np]) * (23.0 / 48.0);
+    g[(long long)(2 * i + 1) * np + j] = v;
+  }
+}
+
+__global__ void k_sem_rho(int nx, int np, double dx, const double *g, const double *phr, const double *phi,
+                          double2 *rho) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nx * nx) return;
+  const int b = e / nx, c = e % nx;
+  if (b > c) return;
+  const double *gr = g + (long long)(b + c) * np;
+  const long long m = (long long)(c - b + nx - 1) * np;
+  double re = 0.0, im = 0.0;
+  for (int j = 0; j < np; ++j) {
+    re = fma(gr[j], phr[m + j], re);
+    im = fma(-gr[j], phi[m + j], im);
+  }
+  rho[(long long)b * nx + c] = make_double2(dx * re, b == c ? 0.0 : dx * im);
+  rho[(long long)c * nx + b] = make_double2(dx * re, b == c ? 0.0 : -dx * im);
+}
+
 inline int grid_for(long long n, int nt) {
   long long g = (n + nt - 1) / nt;
   return (int)(g < 152LL * 32 ? (g > 0 ? g : 1) : 152LL * 32);
@@ -516,6 +579,11 @@ cudaError_t launch_sem_tables(const SemTabArgs &a, cudaStream_t s) {
   k_sem_phi<<<grid_for((long long)(2 * a.h + 1) * a.np, 256), 256, 0, s>>>(a);
   const long long nas = (long long)4 * (a.h + 1) * a.np * 2 + (long long)a.np * 2 * (2 * a.h + 1);
   k_sem_assemble<<<grid_for(nas, 256), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sem_phi(const SemTabArgs &a, cudaStream_t s) {
+  k_sem_phi<<<grid_for((long long)(2 * a.h + 1) * a.np, 256), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -573,6 +641,14 @@ cudaError_t launch_sem_adv(int axis, const SemAdvArgs &a, cudaStream_t s, int df
 cudaError_t launch_sem_axpy(long long n, const double *x, double a, const double *y, const double *y2, double *out,
                             cudaStream_t s) {
   k_sem_axpy<<<grid_for(n, 256), 256, 0, s>>>(n, x, a, y, y2, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sem_rdm(int nx, int np, double dx, const double *f, const double *w, const double *cp, double *f1,
+                           double *eta, double *g, const double *phr, const double *phi, double2 *rho, cudaStream_t s) {
+  k_sem_f1<<<nx * np, 128, 0, s>>>(nx, np, dx, f, w, f1);
+  k_sem_halfgrid<<<(np + 63) / 64, 64, 0, s>>>(nx, np, f1, cp, eta, g);
+  k_sem_rho<<<(nx * nx + 127) / 128, 128, 0, s>>>(nx, np, dx, g, phr, phi, rho);
   return cudaGetLastError();
 }
 

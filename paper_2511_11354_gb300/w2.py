@@ -38,7 +38,8 @@ EXPORTS = ("w2_create", "w2_set_potentials", "w2_set_state", "w2_get_state", "w2
            "w2_mlp_set_scales", "w2_mlp_forward", "w2_mlp_train_step", "w2_mlp_gradients", "w2_mlp_destroy",
            "w2_features", "w2_theta_pair", "w2_learned_attach", "w2_learned_report",
            "w2_sem_create", "w2_sem_set_potentials", "w2_sem_momenta", "w2_sem_set_state", "w2_sem_get_state",
-           "w2_sem_theta", "w2_sem_advect", "w2_sem_step", "w2_sem_observables", "w2_sem_destroy")
+           "w2_sem_theta", "w2_sem_advect", "w2_sem_step", "w2_sem_observables", "w2_sem_occupations",
+           "w2_sem_destroy")
 STEP_KERNELS = ("xsum_f", "tables_f", "theta_predictor", "shift_x2", "shift_x1_lawson", "xsum_ftilde",
                 "tables_ftilde", "theta_corrector")
 
@@ -128,6 +129,7 @@ def load(path: str = LIB_PATH):
     lib.w2_sem_advect.argtypes = [vp, vp, vp]
     lib.w2_sem_step.argtypes = [vp, ctypes.c_int32]
     lib.w2_sem_observables.argtypes = [vp, ctypes.POINTER(Obs), dp]
+    lib.w2_sem_occupations.argtypes = [vp, dp, dp]
     lib.w2_sem_destroy.argtypes = [vp]
     lib.w2_sem_destroy.restype = None
     lib.w2_status_string.argtypes = [ctypes.c_int]
@@ -560,6 +562,15 @@ class SemContext:
         _check(self.lib.w2_sem_observables(self.h, ctypes.byref(o), n1.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
                "w2_sem_observables")
         return Observables(o.mass, o.energy, o.purity, o.entropy_lin, o.l2norm, o.step, n1, None, "W2_OK")
+
+    def occupations(self):
+        """(occupation numbers of the one-body density matrix, largest first;
+        correlation entropy)."""
+        occ = np.zeros(self.nx)
+        s = ctypes.c_double()
+        _check(self.lib.w2_sem_occupations(self.h, occ.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                           ctypes.byref(s)), "w2_sem_occupations")
+        return occ, s.value
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

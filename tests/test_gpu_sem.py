@@ -180,3 +180,39 @@ def test_paper_mesh_sampled(prec):
     g = ctx.get_state(torch.empty_like(d))
     asym = (g - g.permute(1, 0, 3, 2)).abs().max().item()
     assert math.isfinite(asym) and asym <= (1e-13 if prec == "W2_F64" else 1e-11) * g.abs().max().item()
+
+
+@pytest.mark.parametrize("prec", ["W2_F64", "W2_F64_SLICED"])
+def test_occupations_parity(prec):
+    """Occupation numbers and correlation entropy of an evolved correlated
+    state against the oracle (exact inverse Wigner transform over the cells,
+    numpy's Hermitian eigensolver)."""
+    from oracle.rdm_ref import correlation_entropy
+    prob, f = _case(21, 2, 8, 12.0, "IV")
+    ctx = _ctx(prob, prec)
+    ctx.set_state(f)
+    ctx.step(2)
+    g = ctx.get_state()
+    occ, s = ctx.occupations()
+    ref = SemOracle(prob).occupations(g)
+    assert np.abs(occ - ref).max() < 1e-11 * ref[0]
+    assert abs(s - correlation_entropy(ref)) < 1e-10 * max(1.0, abs(s))
+    assert abs(occ.sum() - ctx.observables().mass) < 1e-10 * occ.sum()
+
+
+def test_occupations_of_a_two_packet_mixture():
+    """f = f1 (x) f1 with f1 the 50/50 mixture of two unit-width Gaussians 4
+    apart: occupations (1 +- e^-2)/2 (the overlap of the packets is e^-2)."""
+    prob = inputs.sem_correlated_problem("I", nx=121, ncell=8, nq=12, L=30.0)
+    o = SemOracle(prob)
+    x, p = o.x, o.p
+    f1 = sum(np.exp(-0.5 * (x[:, None] - c) ** 2 - 2 * p[None, :] ** 2) for c in (-2.0, 2.0)) / (2 * math.pi)
+    m1 = o.dx * np.dot(f1.sum(axis=0), o.w)
+    f = np.einsum("ac,bd->abcd", f1, f1 / m1)
+    ctx = _ctx(prob)
+    ctx.set_state(f)
+    occ, s = ctx.occupations()
+    e = math.exp(-2.0)
+    assert abs(occ[0] - 0.5 * (1 + e)) < 1e-5 and abs(occ[1] - 0.5 * (1 - e)) < 1e-5, occ[:3]
+    exact = sum(v * math.log(v) for v in (0.5 * (1 + e), 0.5 * (1 - e)))
+    assert abs(s - exact) < 5e-3

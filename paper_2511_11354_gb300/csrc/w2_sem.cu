@@ -32,6 +32,9 @@ struct w2_sem_ctx {
   float2 *cpdf = nullptr, *wtsdf = nullptr;  // spline tables as double-float pairs (sliced context)
   double *dtab = nullptr;  // [2][2nx-1][4h+1] w (W(rho + u) - W(rho - u)), w = 1, 2 (sliced context)
   uint16_t *psiP = nullptr, *utP = nullptr;  // slices of psi (columns) and of the U-Toeplitz rows
+  uint16_t *phP2 = nullptr;                  // slices of Ph' (Ph with its last np columns negated)
+  double *ph2 = nullptr;
+  int *phE2 = nullptr;
   int *psiE = nullptr, *utE = nullptr, Kp5 = 0;
   long long ldpsi = 0;  // row stride of the psi slices: np^2 rounded up to a multiple of 8
   // occupation numbers (allocated by the first w2_sem_occupations)
@@ -64,7 +67,7 @@ static void sem_free(w2_sem_ctx *c) {
   for (double *q : d)
     if (q) cudaFree(q);
   if (c->k0) cudaFree(c->k0);
-  void *v[] = {c->rf1, c->reta, c->rg, c->rosc, c->rphr, c->rphi, c->reig, c->rrho, c->psiP, c->utP, c->psiE, c->utE, c->dtab, c->cpdf, c->wtsdf, c->ee, c->phrP, c->phiP, c->phP, c->ehP, c->eeP, c->gP, c->frP, c->fcP, c->tP, c->bP, c->sP,
+  void *v[] = {c->phP2, c->ph2, c->phE2, c->rf1, c->reta, c->rg, c->rosc, c->rphr, c->rphi, c->reig, c->rrho, c->psiP, c->utP, c->psiE, c->utE, c->dtab, c->cpdf, c->wtsdf, c->ee, c->phrP, c->phiP, c->phP, c->ehP, c->eeP, c->gP, c->frP, c->fcP, c->tP, c->bP, c->sP,
                c->phrE, c->phiE, c->phE, c->ehE, c->eeE, c->gE, c->frE, c->fcE, c->tE, c->bE, c->sE};
   for (void *q : v)
     if (q) cudaFree(q);
@@ -163,6 +166,7 @@ extern "C" w2_status w2_sem_create(const w2_sem_config *cfg, void *cuda_stream, 
   if (sliced) {
     SEM_ALLOC(ctx->psiP, 6LL * ctx->Kp5 * ctx->ldpsi) SEM_ALLOC(ctx->psiE, (long long)np * np)
     SEM_ALLOC(ctx->utP, 6LL * 2 * nx * ctx->Kp5) SEM_ALLOC(ctx->utE, 2 * nx)
+    SEM_ALLOC(ctx->phP2, 6LL * 2 * Nyh * Kp2) SEM_ALLOC(ctx->ph2, 4LL * Nyh * np) SEM_ALLOC(ctx->phE2, 2 * Nyh)
     SEM_ALLOC(ctx->cpdf, nx) SEM_ALLOC(ctx->wtsdf, 4 * np) SEM_ALLOC(ctx->dtab, 2LL * (2 * nx - 1) * (4 * ctx->h + 1))
     SEM_ALLOC(ctx->ee, 2LL * np * Ny)
     SEM_ALLOC(ctx->phrP, 6LL * Ny * Kp1) SEM_ALLOC(ctx->phiP, 6LL * Ny * Kp1) SEM_ALLOC(ctx->phP, 6LL * 2 * Nyh * Kp2)
@@ -205,6 +209,8 @@ extern "C" w2_status w2_sem_create(const w2_sem_config *cfg, void *cuda_stream, 
     rows(ctx->phir, Ny, np, Kp1, ctx->phrP, ctx->phrE);
     rows(ctx->phii, Ny, np, Kp1, ctx->phiP, ctx->phiE);
     rows(ctx->ph, 2 * Nyh, 2 * np, Kp2, ctx->phP, ctx->phE);
+    if (e == cudaSuccess) e = launch_sem_negcols(2 * Nyh, 2 * np, np, ctx->ph, ctx->ph2, ctx->stream);
+    rows(ctx->ph2, 2 * Nyh, 2 * np, Kp2, ctx->phP2, ctx->phE2);
     rows(ctx->eh, np, 2 * Nyh, Kp3, ctx->ehP, ctx->ehE);
     rows(ctx->eh + (long long)np * 2 * Nyh, np, 2 * Nyh, Kp3, ctx->ehP + 6LL * np * Kp3, ctx->ehE + np);
     // psi as columns (i, j) over the offset d: the B operand of the table product
@@ -414,21 +420,32 @@ static w2_status sem_theta_sliced(w2_sem_ctx *ctx, const double *in, double *out
                  ctx->gE + (long long)nx * np, 0, np, out + x0 * np2, np, nx * np2, np2, 1, nb, nx};
     SEM_TRY(gemm_k(a2, np, 0));
     if (ctx->gamma == 0.0) continue;
-    // T^T_X = [Phr F_X^T | Phi F_X^T]
-    GemmSArgs t{Ny, np, np, 0, ctx->phrP, Kp1, (long long)Ny * Kp1, 0, 0, ctx->phrE, 0, 0, ctx->frP, Kp1,
-                (long long)np * Kp1, frS, 0, ctx->frE, np, 0, ctx->cT, 2 * np, (long long)Ny * 2 * np, 0, 0, nb, 1};
+    // T^T_X = [Phr F_X^T | Phi F_X^T] on the rows y2 >= 0 only: F is real, so
+    // the row -y2 is the conjugate [Tr | -Ti] of the row y2
+    const long long hK1 = (long long)ctx->h * Kp1;
+    GemmSArgs t{Nyh, np, np, 0, ctx->phrP + hK1, Kp1, (long long)Ny * Kp1, 0, 0, ctx->phrE + ctx->h, 0, 0, ctx->frP,
+                Kp1, (long long)np * Kp1, frS, 0, ctx->frE, np, 0, ctx->cT, 2 * np, (long long)Nyh * 2 * np, 0, 0, nb,
+                1};
     SEM_TRY(gemm_k(t, np, 0));
-    t.A = ctx->phiP;
-    t.Ae = ctx->phiE;
+    t.A = ctx->phiP + hK1;
+    t.Ae = ctx->phiE + ctx->h;
     t.C = ctx->cT + np;
     SEM_TRY(gemm_k(t, np, 0));
-    SliceArgs ts{Ny, 2 * np, Kp2, 0, ctx->cT, 2 * np, 1, (long long)Ny * 2 * np, 0, ctx->tP, (long long)Ny * Kp2, tS,
-                 ctx->tE, Ny, nb, 1, nullptr, nx, ctx->h, 0};
+    SliceArgs ts{Nyh, 2 * np, Kp2, 0, ctx->cT, 2 * np, 1, (long long)Nyh * 2 * np, 0, ctx->tP, (long long)Nyh * Kp2,
+                 tS, ctx->tE, Nyh, nb, 1, nullptr, nx, ctx->h, 0};
     SEM_TRY(launch_slice(0, 0, ts, s));
-    // A^T_X = T^T_X Ph^T
-    GemmSArgs aa{Ny, 2 * Nyh, 2 * np, 0, ctx->tP, Kp2, (long long)Ny * Kp2, tS, 0, ctx->tE, Ny, 0, ctx->phP, Kp2,
-                 2LL * Nyh * Kp2, 0, 0, ctx->phE, 0, 0, ctx->cA, 2 * Nyh, (long long)Ny * 2 * Nyh, 0, 0, nb, 1};
+    // A^T_X rows y2 >= 0: T^T Ph^T; rows y2 = -y < 0: [Tr | -Ti](y) Ph^T = T^T(y) Ph'^T
+    // (Ph' = Ph with its last np columns negated), written upwards from row h - 1
+    GemmSArgs aa{Nyh, 2 * Nyh, 2 * np, 0, ctx->tP, Kp2, (long long)Nyh * Kp2, tS, 0, ctx->tE, Nyh, 0, ctx->phP, Kp2,
+                 2LL * Nyh * Kp2, 0, 0, ctx->phE, 0, 0, ctx->cA + (long long)ctx->h * 2 * Nyh, 2 * Nyh,
+                 (long long)Ny * 2 * Nyh, 0, 0, nb, 1};
     SEM_TRY(gemm_k(aa, 2 * np, 0));
+    if (ctx->h > 0) {
+      GemmSArgs an{ctx->h, 2 * Nyh, 2 * np, 0, ctx->tP + Kp2, Kp2, (long long)Nyh * Kp2, tS, 0, ctx->tE + 1, Nyh, 0,
+                   ctx->phP2, Kp2, 2LL * Nyh * Kp2, 0, 0, ctx->phE2, 0, 0,
+                   ctx->cA + (long long)(ctx->h - 1) * 2 * Nyh, -2LL * Nyh, (long long)Ny * 2 * Nyh, 0, 0, nb, 1};
+      SEM_TRY(gemm_k(an, 2 * np, 0));
+    }
     // slices of B^T_X = w D (.) A^T_X
     SliceArgs bs{Ny, 2 * Nyh, Kp3, 0, ctx->cA, 2 * Nyh, 1, (long long)Ny * 2 * Nyh, 0, ctx->bP, (long long)Ny * Kp3,
                  bS, ctx->bE, Ny, nb, 1, ctx->dtab, nx, ctx->h, (int)x0};

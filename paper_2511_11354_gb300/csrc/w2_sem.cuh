@@ -109,6 +109,9 @@ cudaError_t launch_sem_obs(const SemObsArgs &a, cudaStream_t s);
 cudaError_t launch_sem_rdm(int nx, int np, double dx, const double *f, const double *w, const double *cp, double *f1,
                            double *eta, double *g, const double *phr, const double *phi, double2 *rho, cudaStream_t s);
 
+// out[r][c] = in[r][c] for c < c0, -in[r][c] for c >= c0 (rows x cols, row-major).
+cudaError_t launch_sem_negcols(int rows, int cols, int c0, const double *in, double *out, cudaStream_t s);
+
 // Scaling: out = a * in (n elements).
 cudaError_t launch_sem_scale(long long n, double a, const double *in, double *out, cudaStream_t s);
 

@@ -395,6 +395,12 @@ __global__ void __launch_bounds__(256) k_sem_adv_df(SemAdvArgs a) {
   }
 }
 
+__global__ void k_sem_negcols(int rows, int cols, int c0, const double *in, double *out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)rows * cols;
+       e += (long long)gridDim.x * blockDim.x)
+    out[e] = (e % cols) < c0 ? in[e] : -in[e];
+}
+
 __global__ void k_sem_scale(long long n, double a, const double *__restrict__ in, double *out) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
     out[e] = a * in[e];
@@ -649,6 +655,11 @@ cudaError_t launch_sem_rdm(int nx, int np, double dx, const double *f, const dou
   k_sem_f1<<<nx * np, 128, 0, s>>>(nx, np, dx, f, w, f1);
   k_sem_halfgrid<<<(np + 63) / 64, 64, 0, s>>>(nx, np, f1, cp, eta, g);
   k_sem_rho<<<(nx * nx + 127) / 128, 128, 0, s>>>(nx, np, dx, g, phr, phi, rho);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sem_negcols(int rows, int cols, int c0, const double *in, double *out, cudaStream_t s) {
+  k_sem_negcols<<<grid_for((long long)rows * cols, 256), 256, 0, s>>>(rows, cols, c0, in, out);
   return cudaGetLastError();
 }
 

@@ -30,6 +30,7 @@ struct w2_sem_ctx {
   double *cT = nullptr, *cA = nullptr, *cS = nullptr, *xpart = nullptr, *obs = nullptr, *h_obs = nullptr;
   int *k0 = nullptr;
   float2 *cpdf = nullptr, *wtsdf = nullptr;  // spline tables as double-float pairs (sliced context)
+  float2 *fwdc = nullptr, *bwdc = nullptr;   // start-sum coefficients of the piecewise recursion
   double *dtab = nullptr;  // [2][2nx-1][4h+1] w (W(rho + u) - W(rho - u)), w = 1, 2 (sliced context)
   uint16_t *psiP = nullptr, *utP = nullptr;  // slices of psi (columns) and of the U-Toeplitz rows
   uint16_t *phP2 = nullptr;                  // slices of Ph' (Ph with its last np columns negated)
@@ -67,7 +68,7 @@ static void sem_free(w2_sem_ctx *c) {
   for (double *q : d)
     if (q) cudaFree(q);
   if (c->k0) cudaFree(c->k0);
-  void *v[] = {c->phP2, c->ph2, c->phE2, c->rf1, c->reta, c->rg, c->rosc, c->rphr, c->rphi, c->reig, c->rrho, c->psiP, c->utP, c->psiE, c->utE, c->dtab, c->cpdf, c->wtsdf, c->ee, c->phrP, c->phiP, c->phP, c->ehP, c->eeP, c->gP, c->frP, c->fcP, c->tP, c->bP, c->sP,
+  void *v[] = {c->fwdc, c->bwdc, c->phP2, c->ph2, c->phE2, c->rf1, c->reta, c->rg, c->rosc, c->rphr, c->rphi, c->reig, c->rrho, c->psiP, c->utP, c->psiE, c->utE, c->dtab, c->cpdf, c->wtsdf, c->ee, c->phrP, c->phiP, c->phP, c->ehP, c->eeP, c->gP, c->frP, c->fcP, c->tP, c->bP, c->sP,
                c->phrE, c->phiE, c->phE, c->ehE, c->eeE, c->gE, c->frE, c->fcE, c->tE, c->bE, c->sE};
   for (void *q : v)
     if (q) cudaFree(q);
@@ -167,7 +168,7 @@ extern "C" w2_status w2_sem_create(const w2_sem_config *cfg, void *cuda_stream, 
     SEM_ALLOC(ctx->psiP, 6LL * ctx->Kp5 * ctx->ldpsi) SEM_ALLOC(ctx->psiE, (long long)np * np)
     SEM_ALLOC(ctx->utP, 6LL * 2 * nx * ctx->Kp5) SEM_ALLOC(ctx->utE, 2 * nx)
     SEM_ALLOC(ctx->phP2, 6LL * 2 * Nyh * Kp2) SEM_ALLOC(ctx->ph2, 4LL * Nyh * np) SEM_ALLOC(ctx->phE2, 2 * Nyh)
-    SEM_ALLOC(ctx->cpdf, nx) SEM_ALLOC(ctx->wtsdf, 4 * np) SEM_ALLOC(ctx->dtab, 2LL * (2 * nx - 1) * (4 * ctx->h + 1))
+    SEM_ALLOC(ctx->cpdf, nx) SEM_ALLOC(ctx->wtsdf, 4 * np) SEM_ALLOC(ctx->fwdc, 28) SEM_ALLOC(ctx->bwdc, 28) SEM_ALLOC(ctx->dtab, 2LL * (2 * nx - 1) * (4 * ctx->h + 1))
     SEM_ALLOC(ctx->ee, 2LL * np * Ny)
     SEM_ALLOC(ctx->phrP, 6LL * Ny * Kp1) SEM_ALLOC(ctx->phiP, 6LL * Ny * Kp1) SEM_ALLOC(ctx->phP, 6LL * 2 * Nyh * Kp2)
     SEM_ALLOC(ctx->ehP, 2 * 6LL * np * Kp3) SEM_ALLOC(ctx->eeP, 6LL * np * Kp4) SEM_ALLOC(ctx->gP, 6LL * 2 * nx * np * Kp1)
@@ -193,7 +194,19 @@ extern "C" w2_status w2_sem_create(const w2_sem_config *cfg, void *cuda_stream, 
   auto pair = [](double v) { const float h = (float)v; return make_float2(h, (float)(v - (double)h)); };
   for (int i = 0; i < nx; ++i) cpdf[i] = pair(cp[i]);
   for (int j = 0; j < 4 * np; ++j) wtsdf[j] = pair(wts[j]);
+  std::vector<float2> fwdc(28), bwdc(28);
+  {
+    const double cs = 2.0 - sqrt(3.0);
+    double pw = 1.0;  // c*^k
+    for (int k = 0; k < 28; ++k) {
+      bwdc[k] = pair((k & 1) ? -pw : pw);
+      fwdc[k] = pair((k & 1) ? -pw * cs : pw * cs);
+      pw *= cs;
+    }
+  }
   if (sliced) {
+    up(ctx->fwdc, fwdc.data(), sizeof(float2) * 28);
+    up(ctx->bwdc, bwdc.data(), sizeof(float2) * 28);
     up(ctx->cpdf, cpdf.data(), sizeof(float2) * nx);
     up(ctx->wtsdf, wtsdf.data(), sizeof(float2) * 4 * np);
   }
@@ -472,7 +485,8 @@ static w2_status sem_theta_sliced(w2_sem_ctx *ctx, const double *in, double *out
 // FP64-pipe context in FP64.
 static w2_status sem_advect(w2_sem_ctx *ctx, const double *in, double *out) {
   const int df = ctx->prec == W2_F64_SLICED;
-  SemAdvArgs aa{ctx->nx, ctx->np, ctx->C, in, ctx->t, ctx->cp, ctx->k0, ctx->wts, ctx->cpdf, ctx->wtsdf};
+  SemAdvArgs aa{ctx->nx, ctx->np, ctx->C, in, ctx->t, ctx->cp, ctx->k0, ctx->wts, ctx->cpdf, ctx->wtsdf, ctx->fwdc,
+                ctx->bwdc};
   SEM_TRY(launch_sem_adv(0, aa, ctx->stream, df));
   aa.in = ctx->t;
   aa.out = out;

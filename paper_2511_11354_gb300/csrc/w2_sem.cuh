@@ -80,6 +80,8 @@ struct SemAdvArgs {
   const double *wts;    // [np][4] B-spline weights
   const float2 *cpdf = nullptr;   // the same factors and weights as double-float (hi, lo) pairs
   const float2 *wtsdf = nullptr;
+  const float2 *fwdc = nullptr;   // [28] (-1)^k c*^(k+1) and (-c*)^k, c* = 2 - sqrt(3), as pairs
+  const float2 *bwdc = nullptr;
 };
 // df = 1: the recursion and the four-term evaluation in double-float pairs on
 // the FP32 pipe (FP64 in and out, converted with integer operations).

@@ -333,6 +333,8 @@ __device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a
 // line (zero, zero, ghost | ghost, zero, zero), so a foot index is clamped
 // into [-3, N + 3] instead of branched on; thread t works on column t % C and
 // rows t / C + 4 k.
+constexpr int kStart = 28, kPieceMin = 48;
+
 template <int AXIS>
 __global__ void __launch_bounds__(256) k_sem_adv_df(SemAdvArgs a) {
   extern __shared__ float2 sf[];
@@ -355,30 +357,76 @@ __global__ void __launch_bounds__(256) k_sem_adv_df(SemAdvArgs a) {
     col[-3 * C] = z; col[-2 * C] = z; col[(N + 2) * C] = z; col[(N + 3) * C] = z;
   }
   __syncthreads();
-  if (r0 == 0 && live) {
-    const float2 six = make_float2(6.f, 0.f), two = make_float2(2.f, 0.f);
+  const float2 six = make_float2(6.f, 0.f), two = make_float2(2.f, 0.f);
+  if (N - 1 < 4 * kPieceMin) {  // short lines: one thread per column
+    if (r0 == 0 && live) {
+      const float2 f0 = col[0], fN = col[N * C];
+      // forward: d'_i = (r_i - d'_{i-1}) c'_i, r_i = 6 f_i - [i==1] f_0 - [i==N-1] f_N
+      float2 dprev = df_mulv(df_add(df_mulv(col[C], six), df_neg(f0)), a.cpdf[1]);
+      if (N - 1 == 1) dprev = df_mulv(df_add(df_add(df_mulv(col[C], six), df_neg(f0)), df_neg(fN)), a.cpdf[1]);
+      col[C] = dprev;
+      for (int i = 2; i <= N - 2; ++i) {
+        dprev = df_mulv(df_add(df_mulv(col[i * C], six), df_neg(dprev)), a.cpdf[i]);
+        col[i * C] = dprev;
+      }
+      if (N - 1 >= 2) {
+        const int i = N - 1;
+        dprev = df_mulv(df_add(df_add(df_mulv(col[i * C], six), df_neg(fN)), df_neg(dprev)), a.cpdf[i]);
+        col[i * C] = dprev;
+      }
+      // backward: eta_{N-1} = d'_{N-1}, eta_i = d'_i - c'_i eta_{i+1}
+      float2 enext = dprev;
+      for (int i = N - 2; i >= 1; --i) {
+        enext = df_add(col[i * C], df_neg(df_mulv(a.cpdf[i], enext)));
+        col[i * C] = enext;
+      }
+      col[-C] = df_add(df_mulv(col[0], two), df_neg(col[C]));
+      col[(N + 1) * C] = df_add(df_mulv(col[N * C], two), df_neg(col[(N - 1) * C]));
+    }
+  } else {
+    // Four threads per column, one piece [lo, hi) of the interior rows each.
+    // Where c'_i has settled to c* = 2 - sqrt(3), the recursions unroll into
+    // geometric sums, so piece p > 0 starts its forward pass from
+    // d'_{lo-1} = sum_{k<kStart} (-1)^k c*^(k+1) 6 f_{lo-1-k} and piece p < 3
+    // its backward pass from eta_hi = sum_k (-c*)^k d'_{hi+k} (kStart = 28
+    // terms: the tail is below 2^-53 of the scale).  The start values are
+    // read before any piece overwrites its rows.
+    const int n = N - 1, lo = 1 + (r0 * n) / 4, hi = 1 + ((r0 + 1) * n) / 4;
+    float2 dprev = make_float2(0.f, 0.f);
+    if (live && r0 > 0)
+      for (int k = 0; k < kStart; ++k) dprev = df_add(dprev, df_mulv(a.fwdc[k], df_mulv(col[(lo - 1 - k) * C], six)));
     const float2 f0 = col[0], fN = col[N * C];
-    // forward: d'_i = (r_i - d'_{i-1}) c'_i, r_i = 6 f_i - [i==1] f_0 - [i==N-1] f_N
-    float2 dprev = df_mulv(df_add(df_mulv(col[C], six), df_neg(f0)), a.cpdf[1]);
-    if (N - 1 == 1) dprev = df_mulv(df_add(df_add(df_mulv(col[C], six), df_neg(f0)), df_neg(fN)), a.cpdf[1]);
-    col[C] = dprev;
-    for (int i = 2; i <= N - 2; ++i) {
-      dprev = df_mulv(df_add(df_mulv(col[i * C], six), df_neg(dprev)), a.cpdf[i]);
-      col[i * C] = dprev;
+    __syncthreads();
+    if (live) {
+      for (int i = lo; i < hi; ++i) {
+        float2 r = df_mulv(col[i * C], six);
+        if (i == 1) r = df_add(r, df_neg(f0));
+        if (i == N - 1) r = df_add(r, df_neg(fN));
+        dprev = df_mulv(df_add(r, df_neg(dprev)), a.cpdf[i]);
+        col[i * C] = dprev;
+      }
     }
-    if (N - 1 >= 2) {
-      const int i = N - 1;
-      dprev = df_mulv(df_add(df_add(df_mulv(col[i * C], six), df_neg(fN)), df_neg(dprev)), a.cpdf[i]);
-      col[i * C] = dprev;
+    __syncthreads();
+    float2 enext = make_float2(0.f, 0.f);
+    if (live && r0 < 3)
+      for (int k = 0; k < kStart && hi + k <= N - 1; ++k) enext = df_add(enext, df_mulv(a.bwdc[k], col[(hi + k) * C]));
+    __syncthreads();
+    if (live) {
+      int i = hi - 1;
+      if (r0 == 3) {  // eta_{N-1} = d'_{N-1}
+        enext = col[i * C];
+        --i;
+      }
+      for (; i >= lo; --i) {
+        enext = df_add(col[i * C], df_neg(df_mulv(a.cpdf[i], enext)));
+        col[i * C] = enext;
+      }
     }
-    // backward: eta_{N-1} = d'_{N-1}, eta_i = d'_i - c'_i eta_{i+1}
-    float2 enext = dprev;
-    for (int i = N - 2; i >= 1; --i) {
-      enext = df_add(col[i * C], df_neg(df_mulv(a.cpdf[i], enext)));
-      col[i * C] = enext;
+    __syncthreads();
+    if (live && r0 == 0) {
+      col[-C] = df_add(df_mulv(col[0], two), df_neg(col[C]));
+      col[(N + 1) * C] = df_add(df_mulv(col[N * C], two), df_neg(col[(N - 1) * C]));
     }
-    col[-C] = df_add(df_mulv(col[0], two), df_neg(col[C]));
-    col[(N + 1) * C] = df_add(df_mulv(col[N * C], two), df_neg(col[(N - 1) * C]));
   }
   __syncthreads();
   if (!live) return;

@@ -170,6 +170,54 @@ __global__ void __launch_bounds__(256) k_slice_cols(SliceArgs a) {
   }
 }
 
+// Column slices of the D_V-weighted second transform for S'^T = E B: line
+// y1 (a column of the planes) runs over k = [re | im] x y2, k < 2 Ny, with
+// B(k, y1) = w(y1) D(rho; y1, y2) A^T[y2][part Nyh + y1] (part = k / Ny,
+// y2 = k % Ny - h), A^T [Ny][2 Nyh] per X; planes [6][Kp][ldp] row-major.
+__global__ void __launch_bounds__(256) k_slice_dstack(SliceArgs a) {
+  __shared__ int red[8][32];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int y1 = blockIdx.x * 32 + tx;
+  const int b = blockIdx.y;
+  const int Nyh = a.h + 1, Ny = 2 * a.h + 1, K = 2 * Ny;
+  const double *in = a.in + (long long)b * a.sIn1;  // A^T of this X, row stride ls = 2 Nyh
+  const int X = a.x0 + b, rho = X / a.nx - X % a.nx;
+  const double *drow = a.dtab + (y1 > 0 ? (long long)(2 * a.nx - 1) * (4 * a.h + 1) : 0) +
+                       (long long)(rho + a.nx - 1) * (4 * a.h + 1) + 2 * a.h + y1 + a.h;  // + (-c) gives u = y1 - (c - h)
+  auto val = [&](int k) -> double {
+    const int part = k >= Ny, c = k - part * Ny;
+    return in[(long long)c * a.ls + part * Nyh + y1] * drow[-c];
+  };
+  int emax = 0;
+  if (y1 < Nyh)
+    for (int k = ty; k < K; k += 8) {
+      const int e = expo(val(k));
+      emax = e > emax ? e : emax;
+    }
+  red[ty][tx] = emax;
+  __syncthreads();
+  if (ty == 0) {
+    for (int i = 1; i < 8; ++i) emax = red[i][tx] > emax ? red[i][tx] : emax;
+    red[0][tx] = emax;
+  }
+  __syncthreads();
+  const int E = line_exp(red[0][tx]);
+  if (ty == 0 && y1 < Nyh) a.ex[b * a.sE + y1] = E;
+  uint16_t *P = a.planes + b * a.sP;
+  if (y1 >= a.ldp) return;
+  for (int k = ty; k < a.Kp; k += 8) {
+    int d[kDig];
+    if (y1 < Nyh && k < K && E != kBadExp) {
+      digits6(val(k), E, d);
+    } else {
+#pragma unroll
+      for (int s = 0; s < kDig; ++s) d[s] = 0;
+    }
+#pragma unroll
+    for (int s = 0; s < kDig; ++s) P[(long long)s * a.pP + (long long)k * a.ldp + y1] = bf16_int(d[s]);
+  }
+}
+
 __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
   asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
       "{%0,%1,%2,%3};\n"
@@ -350,6 +398,14 @@ cudaError_t launch_slice(int cols, int mode, const SliceArgs &a, cudaStream_t s)
     dim3 grid((a.ldp + 31) / 32, a.nbatch);
     k_slice_cols<<<grid, 256, 0, s>>>(a);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slice_dstack(const SliceArgs &a, cudaStream_t s) {
+  if (a.nbatch <= 0) return cudaSuccess;
+  if (a.nbatch > 65535 || a.ldp % 8 || a.ldp < a.h + 1 || a.Kp < 2 * (2 * a.h + 1)) return cudaErrorInvalidValue;
+  dim3 grid((a.ldp + 31) / 32, a.nbatch);
+  k_slice_dstack<<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

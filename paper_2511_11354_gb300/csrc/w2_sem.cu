@@ -31,6 +31,12 @@ struct w2_sem_ctx {
   int *k0 = nullptr;
   float2 *cpdf = nullptr, *wtsdf = nullptr;  // spline tables as double-float pairs (sliced context)
   float2 *fwdc = nullptr, *bwdc = nullptr;   // start-sum coefficients of the piecewise recursion
+  // S'^T = E B form of the last two products: slices of [Er | -Ei], [Ei | Er] (rows
+  // over 2 Ny) and of alpha [Ei_h | Er_h] (rows over 2 Nyh)
+  double *erm = nullptr, *eha = nullptr;
+  uint16_t *ermP = nullptr, *eiP = nullptr, *ehaP = nullptr;
+  int *ermE = nullptr, *eiE = nullptr, *ehaE = nullptr, ldq = 0;
+  long long bsz = 0;  // per-X size of the B slices
   double *dtab = nullptr;  // [2][2nx-1][4h+1] w (W(rho + u) - W(rho - u)), w = 1, 2 (sliced context)
   uint16_t *psiP = nullptr, *utP = nullptr;  // slices of psi (columns) and of the U-Toeplitz rows
   uint16_t *phP2 = nullptr;                  // slices of Ph' (Ph with its last np columns negated)
@@ -44,10 +50,9 @@ struct w2_sem_ctx {
   double2 *rrho = nullptr;
   // tensor-core products (W2_F64_SLICED): digit planes and line exponents
   int prec = W2_F64, Kp1 = 0, Kp2 = 0, Kp3 = 0, Kp4 = 0, ldp = 0;
-  double *ee = nullptr;                       // gamma dx^2 / (pi^2 hbar^3) [Ei | Er]
-  uint16_t *phrP = nullptr, *phiP = nullptr, *phP = nullptr, *ehP = nullptr, *eeP = nullptr, *gP = nullptr;
+  uint16_t *phrP = nullptr, *phiP = nullptr, *phP = nullptr, *gP = nullptr;
   uint16_t *frP = nullptr, *fcP = nullptr, *tP = nullptr, *bP = nullptr, *sP = nullptr;
-  int *phrE = nullptr, *phiE = nullptr, *phE = nullptr, *ehE = nullptr, *eeE = nullptr, *gE = nullptr;
+  int *phrE = nullptr, *phiE = nullptr, *phE = nullptr, *gE = nullptr;
   int *frE = nullptr, *fcE = nullptr, *tE = nullptr, *bE = nullptr, *sE = nullptr;
 };
 
@@ -68,8 +73,8 @@ static void sem_free(w2_sem_ctx *c) {
   for (double *q : d)
     if (q) cudaFree(q);
   if (c->k0) cudaFree(c->k0);
-  void *v[] = {c->fwdc, c->bwdc, c->phP2, c->ph2, c->phE2, c->rf1, c->reta, c->rg, c->rosc, c->rphr, c->rphi, c->reig, c->rrho, c->psiP, c->utP, c->psiE, c->utE, c->dtab, c->cpdf, c->wtsdf, c->ee, c->phrP, c->phiP, c->phP, c->ehP, c->eeP, c->gP, c->frP, c->fcP, c->tP, c->bP, c->sP,
-               c->phrE, c->phiE, c->phE, c->ehE, c->eeE, c->gE, c->frE, c->fcE, c->tE, c->bE, c->sE};
+  void *v[] = {c->erm, c->eha, c->ermP, c->eiP, c->ehaP, c->ermE, c->eiE, c->ehaE, c->fwdc, c->bwdc, c->phP2, c->ph2, c->phE2, c->rf1, c->reta, c->rg, c->rosc, c->rphr, c->rphi, c->reig, c->rrho, c->psiP, c->utP, c->psiE, c->utE, c->dtab, c->cpdf, c->wtsdf, c->phrP, c->phiP, c->phP, c->gP, c->frP, c->fcP, c->tP, c->bP, c->sP,
+               c->phrE, c->phiE, c->phE, c->gE, c->frE, c->fcE, c->tE, c->bE, c->sE};
   for (void *q : v)
     if (q) cudaFree(q);
   if (c->h_obs) cudaFreeHost(c->h_obs);
@@ -101,6 +106,10 @@ extern "C" w2_status w2_sem_create(const w2_sem_config *cfg, void *cuda_stream, 
   ctx->Kp1 = slice_kp(np); ctx->Kp2 = slice_kp(2 * np); ctx->Kp3 = slice_kp(2 * Nyh); ctx->Kp4 = slice_kp(2 * Ny);
   ctx->ldp = (np + 7) / 8 * 8;
   ctx->Kp5 = slice_kp(2 * nx - 1);
+  ctx->ldq = (Nyh + 7) / 8 * 8;
+  ctx->bsz = 6LL * ((long long)slice_kp(2 * Ny) * ctx->ldq > (long long)Ny * slice_kp(2 * Nyh)
+                        ? (long long)slice_kp(2 * Ny) * ctx->ldq
+                        : (long long)Ny * slice_kp(2 * Nyh));
   ctx->ldpsi = ((long long)np * np + 7) / 8 * 8;
   const int Kp1 = ctx->Kp1, Kp2 = ctx->Kp2, Kp3 = ctx->Kp3, Kp4 = ctx->Kp4, ldp = ctx->ldp;
   // two-body chain chunk: about 256 MB of FP64 intermediates (4 GB with the
@@ -169,13 +178,15 @@ extern "C" w2_status w2_sem_create(const w2_sem_config *cfg, void *cuda_stream, 
     SEM_ALLOC(ctx->utP, 6LL * 2 * nx * ctx->Kp5) SEM_ALLOC(ctx->utE, 2 * nx)
     SEM_ALLOC(ctx->phP2, 6LL * 2 * Nyh * Kp2) SEM_ALLOC(ctx->ph2, 4LL * Nyh * np) SEM_ALLOC(ctx->phE2, 2 * Nyh)
     SEM_ALLOC(ctx->cpdf, nx) SEM_ALLOC(ctx->wtsdf, 4 * np) SEM_ALLOC(ctx->fwdc, 28) SEM_ALLOC(ctx->bwdc, 28) SEM_ALLOC(ctx->dtab, 2LL * (2 * nx - 1) * (4 * ctx->h + 1))
-    SEM_ALLOC(ctx->ee, 2LL * np * Ny)
     SEM_ALLOC(ctx->phrP, 6LL * Ny * Kp1) SEM_ALLOC(ctx->phiP, 6LL * Ny * Kp1) SEM_ALLOC(ctx->phP, 6LL * 2 * Nyh * Kp2)
-    SEM_ALLOC(ctx->ehP, 2 * 6LL * np * Kp3) SEM_ALLOC(ctx->eeP, 6LL * np * Kp4) SEM_ALLOC(ctx->gP, 6LL * 2 * nx * np * Kp1)
+    SEM_ALLOC(ctx->gP, 6LL * 2 * nx * np * Kp1)
     SEM_ALLOC(ctx->frP, bx * 6 * np * Kp1) SEM_ALLOC(ctx->fcP, bx * 6 * Kp1 * ldp) SEM_ALLOC(ctx->tP, bx * 6 * Ny * Kp2)
-    SEM_ALLOC(ctx->bP, bx * 6 * Ny * Kp3) SEM_ALLOC(ctx->sP, bx * 6 * np * Kp4)
-    SEM_ALLOC(ctx->phrE, Ny) SEM_ALLOC(ctx->phiE, Ny) SEM_ALLOC(ctx->phE, 2 * Nyh) SEM_ALLOC(ctx->ehE, 2 * np)
-    SEM_ALLOC(ctx->eeE, np) SEM_ALLOC(ctx->gE, 2LL * nx * np) SEM_ALLOC(ctx->frE, bx * np) SEM_ALLOC(ctx->fcE, bx * np)
+    SEM_ALLOC(ctx->bP, bx * ctx->bsz) SEM_ALLOC(ctx->sP, bx * 6 * np * Kp4)
+    SEM_ALLOC(ctx->erm, 2LL * np * Ny) SEM_ALLOC(ctx->eha, 2LL * np * Nyh)
+    SEM_ALLOC(ctx->ermP, 6LL * np * Kp4) SEM_ALLOC(ctx->eiP, 6LL * np * Kp4) SEM_ALLOC(ctx->ehaP, 6LL * np * Kp3)
+    SEM_ALLOC(ctx->ermE, np) SEM_ALLOC(ctx->eiE, np) SEM_ALLOC(ctx->ehaE, np)
+    SEM_ALLOC(ctx->phrE, Ny) SEM_ALLOC(ctx->phiE, Ny) SEM_ALLOC(ctx->phE, 2 * Nyh)
+    SEM_ALLOC(ctx->gE, 2LL * nx * np) SEM_ALLOC(ctx->frE, bx * np) SEM_ALLOC(ctx->fcE, bx * np)
     SEM_ALLOC(ctx->tE, bx * Ny) SEM_ALLOC(ctx->bE, bx * Ny) SEM_ALLOC(ctx->sE, bx * np)
   }
 #undef SEM_ALLOC
@@ -214,7 +225,7 @@ extern "C" w2_status w2_sem_create(const w2_sem_config *cfg, void *cuda_stream, 
                 ctx->osc, ctx->psi, ctx->phir, ctx->phii, ctx->ph, ctx->eh, ctx->eier};
   if (e == cudaSuccess) e = launch_sem_osc(ta, ctx->stream);
   if (e == cudaSuccess) e = launch_sem_tables(ta, ctx->stream);
-  if (sliced) {  // static slices: Phi rows (K = np), Ph rows (K = 2 np), the two Eh blocks (K = 2 Nyh)
+  if (sliced) {  // static slices: Phi rows (K = np), Ph and Ph' rows (K = 2 np), [Er | -Ei] and [Ei | Er] rows (K = 2 Ny)
     auto rows = [&](const double *in, int L, int K, int Kp, uint16_t *P, int *E) {
       SliceArgs sa{L, K, Kp, 0, in, K, 1, 0, 0, P, (long long)L * Kp, 0, E, 0, 1, 1, nullptr, nx, ctx->h, 0};
       if (e == cudaSuccess) e = launch_slice(0, 0, sa, ctx->stream);
@@ -224,8 +235,9 @@ extern "C" w2_status w2_sem_create(const w2_sem_config *cfg, void *cuda_stream, 
     rows(ctx->ph, 2 * Nyh, 2 * np, Kp2, ctx->phP, ctx->phE);
     if (e == cudaSuccess) e = launch_sem_negcols(2 * Nyh, 2 * np, np, ctx->ph, ctx->ph2, ctx->stream);
     rows(ctx->ph2, 2 * Nyh, 2 * np, Kp2, ctx->phP2, ctx->phE2);
-    rows(ctx->eh, np, 2 * Nyh, Kp3, ctx->ehP, ctx->ehE);
-    rows(ctx->eh + (long long)np * 2 * Nyh, np, 2 * Nyh, Kp3, ctx->ehP + 6LL * np * Kp3, ctx->ehE + np);
+    if (e == cudaSuccess) e = launch_sem_erm(np, Ny, ctx->eier, ctx->erm, ctx->stream);
+    rows(ctx->erm, np, 2 * Ny, Kp4, ctx->ermP, ctx->ermE);
+    rows(ctx->eier, np, 2 * Ny, Kp4, ctx->eiP, ctx->eiE);
     // psi as columns (i, j) over the offset d: the B operand of the table product
     SliceArgs sp{np * np, 2 * nx - 1, ctx->Kp5, (int)ctx->ldpsi, ctx->psi, 1, (long long)np * np, 0, 0, ctx->psiP,
                  (long long)ctx->Kp5 * ctx->ldpsi, 0, ctx->psiE, 0, 1, 1, nullptr, nx, ctx->h, 0};
@@ -261,10 +273,10 @@ extern "C" w2_status w2_sem_set_potentials(w2_sem_ctx *ctx, w2_fn vext, void *ue
   SEM_TRY(cudaMemcpyAsync(ctx->wgrid, wg.data(), sizeof(double) * wg.size(), cudaMemcpyHostToDevice, ctx->stream));
   if (ctx->prec == W2_F64_SLICED) {
     const double alpha = gamma * ctx->dx * ctx->dx / (M_PI * M_PI * ctx->hbar * ctx->hbar * ctx->hbar);
-    const long long n = 2LL * ctx->np * ctx->Ny;
-    SEM_TRY(launch_sem_scale(n, alpha, ctx->eier, ctx->ee, ctx->stream));
-    SliceArgs sa{ctx->np, 2 * ctx->Ny, ctx->Kp4, 0, ctx->ee, 2 * ctx->Ny, 1, 0, 0, ctx->eeP,
-                 (long long)ctx->np * ctx->Kp4, 0, ctx->eeE, 0, 1, 1, nullptr, nx, ctx->h, 0};
+    const long long n = 2LL * ctx->np * ctx->Nyh;
+    SEM_TRY(launch_sem_scale(n, alpha, ctx->eh + (long long)ctx->np * 2 * ctx->Nyh, ctx->eha, ctx->stream));
+    SliceArgs sa{ctx->np, 2 * ctx->Nyh, ctx->Kp3, 0, ctx->eha, 2 * ctx->Nyh, 1, 0, 0, ctx->ehaP,
+                 (long long)ctx->np * ctx->Kp3, 0, ctx->ehaE, 0, 1, 1, nullptr, nx, ctx->h, 0};
     SEM_TRY(launch_slice(0, 0, sa, ctx->stream));
     // D_V weights of the two-body chain, w (W(rho + u) - W(rho - u)) for w = 1 and 2
     const int nr = 2 * nx - 1, nu = 4 * ctx->h + 1;
@@ -374,10 +386,12 @@ static w2_status sem_theta(w2_sem_ctx *ctx, const double *in, double *out) {
 
 // The same operator from exact slices on the BF16 tensor cores (w2_gemms.cu).
 // Layouts chosen so that every sliced line runs along the contraction index:
-// T^T = Phi F^T ([Ny][2np]: [Tr | Ti]), A^T = T^T Ph^T ([Ny][2Nyh]), the D_V
-// weighting folded into the slicing of A^T, S = Eh B ([np][2Ny]: [Sr | Si]),
-// out += S (alpha [Ei | Er])^T; the one-body products use F's row slices
-// (F G2^T, and T^T) and its column slices (G1 F).
+// T^T = Phi F^T ([Nyh][2np]: [Tr | Ti] for y2 >= 0), A^T = T^T Ph^T and
+// T^T Ph'^T ([Ny][2Nyh]), B = w D (.) A sliced along [re | im] x y2,
+// S'^T = [[Er | -Ei] B | [Ei | Er] B] ([np][2Nyh]), out += alpha [Ei_h | Er_h] S'
+// -- the sums over y2 before those over y1, which halves the last product;
+// the one-body products use F's row slices (F G2^T, and T^T) and its column
+// slices (G1 F).
 static w2_status sem_theta_sliced(w2_sem_ctx *ctx, const double *in, double *out) {
   const int nx = ctx->nx, np = ctx->np, Ny = ctx->Ny, Nyh = ctx->Nyh;
   const int Kp1 = ctx->Kp1, Kp2 = ctx->Kp2, Kp3 = ctx->Kp3, Kp4 = ctx->Kp4, ldp = ctx->ldp;
@@ -410,7 +424,7 @@ static w2_status sem_theta_sliced(w2_sem_ctx *ctx, const double *in, double *out
                  nullptr, nx, ctx->h, 0};
     SEM_TRY(launch_slice(0, 0, sa, s));
   }
-  const long long frS = 6LL * np * Kp1, fcS = 6LL * Kp1 * ldp, tS = 6LL * Ny * Kp2, bS = 6LL * Ny * Kp3,
+  const long long frS = 6LL * np * Kp1, fcS = 6LL * Kp1 * ldp, tS = 6LL * Ny * Kp2,
                   sS = 6LL * np * Kp4;
   for (long long x0 = 0; x0 < nX; x0 += ctx->bx) {
     const int nb = (int)((nX - x0) < ctx->bx ? (nX - x0) : ctx->bx);
@@ -459,24 +473,24 @@ static w2_status sem_theta_sliced(w2_sem_ctx *ctx, const double *in, double *out
                    ctx->cA + (long long)(ctx->h - 1) * 2 * Nyh, -2LL * Nyh, (long long)Ny * 2 * Nyh, 0, 0, nb, 1};
       SEM_TRY(gemm_k(an, 2 * np, 0));
     }
-    // slices of B^T_X = w D (.) A^T_X
-    SliceArgs bs{Ny, 2 * Nyh, Kp3, 0, ctx->cA, 2 * Nyh, 1, (long long)Ny * 2 * Nyh, 0, ctx->bP, (long long)Ny * Kp3,
-                 bS, ctx->bE, Ny, nb, 1, ctx->dtab, nx, ctx->h, (int)x0};
-    SEM_TRY(launch_slice(0, 1, bs, s));
-    // [Sr | Si]_X = [Er_h | -Ei_h] B, [Ei_h | Er_h] B
+    // B(k, y1) = w D (.) A over k = [re | im] x y2, sliced along k (columns y1)
+    SliceArgs bs{Nyh, 2 * Ny, Kp4, ctx->ldq, ctx->cA, 2 * Nyh, 1, (long long)Ny * 2 * Nyh, 0, ctx->bP,
+                 (long long)Kp4 * ctx->ldq, ctx->bsz, ctx->bE, Nyh, nb, 1, ctx->dtab, nx, ctx->h, (int)x0};
+    SEM_TRY(launch_slice_dstack(bs, s));
+    // S'^T_X = [[Er | -Ei] B | [Ei | Er] B]  ([np][2 Nyh]: S'r^T, S'i^T)
     for (int blk = 0; blk < 2; ++blk) {
-      GemmSArgs sg{np, Ny, 2 * Nyh, 0, ctx->ehP + blk * 6LL * np * Kp3, Kp3, (long long)np * Kp3, 0, 0,
-                   ctx->ehE + blk * np, 0, 0, ctx->bP, Kp3, (long long)Ny * Kp3, bS, 0, ctx->bE, Ny, 0,
-                   ctx->cS + blk * Ny, 2 * Ny, (long long)np * 2 * Ny, 0, 0, nb, 1};
-      SEM_TRY(gemm_k(sg, 2 * Nyh, 0));
+      GemmSArgs sg{np, Nyh, 2 * Ny, 0, blk ? ctx->eiP : ctx->ermP, Kp4, (long long)np * Kp4, 0, 0,
+                   blk ? ctx->eiE : ctx->ermE, 0, 0, ctx->bP, ctx->ldq, (long long)Kp4 * ctx->ldq, ctx->bsz, 0,
+                   ctx->bE, Nyh, 0, ctx->cS + blk * Nyh, 2 * Nyh, (long long)np * 2 * Nyh, 0, 0, nb, 1};
+      SEM_TRY(gemm_k(sg, 2 * Ny, 1));
     }
-    SliceArgs ss{np, 2 * Ny, Kp4, 0, ctx->cS, 2 * Ny, 1, (long long)np * 2 * Ny, 0, ctx->sP, (long long)np * Kp4, sS,
-                 ctx->sE, np, nb, 1, nullptr, nx, ctx->h, 0};
+    SliceArgs ss{np, 2 * Nyh, Kp3, 0, ctx->cS, 2 * Nyh, 1, (long long)np * 2 * Nyh, 0, ctx->sP, (long long)np * Kp3,
+                 sS, ctx->sE, np, nb, 1, nullptr, nx, ctx->h, 0};
     SEM_TRY(launch_slice(0, 0, ss, s));
-    // out_X += S_X (alpha [Ei | Er])^T
-    GemmSArgs fo{np, np, 2 * Ny, 0, ctx->sP, Kp4, (long long)np * Kp4, sS, 0, ctx->sE, np, 0, ctx->eeP, Kp4,
-                 (long long)np * Kp4, 0, 0, ctx->eeE, 0, 0, out + x0 * np2, np, np2, 0, 1, nb, 1};
-    SEM_TRY(gemm_k(fo, 2 * Ny, 0));
+    // out_X += alpha [Ei_h | Er_h] S'_X
+    GemmSArgs fo{np, np, 2 * Nyh, 0, ctx->ehaP, Kp3, (long long)np * Kp3, 0, 0, ctx->ehaE, 0, 0, ctx->sP, Kp3,
+                 (long long)np * Kp3, sS, 0, ctx->sE, np, 0, out + x0 * np2, np, np2, 0, 1, nb, 1};
+    SEM_TRY(gemm_k(fo, 2 * Nyh, 0));
   }
   return W2_OK;
 }

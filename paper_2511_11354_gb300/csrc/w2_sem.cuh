@@ -111,6 +111,9 @@ cudaError_t launch_sem_obs(const SemObsArgs &a, cudaStream_t s);
 cudaError_t launch_sem_rdm(int nx, int np, double dx, const double *f, const double *w, const double *cp, double *f1,
                            double *eta, double *g, const double *phr, const double *phi, double2 *rho, cudaStream_t s);
 
+// erm[i] = [Er | -Ei](i) from eier[i] = [Ei | Er](i) (np rows of 2 Ny).
+cudaError_t launch_sem_erm(int np, int Ny, const double *eier, double *erm, cudaStream_t s);
+
 // out[r][c] = in[r][c] for c < c0, -in[r][c] for c >= c0 (rows x cols, row-major).
 cudaError_t launch_sem_negcols(int rows, int cols, int c0, const double *in, double *out, cudaStream_t s);
 
@@ -141,6 +144,9 @@ struct SliceArgs {
   int nx, h, x0;
 };
 cudaError_t launch_slice(int cols, int mode, const SliceArgs &a, cudaStream_t s);
+// Column slices of w D (.) A for S'^T = E B (see k_slice_dstack): L = Nyh lines,
+// K = 2 Ny, in = A^T per X (row stride ls, batch stride sIn1), dtab, nx, h, x0.
+cudaError_t launch_slice_dstack(const SliceArgs &a, cudaStream_t s);
 int slice_kp(int K);
 
 // C_b (=|+=) A_b B_b from slices: A planes [6][M][lda] (pA plane stride,

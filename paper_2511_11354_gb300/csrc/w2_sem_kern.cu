@@ -443,6 +443,15 @@ __global__ void __launch_bounds__(256) k_sem_adv_df(SemAdvArgs a) {
   }
 }
 
+__global__ void k_sem_erm(int np, int Ny, const double *eier, double *erm) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)np * 2 * Ny;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / (2 * Ny);
+    const int c = (int)(e % (2 * Ny));
+    erm[e] = c < Ny ? eier[i * 2 * Ny + Ny + c] : -eier[i * 2 * Ny + c - Ny];
+  }
+}
+
 __global__ void k_sem_negcols(int rows, int cols, int c0, const double *in, double *out) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)rows * cols;
        e += (long long)gridDim.x * blockDim.x)
@@ -703,6 +712,11 @@ cudaError_t launch_sem_rdm(int nx, int np, double dx, const double *f, const dou
   k_sem_f1<<<nx * np, 128, 0, s>>>(nx, np, dx, f, w, f1);
   k_sem_halfgrid<<<(np + 63) / 64, 64, 0, s>>>(nx, np, f1, cp, eta, g);
   k_sem_rho<<<(nx * nx + 127) / 128, 128, 0, s>>>(nx, np, dx, g, phr, phi, rho);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sem_erm(int np, int Ny, const double *eier, double *erm, cudaStream_t s) {
+  k_sem_erm<<<grid_for((long long)np * 2 * Ny, 256), 256, 0, s>>>(np, Ny, eier, erm);
   return cudaGetLastError();
 }
 

@@ -117,7 +117,7 @@ def test_advect_parity(case, prec):
 
 
 @pytest.mark.parametrize("prec", ["W2_F64", "W2_F64_SLICED"])
-@pytest.mark.parametrize("case", [CASES[0], CASES[1]])
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], (41, 4, 8, 30.0, "IV")])
 def test_steps_parity(case, prec):
     prob, f = _case(*case)
     ctx = _ctx(prob, prec)

@@ -355,6 +355,22 @@ __global__ void __launch_bounds__(GT, 3) k_gemms(GemmSArgs g) {
   double *C = g.C + b1 * g.sC1 + b2 * g.sC2;
   const int *Ae = g.Ae + b1 * g.sAe1 + b2 * g.sAe2;
   const int *Be = g.Be + b1 * g.sBe1 + b2 * g.sBe2;
+  // Outputs of this thread: rows m0 + wm 32 + mt 16 + ln/4 (+ 8), columns
+  // n0 + wn 16 + nt 8 + 2 (ln & 3) (+ 1).  With beta the old values are all
+  // requested before any is used, so their latencies overlap.
+  double old[2][4][2];
+  if (g.beta) {
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          const int row = m0 + wm * 32 + mt * 16 + (ln >> 2) + (e >= 2 ? 8 : 0);
+          const int col = n0 + wn * 16 + nt * 8 + 2 * (ln & 3) + (e & 1);
+          old[mt][e][nt] = (row < g.M && col < g.N) ? C[(long long)row * g.ldc + col] : 0.0;
+        }
+  }
 #pragma unroll
   for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
@@ -374,8 +390,7 @@ __global__ void __launch_bounds__(GT, 3) k_gemms(GemmSArgs g) {
                             __float2ll_rn(acc[4][mt][nt][e]) * (1ll << 8) + __float2ll_rn(acc[5][mt][nt][e]);
         double v = (ea == kBadExp || eb == kBadExp) ? __longlong_as_double(0x7ff8000000000000ll)
                                                     : w2::ll_to_double_scaled(I, ea + eb - 54);
-        double *c = C + (long long)row * g.ldc + col;
-        *c = g.beta ? *c + v : v;
+        C[(long long)row * g.ldc + col] = g.beta ? old[mt][e][nt] + v : v;
       }
     }
 }

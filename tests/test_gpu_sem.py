@@ -217,3 +217,18 @@ def test_occupations_of_a_two_packet_mixture():
     assert abs(occ[0] - 0.5 * (1 + e)) < 1e-5 and abs(occ[1] - 0.5 * (1 - e)) < 1e-5, occ[:3]
     exact = sum(v * math.log(v) for v in (0.5 * (1 + e), 0.5 * (1 - e)))
     assert abs(s - exact) < 5e-3
+
+
+@pytest.mark.parametrize("prec", ["W2_F64", "W2_F64_SLICED"])
+def test_theta_parity_widest_momentum_axis(prec):
+    """The largest momentum axis (8 cells x 32 points = 256: contractions over
+    2 np = 512 split in two on the sliced path) on the smallest box (8 points,
+    y grid of 7)."""
+    prob, f = _case(8, 8, 32, 10.0, "IV")
+    ctx = _ctx(prob, prec)
+    d = torch.from_numpy(f).cuda()
+    out = torch.empty_like(d)
+    ctx.theta(d, out)
+    err = rel(out.cpu().numpy(), SemOracle(prob).theta(f))
+    print(f"theta widest {prec}: {err:.3e}")
+    assert err < THETA_BAR[prec]

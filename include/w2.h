@@ -367,17 +367,22 @@ w2_status w2_learned_report(w2_ctx *ctx, int32_t *active, int32_t *judged, doubl
  * torus, mu = b + nu (for odd b + c a half point, where f1 comes from its
  * periodic trigonometric interpolant), rho1 made Hermitian as
  * (rho1 + rho1^H)/2.  occ[k] (host, nx values, largest first) are the
- * eigenvalues of rho1 dx (a cyclic Jacobi eigensolver on the device, FP64);
+ * eigenvalues of rho1 dx (the device eigensolver of w2_hermitian_eigvals, FP64);
  * *entropy (host) = sum_k n_k ln n_k / sum_k n_k over n_k > 1e-14 n_0.
  * Either pointer may be NULL.  Synchronises the stream.
  * Errors: W2_ERR_ARG, W2_ERR_STATE (no state), W2_ERR_OOM, W2_ERR_CUDA. */
 w2_status w2_occupations(w2_ctx *ctx, double *occ, double *entropy);
 
 /* Eigenvalues of batch complex Hermitian n x n matrices (device, row-major,
- * interleaved re/im doubles, 16-byte aligned; overwritten), one CTA per
- * matrix, cyclic Jacobi with the round-robin ordering (at most 40 sweeps;
- * stops when the off-diagonal part is below 1e-14 of the matrix).  eig:
- * device [batch][n], largest first.  Queued on cuda_stream.
+ * interleaved re/im doubles, 16-byte aligned; overwritten).  Up to n = 320
+ * (the matrix spread over the shared memory of a cluster of 8 CTAs):
+ * Householder reduction to tridiagonal form, then bisection on Sturm counts
+ * (one warp per eigenvalue, 32 points a round, down to a few ulps; absolute
+ * error a small multiple of n eps |A|).  Larger n (or a device without room
+ * for the cluster): one CTA per matrix, cyclic Jacobi with the round-robin
+ * ordering (at most 40 sweeps; stops when the off-diagonal part is below
+ * 1e-14 of the matrix).  eig: device [batch][n], largest first.  Queued on
+ * cuda_stream.
  * Errors: W2_ERR_ARG (NULL, misaligned, n outside [1, 4096]), W2_ERR_CUDA. */
 w2_status w2_hermitian_eigvals(void *a, int32_t n, int32_t batch, double *eig, void *cuda_stream);
 

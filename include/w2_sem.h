@@ -134,7 +134,7 @@ w2_status w2_sem_observables(w2_sem_ctx *ctx, w2_obs *out, double *n1);
  * taken exactly over the cell expansions (the transform of the two-body term
  * at half the offset), f1 at half points from the natural cubic spline;
  * occ[nx] (host, may be NULL) receives the eigenvalues of rho1 dx, largest
- * first, by the cyclic Jacobi method of w2_hermitian_eigvals, and *entropy
+ * first, by the eigensolver of w2_hermitian_eigvals, and *entropy
  * (may be NULL) s = sum n ln n / sum n over the occupations above 1e-14 of
  * the largest.  The first call allocates its work arrays (about
  * 16 nx^2 + 40 nx np bytes).  Synchronises. */

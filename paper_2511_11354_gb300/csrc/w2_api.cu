@@ -957,7 +957,7 @@ extern "C" w2_status w2_occupations(w2_ctx *ctx, double *occ, double *entropy) {
   cudaStream_t s = ctx->stream;
   W2_TRY(launch_rdm_f1(ctx->f, f64_state(ctx->prec), ctx->rdm_f1, nx, nk, ctx->dx, ctx->dp, s));
   W2_TRY(launch_rdm_rho(ctx->rdm_f1, ctx->rdm_kh, ctx->rdm_fh, ctx->rdm_ph, ctx->rdm_rho, nx, nk, ctx->dx, s));
-  W2_TRY(launch_jacobi_herm(ctx->rdm_rho, nx, 1, ctx->rdm_eig, s));
+  W2_TRY(launch_herm_eigvals(ctx->rdm_rho, nx, 1, ctx->rdm_eig, s));
   W2_TRY(launch_corr_entropy(ctx->rdm_eig, nx, ctx->rdm_eig + nx, s));
   if (occ) W2_TRY(cudaMemcpyAsync(occ, ctx->rdm_eig, sizeof(double) * nx, cudaMemcpyDeviceToHost, s));
   if (entropy) W2_TRY(cudaMemcpyAsync(entropy, ctx->rdm_eig + nx, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -968,7 +968,7 @@ extern "C" w2_status w2_occupations(w2_ctx *ctx, double *occ, double *entropy) {
 extern "C" w2_status w2_hermitian_eigvals(void *a, int32_t n, int32_t batch, double *eig, void *cuda_stream) {
   if (!a || !eig || n < 1 || n > 4096 || batch < 1) return W2_ERR_ARG;
   if ((uintptr_t)a & 15) return W2_ERR_ARG;
-  cudaError_t e = launch_jacobi_herm((double2 *)a, n, batch, eig, (cudaStream_t)cuda_stream);
+  cudaError_t e = launch_herm_eigvals((double2 *)a, n, batch, eig, (cudaStream_t)cuda_stream);
   if (e != cudaSuccess) {
     note_cuda_error(e);
     return W2_ERR_CUDA;

@@ -149,6 +149,12 @@ cudaError_t launch_rdm_rho(const double *f1, const double *kh, double *fh, const
                            int nk, double dx, cudaStream_t s);
 cudaError_t launch_jacobi_herm(double2 *mats, int n, int batch, double *eig, cudaStream_t s);
 cudaError_t launch_corr_entropy(const double *eig, int n, double *entropy, cudaStream_t s);
+// Eigenvalues of Hermitian matrices (w2_heig.cu): Householder tridiagonal
+// reduction in a cluster of 8 CTAs (matrix in shared memory) and bisection,
+// for n up to herm_eig_tridiag_max_n(); the Jacobi solver above beyond.  The
+// matrices are overwritten; eig [batch][n], largest first.
+cudaError_t launch_herm_eigvals(double2 *mats, int n, int batch, double *eig, cudaStream_t s);
+int herm_eig_tridiag_max_n();
 
 // Record the CUDA error behind a W2_ERR_CUDA return (read by w2_last_cuda_error).
 void note_cuda_error(cudaError_t e);

@@ -589,7 +589,7 @@ extern "C" w2_status w2_sem_occupations(w2_sem_ctx *ctx, double *occ, double *en
   }
   SEM_TRY(launch_sem_rdm(nx, np, ctx->dx, ctx->f, ctx->w, ctx->cp, ctx->rf1, ctx->reta, ctx->rg, ctx->rphr, ctx->rphi,
                          ctx->rrho, s));
-  SEM_TRY(w2::launch_jacobi_herm(ctx->rrho, nx, 1, ctx->reig, s));
+  SEM_TRY(w2::launch_herm_eigvals(ctx->rrho, nx, 1, ctx->reig, s));
   SEM_TRY(w2::launch_corr_entropy(ctx->reig, nx, ctx->reig + nx, s));
   if (occ) SEM_TRY(cudaMemcpyAsync(occ, ctx->reig, sizeof(double) * nx, cudaMemcpyDeviceToHost, s));
   if (entropy) SEM_TRY(cudaMemcpyAsync(entropy, ctx->reig + nx, sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -22,8 +22,11 @@ def _lib():
     build.build()
 
 
-@pytest.mark.parametrize("n,batch", [(1, 2), (5, 3), (16, 4), (64, 2), (97, 1)])
+@pytest.mark.parametrize("n,batch", [(1, 2), (2, 3), (5, 3), (16, 4), (64, 2), (97, 1), (201, 2), (320, 1),
+                                     (321, 1)])
 def test_batched_hermitian_eigvals(n, batch):
+    """Householder tridiagonal reduction + bisection up to n = 320 (the rows
+    in the shared memory of a cluster of 8 CTAs), cyclic Jacobi beyond."""
     from paper_2511_11354_gb300 import w2
     rng = np.random.default_rng(n)
     b = rng.standard_normal((batch, n, n)) + 1j * rng.standard_normal((batch, n, n))
@@ -33,6 +36,40 @@ def test_batched_hermitian_eigvals(n, batch):
     for k in range(batch):
         want = np.sort(np.linalg.eigvalsh(h[k]))[::-1]
         assert np.abs(eig[k] - want).max() < 1e-12 * max(1.0, np.abs(want).max())
+
+
+@pytest.mark.parametrize("kind", ["diagonal", "scaled_identity", "zero", "graded", "block"])
+def test_hermitian_eigvals_structured(kind):
+    """Matrices where reflections are skipped (a zero column below the
+    diagonal), every eigenvalue is the same, or the spectrum spans 30
+    decades like the occupations of a nearly pure state (absolute bar)."""
+    from paper_2511_11354_gb300 import w2
+    n = 57
+    rng = np.random.default_rng(7)
+    q, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    if kind == "diagonal":
+        want = rng.standard_normal(n)
+        h = np.diag(want).astype(np.complex128)
+    elif kind == "scaled_identity":
+        want = np.full(n, 3.0)
+        h = 3.0 * np.eye(n, dtype=np.complex128)
+    elif kind == "zero":
+        want = np.zeros(n)
+        h = np.zeros((n, n), dtype=np.complex128)
+    elif kind == "graded":
+        want = 10.0 ** -np.linspace(0, 30, n)
+        h = (q * want) @ q.conj().T
+    else:  # two decoupled Hermitian blocks
+        b = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        b[:20, 20:] = 0
+        b[20:, :20] = 0
+        h = b + b.conj().T
+        want = np.linalg.eigvalsh(h)
+    h = 0.5 * (h + h.conj().T)
+    eig = w2.hermitian_eigvals(torch.from_numpy(h[None].copy()).cuda()).cpu().numpy()[0]
+    want = np.sort(want)[::-1]
+    assert np.all(np.diff(eig) <= 1e-15 * max(1.0, np.abs(want).max()))
+    assert np.abs(eig - want).max() <= 1e-13 * max(1.0, np.abs(want).max())
 
 
 def _reference(prob, f):

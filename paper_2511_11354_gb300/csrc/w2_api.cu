@@ -156,7 +156,7 @@ extern "C" w2_status w2_create(const w2_config *cfg, void *cuda_stream, w2_ctx *
   W2_ALLOC(ctx->vext_fine, sizeof(double) * nx * M) W2_ALLOC(ctx->w_fine, sizeof(double) * nx * M)
   W2_ALLOC(ctx->d_fine, sizeof(double) * nx * M) W2_ALLOC(ctx->sintab, sizeof(double) * M)
   W2_ALLOC(ctx->vext_grid, sizeof(double) * nx) W2_ALLOC(ctx->k0tab, sizeof(int) * nk)
-  W2_ALLOC(ctx->wtab, sizeof(double) * 4 * nk) W2_ALLOC(ctx->xpart, sizeof(double) * nx * nx * (3 + nk))
+  W2_ALLOC(ctx->wtab, sizeof(double) * 4 * nk) W2_ALLOC(ctx->xpart, sizeof(double) * (nx * nx * (3 + nk) + 8 * nx))
   W2_ALLOC(ctx->obs_out, sizeof(double) * (8 + nx + nx * nx))
   W2_ALLOC(ctx->wtab32, sizeof(float) * 4 * nk) W2_ALLOC(ctx->ctab32, sizeof(float) * 8 * nk)
   W2_ALLOC(ctx->wdf, sizeof(float2) * 4 * nk) W2_ALLOC(ctx->zpow, sizeof(float2) * 32)

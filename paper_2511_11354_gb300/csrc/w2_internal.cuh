@@ -68,7 +68,7 @@ struct ObsArgs {
   const float *f32;         // FP32 state (exactly one is non-null)
   const double *vext_grid;  // [nx]
   const double *w_fine;     // [nx][M]; column 0 is W(fold(d dx))
-  double *xpart;            // [nx*nx][3 + nk] per-X partials
+  double *xpart;            // [nx*nx][3 + nk] per-X partials, then [nx][8] per-x1 partials
   double *out;              // [8 + nx + nx*nx]
   const double *h_fine = nullptr;  // as in TabArgs (column 0: the kernel at grid distances)
 };

@@ -134,91 +134,145 @@ cudaError_t launch_xsum_f32(int nx, int nk, const float *f, double *xsum, cudaSt
 }
 
 // Per-X partials: [0] sum f, [1] sum f (p1^2 + p2^2), [2] sum f^2, [3 + n1] sum_{n2} f.
+// One block per X, one thread per row n1 (lanes on neighbouring rows; each
+// thread walks its row in pairs).  p2^2 comes from a table and p1^2 multiplies
+// the row sum: three FP64 operations per element, no per-row reductions.
+__device__ __forceinline__ void load_pair(const double *p, double &a, double &b) {
+  const double2 v = *reinterpret_cast<const double2 *>(p);
+  a = v.x;
+  b = v.y;
+}
+__device__ __forceinline__ void load_pair(const float *p, double &a, double &b) {
+  const float2 v = *reinterpret_cast<const float2 *>(p);
+  a = v.x;
+  b = v.y;
+}
+
 template <typename T>
-__global__ void k_obs_x(ObsArgs a, const T *f) {
-  __shared__ double red[3][128];
-  const int nk = a.nk, X = blockIdx.x, tid = threadIdx.x;
-  const size_t base = (size_t)X * nk * nk;
+__global__ void __launch_bounds__(256) k_obs_x(ObsArgs a, const T *f) {
+  __shared__ double red[3][8];
+  extern __shared__ double psq[];  // [nk] (p_n)^2
+  const int nk = a.nk, X = blockIdx.x, nt = blockDim.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int c = threadIdx.x; c < nk; c += nt) {
+    const double p = (c - nk / 2) * a.dp;
+    psq[c] = p * p;
+  }
+  __syncthreads();
+  const T *fx = f + (size_t)X * nk * nk;
   double *xp = a.xpart + (size_t)X * (3 + nk);
   double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-  for (int r = 0; r < nk; ++r) {
-    // row sums: thread tid handles column block; reduce per row below
+  for (int r = threadIdx.x; r < nk; r += nt) {
+    const T *row = fx + (size_t)r * nk;  // nk is even: pairs stay aligned
     double rv = 0.0;
-    for (int c = tid; c < nk; c += blockDim.x) {
-      const double v = (double)f[base + (size_t)r * nk + c];
-      const double p1 = (r - nk / 2) * a.dp, p2 = (c - nk / 2) * a.dp;
-      rv += v;
-      s1 += v * (p1 * p1 + p2 * p2);
-      s2 += v * v;
+    for (int c = 0; c < nk; c += 2) {
+      double v0, v1;
+      load_pair(row + c, v0, v1);
+      rv += v0;
+      rv += v1;
+      s1 = fma(psq[c], v0, s1);
+      s1 = fma(psq[c + 1], v1, s1);
+      s2 = fma(v0, v0, s2);
+      s2 = fma(v1, v1, s2);
     }
+    xp[3 + r] = rv;
     s0 += rv;
-    red[0][tid] = rv;
-    __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-      if (tid < h) red[0][tid] += red[0][tid + h];
-      __syncthreads();
-    }
-    if (tid == 0) xp[3 + r] = red[0][0];
-    __syncthreads();
+    s1 = fma(psq[r], rv, s1);
   }
-  red[0][tid] = s0;
-  red[1][tid] = s1;
-  red[2][tid] = s2;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  if (lane == 0) {
+    red[0][w] = s0;
+    red[1][w] = s1;
+    red[2][w] = s2;
+  }
   __syncthreads();
-  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-    if (tid < h) {
-      red[0][tid] += red[0][tid + h];
-      red[1][tid] += red[1][tid + h];
-      red[2][tid] += red[2][tid + h];
-    }
-    __syncthreads();
-  }
-  if (tid == 0) {
-    xp[0] = red[0][0];
-    xp[1] = red[1][0];
-    xp[2] = red[2][0];
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int q = 0; q < nt / 32; ++q) t += red[threadIdx.x][q];
+    xp[threadIdx.x] = t;
   }
 }
 
-// Single block: fixed-order final reductions.
+// One block per i (256 threads), over the partials of X = (i, i2):
+// mid[i][0..7] = sum f, sum f p^2, sum f (V(x_i) + V(x_i2) + gamma W), sum f^2,
+// a non-finite flag, n1 and n2 sums at x_i (raw), sum_n f1(x_i, p_n)^2; and
+// out[8 + nx + X] = n12.
+__global__ void __launch_bounds__(256) k_obs_mid(ObsArgs a, double *mid) {
+  __shared__ double red[8][8];
+  const int nx = a.nx, nk = a.nk, M = a.M, i = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const size_t ld = 3 + (size_t)nk;
+  double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int i2 = tid; i2 < nx; i2 += 256) {
+    const double *xp = a.xpart + ((size_t)i * nx + i2) * ld;
+    int d = i - i2;
+    d += (d < 0) ? nx : 0;
+    const double vx = a.vext_grid[i] + a.vext_grid[i2] + a.gamma * a.w_fine[(size_t)d * M];
+    v[0] += xp[0];
+    v[1] += xp[1];
+    v[2] += xp[0] * vx;
+    v[3] += xp[2];
+    if (!isfinite(xp[0]) || !isfinite(xp[1]) || !isfinite(xp[2])) v[4] = 1.0;
+    v[5] += xp[0];
+    a.out[8 + nx + (size_t)i * nx + i2] = xp[0] * a.dp * a.dp;
+  }
+  for (int i1 = tid; i1 < nx; i1 += 256) v[6] += a.xpart[((size_t)i1 * nx + i) * ld];
+  for (int r = tid; r < nk; r += 256) {
+    double sr = 0.0;
+#pragma unroll 8
+    for (int i2 = 0; i2 < nx; ++i2) sr += a.xpart[((size_t)i * nx + i2) * ld + 3 + r];
+    const double f1 = sr * a.dx * a.dp;
+    v[7] += f1 * f1;
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const double t = __shfl_xor_sync(0xffffffffu, v[q], o);
+      v[q] = q == 4 ? fmax(v[q], t) : v[q] + t;
+    }
+    if (lane == 0) red[q][w] = v[q];
+  }
+  __syncthreads();
+  if (tid < 8) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t = tid == 4 ? fmax(t, red[tid][q]) : t + red[tid][q];
+    mid[(size_t)i * 8 + tid] = t;
+  }
+}
+
+// Single block: the Hartree energy and fixed-order sums of the per-i partials.
 // out: [0] mass [1] energy [2] purity [3] l2norm [4] nonfinite flag
-//      [8 .. 8+nx) n_1 ; [8+nx .. 8+nx+nx*nx) n_12
-__global__ void k_obs_final(ObsArgs a) {
+//      [8 .. 8+nx) n_1 ; [8+nx .. 8+nx+nx*nx) n_12 (written by k_obs_mid)
+__global__ void k_obs_final(ObsArgs a, const double *mid) {
   __shared__ double red[6][256];
   extern __shared__ double dyn[];  // n1[nx], n2[nx]
-  const int nx = a.nx, nk = a.nk, M = a.M, tid = threadIdx.x, nt = blockDim.x;
+  const int nx = a.nx, M = a.M, tid = threadIdx.x, nt = blockDim.x;
   const double dV = a.dx * a.dx * a.dp * a.dp;
   double *n1 = dyn, *n2 = dyn + nx;
-  double m0 = 0, ek = 0, ep = 0, l2 = 0, bad = 0;
-  for (int X = tid; X < nx * nx; X += nt) {
-    const double *xp = a.xpart + (size_t)X * (3 + nk);
-    const int i1 = X / nx, i2 = X % nx;
-    int d = i1 - i2;
-    d += (d < 0) ? nx : 0;
-    const double vx = a.vext_grid[i1] + a.vext_grid[i2] + a.gamma * a.w_fine[(size_t)d * M];
-    m0 += xp[0];
-    ek += xp[1];
-    l2 += xp[2];
-    ep += xp[0] * vx;
-    if (!isfinite(xp[0]) || !isfinite(xp[1]) || !isfinite(xp[2])) bad = 1.0;
-    a.out[8 + nx + X] = xp[0] * a.dp * a.dp;
-  }
+  double m0 = 0, ek = 0, ep = 0, l2 = 0, bad = 0, pur = 0;
   for (int i = tid; i < nx; i += nt) {
-    double s1 = 0.0, s2 = 0.0;
-    for (int k = 0; k < nx; ++k) {
-      s1 += a.xpart[((size_t)i * nx + k) * (3 + nk)];
-      s2 += a.xpart[((size_t)k * nx + i) * (3 + nk)];
-    }
-    n1[i] = s1 * a.dx * a.dp * a.dp;
-    n2[i] = s2 * a.dx * a.dp * a.dp;
+    const double *m = mid + (size_t)i * 8;
+    m0 += m[0];
+    ek += m[1];
+    ep += m[2];
+    l2 += m[3];
+    bad = fmax(bad, m[4]);
+    pur += m[7];
+    n1[i] = m[5] * a.dx * a.dp * a.dp;
+    n2[i] = m[6] * a.dx * a.dp * a.dp;
     a.out[8 + i] = n1[i];
   }
   __syncthreads();
-  // Hartree energy and purity
-  double eh = 0.0, pur = 0.0;
+  // Hartree energy
+  double eh = 0.0;
   if (a.c_h != 0.0) {
     for (int i = tid; i < nx; i += nt) {
       double va = 0.0, vb = 0.0;
+#pragma unroll 8
       for (int q = 0; q < nx; ++q) {
         int d = i - q;
         d += (d < 0) ? nx : 0;
@@ -228,19 +282,12 @@ __global__ void k_obs_final(ObsArgs a) {
       eh += 0.5 * a.c_h * (a.h_fine ? 1.0 : a.gamma * a.dx) * (va * n1[i] + vb * n2[i]) * a.dx;
     }
   }
-  for (int e = tid; e < nx * nk; e += nt) {
-    const int i1 = e / nk, r = e % nk;
-    double s = 0.0;
-    for (int i2 = 0; i2 < nx; ++i2) s += a.xpart[((size_t)i1 * nx + i2) * (3 + nk) + 3 + r];
-    const double f1 = s * a.dx * a.dp;
-    pur += f1 * f1;
-  }
   red[0][tid] = m0;
   red[1][tid] = ek;
   red[2][tid] = ep;
   red[3][tid] = l2;
   red[4][tid] = eh;
-  red[5][tid] = pur + bad * 0.0;
+  red[5][tid] = pur;
   __shared__ int sbad;
   if (tid == 0) sbad = 0;
   __syncthreads();
@@ -264,13 +311,17 @@ __global__ void k_obs_final(ObsArgs a) {
 }
 
 cudaError_t launch_obs(const ObsArgs &a, cudaStream_t s) {
+  const int nt = a.nk >= 256 ? 256 : 32 * ((a.nk + 31) / 32);  // a thread per row
   if (a.f32)
-    k_obs_x<float><<<a.nx * a.nx, 128, 0, s>>>(a, a.f32);
+    k_obs_x<float><<<a.nx * a.nx, nt, sizeof(double) * a.nk, s>>>(a, a.f32);
   else
-    k_obs_x<double><<<a.nx * a.nx, 128, 0, s>>>(a, a.f);
+    k_obs_x<double><<<a.nx * a.nx, nt, sizeof(double) * a.nk, s>>>(a, a.f);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_obs_final<<<1, 256, sizeof(double) * 2 * a.nx, s>>>(a);
+  double *mid = a.xpart + (size_t)a.nx * a.nx * (3 + a.nk);
+  k_obs_mid<<<a.nx, 256, 0, s>>>(a, mid);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_obs_final<<<1, 256, sizeof(double) * 2 * a.nx, s>>>(a, mid);
   return cudaGetLastError();
 }
 

@@ -172,7 +172,7 @@ extern "C" w2_status w2_sem_create(const w2_sem_config *cfg, void *cuda_stream, 
   SEM_ALLOC(ctx->wgrid, 4 * nx - 3) SEM_ALLOC(ctx->xs, (long long)nx * nx) SEM_ALLOC(ctx->n, 2 * nx)
   SEM_ALLOC(ctx->U, 2 * nx) SEM_ALLOC(ctx->ut, 2LL * nx * (2 * nx - 1)) SEM_ALLOC(ctx->G, 2LL * nx * np * np)
   SEM_ALLOC(ctx->cT, bx * 2 * np * Ny) SEM_ALLOC(ctx->cA, bx * 2 * Nyh * Ny) SEM_ALLOC(ctx->cS, bx * 2 * np * Ny)
-  SEM_ALLOC(ctx->xpart, (long long)nx * nx * (4 + np)) SEM_ALLOC(ctx->obs, 8 + nx)
+  SEM_ALLOC(ctx->xpart, (long long)nx * nx * (4 + np) + 5 * nx) SEM_ALLOC(ctx->obs, 8 + nx)
   if (sliced) {
     SEM_ALLOC(ctx->psiP, 6LL * ctx->Kp5 * ctx->ldpsi) SEM_ALLOC(ctx->psiE, (long long)np * np)
     SEM_ALLOC(ctx->utP, 6LL * 2 * nx * ctx->Kp5) SEM_ALLOC(ctx->utE, 2 * nx)
@@ -546,9 +546,8 @@ extern "C" w2_status w2_sem_observables(w2_sem_ctx *ctx, w2_obs *out, double *n1
   if (ctx->sticky) return ctx->sticky;
   if (!ctx->have_pot || !ctx->have_state) return W2_ERR_STATE;
   const int nx = ctx->nx;
-  SEM_TRY(launch_sem_marginal(nx, ctx->np, ctx->dx, ctx->f, ctx->w, ctx->xs, ctx->n, ctx->stream));
   SemObsArgs oa{nx, ctx->np, ctx->dx, ctx->hbar, ctx->mass, ctx->gamma, ctx->c_h, ctx->f, ctx->p, ctx->w,
-                ctx->vext, ctx->wgrid, ctx->n, ctx->xpart, ctx->obs};
+                ctx->vext, ctx->wgrid, ctx->xpart, ctx->obs};
   SEM_TRY(launch_sem_obs(oa, ctx->stream));
   SEM_TRY(cudaMemcpyAsync(ctx->h_obs, ctx->obs, sizeof(double) * (8 + nx), cudaMemcpyDeviceToHost, ctx->stream));
   SEM_TRY(cudaStreamSynchronize(ctx->stream));

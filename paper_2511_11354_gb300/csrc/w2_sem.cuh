@@ -92,12 +92,13 @@ int sem_adv_cols(int nx, int np);
 cudaError_t launch_sem_axpy(long long n, const double *x, double a, const double *y, const double *y2, double *out,
                             cudaStream_t s);
 
-// Observables: per-X partials then one fixed-order reduction.
+// Observables: per-X partials, per-x1 partials (with the densities), then one
+// fixed-order reduction.
 struct SemObsArgs {
   int nx, np;
   double dx, hbar, mass, gamma, c_h;
-  const double *f, *p, *w, *vext, *wgrid, *n;
-  double *xpart;        // [nx*nx][4 + np]
+  const double *f, *p, *w, *vext, *wgrid;
+  double *xpart;        // [nx*nx][4 + np] per-X partials, then [nx][5] per-x1 partials
   double *out;          // [8 + nx]
 };
 cudaError_t launch_sem_obs(const SemObsArgs &a, cudaStream_t s);

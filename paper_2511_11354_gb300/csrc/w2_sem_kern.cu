@@ -471,83 +471,144 @@ __global__ void k_sem_axpy(long long n, const double *__restrict__ x, double a, 
   }
 }
 
-// Per-X partials: {sum ww f, sum ww f (p1^2 + p2^2)/2m, sum ww f^2, 0} and the
-// row sums r[j1] = sum_j2 w_j2 f (one warp per row, fixed order).
+// Per-X partials xp = [sum_j1 w r0, sum_j1 w (p^2 r0 + r2) / (2m), sum_j1 w r3, 0,
+// r0(j1) for j1 < np] with r0(j1) = sum_j2 w f, r2 = sum_j2 w p^2 f,
+// r3 = sum_j2 w f^2.  One block per X, one thread per row j1 (w and w p^2
+// from shared tables: four FP64 operations per element, no per-row
+// reductions).
 __global__ void __launch_bounds__(256) k_sem_obs_x(SemObsArgs a) {
-  extern __shared__ double rows[];  // [np][3]
+  __shared__ double red[3][8];
+  extern __shared__ double sm[];  // w [np], w p^2 [np]
   const long long X = blockIdx.x;
-  const int np = a.np, wid = threadIdx.x >> 5, ln = threadIdx.x & 31;
-  const double *fx = a.f + X * np * np;
-  for (int j1 = wid; j1 < np; j1 += 8) {
-    double r0 = 0.0, r2 = 0.0, r3 = 0.0;
-    for (int j2 = ln; j2 < np; j2 += 32) {
-      const double v = fx[j1 * np + j2], w = a.w[j2];
-      r0 = fma(w, v, r0);
-      r2 = fma(w * a.p[j2] * a.p[j2], v, r2);
-      r3 = fma(w * v, v, r3);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      r0 += __shfl_xor_sync(0xffffffffu, r0, o);
-      r2 += __shfl_xor_sync(0xffffffffu, r2, o);
-      r3 += __shfl_xor_sync(0xffffffffu, r3, o);
-    }
-    if (ln == 0) { rows[j1 * 3] = r0; rows[j1 * 3 + 1] = r2; rows[j1 * 3 + 2] = r3; }
+  const int np = a.np, nt = blockDim.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double *ws = sm, *wp2 = sm + np;
+  for (int j = threadIdx.x; j < np; j += nt) {
+    ws[j] = a.w[j];
+    wp2[j] = a.w[j] * a.p[j] * a.p[j];
   }
   __syncthreads();
+  const double *fx = a.f + X * np * np;
   double *xp = a.xpart + X * (4 + np);
-  for (int j1 = threadIdx.x; j1 < np; j1 += 256) xp[4 + j1] = rows[j1 * 3];
-  if (threadIdx.x == 0) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int j1 = 0; j1 < np; ++j1) {
-      const double w = a.w[j1];
-      s0 = fma(w, rows[j1 * 3], s0);
-      s1 = fma(w, a.p[j1] * a.p[j1] * rows[j1 * 3] + rows[j1 * 3 + 1], s1);
-      s2 = fma(w, rows[j1 * 3 + 2], s2);
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int j1 = threadIdx.x; j1 < np; j1 += nt) {
+    const double *row = fx + (long long)j1 * np;
+    double r0 = 0.0, r2 = 0.0, r3 = 0.0;
+    int j2 = 0;
+    if ((np & 1) == 0) {
+      for (; j2 < np; j2 += 2) {
+        const double2 v = *reinterpret_cast<const double2 *>(row + j2);
+        const double w0 = ws[j2] * v.x, w1 = ws[j2 + 1] * v.y;
+        r0 += w0;
+        r0 += w1;
+        r2 = fma(wp2[j2], v.x, r2);
+        r2 = fma(wp2[j2 + 1], v.y, r2);
+        r3 = fma(w0, v.x, r3);
+        r3 = fma(w1, v.y, r3);
+      }
     }
-    xp[0] = s0;
-    xp[1] = s1 / (2.0 * a.mass);
-    xp[2] = s2;
+    for (; j2 < np; ++j2) {
+      const double v = row[j2], wv = ws[j2] * v;
+      r0 += wv;
+      r2 = fma(wp2[j2], v, r2);
+      r3 = fma(wv, v, r3);
+    }
+    xp[4 + j1] = r0;
+    s0 = fma(ws[j1], r0, s0);
+    s1 = fma(wp2[j1], r0, fma(ws[j1], r2, s1));
+    s2 = fma(ws[j1], r3, s2);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  if (lane == 0) {
+    red[0][wid] = s0;
+    red[1][wid] = s1;
+    red[2][wid] = s2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+    for (int q = 0; q < nt / 32; ++q) {
+      t0 += red[0][q];
+      t1 += red[1][q];
+      t2 += red[2][q];
+    }
+    xp[0] = t0;
+    xp[1] = t1 / (2.0 * a.mass);
+    xp[2] = t2;
     xp[3] = 0.0;
   }
 }
 
-// One block: out = {mass, energy, purity, entropy_lin, l2norm, 0, 0, 0, n1[nx]}.
-__global__ void __launch_bounds__(1024) k_sem_obs_fin(SemObsArgs a) {
-  __shared__ double red[32];
-  const int nx = a.nx, np = a.np, W0 = 2 * (nx - 1);
-  const long long nX = (long long)nx * nx;
-  double m = 0.0, e = 0.0, l2 = 0.0;
-  for (long long X = threadIdx.x; X < nX; X += blockDim.x) {
-    const double *xp = a.xpart + X * (4 + np);
-    const int i1 = (int)(X / nx), i2 = (int)(X % nx);
+// One block per x1 = x_i (256 threads): mid[i] = {sum_i2 xp[0], sum_i2 (xp[1] +
+// xp[0] (V(x1) + V(x2) + gamma W(x1 - x2))), sum_i2 xp[2],
+// sum_j1 w_j1 f1(x_i, p_j1)^2 with f1 = dx sum_i2 r0, and sum_i1 xp[0] at
+// x2 = x_i}: the densities are dx times the first and the last.
+__global__ void __launch_bounds__(256) k_sem_obs_mid(SemObsArgs a, double *mid) {
+  __shared__ double red[8];
+  const int nx = a.nx, np = a.np, W0 = 2 * (nx - 1), i1 = blockIdx.x;
+  const double *xrow = a.xpart + (long long)i1 * nx * (4 + np);
+  double m = 0.0, e = 0.0, l2 = 0.0, pu = 0.0, nc = 0.0;
+  for (int i2 = threadIdx.x; i2 < nx; i2 += 256) {
+    const double *xp = xrow + (long long)i2 * (4 + np);
     m += xp[0];
     l2 += xp[2];
     e += xp[1] + xp[0] * (a.vext[i1] + a.vext[i2] + a.gamma * a.wgrid[i1 - i2 + W0]);
+    nc += a.xpart[((long long)i2 * nx + i1) * (4 + np)];
+  }
+  for (int j1 = threadIdx.x; j1 < np; j1 += 256) {
+    double f1 = 0.0;
+#pragma unroll 8
+    for (int i2 = 0; i2 < nx; ++i2) f1 += xrow[(long long)i2 * (4 + np) + 4 + j1];
+    f1 *= a.dx;
+    pu = fma(a.w[j1] * f1, f1, pu);
+  }
+  m = block_sum<256>(m, red);
+  e = block_sum<256>(e, red);
+  l2 = block_sum<256>(l2, red);
+  pu = block_sum<256>(pu, red);
+  nc = block_sum<256>(nc, red);
+  if (threadIdx.x == 0) {
+    mid[5 * i1] = m;
+    mid[5 * i1 + 1] = e;
+    mid[5 * i1 + 2] = l2;
+    mid[5 * i1 + 3] = pu;
+    mid[5 * i1 + 4] = nc;
+  }
+}
+
+// One block: out = {mass, energy, purity, entropy_lin, l2norm, 0, 0, 0, n1[nx]}.
+__global__ void __launch_bounds__(1024) k_sem_obs_fin(SemObsArgs a, const double *mid) {
+  __shared__ double red[32];
+  extern __shared__ double dens[];  // n1 [nx], n2 [nx]
+  const int nx = a.nx, W0 = 2 * (nx - 1);
+  double m = 0.0, e = 0.0, l2 = 0.0, pu = 0.0;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    m += mid[5 * i];
+    e += mid[5 * i + 1];
+    l2 += mid[5 * i + 2];
+    pu += mid[5 * i + 3];
+    dens[i] = a.dx * mid[5 * i];
+    dens[nx + i] = a.dx * mid[5 * i + 4];
   }
   m = block_sum<1024>(m, red);
   e = block_sum<1024>(e, red);
   l2 = block_sum<1024>(l2, red);
+  pu = block_sum<1024>(pu, red);  // its barriers also publish dens
   // Hartree energy (c_h / 2) dx sum_i n_k(x_i) V_H[n_k](x_i), both particles
   double eh = 0.0;
   for (int t = threadIdx.x; t < 2 * nx; t += blockDim.x) {
     const int k = t / nx, i = t % nx;
-    const double *n = a.n + k * nx;
+    const double *n = dens + k * nx;
     double vh = 0.0;
+#pragma unroll 8
     for (int q = 0; q < nx; ++q) vh = fma(a.wgrid[i - q + W0], n[q], vh);
     eh += n[i] * a.dx * (a.dx * vh);  // n(x_i) dx V_H[n](x_i)
   }
   eh = block_sum<1024>(eh, red);
-  // purity 2 pi hbar dx sum_{i1,j1} w_j1 f1^2, f1 = dx sum_i2 r_X[j1]
-  double pu = 0.0;
-  for (long long t = threadIdx.x; t < (long long)nx * np; t += blockDim.x) {
-    const int i1 = (int)(t / np), j1 = (int)(t % np);
-    double f1 = 0.0;
-    for (int i2 = 0; i2 < nx; ++i2) f1 += a.xpart[((long long)i1 * nx + i2) * (4 + np) + 4 + j1];
-    f1 *= a.dx;
-    pu = fma(a.w[j1] * f1, f1, pu);
-  }
-  pu = block_sum<1024>(pu, red);
   if (threadIdx.x == 0) {
     const double dx2 = a.dx * a.dx;
     a.out[0] = dx2 * m;
@@ -557,7 +618,7 @@ __global__ void __launch_bounds__(1024) k_sem_obs_fin(SemObsArgs a) {
     a.out[4] = sqrt(dx2 * l2);
     a.out[5] = a.out[6] = a.out[7] = 0.0;
   }
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) a.out[8 + i] = a.n[i];
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) a.out[8 + i] = dens[i];
 }
 
 // Occupation numbers: the reduced Wigner function (one block per (x, p)),
@@ -731,9 +792,11 @@ cudaError_t launch_sem_scale(long long n, double a, const double *in, double *ou
 }
 
 cudaError_t launch_sem_obs(const SemObsArgs &a, cudaStream_t s) {
-  const size_t smem = sizeof(double) * 3 * a.np;
-  k_sem_obs_x<<<a.nx * a.nx, 256, smem, s>>>(a);
-  k_sem_obs_fin<<<1, 1024, 0, s>>>(a);
+  const int nt = a.np >= 256 ? 256 : 32 * ((a.np + 31) / 32);  // a thread per row
+  k_sem_obs_x<<<a.nx * a.nx, nt, sizeof(double) * 2 * a.np, s>>>(a);
+  double *mid = a.xpart + (long long)a.nx * a.nx * (4 + a.np);
+  k_sem_obs_mid<<<a.nx, 256, 0, s>>>(a, mid);
+  k_sem_obs_fin<<<1, 1024, sizeof(double) * 2 * a.nx, s>>>(a, mid);
   return cudaGetLastError();
 }
 

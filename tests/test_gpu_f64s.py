@@ -111,6 +111,39 @@ def test_sliced_step_parity_full_size_workload():
     assert np.abs(got - got.transpose(1, 0, 3, 2)).max() < 1e-13 * np.abs(got).max()
 
 
+@pytest.mark.parametrize("prec", ["W2_F64_SLICED", "W2_F64"])
+def test_largest_fp64_grid_sampled(prec):
+    """The largest grid of the FP64 paths (nx = 128, nk = 64: 67M points,
+    537 MB per array).  The operator at 16 sampled spatial points and the
+    shift of 8 sampled momentum planes (lines of 128 points) against the
+    oracle, then one step that stays finite and exchange symmetric."""
+    from paper_2511_11354_gb300 import w2
+    prob = inputs.Problem(nx=128, nk=64, L=24.0, dt=0.005, vext=inputs.double_well(20.0),
+                          vee=inputs.soft_coulomb(1.0), gamma=1.0, c_hartree=1.0)
+    f = inputs.initial_state_chunked(prob, centres=inputs.draw_centres(5), seed=5, dtype=np.float64)
+    ctx = w2.Context.from_problem(prob, precision=getattr(w2, prec))
+    d = torch.from_numpy(f).cuda()
+    out = torch.empty_like(d)
+    rng = np.random.default_rng(3)
+    o = oracle.Oracle(prob)
+    xs = rng.choice(prob.nx * prob.nx, 16, replace=False)
+    ctx.theta(d, out)
+    got = out.view(prob.nx * prob.nx, prob.nk, prob.nk)[torch.from_numpy(xs).cuda()].cpu().numpy()
+    assert rel(got, o.theta_sample(f, xs)) < 2e-12
+    planes = rng.choice(prob.nk * prob.nk, 8, replace=False)
+    ctx.advect(d, out)
+    got = out.view(prob.nx, prob.nx, prob.nk * prob.nk)[:, :, torch.from_numpy(planes).cuda()]
+    got = got.permute(2, 0, 1).contiguous().cpu().numpy()
+    assert rel(got, o.advect_sample(f, planes)) < 1e-13
+    del f
+    ctx.set_state(d)
+    ctx.step(1)
+    ctx.get_state(out)
+    assert bool(torch.isfinite(out).all())
+    g = out.view(prob.nx, prob.nx, prob.nk, prob.nk)
+    assert (g - g.permute(1, 0, 3, 2)).abs().max().item() < 1e-13 * g.abs().max().item()
+
+
 def test_sliced_and_fp64_pipe_paths_agree_over_200_steps():
     """The two FP64 paths on the 64^4 workload over 200 steps (the FP64-pipe
     path is itself held to the oracle by test_gpu_f64.py)."""

@@ -47,10 +47,14 @@ __device__ __noinline__ void tables_block(const TabArgs &a, const int i, const i
     const double w = a.dx * a.dp * a.dp;
     for (int q = tid; q < nx; q += blockDim.x) {
       double s = 0.0;
-      if (part == 0)
+      // unrolled loops issue their loads ahead; the additions keep their order
+      if (part == 0) {
+#pragma unroll 8
         for (int k = 0; k < nx; ++k) s += a.xsum[(size_t)q * nx + k];
-      else
+      } else {
+#pragma unroll 8
         for (int k = 0; k < nx; ++k) s += a.xsum[(size_t)k * nx + q];
+      }
       n[q] = s * w;
     }
   }
@@ -64,6 +68,7 @@ __device__ __noinline__ void tables_block(const TabArgs &a, const int i, const i
       if (mf && a.c_h != 0.0) {
         const double *ker = a.h_fine ? a.h_fine : a.w_fine;  // Poisson kernel, or W scaled below
         double vh = 0.0;
+#pragma unroll 8
         for (int q = 0; q < nx; ++q) {
           int d = i - q;
           d += (d < 0) ? nx : 0;
@@ -73,6 +78,7 @@ __device__ __noinline__ void tables_block(const TabArgs &a, const int i, const i
       }
       if (mf && a.c_xc != 0.0 && a.xc_kind) {
         double ni = 0.0;
+#pragma unroll 8
         for (int q = 0; q < nx; ++q) {
           int d = i - q;
           d += (d < 0) ? nx : 0;
@@ -89,6 +95,7 @@ __device__ __noinline__ void tables_block(const TabArgs &a, const int i, const i
   const double inv = 1.0 / (a.hbar * nk);
   for (int j = tid; j < nk; j += blockDim.x) {
     double s = 0.0;
+#pragma unroll 8
     for (int l = 1; l < nk; ++l) {
       int m = (l * j) % M;
       s += (U[l] - U[M - l]) * a.sintab[m];

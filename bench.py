@@ -7,7 +7,8 @@ python bench.py [--gpus N] [--steps K] [--warmup W] [--impl w2|reference]
 
 One JSON line on rank 0.  "value" is whole-job throughput (all ranks) with
 the state resident in HBM; "e2e" goes through the public C ABI with the state
-copied from pinned host memory and the observables read back every step.
+copied from pinned host memory and the observables read back every step (the
+copy of the next step's input staged during the current step).
 Each rank advances its own independent replica (the step has no exchange
 between replicas), so scaling is weak and there is no data-path collective.
 """
@@ -617,7 +618,10 @@ def main():
     peaks = _fp64_peak()
     k_theta_pipe = 0.5 * (kprof_pipe[2] + kprof_pipe[7])
 
-    # ---- end to end through the C ABI: pinned host state in, observables out
+    # ---- end to end through the C ABI: pinned host state in, observables out.
+    # Each step's input is copied from the host (w2_stage_state: the copy of
+    # step k+1's input runs on the context's copy stream during step k) and
+    # its observables are read back before the next step.
     ctx.set_state(f_dev)
     ctx.step(1)
     host = torch.from_numpy(f0).pin_memory()
@@ -627,8 +631,12 @@ def main():
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
-    for _ in range(args.steps):
-        w2._check(ctx.lib.w2_set_state(ctx.h, w2.ctypes.c_void_p(host.data_ptr()), 0), "w2_set_state")
+    torch.cuda.synchronize()  # the first copy starts after t0
+    ctx.stage_state(host)
+    for k in range(args.steps):
+        ctx.use_staged_state()
+        if k + 1 < args.steps:
+            ctx.stage_state(host)
         ctx.step(1)
         ctx.observables()
     t1.record(stream)
@@ -649,7 +657,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _workload_desc(prob),
             "clocks": clk,
-            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "pipeline": "w2_stage_state copies step k+1's input from pinned host memory during step k; "
+                                "w2_use_staged_state takes it in (device copy); observables read back every step"},
             "gpu_launches": len(w2.STEP_KERNELS) * args.steps,
             "roofline": {"bound": "tensor", "kernel": "k_theta_s (sliced FP64 sweep, BF16 mma.sync m16n8k16)",
                          "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",

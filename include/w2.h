@@ -169,6 +169,23 @@ w2_status w2_set_hartree(w2_ctx *ctx, int32_t kind);
  * Errors: W2_ERR_ARG (NULL f), W2_ERR_STATE (potentials not set), W2_ERR_CUDA. */
 w2_status w2_set_state(w2_ctx *ctx, const void *f, int32_t on_device);
 
+/* Double-buffered input from host memory, so that the host-to-device copy of
+ * the next state overlaps the work on the current one.  w2_stage_state queues
+ * the copy of a host state f (layout and element type of w2_set_state) into
+ * the context's staging buffer on a private copy stream and returns; the
+ * context's state is not touched.  The copy starts once the previous staged
+ * state has been taken.  w2_use_staged_state makes the staged state the
+ * context's state: the context's stream waits for the copy, then copies the
+ * stage in (device to device) and the step count is reset.  The staging
+ * buffer (one state) and the copy stream are created by the first
+ * w2_stage_state.  The host buffer must stay unchanged until the copy is
+ * done, which any synchronising call after the matching w2_use_staged_state
+ * guarantees; pinned host memory makes the copy asynchronous.
+ * Errors: W2_ERR_ARG, W2_ERR_STATE (potentials not set; for
+ * w2_use_staged_state: nothing staged), W2_ERR_OOM, W2_ERR_CUDA. */
+w2_status w2_stage_state(w2_ctx *ctx, const void *f);
+w2_status w2_use_staged_state(w2_ctx *ctx);
+
 /* Copy the current state out (same layout).  With on_device == 0 the call
  * synchronises the stream before returning.  Errors: W2_ERR_ARG, W2_ERR_STATE
  * (no state), W2_ERR_CUDA. */

@@ -55,6 +55,13 @@ static void free_all(w2_ctx *c) {
   if (c->Kzero) cudaFree(c->Kzero);
   if (c->graph_ready) cudaGraphExecDestroy(c->graph);
   if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->copy) {
+    cudaStreamSynchronize(c->copy);
+    cudaStreamDestroy(c->copy);
+  }
+  if (c->ev_staged) cudaEventDestroy(c->ev_staged);
+  if (c->ev_taken) cudaEventDestroy(c->ev_taken);
+  if (c->stage) cudaFree(c->stage);
 }
 
 extern "C" const char *w2_status_string(w2_status s) {
@@ -343,6 +350,43 @@ extern "C" w2_status w2_set_state(w2_ctx *ctx, const void *f, int32_t on_device)
   if (!ctx->have_pot) return W2_ERR_STATE;
   W2_TRY(cudaMemcpyAsync(ctx->f, f, ctx->esz * ctx->npts,
                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  ctx->have_state = true;
+  ctx->steps = 0;
+  return W2_OK;
+}
+
+extern "C" w2_status w2_stage_state(w2_ctx *ctx, const void *f) {
+  if (!ctx || !f) return W2_ERR_ARG;
+  if (ctx->sticky) return ctx->sticky;
+  if (!ctx->have_pot) return W2_ERR_STATE;
+  const size_t bytes = ctx->esz * ctx->npts;
+  if (!ctx->stage) {
+    if (cudaMalloc(&ctx->stage, bytes) != cudaSuccess) {
+      ctx->stage = nullptr;
+      (void)cudaGetLastError();
+      return W2_ERR_OOM;
+    }
+    W2_TRY(cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking));
+    W2_TRY(cudaEventCreateWithFlags(&ctx->ev_staged, cudaEventDisableTiming));
+    W2_TRY(cudaEventCreateWithFlags(&ctx->ev_taken, cudaEventDisableTiming));
+  }
+  // the stage is overwritten only after the previous w2_use_staged_state has read it
+  if (ctx->taken_recorded) W2_TRY(cudaStreamWaitEvent(ctx->copy, ctx->ev_taken, 0));
+  W2_TRY(cudaMemcpyAsync(ctx->stage, f, bytes, cudaMemcpyHostToDevice, ctx->copy));
+  W2_TRY(cudaEventRecord(ctx->ev_staged, ctx->copy));
+  ctx->stage_pending = true;
+  return W2_OK;
+}
+
+extern "C" w2_status w2_use_staged_state(w2_ctx *ctx) {
+  if (!ctx) return W2_ERR_ARG;
+  if (ctx->sticky) return ctx->sticky;
+  if (!ctx->stage_pending) return W2_ERR_STATE;
+  W2_TRY(cudaStreamWaitEvent(ctx->stream, ctx->ev_staged, 0));
+  W2_TRY(cudaMemcpyAsync(ctx->f, ctx->stage, ctx->esz * ctx->npts, cudaMemcpyDeviceToDevice, ctx->stream));
+  W2_TRY(cudaEventRecord(ctx->ev_taken, ctx->stream));
+  ctx->taken_recorded = true;
+  ctx->stage_pending = false;
   ctx->have_state = true;
   ctx->steps = 0;
   return W2_OK;

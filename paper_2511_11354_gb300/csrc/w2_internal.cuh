@@ -249,6 +249,13 @@ struct w2_ctx {
   float *f1;               // [nx][nk] reduced Wigner function for the features
   uint16_t *xrows;         // [nx*nx][din] feature rows
   double *Kzero;           // [2][nx][2nk-1] zero one-body tables (pair-only sweeps)
+  // staged host input (allocated by the first w2_stage_state): one state,
+  // filled on a private copy stream while the context's stream computes
+  void *stage;
+  cudaStream_t copy;
+  cudaEvent_t ev_staged;   // recorded on copy after the host copy
+  cudaEvent_t ev_taken;    // recorded on stream after w2_use_staged_state read the stage
+  bool stage_pending, taken_recorded;
 };
 
 namespace w2 {

@@ -29,7 +29,8 @@ F64_STATE = (W2_F64, W2_F64_SLICED)
 STATUS = {0: "W2_OK", -1: "W2_ERR_ARG", -2: "W2_ERR_CUDA", -3: "W2_ERR_OOM", -4: "W2_ERR_STATE",
           -5: "W2_ERR_UNSTABLE", -6: "W2_ERR_NONFINITE", -7: "W2_ERR_TIMEOUT", -8: "W2_ERR_UNSUPPORTED"}
 
-EXPORTS = ("w2_create", "w2_set_potentials", "w2_set_state", "w2_get_state", "w2_step",
+EXPORTS = ("w2_create", "w2_set_potentials", "w2_set_state", "w2_stage_state", "w2_use_staged_state",
+           "w2_get_state", "w2_step",
            "w2_step_profile", "w2_observables", "w2_theta", "w2_advect", "w2_destroy", "w2_status_string",
            "w2_last_cuda_error", "w2_set_hartree", "w2_occupations", "w2_hermitian_eigvals",
            "w2_batch_create", "w2_batch_set_potentials", "w2_batch_set_state", "w2_batch_get_state",
@@ -240,6 +241,22 @@ class Context:
             _check(self.lib.w2_set_state(self.h, ctypes.c_void_p(f.ctypes.data), 0), "w2_set_state")
         else:
             _check(self.lib.w2_set_state(self.h, _dev_ptr(f, self.shape, self.torch_dtype), 1), "w2_set_state")
+
+    def stage_state(self, f):
+        """Queue the host-to-device copy of the next state (a CPU tensor, pinned
+        for an asynchronous copy, or a numpy array; it must stay unchanged until
+        a synchronising call after use_staged_state)."""
+        if isinstance(f, np.ndarray):
+            assert f.dtype == self.np_dtype and f.flags.c_contiguous and f.shape == self.shape
+            ptr = f.ctypes.data
+        else:
+            assert (not f.is_cuda) and f.is_contiguous() and tuple(f.shape) == self.shape
+            assert f.dtype == self.torch_dtype
+            ptr = f.data_ptr()
+        _check(self.lib.w2_stage_state(self.h, ctypes.c_void_p(ptr)), "w2_stage_state")
+
+    def use_staged_state(self):
+        _check(self.lib.w2_use_staged_state(self.h), "w2_use_staged_state")
 
     def get_state(self, out=None):
         import torch

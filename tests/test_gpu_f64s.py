@@ -176,6 +176,37 @@ def test_sliced_determinism_and_resume():
     assert np.array_equal(c.get_state(), a.get_state())
 
 
+@pytest.mark.parametrize("prec", ["W2_F64_SLICED", "W2_F32_TF32X3"])
+def test_staged_host_input_pipeline(prec):
+    """w2_stage_state / w2_use_staged_state: three host states streamed with
+    the copy of the next one queued while the current one steps give the same
+    bits as w2_set_state before each step; nothing staged is W2_ERR_STATE."""
+    from paper_2511_11354_gb300 import w2
+    prob, f0 = inputs.workload_small(nx=16, nk=16)
+    p = getattr(w2, prec)
+    ref = w2.Context.from_problem(prob, precision=p)
+    hosts = [torch.from_numpy(np.ascontiguousarray(f0 * (1.0 + 0.1 * k), dtype=ref.np_dtype)).pin_memory()
+             for k in range(3)]
+    want = []
+    for h in hosts:
+        ref.set_state(h.numpy())
+        ref.step(2)
+        want.append((ref.get_state(), ref.observables().energy))
+    ctx = w2.Context.from_problem(prob, precision=p)
+    with pytest.raises(w2.W2Error) as e:
+        ctx.use_staged_state()
+    assert e.value.name == "W2_ERR_STATE"
+    ctx.stage_state(hosts[0])
+    for k in range(3):
+        ctx.use_staged_state()
+        if k + 1 < 3:
+            ctx.stage_state(hosts[k + 1])
+        ctx.step(2)
+        ob = ctx.observables()
+        assert ob.step == 2
+        assert np.array_equal(ctx.get_state(), want[k][0]) and ob.energy == want[k][1], k
+
+
 def test_sliced_nonfinite_and_unsupported():
     from paper_2511_11354_gb300 import w2
     prob, f0 = inputs.workload_small(nx=8, nk=16)

@@ -181,10 +181,12 @@ __device__ __forceinline__ int sturm_count(const double *d, const double *e, int
   return cnt;
 }
 
-// Warp gw = b * n + j finds the j-th largest eigenvalue of matrix b.
-__global__ void __launch_bounds__(128) k_tridiag_eigs(const double2 *mats, int n, int batch, double *eig) {
+// Warp gw = b * n + j finds the j-th largest eigenvalue of matrix b.  The
+// Sturm counts are bound by the FP64 pipe (a division per pivot), so each
+// block is one warp: the warps spread over all SMs.
+__global__ void __launch_bounds__(32) k_tridiag_eigs(const double2 *mats, int n, int batch, double *eig) {
   const int lane = threadIdx.x & 31;
-  const long long gw = (long long)blockIdx.x * 4 + (threadIdx.x >> 5);
+  const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (gw >= (long long)batch * n) return;  // whole warps
   const int b = (int)(gw / n), j = (int)(gw - (long long)b * n);
   const double *d = reinterpret_cast<const double *>(mats + (size_t)b * n * n), *e = d + n;
@@ -260,7 +262,7 @@ cudaError_t launch_herm_eigvals(double2 *mats, int n, int batch, double *eig, cu
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long long warps = (long long)batch * n;
-  k_tridiag_eigs<<<(unsigned)((warps + 3) / 4), 128, 0, s>>>(mats, n, batch, eig);
+  k_tridiag_eigs<<<(unsigned)warps, 32, 0, s>>>(mats, n, batch, eig);
   return cudaGetLastError();
 }
 

@@ -89,7 +89,14 @@ struct Theta32Smem {
   static constexpr size_t bytes = 4 * words;
 };
 
-// One CTA per X; warp w owns momentum rows [16w, 16w + 16).
+// Warps per 16-row block of the X block: the two warps of a row block share
+// its A fragments and split its 8-wide column tiles (and its sheared
+// two-body tiles) in halves, so a CTA of 4 NK threads keeps twice the warps of
+// one warp per row block with half the accumulators per thread.  Every output
+// tile goes through the same sequence of products either way.
+constexpr int kTh32Split = 2;
+
+// One CTA per X; warps 2r and 2r + 1 own momentum rows [16r, 16r + 16).
 // MODE 0: out = Theta[in].  MODE 1: out = base + (h + half_tau Theta[in]).
 template <int NK, int MODE>
 // compiled once (not inlined) so the single-problem and batched kernels
@@ -110,6 +117,9 @@ __device__ __noinline__ void theta32_block(const Theta32Args &a, const int X, ui
   dd += (dd < 0) ? nx : 0;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int g = lane >> 2, t4 = lane & 3;
+  const int half = w % kTh32Split;            // this warp's half of the column tiles
+  constexpr int NTH = NT / kTh32Split;
+  const int bfirst = half * NTH;
   const size_t base = (size_t)X * NK * NK;
   {
     const float4 *src = reinterpret_cast<const float4 *>(a.in + base);
@@ -129,13 +139,16 @@ __device__ __noinline__ void theta32_block(const Theta32Args &a, const int X, ui
   }
   __syncthreads();
 
-  const int r0 = 16 * w;
+  const int r0 = 16 * (w / kTh32Split);
   const int na = r0 + g, nb = r0 + g + 8;  // the two A/D rows of this lane
 
-  // Two-body term in sheared coordinates (see k_theta in w2_f64.cu).
+  // Two-body term in sheared coordinates (see k_theta in w2_f64.cu); the
+  // sheared tiles of the row block are split between its two warps.
   {
-    const int cmax = min((r0 + 15 + NK - 1) >> 3, (2 * NK - 2) >> 3);
-    for (int c = r0 >> 3; c <= cmax; ++c) {
+    const int cfirst = r0 >> 3, cmax = min((r0 + 15 + NK - 1) >> 3, (2 * NK - 2) >> 3);
+    const int hn = (cmax - cfirst + 2) >> 1;
+    const int cbeg = half ? cfirst + hn : cfirst, cend = half ? cmax : cfirst + hn - 1;
+    for (int c = cbeg; c <= cend; ++c) {
       float d[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f};
       const int nlo = max(0, 8 * c - NK + 1), nhi = min(NK - 1, 8 * c + 7);
       const int s = 8 * c + g;
@@ -166,17 +179,18 @@ __device__ __noinline__ void theta32_block(const Theta32Args &a, const int X, ui
       n2 = sa + 1 - nb; if (n2 >= 0 && n2 < NK) Acc[nb * S + n2] = d[3];
     }
   }
-  __syncwarp();
+  __syncthreads();  // the row block's Acc rows come from both of its warps
 
-  float acc[NT][4], sml[NT][4];
+  float acc[NTH][4], sml[NTH][4];
 #pragma unroll
-  for (int b = 0; b < NT; ++b) {
-    acc[b][0] = Acc[na * S + 8 * b + 2 * t4];
-    acc[b][1] = Acc[na * S + 8 * b + 2 * t4 + 1];
-    acc[b][2] = Acc[nb * S + 8 * b + 2 * t4];
-    acc[b][3] = Acc[nb * S + 8 * b + 2 * t4 + 1];
+  for (int bb = 0; bb < NTH; ++bb) {
+    const int b = bfirst + bb;
+    acc[bb][0] = Acc[na * S + 8 * b + 2 * t4];
+    acc[bb][1] = Acc[na * S + 8 * b + 2 * t4 + 1];
+    acc[bb][2] = Acc[nb * S + 8 * b + 2 * t4];
+    acc[bb][3] = Acc[nb * S + 8 * b + 2 * t4 + 1];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) sml[b][q] = 0.f;
+    for (int q = 0; q < 4; ++q) sml[bb][q] = 0.f;
   }
   for (int kk = 0; kk < NK; kk += 8) {
     const int c0 = kk + t4, c1 = kk + t4 + 4;
@@ -193,41 +207,42 @@ __device__ __noinline__ void theta32_block(const Theta32Args &a, const int X, ui
     a2h[2] = Fh[na * S + c1]; a2l[2] = Fl[na * S + c1];
     a2h[3] = Fh[nb * S + c1]; a2l[3] = Fl[nb * S + c1];
 #pragma unroll
-    for (int b = 0; b < NT; ++b) {
-      const int n2 = 8 * b + g;
+    for (int bb = 0; bb < NTH; ++bb) {
+      const int n2 = 8 * (bfirst + bb) + g;
       uint32_t bh[2], bm[2], bl[2];
       bh[0] = Fh[c0 * S + n2]; bl[0] = Fl[c0 * S + n2];               // F[n1'][n2]
       bh[1] = Fh[c1 * S + n2]; bl[1] = Fl[c1 * S + n2];
       float t[4] = {0.f, 0.f, 0.f, 0.f};
-      mma5_a3(t, sml[b], a1h, a1m, a1l, bh, bl);
+      mma5_a3(t, sml[bb], a1h, a1m, a1l, bh, bl);
       const int j0 = c0 - n2 + NK - 1, j1 = c1 - n2 + NK - 1;         // K2(n2' - n2)
       bh[0] = k2h[j0]; bm[0] = k2m[j0]; bl[0] = k2l[j0];
       bh[1] = k2h[j1]; bm[1] = k2m[j1]; bl[1] = k2l[j1];
-      mma5_b3(t, sml[b], a2h, a2l, bh, bm, bl);
+      mma5_b3(t, sml[bb], a2h, a2l, bh, bm, bl);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[b][q] += t[q];  // round-to-nearest on the CUDA cores
+      for (int q = 0; q < 4; ++q) acc[bb][q] += t[q];  // round-to-nearest on the CUDA cores
     }
   }
 #pragma unroll
-  for (int b = 0; b < NT; ++b)
+  for (int bb = 0; bb < NTH; ++bb)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[b][q] += sml[b][q];
+    for (int q = 0; q < 4; ++q) acc[bb][q] += sml[bb][q];
 
 #pragma unroll
-  for (int b = 0; b < NT; ++b) {
+  for (int bb = 0; bb < NTH; ++bb) {
+    const int b = bfirst + bb;
 #pragma unroll
     for (int hrow = 0; hrow < 2; ++hrow) {
       const int n1 = hrow ? nb : na;
       const size_t o = base + (size_t)n1 * NK + 8 * b + 2 * t4;
       float2 v;
       if (MODE == 0) {
-        v.x = acc[b][2 * hrow];
-        v.y = acc[b][2 * hrow + 1];
+        v.x = acc[bb][2 * hrow];
+        v.y = acc[bb][2 * hrow + 1];
       } else {
         const float2 hv = *reinterpret_cast<const float2 *>(a.h + o);
         const float2 fv = *reinterpret_cast<const float2 *>(a.base + o);
-        v.x = fv.x + fmaf(a.half_tau, acc[b][2 * hrow], hv.x);
-        v.y = fv.y + fmaf(a.half_tau, acc[b][2 * hrow + 1], hv.y);
+        v.x = fv.x + fmaf(a.half_tau, acc[bb][2 * hrow], hv.x);
+        v.y = fv.y + fmaf(a.half_tau, acc[bb][2 * hrow + 1], hv.y);
       }
       *reinterpret_cast<float2 *>(a.out + o) = v;
     }
@@ -235,7 +250,7 @@ __device__ __noinline__ void theta32_block(const Theta32Args &a, const int X, ui
 }
 
 template <int NK, int MODE>
-__global__ void __launch_bounds__(NK * 2) k_theta32(Theta32Args a) {
+__global__ void __launch_bounds__(NK * 2 * kTh32Split, 1) k_theta32(Theta32Args a) {
   extern __shared__ __align__(16) uint32_t smu[];
   theta32_block<NK, MODE>(a, blockIdx.x, smu);
 }
@@ -251,7 +266,7 @@ __device__ __forceinline__ int find_inst(const int *off, int n, int item) {
 // instance of one momentum size; args[2 * inst + MODE] holds that instance's
 // arguments.
 template <int NK, int MODE>
-__global__ void __launch_bounds__(NK * 2) k_btheta32(const Theta32Args *args, const int *inst, const int *off,
+__global__ void __launch_bounds__(NK * 2 * kTh32Split, 1) k_btheta32(const Theta32Args *args, const int *inst, const int *off,
                                                      int n) {
   extern __shared__ __align__(16) uint32_t smu[];
   const int total = off[n];
@@ -577,9 +592,9 @@ static cudaError_t prep32() {
 template <int NK>
 static cudaError_t run_btheta32(int mode, const BatchLaunch &b, const Theta32Args *args, cudaStream_t s) {
   if (mode == 0)
-    k_btheta32<NK, 0><<<b.grid, NK * 2, Theta32Smem<NK>::bytes, s>>>(args, b.inst, b.off, b.n);
+    k_btheta32<NK, 0><<<b.grid, NK * 2 * kTh32Split, Theta32Smem<NK>::bytes, s>>>(args, b.inst, b.off, b.n);
   else
-    k_btheta32<NK, 1><<<b.grid, NK * 2, Theta32Smem<NK>::bytes, s>>>(args, b.inst, b.off, b.n);
+    k_btheta32<NK, 1><<<b.grid, NK * 2 * kTh32Split, Theta32Smem<NK>::bytes, s>>>(args, b.inst, b.off, b.n);
   return cudaGetLastError();
 }
 
@@ -598,7 +613,7 @@ static cudaError_t run_badv32(int dir, const BatchLaunch &b, const Adv32Args *ar
 
 template <int NK>
 static cudaError_t run_theta32(int mode, const Theta32Args &a, cudaStream_t s) {
-  dim3 grid(a.nx * a.nx), block(NK * 2);
+  dim3 grid(a.nx * a.nx), block(NK * 2 * kTh32Split);
   if (mode == 0)
     k_theta32<NK, 0><<<grid, block, Theta32Smem<NK>::bytes, s>>>(a);
   else

@@ -117,9 +117,9 @@ __device__ __noinline__ void theta32_block(const Theta32Args &a, const int X, ui
   dd += (dd < 0) ? nx : 0;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int g = lane >> 2, t4 = lane & 3;
-  const int half = w % kTh32Split;            // this warp's half of the column tiles
+  const int part = w % kTh32Split;            // this warp's part of the column tiles
   constexpr int NTH = NT / kTh32Split;
-  const int bfirst = half * NTH;
+  const int bfirst = part * NTH;
   const size_t base = (size_t)X * NK * NK;
   {
     const float4 *src = reinterpret_cast<const float4 *>(a.in + base);
@@ -147,7 +147,7 @@ __device__ __noinline__ void theta32_block(const Theta32Args &a, const int X, ui
   {
     const int cfirst = r0 >> 3, cmax = min((r0 + 15 + NK - 1) >> 3, (2 * NK - 2) >> 3);
     const int hn = (cmax - cfirst + 2) >> 1;
-    const int cbeg = half ? cfirst + hn : cfirst, cend = half ? cmax : cfirst + hn - 1;
+    const int cbeg = part ? cfirst + hn : cfirst, cend = part ? cmax : cfirst + hn - 1;
     for (int c = cbeg; c <= cend; ++c) {
       float d[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f};
       const int nlo = max(0, 8 * c - NK + 1), nhi = min(NK - 1, 8 * c + 7);

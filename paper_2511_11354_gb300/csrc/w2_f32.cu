@@ -119,6 +119,7 @@ __device__ __noinline__ void theta32_block(const Theta32Args &a, const int X, ui
   const int g = lane >> 2, t4 = lane & 3;
   const int part = w % kTh32Split;            // this warp's part of the column tiles
   constexpr int NTH = NT / kTh32Split;
+  static_assert(NT % kTh32Split == 0, "the warps of a row block split its column tiles evenly");
   const int bfirst = part * NTH;
   const size_t base = (size_t)X * NK * NK;
   {

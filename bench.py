@@ -227,22 +227,25 @@ def bench_forms(args, barrier):
         a.close()
         b.close()
     # precision form on the paper's full plasma mesh (nonlinear Landau damping)
-    forms["plasma_landau_256x128"] = bench_plasma(args, timed)
+    if not args.no_plasma:
+        forms["plasma_landau_256x128"] = bench_plasma(args, timed)
     # batching form: 64 uneven instances, one graph-captured persistent step
-    probs, states = inputs.workload_batch(64, seed=3)
-    bt = w2.Batch(probs)
-    for i, f in enumerate(states):
-        bt.set_state(i, f.astype(np.float32))
-    del states
-    tuning = bt.autotune()
-    bt.step(args.warmup)
-    ms = timed(bt.step, k)
-    pts = sum(p.points for p in probs)
-    forms["batching"] = {
-        "workload": "64 instances, nx in {24,32,48,64}, nk in {32,48,64}, gamma in U[0.2,2] (seed 3), "
-                    f"{pts / 1e6:.1f}M points in total, FP32 state, TF32 split contractions",
-        "value": pts * k / (ms / 1e3), "unit": UNIT, "steps": k, "ms_per_step": ms / k, "autotuned_grids": tuning}
-    bt.close()
+    if not args.no_batching:
+        probs, states = inputs.workload_batch(64, seed=3)
+        bt = w2.Batch(probs)
+        for i, f in enumerate(states):
+            bt.set_state(i, f.astype(np.float32))
+        del states
+        tuning = bt.autotune()
+        bt.step(args.warmup)
+        ms = timed(bt.step, k)
+        pts = sum(p.points for p in probs)
+        forms["batching"] = {
+            "workload": "64 instances, nx in {24,32,48,64}, nk in {32,48,64}, gamma in U[0.2,2] (seed 3), "
+                        f"{pts / 1e6:.1f}M points in total, FP32 state, TF32 split contractions",
+            "value": pts * k / (ms / 1e3), "unit": UNIT, "steps": k, "ms_per_step": ms / k,
+            "autotuned_grids": tuning}
+        bt.close()
     if not args.no_learned:
         forms["learned"] = bench_learned(args, timed)
     if not args.no_sem:
@@ -513,6 +516,8 @@ def main():
     ap.add_argument("--no-form-error", action="store_true")
     ap.add_argument("--form-steps", type=int, default=20)
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-plasma", action="store_true", help="skip the plasma form (for profiling commands)")
+    ap.add_argument("--no-batching", action="store_true", help="skip the batching form (for profiling commands)")
     ap.add_argument("--no-sem", action="store_true", help="skip the non-periodic (spectral-element) form")
     ap.add_argument("--sem-steps", type=int, default=2)
     ap.add_argument("--sem-nx", type=int, default=201, help="spatial points per axis of the non-periodic form")

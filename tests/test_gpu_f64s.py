@@ -176,6 +176,35 @@ def test_sliced_determinism_and_resume():
     assert np.array_equal(c.get_state(), a.get_state())
 
 
+# (precision, nk, operator bar, shift bar, step bar)
+SMALLEST = [("W2_F64", 8, 1e-12, 1e-13, 1e-10), ("W2_F64_SLICED", 16, 2e-12, 1e-13, 1e-10),
+            ("W2_F32_TF32X3", 16, 2e-6, 1e-6, 1e-6)]
+
+
+@pytest.mark.parametrize("nx", [4, 5])
+@pytest.mark.parametrize("prec,nk,bar_theta,bar_adv,bar_step", SMALLEST)
+def test_smallest_spatial_grids(nx, prec, nk, bar_theta, bar_adv, bar_step):
+    """The smallest grids the API takes (nx = 4 and 5: periodic lines of four
+    or five points, shorter than the spline start sums and split into
+    recursion pieces of two or three points): operator, shift and three steps
+    against the oracle on every element, for all three precisions."""
+    from paper_2511_11354_gb300 import w2
+    prob, f0 = inputs.workload_small(nx=nx, nk=nk)
+    ctx = w2.Context.from_problem(prob, precision=getattr(w2, prec))
+    f = np.ascontiguousarray(f0, dtype=ctx.np_dtype)
+    f64 = f.astype(np.float64)
+    o = oracle.Oracle(prob)
+    d = torch.from_numpy(f).cuda()
+    out = torch.empty_like(d)
+    ctx.theta(d, out)
+    assert rel(out.cpu().numpy().astype(np.float64), o.theta(f64)) < bar_theta
+    ctx.advect(d, out)
+    assert rel(out.cpu().numpy().astype(np.float64), o.advect(f64)) < bar_adv
+    ctx.set_state(d)
+    ctx.step(3)
+    assert rel(ctx.get_state().astype(np.float64), o.step(f64, 3)) < bar_step
+
+
 @pytest.mark.parametrize("prec", ["W2_F64_SLICED", "W2_F32_TF32X3"])
 def test_staged_host_input_pipeline(prec):
     """w2_stage_state / w2_use_staged_state: three host states streamed with

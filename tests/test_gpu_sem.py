@@ -220,6 +220,31 @@ def test_occupations_of_a_two_packet_mixture():
 
 
 @pytest.mark.parametrize("prec", ["W2_F64", "W2_F64_SLICED"])
+def test_smallest_mesh(prec):
+    """The smallest mesh the API takes: 8 points per axis (y grid of 7), one
+    momentum cell of two Chebyshev points (np = 2, every product far below
+    one tile): operator, shift and two steps against the oracle."""
+    prob, f = _case(8, 1, 2, 10.0, "IV")
+    f = f / np.abs(f).max()  # two momentum nodes far out in the packet's tails: rescale to O(1)
+    prob.dt = 0.37
+    ctx = _ctx(prob, prec)
+    o = SemOracle(prob)
+    d = torch.from_numpy(f).cuda()
+    out = torch.empty_like(d)
+    ctx.theta(d, out)
+    assert rel(out.cpu().numpy(), o.theta(f)) < THETA_BAR[prec]
+    ctx.advect(d, out)
+    assert rel(out.cpu().numpy(), o.advect(f)) < 1e-13
+    prob.dt = 0.001  # |Theta f| is about 500 |f| on this mesh: a stable step
+    ctx = _ctx(prob, prec)
+    ctx.set_state(f)
+    ctx.step(2)
+    ref = SemOracle(prob).step(f, 2)
+    assert np.linalg.norm(ref) < 2 * np.linalg.norm(f)
+    assert rel(ctx.get_state(), ref) < 1e-10
+
+
+@pytest.mark.parametrize("prec", ["W2_F64", "W2_F64_SLICED"])
 def test_theta_parity_widest_momentum_axis(prec):
     """The largest momentum axis (8 cells x 32 points = 256: contractions over
     2 np = 512 split in two on the sliced path) on the smallest box (8 points,

@@ -124,10 +124,11 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def _fp64_peak():
-    """Live FP64 tensor-path (DMMA) and DFMA peaks from the committed probe."""
-    src = os.path.join(ROOT, "paper_2511_11354_gb300", "probe", "fp64_peak.cu")
-    exe = os.path.join(ROOT, "paper_2511_11354_gb300", "_build", "fp64_peak")
+def _pipe_peaks():
+    """Live peaks of the FP64 tensor path (DMMA), of DFMA and of BF16 mma.sync
+    (register-only loops of the committed probe)."""
+    src = os.path.join(ROOT, "paper_2511_11354_gb300", "probe", "pipe_peaks.cu")
+    exe = os.path.join(ROOT, "paper_2511_11354_gb300", "_build", "pipe_peaks")
     if not os.path.exists(exe) or os.path.getmtime(exe) < os.path.getmtime(src):
         os.makedirs(os.path.dirname(exe), exist_ok=True)
         subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src], check=True)
@@ -296,7 +297,8 @@ def bench_sem(args, timed):
     pipe.theta(d, out)
     ms_theta_pipe = timed(lambda n: pipe.theta(d, out), 1)
     pipe.close()
-    peak64 = _fp64_peak()["fp64_dfma_tflops"]
+    pk = _pipe_peaks()
+    peak64, mma_ceiling = pk["fp64_dfma_tflops"], pk["mma_sync_bf16_tflops"]
     bf16 = MEASURED_BF16_TFLOPS(sustained=True)
     sliced_flops = 21.0 * (one + two)
     ach = sliced_flops / (ms_theta * 1e-3) / 1e12
@@ -313,12 +315,15 @@ def bench_sem(args, timed):
                         "flops_rule": "21 slice products x the FP64 flops of the operator's products",
                         "fp64_equivalent_tflops": (one + two) / (ms_theta * 1e-3) / 1e12,
                         "peak_source": "bf16_tflops_sustained of measured (MEASURED_PEAKS.json, cuBLAS); the whole "
-                                       "operator call is timed (slicing, tables and densities included)"},
+                                       "operator call is timed (slicing, tables and densities included)",
+                        "mma_sync_bf16_ceiling_tflops": mma_ceiling, "frac_of_mma_sync_ceiling": ach / mma_ceiling,
+                        "ceiling_source": "register-only mma.sync m16n8k16 BF16 loop, measured live by "
+                                          "paper_2511_11354_gb300/probe/pipe_peaks.cu"},
            "fp64_pipe_path": {"theta_ms": ms_theta_pipe, "bound": "alu", "achieved": ach64, "peak": peak64,
                               "unit": "TFLOP/s", "frac": ach64 / peak64, "flops_per_operator": one + two,
                               "two_body_share_of_flops": two / (one + two),
                               "peak_source": "fp64_dfma_tflops measured live by "
-                                             "paper_2511_11354_gb300/probe/fp64_peak.cu"},
+                                             "paper_2511_11354_gb300/probe/pipe_peaks.cu"},
            "mass_drift": (ob.mass - ob0.mass) / ob0.mass, "energy": ob.energy,
            "correlation_entropy": s_corr, "occupations_top3": [float(v) for v in occ[:3]], "occupations_ms": ms_occ}
     del d, out
@@ -620,7 +625,7 @@ def main():
     ms_pipe = max_over_ranks(p0.elapsed_time(p1))
     kprof_pipe = pipe.step_profile(min(kp, 20))
     pipe.close()
-    peaks = _fp64_peak()
+    peaks = _pipe_peaks()
     k_theta_pipe = 0.5 * (kprof_pipe[2] + kprof_pipe[7])
 
     # ---- end to end through the C ABI: pinned host state in, observables out.
@@ -676,7 +681,12 @@ def main():
                                        "flop per point)",
                          "executed_mma_flops_per_launch": exec_flops,
                          "fp64_equivalent_tflops": fp64_flops / (k_theta * 1e-3) / 1e12,
-                         "ms_per_launch": k_theta},
+                         "ms_per_launch": k_theta,
+                         "mma_sync_bf16_ceiling_tflops": peaks["mma_sync_bf16_tflops"],
+                         "executed_frac_of_mma_sync_ceiling":
+                             exec_flops / (k_theta * 1e-3) / 1e12 / peaks["mma_sync_bf16_tflops"],
+                         "ceiling_source": "register-only mma.sync m16n8k16 BF16 loop, measured live by "
+                                           "paper_2511_11354_gb300/probe/pipe_peaks.cu"},
             "roofline_shift": {"bound": "hbm", "kernel": "k_adv_df<64,1,1> (x1 lines, double-float)",
                                "achieved": shift_bytes / (k_shift * 1e-3) / 1e9,
                                "peak": MEASURED_HBM_GBS(), "unit": "GB/s",
@@ -692,7 +702,7 @@ def main():
                 "kernel_ms": dict(zip(w2.STEP_KERNELS, [float(x) for x in kprof_pipe])),
                 "theta_fp64_tflops": fp64_flops / (k_theta_pipe * 1e-3) / 1e12,
                 "fp64_dmma_peak_tflops": peaks["fp64_dmma_tflops"], "fp64_dfma_peak_tflops": peaks["fp64_dfma_tflops"],
-                "peak_source": "measured live by paper_2511_11354_gb300/probe/fp64_peak.cu"},
+                "peak_source": "measured live by paper_2511_11354_gb300/probe/pipe_peaks.cu"},
             "observables": {"mass": ob.mass, "energy": ob.energy, "entropy_lin": ob.entropy_lin,
                             "status": ob.status, "correlation_entropy": s_corr,
                             "occupations_top3": [float(v) for v in occ[:3]],

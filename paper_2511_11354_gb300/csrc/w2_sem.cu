@@ -204,7 +204,7 @@ extern "C" w2_status w2_sem_create(const w2_sem_config *cfg, void *cuda_stream, 
   std::vector<float2> cpdf(nx), wtsdf(4 * np);
   auto pair = [](double v) { const float h = (float)v; return make_float2(h, (float)(v - (double)h)); };
   for (int i = 0; i < nx; ++i) cpdf[i] = pair(cp[i]);
-  for (int j = 0; j < 4 * np; ++j) wtsdf[j] = pair(wts[j]);
+  for (int j = 0; j < 4 * np; ++j) wtsdf[j] = pair(6.0 * wts[j]);  // the double-float solve runs on eta / 6
   std::vector<float2> fwdc(28), bwdc(28);
   {
     const double cs = 2.0 - sqrt(3.0);

@@ -78,8 +78,8 @@ struct SemAdvArgs {
   const double *cp;     // [nx] Thomas factors c'_i of the (1,4,1) interior system
   const int *k0;        // [np] integer part of the foot offset
   const double *wts;    // [np][4] B-spline weights
-  const float2 *cpdf = nullptr;   // the same factors and weights as double-float (hi, lo) pairs
-  const float2 *wtsdf = nullptr;
+  const float2 *cpdf = nullptr;   // the same factors as double-float (hi, lo) pairs
+  const float2 *wtsdf = nullptr;  // 6 times the weights, as pairs (the pair solve runs on eta / 6)
   const float2 *fwdc = nullptr;   // [28] (-1)^k c*^(k+1) and (-c*)^k, c* = 2 - sqrt(3), as pairs
   const float2 *bwdc = nullptr;
 };

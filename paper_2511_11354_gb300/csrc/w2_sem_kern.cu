@@ -329,10 +329,13 @@ __device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a
 // The shift of k_sem_adv with the line values held as double-float pairs in
 // shared memory: the FP64 pipe of this GPU runs at about 1/64 of the FP32
 // rate, and the recursion plus the evaluation cost about seven FP64
-// operations per value.  Each column keeps three rows below and above the
-// line (zero, zero, ghost | ghost, zero, zero), so a foot index is clamped
-// into [-3, N + 3] instead of branched on; thread t works on column t % C and
-// rows t / C + 4 k.
+// operations per value.  The solve runs on h = eta / 6 (the factor 6 of the
+// (1, 4, 1) system moves into the B-spline weights, which the caller passes
+// as 6 w): g_i = (f_i - [i==1] f_0/6 - [i==N-1] f_N/6 - g_{i-1}) c'_i,
+// h_i = g_i - c'_i h_{i+1}, h_0 = f_0 / 6, h_N = f_N / 6.  Each column keeps
+// three rows below and above the line (zero, zero, ghost | ghost, zero,
+// zero), so a foot index is clamped into [-3, N + 3] instead of branched on;
+// thread t works on column t % C and rows t / C + 4 k.
 constexpr int kStart = 28, kPieceMin = 48;
 
 template <int AXIS>
@@ -357,49 +360,51 @@ __global__ void __launch_bounds__(256) k_sem_adv_df(SemAdvArgs a) {
     col[-3 * C] = z; col[-2 * C] = z; col[(N + 2) * C] = z; col[(N + 3) * C] = z;
   }
   __syncthreads();
-  const float2 six = make_float2(6.f, 0.f), two = make_float2(2.f, 0.f);
+  const float2 sixth = make_float2(0.1666666716337204f, -4.967053879312289e-09f), two = make_float2(2.f, 0.f);
   if (N - 1 < 4 * kPieceMin) {  // short lines: one thread per column
     if (r0 == 0 && live) {
-      const float2 f0 = col[0], fN = col[N * C];
-      // forward: d'_i = (r_i - d'_{i-1}) c'_i, r_i = 6 f_i - [i==1] f_0 - [i==N-1] f_N
-      float2 dprev = df_mulv(df_add(df_mulv(col[C], six), df_neg(f0)), a.cpdf[1]);
-      if (N - 1 == 1) dprev = df_mulv(df_add(df_add(df_mulv(col[C], six), df_neg(f0)), df_neg(fN)), a.cpdf[1]);
+      const float2 f0 = df_mulv(col[0], sixth), fN = df_mulv(col[N * C], sixth);
+      // forward: g_i = (r_i - g_{i-1}) c'_i, r_i = f_i - [i==1] f_0/6 - [i==N-1] f_N/6
+      float2 dprev = df_mulv(df_add(col[C], df_neg(f0)), a.cpdf[1]);
+      if (N - 1 == 1) dprev = df_mulv(df_add(df_add(col[C], df_neg(f0)), df_neg(fN)), a.cpdf[1]);
       col[C] = dprev;
       for (int i = 2; i <= N - 2; ++i) {
-        dprev = df_mulv(df_add(df_mulv(col[i * C], six), df_neg(dprev)), a.cpdf[i]);
+        dprev = df_mulv(df_add(col[i * C], df_neg(dprev)), a.cpdf[i]);
         col[i * C] = dprev;
       }
       if (N - 1 >= 2) {
         const int i = N - 1;
-        dprev = df_mulv(df_add(df_add(df_mulv(col[i * C], six), df_neg(fN)), df_neg(dprev)), a.cpdf[i]);
+        dprev = df_mulv(df_add(df_add(col[i * C], df_neg(fN)), df_neg(dprev)), a.cpdf[i]);
         col[i * C] = dprev;
       }
-      // backward: eta_{N-1} = d'_{N-1}, eta_i = d'_i - c'_i eta_{i+1}
+      // backward: h_{N-1} = g_{N-1}, h_i = g_i - c'_i h_{i+1}
       float2 enext = dprev;
       for (int i = N - 2; i >= 1; --i) {
         enext = df_add(col[i * C], df_neg(df_mulv(a.cpdf[i], enext)));
         col[i * C] = enext;
       }
-      col[-C] = df_add(df_mulv(col[0], two), df_neg(col[C]));
-      col[(N + 1) * C] = df_add(df_mulv(col[N * C], two), df_neg(col[(N - 1) * C]));
+      col[0] = f0;
+      col[N * C] = fN;
+      col[-C] = df_add(df_mulv(f0, two), df_neg(col[C]));
+      col[(N + 1) * C] = df_add(df_mulv(fN, two), df_neg(col[(N - 1) * C]));
     }
   } else {
     // Four threads per column, one piece [lo, hi) of the interior rows each.
     // Where c'_i has settled to c* = 2 - sqrt(3), the recursions unroll into
     // geometric sums, so piece p > 0 starts its forward pass from
-    // d'_{lo-1} = sum_{k<kStart} (-1)^k c*^(k+1) 6 f_{lo-1-k} and piece p < 3
-    // its backward pass from eta_hi = sum_k (-c*)^k d'_{hi+k} (kStart = 28
+    // g_{lo-1} = sum_{k<kStart} (-1)^k c*^(k+1) f_{lo-1-k} and piece p < 3
+    // its backward pass from h_hi = sum_k (-c*)^k g_{hi+k} (kStart = 28
     // terms: the tail is below 2^-53 of the scale).  The start values are
     // read before any piece overwrites its rows.
     const int n = N - 1, lo = 1 + (r0 * n) / 4, hi = 1 + ((r0 + 1) * n) / 4;
     float2 dprev = make_float2(0.f, 0.f);
     if (live && r0 > 0)
-      for (int k = 0; k < kStart; ++k) dprev = df_add(dprev, df_mulv(a.fwdc[k], df_mulv(col[(lo - 1 - k) * C], six)));
-    const float2 f0 = col[0], fN = col[N * C];
+      for (int k = 0; k < kStart; ++k) dprev = df_add(dprev, df_mulv(a.fwdc[k], col[(lo - 1 - k) * C]));
+    const float2 f0 = df_mulv(col[0], sixth), fN = df_mulv(col[N * C], sixth);
     __syncthreads();
     if (live) {
       for (int i = lo; i < hi; ++i) {
-        float2 r = df_mulv(col[i * C], six);
+        float2 r = col[i * C];
         if (i == 1) r = df_add(r, df_neg(f0));
         if (i == N - 1) r = df_add(r, df_neg(fN));
         dprev = df_mulv(df_add(r, df_neg(dprev)), a.cpdf[i]);
@@ -424,8 +429,10 @@ __global__ void __launch_bounds__(256) k_sem_adv_df(SemAdvArgs a) {
     }
     __syncthreads();
     if (live && r0 == 0) {
-      col[-C] = df_add(df_mulv(col[0], two), df_neg(col[C]));
-      col[(N + 1) * C] = df_add(df_mulv(col[N * C], two), df_neg(col[(N - 1) * C]));
+      col[0] = f0;
+      col[N * C] = fN;
+      col[-C] = df_add(df_mulv(f0, two), df_neg(col[C]));
+      col[(N + 1) * C] = df_add(df_mulv(fN, two), df_neg(col[(N - 1) * C]));
     }
   }
   __syncthreads();
@@ -438,8 +445,18 @@ __global__ void __launch_bounds__(256) k_sem_adv_df(SemAdvArgs a) {
     const int nu = i + k0 - 1;
     const float2 e0 = col[min(max(nu, -3), N + 3) * C], e1 = col[min(max(nu + 1, -3), N + 3) * C];
     const float2 e2 = col[min(max(nu + 2, -3), N + 3) * C], e3 = col[min(max(nu + 3, -3), N + 3) * C];
-    const float2 v = df_add(df_add(df_mulv(w0, e0), df_mulv(w1, e1)), df_add(df_mulv(w2, e2), df_mulv(w3, e3)));
-    dst[i * stride] = w2::df_join(v.x, v.y);
+    // sum_q (6 w_q) h_q: exact products of the high parts plus cross terms,
+    // accumulated without normalising in between (one normalisation at the end)
+    float sh, se, ph, pe, h, l;
+    w2::df_mul(w0.x, w0.y, e0.x, e0.y, sh, se);
+    w2::df_mul(w1.x, w1.y, e1.x, e1.y, ph, pe);
+    w2::df_acc(sh, se, ph, pe);
+    w2::df_mul(w2.x, w2.y, e2.x, e2.y, ph, pe);
+    w2::df_acc(sh, se, ph, pe);
+    w2::df_mul(w3.x, w3.y, e3.x, e3.y, ph, pe);
+    w2::df_acc(sh, se, ph, pe);
+    w2::fast_two_sum(sh, se, h, l);
+    dst[i * stride] = w2::df_join(h, l);
   }
 }
 

@@ -338,6 +338,16 @@ __device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a
 // thread t works on column t % C and rows t / C + 4 k.
 constexpr int kStart = 28, kPieceMin = 48;
 
+// 8-byte asynchronous copy global -> shared; the wait covers the calling
+// thread's own copies.
+__device__ __forceinline__ void sem_cp_async8(void *dst, const void *src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void sem_cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 template <int AXIS>
 __global__ void __launch_bounds__(256) k_sem_adv_df(SemAdvArgs a) {
   extern __shared__ float2 sf[];
@@ -353,87 +363,68 @@ __global__ void __launch_bounds__(256) k_sem_adv_df(SemAdvArgs a) {
   float2 *col = sf + 3 * C + c;  // row nu of this column at col[nu * C], nu in [-3, N + 3]
   const bool live = c < width;
   const double *src = a.in + base + c0 + c;
-  if (live)
-    for (int i = r0; i < nx; i += 4) col[i * C] = w2::df_split(src[i * stride]);
+  // stage the column's rows with 8-byte asynchronous copies (all in flight at
+  // once), then split each FP64 value into a pair in place (same 8 bytes)
+  if (live) {
+    for (int i = r0; i < nx; i += 4) sem_cp_async8(col + i * C, src + i * stride);
+    sem_cp_async_wait_all();
+    for (int i = r0; i < nx; i += 4) col[i * C] = w2::df_split(*reinterpret_cast<const double *>(col + i * C));
+  }
   if (r0 == 0) {
     const float2 z = make_float2(0.f, 0.f);
     col[-3 * C] = z; col[-2 * C] = z; col[(N + 2) * C] = z; col[(N + 3) * C] = z;
   }
   __syncthreads();
   const float2 sixth = make_float2(0.1666666716337204f, -4.967053879312289e-09f), two = make_float2(2.f, 0.f);
-  if (N - 1 < 4 * kPieceMin) {  // short lines: one thread per column
-    if (r0 == 0 && live) {
-      const float2 f0 = df_mulv(col[0], sixth), fN = df_mulv(col[N * C], sixth);
-      // forward: g_i = (r_i - g_{i-1}) c'_i, r_i = f_i - [i==1] f_0/6 - [i==N-1] f_N/6
-      float2 dprev = df_mulv(df_add(col[C], df_neg(f0)), a.cpdf[1]);
-      if (N - 1 == 1) dprev = df_mulv(df_add(df_add(col[C], df_neg(f0)), df_neg(fN)), a.cpdf[1]);
-      col[C] = dprev;
-      for (int i = 2; i <= N - 2; ++i) {
-        dprev = df_mulv(df_add(col[i * C], df_neg(dprev)), a.cpdf[i]);
-        col[i * C] = dprev;
-      }
-      if (N - 1 >= 2) {
-        const int i = N - 1;
-        dprev = df_mulv(df_add(df_add(col[i * C], df_neg(fN)), df_neg(dprev)), a.cpdf[i]);
-        col[i * C] = dprev;
-      }
-      // backward: h_{N-1} = g_{N-1}, h_i = g_i - c'_i h_{i+1}
-      float2 enext = dprev;
-      for (int i = N - 2; i >= 1; --i) {
-        enext = df_add(col[i * C], df_neg(df_mulv(a.cpdf[i], enext)));
-        col[i * C] = enext;
-      }
-      col[0] = f0;
-      col[N * C] = fN;
-      col[-C] = df_add(df_mulv(f0, two), df_neg(col[C]));
-      col[(N + 1) * C] = df_add(df_mulv(fN, two), df_neg(col[(N - 1) * C]));
+  // P threads per column (P = 1 .. 4), one piece [lo, hi) of the interior
+  // rows each; a piece holds at least kPieceMin rows.  Where c'_i has settled
+  // to c* = 2 - sqrt(3), the recursions unroll into geometric sums, so piece
+  // p > 0 starts its forward pass from
+  // g_{lo-1} = sum_{k<kStart} (-1)^k c*^(k+1) f_{lo-1-k} and piece p < P - 1
+  // its backward pass from h_hi = sum_k (-c*)^k g_{hi+k} (kStart = 28 terms:
+  // the tail is below 2^-53 of the scale).  The start values are read before
+  // any piece overwrites its rows.  With P = 1 this is the plain two-pass
+  // solve.
+  const int n = N - 1;
+  const int P = max(1, min(4, n / kPieceMin));
+  const bool work = live && r0 < P;
+  const int lo = 1 + (r0 * n) / P, hi = 1 + ((r0 + 1) * n) / P;
+  float2 dprev = make_float2(0.f, 0.f);
+  if (work && r0 > 0)
+    for (int k = 0; k < kStart; ++k) dprev = df_add(dprev, df_mulv(a.fwdc[k], col[(lo - 1 - k) * C]));
+  const float2 f0 = df_mulv(col[0], sixth), fN = df_mulv(col[N * C], sixth);
+  __syncthreads();
+  if (work) {  // g_i = (r_i - g_{i-1}) c'_i, r_i = f_i - [i==1] f_0/6 - [i==N-1] f_N/6
+    for (int i = lo; i < hi; ++i) {
+      float2 r = col[i * C];
+      if (i == 1) r = df_add(r, df_neg(f0));
+      if (i == N - 1) r = df_add(r, df_neg(fN));
+      dprev = df_mulv(df_add(r, df_neg(dprev)), a.cpdf[i]);
+      col[i * C] = dprev;
     }
-  } else {
-    // Four threads per column, one piece [lo, hi) of the interior rows each.
-    // Where c'_i has settled to c* = 2 - sqrt(3), the recursions unroll into
-    // geometric sums, so piece p > 0 starts its forward pass from
-    // g_{lo-1} = sum_{k<kStart} (-1)^k c*^(k+1) f_{lo-1-k} and piece p < 3
-    // its backward pass from h_hi = sum_k (-c*)^k g_{hi+k} (kStart = 28
-    // terms: the tail is below 2^-53 of the scale).  The start values are
-    // read before any piece overwrites its rows.
-    const int n = N - 1, lo = 1 + (r0 * n) / 4, hi = 1 + ((r0 + 1) * n) / 4;
-    float2 dprev = make_float2(0.f, 0.f);
-    if (live && r0 > 0)
-      for (int k = 0; k < kStart; ++k) dprev = df_add(dprev, df_mulv(a.fwdc[k], col[(lo - 1 - k) * C]));
-    const float2 f0 = df_mulv(col[0], sixth), fN = df_mulv(col[N * C], sixth);
-    __syncthreads();
-    if (live) {
-      for (int i = lo; i < hi; ++i) {
-        float2 r = col[i * C];
-        if (i == 1) r = df_add(r, df_neg(f0));
-        if (i == N - 1) r = df_add(r, df_neg(fN));
-        dprev = df_mulv(df_add(r, df_neg(dprev)), a.cpdf[i]);
-        col[i * C] = dprev;
-      }
+  }
+  __syncthreads();
+  float2 enext = make_float2(0.f, 0.f);
+  if (work && r0 < P - 1)
+    for (int k = 0; k < kStart && hi + k <= N - 1; ++k) enext = df_add(enext, df_mulv(a.bwdc[k], col[(hi + k) * C]));
+  __syncthreads();
+  if (work) {  // h_{N-1} = g_{N-1}, h_i = g_i - c'_i h_{i+1}
+    int i = hi - 1;
+    if (r0 == P - 1) {
+      enext = col[i * C];
+      --i;
     }
-    __syncthreads();
-    float2 enext = make_float2(0.f, 0.f);
-    if (live && r0 < 3)
-      for (int k = 0; k < kStart && hi + k <= N - 1; ++k) enext = df_add(enext, df_mulv(a.bwdc[k], col[(hi + k) * C]));
-    __syncthreads();
-    if (live) {
-      int i = hi - 1;
-      if (r0 == 3) {  // eta_{N-1} = d'_{N-1}
-        enext = col[i * C];
-        --i;
-      }
-      for (; i >= lo; --i) {
-        enext = df_add(col[i * C], df_neg(df_mulv(a.cpdf[i], enext)));
-        col[i * C] = enext;
-      }
+    for (; i >= lo; --i) {
+      enext = df_add(col[i * C], df_neg(df_mulv(a.cpdf[i], enext)));
+      col[i * C] = enext;
     }
-    __syncthreads();
-    if (live && r0 == 0) {
-      col[0] = f0;
-      col[N * C] = fN;
-      col[-C] = df_add(df_mulv(f0, two), df_neg(col[C]));
-      col[(N + 1) * C] = df_add(df_mulv(fN, two), df_neg(col[(N - 1) * C]));
-    }
+  }
+  __syncthreads();
+  if (live && r0 == 0) {
+    col[0] = f0;
+    col[N * C] = fN;
+    col[-C] = df_add(df_mulv(f0, two), df_neg(col[C]));
+    col[(N + 1) * C] = df_add(df_mulv(fN, two), df_neg(col[(N - 1) * C]));
   }
   __syncthreads();
   if (!live) return;

@@ -100,11 +100,13 @@ def test_theta_terms_separately(which, prec):
 
 
 @pytest.mark.parametrize("prec", ["W2_F64", "W2_F64_SLICED"])
-@pytest.mark.parametrize("case", CASES[:3] + [(201, 2, 4, 30.0, "IV")])
+@pytest.mark.parametrize("case", CASES[:3] + [(101, 2, 4, 30.0, "IV"), (151, 2, 4, 30.0, "IV"),
+                                   (201, 2, 4, 30.0, "IV")])
 def test_advect_parity(case, prec):
     """The FP64-pipe context shifts in FP64, the sliced one in double-float
-    pairs (about 2^-47 per operation); at 201 points per line the sliced
-    shift solves each line in four pieces started from geometric sums."""
+    pairs (about 2^-47 per operation); at 101, 151 and 201 points per line
+    the sliced shift solves each line in two, three and four pieces started
+    from geometric sums."""
     prob, f = _case(*case)
     prob.dt = 0.37  # feet several cells away, some outside the box
     ctx = _ctx(prob, prec)

@@ -82,6 +82,11 @@ __device__ __forceinline__ void mma5_b3(float (&big)[4], float (&small)[4], cons
   mma_tf32(big, fh, kh);
 }
 
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+
 template <int NK>
 struct Theta32Smem {
   static constexpr int S = NK + 8;  // padded row stride (floats): conflict-free B fragments
@@ -123,19 +128,31 @@ __device__ __noinline__ void theta32_block(const Theta32Args &a, const int X, ui
   const int bfirst = part * NTH;
   const size_t base = (size_t)X * NK * NK;
   {
+    // the raw block goes to the Fl buffer by 16-byte asynchronous copies (all
+    // in flight together, overlapping the kernel-table loads); each thread
+    // then splits the values it copied into their TF32 parts in place
     const float4 *src = reinterpret_cast<const float4 *>(a.in + base);
     for (int e = tid; e < NK * NK / 4; e += blockDim.x) {
-      const float4 v = src[e];
       const int r = (4 * e) / NK, c = 4 * e - r * NK;
-      split_tf32(v.x, Fh[r * S + c], Fl[r * S + c]);
-      split_tf32(v.y, Fh[r * S + c + 1], Fl[r * S + c + 1]);
-      split_tf32(v.z, Fh[r * S + c + 2], Fl[r * S + c + 2]);
-      split_tf32(v.w, Fh[r * S + c + 3], Fl[r * S + c + 3]);
+      cp_async16(Fl + r * S + c, src + e);
     }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
     for (int j = tid; j < W; j += blockDim.x) {
       split3_tf32_d(a.K1[(size_t)i1 * W + j], k1h[j], k1m[j], k1l[j]);
       split3_tf32_d(a.K2[(size_t)i2 * W + j], k2h[j], k2m[j], k2l[j]);
       split3_tf32_d(a.K12[(size_t)dd * W + j], k12h[j], k12m[j], k12l[j]);
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    for (int e = tid; e < NK * NK / 4; e += blockDim.x) {
+      const int r = (4 * e) / NK, c = 4 * e - r * NK;
+      const float4 v = *reinterpret_cast<const float4 *>(Fl + r * S + c);
+      uint4 h, l;
+      split_tf32(v.x, h.x, l.x);
+      split_tf32(v.y, h.y, l.y);
+      split_tf32(v.z, h.z, l.z);
+      split_tf32(v.w, h.w, l.w);
+      *reinterpret_cast<uint4 *>(Fh + r * S + c) = h;
+      *reinterpret_cast<uint4 *>(Fl + r * S + c) = l;
     }
   }
   __syncthreads();
@@ -432,11 +449,6 @@ struct AdvCols {
   static constexpr int C = NK >= 64 ? 64 : NK;
   static constexpr int blocks = NK / C;
 };
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
-}
 
 // Stage rows i = 0..nx-1 of C contiguous floats (global stride lineStride)
 // into rows kGhost + i of a shared slab of stride C, 16 bytes per copy, all

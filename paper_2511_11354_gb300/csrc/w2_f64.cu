@@ -34,75 +34,89 @@ __device__ __forceinline__ double phi_xc(int kind, double n) {
   return 0.0;
 }
 
+// Sum of term(k) over k in [0, len), split over the four lanes of a quad
+// (lane r of the quad takes k = r, r + 4, ...) and combined by two xor
+// shuffles, so the bits do not depend on the block size.  Every lane of the
+// warp calls it; valid = false contributes zero.
+template <typename F>
+__device__ __forceinline__ double quad_sum(bool valid, int len, F term) {
+  const int r = threadIdx.x & 3;
+  double s = 0.0;
+  if (valid) {
+#pragma unroll 4
+    for (int k = r; k < len; k += 4) s += term(k);
+  }
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  return s;
+}
+
 // grid: (nx, 2) for one-body kernels (blockIdx.y = particle), (nx, 1) for the
-// pair kernel.  Dynamic shared memory: (nx + M) doubles.
+// pair kernel.  Dynamic shared memory: (nx + M) doubles; 512 threads.
 // compiled once (not inlined) so the single-problem and batched kernels
 // run the same machine code and give identical bits
 __device__ __noinline__ void tables_block(const TabArgs &a, const int i, const int part, double *sm) {
   const int nx = a.nx, nk = a.nk, M = a.M;
   double *n = sm, *U = sm + nx;
-  const int tid = threadIdx.x;
+  const int quads = blockDim.x >> 2, qd = threadIdx.x >> 2;
+  const bool lead = (threadIdx.x & 3) == 0;
   const bool mf = !a.pair_mode && a.xsum && (a.c_h != 0.0 || (a.c_xc != 0.0 && a.xc_kind));
+  // one quad per item; the item loops run the same number of rounds in every
+  // thread (the quads' shuffles need all lanes)
   if (mf) {
     const double w = a.dx * a.dp * a.dp;
-    for (int q = tid; q < nx; q += blockDim.x) {
-      double s = 0.0;
-      // unrolled loops issue their loads ahead; the additions keep their order
-      if (part == 0) {
-#pragma unroll 8
-        for (int k = 0; k < nx; ++k) s += a.xsum[(size_t)q * nx + k];
-      } else {
-#pragma unroll 8
-        for (int k = 0; k < nx; ++k) s += a.xsum[(size_t)k * nx + q];
-      }
-      n[q] = s * w;
+    for (int b = 0; b < nx; b += quads) {
+      const int q = b + qd;
+      const double s = quad_sum(q < nx, nx, [&](int k) {
+        return part == 0 ? a.xsum[(size_t)q * nx + k] : a.xsum[(size_t)k * nx + q];
+      });
+      if (lead && q < nx) n[q] = s * w;
     }
   }
   __syncthreads();
-  for (int l = tid; l < M; l += blockDim.x) {
-    double u;
+  for (int b = 0; b < M; b += quads) {
+    const int l = b + qd;
+    const bool v = l < M;
+    double u = 0.0;
     if (a.pair_mode) {
-      u = a.gamma * a.w_fine[(size_t)i * M + l];
+      if (v) u = a.gamma * a.w_fine[(size_t)i * M + l];
     } else {
-      u = a.vext_fine[(size_t)i * M + l];
+      if (v) u = a.vext_fine[(size_t)i * M + l];
       if (mf && a.c_h != 0.0) {
         const double *ker = a.h_fine ? a.h_fine : a.w_fine;  // Poisson kernel, or W scaled below
-        double vh = 0.0;
-#pragma unroll 8
-        for (int q = 0; q < nx; ++q) {
+        const double vh = quad_sum(v, nx, [&](int q) {
           int d = i - q;
           d += (d < 0) ? nx : 0;
-          vh += ker[(size_t)d * M + l] * n[q];
-        }
+          return ker[(size_t)d * M + l] * n[q];
+        });
         u += a.c_h * (a.h_fine ? 1.0 : a.gamma * a.dx) * vh;
       }
       if (mf && a.c_xc != 0.0 && a.xc_kind) {
-        double ni = 0.0;
-#pragma unroll 8
-        for (int q = 0; q < nx; ++q) {
+        const double ni = quad_sum(v, nx, [&](int q) {
           int d = i - q;
           d += (d < 0) ? nx : 0;
-          ni += a.d_fine[(size_t)d * M + l] * n[q];
-        }
+          return a.d_fine[(size_t)d * M + l] * n[q];
+        });
         u += a.c_xc * phi_xc(a.xc_kind, ni);
       }
     }
-    U[l] = u;
+    if (lead && v) U[l] = u;
   }
   __syncthreads();
   const int W = 2 * nk - 1;
   double *K = a.K + ((size_t)part * nx + i) * W;
   const double inv = 1.0 / (a.hbar * nk);
-  for (int j = tid; j < nk; j += blockDim.x) {
-    double s = 0.0;
-#pragma unroll 8
-    for (int l = 1; l < nk; ++l) {
-      int m = (l * j) % M;
-      s += (U[l] - U[M - l]) * a.sintab[m];
+  for (int b = 0; b < nk; b += quads) {
+    const int j = b + qd;
+    double s = quad_sum(j < nk, nk - 1, [&](int k) {
+      const int l = k + 1;
+      return (U[l] - U[M - l]) * a.sintab[(l * j) % M];
+    });
+    if (lead && j < nk) {
+      s *= inv;
+      K[nk - 1 + j] = s;
+      K[nk - 1 - j] = -s;
     }
-    s *= inv;
-    K[nk - 1 + j] = s;
-    K[nk - 1 - j] = -s;
   }
 }
 
@@ -128,14 +142,14 @@ __global__ void k_btables(const TabArgs *args, const int *off, int n) {
 
 cudaError_t launch_btables(const TabArgs *args, const int *off, int n, int grid, int nxmax, int mmax,
                            cudaStream_t s) {
-  k_btables<<<grid, 128, sizeof(double) * (nxmax + mmax), s>>>(args, off, n);
+  k_btables<<<grid, 512, sizeof(double) * (nxmax + mmax), s>>>(args, off, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tables(const TabArgs &a, cudaStream_t s) {
   dim3 grid(a.nx, a.pair_mode ? 1 : 2);
   size_t smem = sizeof(double) * (a.nx + a.M);
-  k_tables<<<grid, 128, smem, s>>>(a);
+  k_tables<<<grid, 512, smem, s>>>(a);
   return cudaGetLastError();
 }
 

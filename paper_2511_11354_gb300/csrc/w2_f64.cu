@@ -34,23 +34,6 @@ __device__ __forceinline__ double phi_xc(int kind, double n) {
   return 0.0;
 }
 
-// Sum of term(k) over k in [0, len), split over the four lanes of a quad
-// (lane r of the quad takes k = r, r + 4, ...) and combined by two xor
-// shuffles, so the bits do not depend on the block size.  Every lane of the
-// warp calls it; valid = false contributes zero.
-template <typename F>
-__device__ __forceinline__ double quad_sum(bool valid, int len, F term) {
-  const int r = threadIdx.x & 3;
-  double s = 0.0;
-  if (valid) {
-#pragma unroll 4
-    for (int k = r; k < len; k += 4) s += term(k);
-  }
-  s += __shfl_xor_sync(0xffffffffu, s, 1);
-  s += __shfl_xor_sync(0xffffffffu, s, 2);
-  return s;
-}
-
 // grid: (nx, 2) for one-body kernels (blockIdx.y = particle), (nx, 1) for the
 // pair kernel.  Dynamic shared memory: (nx + M) doubles; 512 threads.
 // compiled once (not inlined) so the single-problem and batched kernels

@@ -7,6 +7,24 @@
 
 namespace w2 {
 
+// Sum of term(k) over k in [0, len), split over the four lanes of a quad
+// (lane r of the quad takes k = r, r + 4, ...) and combined by two xor
+// shuffles, so the bits do not depend on the block size.  Every lane of the
+// warp calls it; valid = false contributes zero.
+template <typename F>
+__device__ __forceinline__ double quad_sum(bool valid, int len, F term) {
+  const int r = threadIdx.x & 3;
+  double s = 0.0;
+  if (valid) {
+#pragma unroll 4
+    for (int k = r; k < len; k += 4) s += term(k);
+  }
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  return s;
+}
+
+
 // Static one-body / pair potential samples and the per-call densities that
 // build the kernels K(x, j) of the pseudo-difference operator (Sec. 3.1):
 //   K(x, j) = 1/(hbar nk) sum_{l=1}^{nk-1} [U(x + l h') - U(x - l h')] sin(pi l j / nk)

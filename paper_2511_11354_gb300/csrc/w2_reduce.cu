@@ -220,12 +220,13 @@ __global__ void __launch_bounds__(256) k_obs_mid(ObsArgs a, double *mid) {
     a.out[8 + nx + (size_t)i * nx + i2] = xp[0] * a.dp * a.dp;
   }
   for (int i1 = tid; i1 < nx; i1 += 256) v[6] += a.xpart[((size_t)i1 * nx + i) * ld];
-  for (int r = tid; r < nk; r += 256) {
-    double sr = 0.0;
-#pragma unroll 8
-    for (int i2 = 0; i2 < nx; ++i2) sr += a.xpart[((size_t)i * nx + i2) * ld + 3 + r];
-    const double f1 = sr * a.dx * a.dp;
-    v[7] += f1 * f1;
+  for (int b = 0; b < nk; b += 64) {  // a quad of lanes per momentum row r
+    const int r = b + (tid >> 2);
+    const double sr = quad_sum(r < nk, nx, [&](int i2) { return a.xpart[((size_t)i * nx + i2) * ld + 3 + r]; });
+    if ((tid & 3) == 0 && r < nk) {
+      const double f1 = sr * a.dx * a.dp;
+      v[7] += f1 * f1;
+    }
   }
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
@@ -270,16 +271,19 @@ __global__ void k_obs_final(ObsArgs a, const double *mid) {
   // Hartree energy
   double eh = 0.0;
   if (a.c_h != 0.0) {
-    for (int i = tid; i < nx; i += nt) {
-      double va = 0.0, vb = 0.0;
-#pragma unroll 8
-      for (int q = 0; q < nx; ++q) {
-        int d = i - q;
-        d += (d < 0) ? nx : 0;
-        va += (a.h_fine ? a.h_fine : a.w_fine)[(size_t)d * M] * n1[q];
-        vb += (a.h_fine ? a.h_fine : a.w_fine)[(size_t)d * M] * n2[q];
-      }
-      eh += 0.5 * a.c_h * (a.h_fine ? 1.0 : a.gamma * a.dx) * (va * n1[i] + vb * n2[i]) * a.dx;
+    const double *ker = a.h_fine ? a.h_fine : a.w_fine;
+    for (int b = 0; b < nx; b += nt >> 2) {  // a quad of lanes per point i
+      const int i = b + (tid >> 2);
+      auto conv = [&](const double *n) {
+        return quad_sum(i < nx, nx, [&](int q) {
+          int d = i - q;
+          d += (d < 0) ? nx : 0;
+          return ker[(size_t)d * M] * n[q];
+        });
+      };
+      const double va = conv(n1), vb = conv(n2);
+      if ((tid & 3) == 0 && i < nx)
+        eh += 0.5 * a.c_h * (a.h_fine ? 1.0 : a.gamma * a.dx) * (va * n1[i] + vb * n2[i]) * a.dx;
     }
   }
   red[0][tid] = m0;

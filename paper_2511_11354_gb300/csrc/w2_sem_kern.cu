@@ -5,6 +5,7 @@
 #include <math.h>
 
 #include "w2_df.cuh"
+#include "w2_internal.cuh"
 #include "w2_sem.cuh"
 
 namespace w2sem {
@@ -169,14 +170,19 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
   return s;  // valid in thread 0
 }
 
+// xs[X] = sum_j1 w_j1 sum_j2 w_j2 f[X][j1][j2]: thread t keeps the column
+// j2 = t % np and walks the rows j1 = t / np + R k (R = 256 / np rows in
+// flight, np <= 256), one FP64 multiply-add per element; w_j2 is applied once.
 __global__ void __launch_bounds__(256) k_sem_xsum(int np, const double *__restrict__ f, const double *__restrict__ w,
                                                   double *xs) {
   __shared__ double red[8];
   const long long X = blockIdx.x;
   const double *fx = f + X * np * np;
+  const int R = 256 / np, j2 = threadIdx.x % np, r0 = threadIdx.x / np;
   double acc = 0.0;
-  for (int e = threadIdx.x; e < np * np; e += 256) acc = fma(w[e / np] * w[e % np], fx[e], acc);
-  const double s = block_sum<256>(acc, red);
+  if (r0 < R)
+    for (int j1 = r0; j1 < np; j1 += R) acc = fma(w[j1], fx[j1 * np + j2], acc);
+  const double s = block_sum<256>(acc * w[j2], red);
   if (threadIdx.x == 0) xs[X] = s;
 }
 
@@ -567,12 +573,13 @@ __global__ void __launch_bounds__(256) k_sem_obs_mid(SemObsArgs a, double *mid) 
     e += xp[1] + xp[0] * (a.vext[i1] + a.vext[i2] + a.gamma * a.wgrid[i1 - i2 + W0]);
     nc += a.xpart[((long long)i2 * nx + i1) * (4 + np)];
   }
-  for (int j1 = threadIdx.x; j1 < np; j1 += 256) {
-    double f1 = 0.0;
-#pragma unroll 8
-    for (int i2 = 0; i2 < nx; ++i2) f1 += xrow[(long long)i2 * (4 + np) + 4 + j1];
-    f1 *= a.dx;
-    pu = fma(a.w[j1] * f1, f1, pu);
+  for (int b = 0; b < np; b += 64) {  // a quad of lanes per momentum row j1
+    const int j1 = b + (threadIdx.x >> 2);
+    double f1 = w2::quad_sum(j1 < np, nx, [&](int i2) { return xrow[(long long)i2 * (4 + np) + 4 + j1]; });
+    if ((threadIdx.x & 3) == 0 && j1 < np) {
+      f1 *= a.dx;
+      pu = fma(a.w[j1] * f1, f1, pu);
+    }
   }
   m = block_sum<256>(m, red);
   e = block_sum<256>(e, red);

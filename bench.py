@@ -22,6 +22,7 @@ import signal
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -86,7 +87,7 @@ def _oracle_sample(prob_full, min_seconds):
 class ClockSampler:
     def __init__(self, index):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"w2_clocks_{os.getpid()}.csv")
         if shutil.which("nvidia-smi") is None:
             return
         os.makedirs(os.path.dirname(self.path), exist_ok=True)

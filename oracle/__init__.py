@@ -13,5 +13,5 @@ leak, exchange symmetry, integer rolls, spline Fourier multipliers),
 convergence to classical rotation in a harmonic well, and a brute-force
 two-particle Schroedinger evolution.
 """
-from .oracle import Oracle, build, lib_path  # noqa: F401
+from .oracle import Oracle, build, lib_path, variant  # noqa: F401
 from .sem_ref import SemOracle  # noqa: F401

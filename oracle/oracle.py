@@ -33,32 +33,65 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def _configure(lib):
+    """Declare the argument types of the oracle's entry points on ``lib``."""
+    lib.orc_create.restype = ctypes.c_void_p
+    lib.orc_create.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 7 + [
+        ctypes.c_int, ORC_FN, ctypes.c_void_p, ORC_FN, ctypes.c_void_p]
+    lib.orc_destroy.argtypes = [ctypes.c_void_p]
+    for name in ("orc_marginals",):
+        getattr(lib, name).argtypes = [ctypes.c_void_p, _dp, _dp, _dp]
+    lib.orc_potential_fine.argtypes = [ctypes.c_void_p, _dp, _dp]
+    lib.orc_theta_with.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, ctypes.c_int, _dp]
+    lib.orc_theta.argtypes = [ctypes.c_void_p, _dp, _dp]
+    _ip = ctypes.POINTER(ctypes.c_int)
+    lib.orc_theta_with_sample.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, ctypes.c_int, _ip, ctypes.c_int, _dp]
+    lib.orc_advect_sample.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, _ip, ctypes.c_int, _dp]
+    lib.orc_shift_line.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, _dp]
+    lib.orc_advect.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, _dp]
+    lib.orc_step.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int]
+    lib.orc_step.restype = ctypes.c_int
+    lib.orc_observables.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp]
+    lib.orc_threads.restype = ctypes.c_int
+    lib.orc_set_hartree_poisson.argtypes = [ctypes.c_void_p]
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            lib.orc_create.restype = ctypes.c_void_p
-            lib.orc_create.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 7 + [
-                ctypes.c_int, ORC_FN, ctypes.c_void_p, ORC_FN, ctypes.c_void_p]
-            lib.orc_destroy.argtypes = [ctypes.c_void_p]
-            for name in ("orc_marginals",):
-                getattr(lib, name).argtypes = [ctypes.c_void_p, _dp, _dp, _dp]
-            lib.orc_potential_fine.argtypes = [ctypes.c_void_p, _dp, _dp]
-            lib.orc_theta_with.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, ctypes.c_int, _dp]
-            lib.orc_theta.argtypes = [ctypes.c_void_p, _dp, _dp]
-            _ip = ctypes.POINTER(ctypes.c_int)
-            lib.orc_theta_with_sample.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, ctypes.c_int, _ip, ctypes.c_int, _dp]
-            lib.orc_advect_sample.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, _ip, ctypes.c_int, _dp]
-            lib.orc_shift_line.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, _dp]
-            lib.orc_advect.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, _dp]
-            lib.orc_step.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int]
-            lib.orc_step.restype = ctypes.c_int
-            lib.orc_observables.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp]
-            lib.orc_threads.restype = ctypes.c_int
-            lib.orc_set_hartree_poisson.argtypes = [ctypes.c_void_p]
-            _lib = lib
+            _lib = _configure(ctypes.CDLL(build()))
     return _lib
+
+
+_variants = {}
+
+
+def variant(name: str, replacements) -> ctypes.CDLL:
+    """A copy of the oracle with a planted mistake, for tests that show a pin
+    catches it: each (old, new) pair of ``replacements`` must occur exactly
+    once in ``w2_oracle.c``.  Compiled into ``_build/variants/<name>.so``."""
+    with _lock:
+        if name in _variants:
+            return _variants[name]
+        src = open(_SRC).read()
+        for old, new in replacements:
+            if src.count(old) != 1:
+                raise ValueError(f"variant {name}: {old!r} occurs {src.count(old)} times")
+            src = src.replace(old, new)
+        d = os.path.join(_HERE, "_build", "variants")
+        os.makedirs(d, exist_ok=True)
+        c_path = os.path.join(d, f"{name}.{os.getpid()}.c")
+        so = os.path.join(d, f"{name}.{os.getpid()}.so")
+        with open(c_path, "w") as fh:
+            fh.write(src)
+        subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", c_path, "-o", so, "-lm"],
+                       check=True)
+        lib = _configure(ctypes.CDLL(so))
+        os.remove(c_path)
+        _variants[name] = lib
+        return lib
 
 
 def _ptr(a: np.ndarray | None):
@@ -71,8 +104,8 @@ def _ptr(a: np.ndarray | None):
 class Oracle:
     """One problem instance: grid, potentials (sampled once), time step."""
 
-    def __init__(self, prob):
-        self.lib = _load()
+    def __init__(self, prob, lib=None):
+        self.lib = _load() if lib is None else lib
         self.prob = prob
         self._cb_ext = ORC_FN(lambda x, _u: float(prob.vext(x)))
         self._cb_ee = ORC_FN(lambda r, _u: float(prob.vee(r)))

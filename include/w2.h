@@ -162,6 +162,24 @@ w2_status w2_set_potentials(w2_ctx *ctx, w2_fn vext, void *ue, w2_fn vee, void *
  * W2_ERR_OOM, W2_ERR_CUDA. */
 w2_status w2_set_hartree(w2_ctx *ctx, int32_t kind);
 
+/* Distributed form of the characteristic shift (Sec. 4.2, local splines with
+ * perfectly matched boundary conditions): the x1 shift is cut into np1
+ * patches of nx / np1 points and the x2 shift into np2 patches (1: the global
+ * spline of Sec. 4.1).  Each patch solves its own spline over its points and
+ * G ghost points per side (G = 1 + the shift's whole cells), with the slopes
+ * of the global spline at the ends of that range as boundary rows; each slope
+ * is a 53-point stencil of the samples (coefficients below 2^-52 beyond), of
+ * which the part over a neighbouring patch is summed by that neighbour and
+ * handed over with the ghost samples, as one rank hands them to the next.
+ * All patches run in this process on this device, the hand-over going
+ * through device buffers; results equal the global spline shift to FP64
+ * rounding.  Applies to w2_step and w2_advect of a W2_F64 context until the
+ * next call (np1 = np2 = 1 restores the global spline).
+ * Errors: W2_ERR_ARG (np < 1), W2_ERR_UNSUPPORTED (another precision, nx not a
+ * multiple of np, or fewer than G + 26 points per patch), W2_ERR_OOM,
+ * W2_ERR_CUDA. */
+w2_status w2_set_patches(w2_ctx *ctx, int32_t np1, int32_t np2);
+
 /* Copy a full state f[nx][nx][nk][nk] (element type of the precision) into the context: from device
  * memory when on_device != 0, else from host memory.  Resets the step count.
  * Queued on the stream (a host source is copied with cudaMemcpyAsync, so a
@@ -227,9 +245,12 @@ w2_status w2_advect(w2_ctx *ctx, const void *f, void *out);
  * W2_STEP_KERNELS kernels directly (no graph) with a CUDA event pair on the
  * context's stream around each, and writes to kernel_ms[k] (host, length
  * W2_STEP_KERNELS) the mean duration in milliseconds of kernel k of a step:
- *   0 per-X sums of f^n   1 kernel tables (f^n)   2 Theta sweep, predictor
+ *   0 per-X sums of f^n (no launch: they come from the previous step's
+ *     corrector, or from w2_set_state / w2_use_staged_state; about 0)
+ *   1 kernel tables (f^n)   2 Theta sweep, predictor
  *   3 shift along x2      4 shift along x1 + Lawson combination
- *   5 per-X sums of f~    6 kernel tables (f~)    7 Theta sweep, corrector
+ *   5 per-X sums of f~    6 kernel tables (f~)
+ *   7 Theta sweep, corrector (with the per-X sums of f^{n+1})
  * The state advances exactly as with w2_step.  Synchronises the stream.
  * Errors: W2_ERR_ARG (nsteps <= 0 or kernel_ms NULL), W2_ERR_STATE, W2_ERR_CUDA. */
 #define W2_STEP_KERNELS 8
@@ -262,7 +283,10 @@ w2_status w2_step_profile(w2_ctx *ctx, int32_t nsteps, double *kernel_ms);
  * calls share the one array and every call rewrites all of it that it reads,
  * so nothing has to be cleared between calls, but calls that overlap on the
  * GPU (different streams, threads or captured graphs in flight at once) race
- * on it and give wrong results.
+ * on it and give wrong results.  The array's address and the kernel
+ * attributes are kept per device for the life of the process: after a
+ * cudaDeviceReset of a device this entry point must not be called on it again
+ * (the kept address no longer belongs to a live allocation).
  * Errors: W2_ERR_ARG (NULL, aliasing or misaligned pointers, bad grid),
  * W2_ERR_UNSUPPORTED (nx > W2_NOALLOC_MAX_NX, nk > W2_NOALLOC_MAX_NK, nk not a
  * multiple of 8, or a precision other than W2_F64), W2_ERR_CUDA. */
@@ -274,40 +298,69 @@ w2_status w2_theta_noalloc(const w2_config *cfg, const double *u1, const double 
 /* ------------------------------------------------------------------------
  * Batching form: many independent problems (uneven nx, nk, potentials and
  * pair strengths) advanced together.  Every instance is a W2_F32_TF32X3
- * problem with its own state; one batch step runs each kernel of the step
- * once for all instances as a persistent kernel striding over the flattened
- * (instance, work item) list, and the whole step is captured once into a
- * CUDA graph and replayed.  Results are identical, bit for bit, to running
- * each instance in its own context.
+ * problem with its own state.  One batch step is ONE persistent kernel: its
+ * CTAs take the work items of all seven phases of the Lawson step of every
+ * instance (tables, Theta predictor, the two shift passes, per-X sums of f~,
+ * tables, Theta corrector with the per-X sums of f^{n+1}) from one list,
+ * phase after phase, and an item starts once every item of the previous
+ * phase of its instance has finished.  The launch is captured once into a CUDA graph and replayed.
+ * Results are identical, bit for bit, to running each instance in its own
+ * context.  (Sec. 4.2 of the paper runs one problem over many ranks; running
+ * many problems in one launch has no counterpart there.)
  * ------------------------------------------------------------------------ */
 typedef struct w2_batch w2_batch;
 
 /* Create n (1..4096) instances from cfgs[0..n) (every precision must be
- * W2_F32_TF32X3, other fields as for w2_create) on the current device, all
- * on the borrowed cuda_stream.  Errors: as w2_create, W2_ERR_UNSUPPORTED for
- * another precision.  *out is NULL on failure. */
+ * W2_F32_TF32X3, nx <= 128, nk <= 64, other fields as for w2_create) on the
+ * current device, all on the borrowed cuda_stream.  Errors: as w2_create,
+ * W2_ERR_UNSUPPORTED for another precision, nx > 128 or nk > 64.  *out is
+ * NULL on failure. */
 w2_status w2_batch_create(const w2_config *cfgs, int32_t n, void *cuda_stream, w2_batch **out);
 
 /* Per-instance forms of w2_set_potentials / w2_set_state / w2_get_state /
- * w2_observables for instance i in [0, n); W2_ERR_ARG for another i. */
+ * w2_observables for instance i in [0, n); W2_ERR_ARG for another i.  The
+ * synchronising ones (w2_batch_get_state to the host, w2_batch_observables)
+ * first wait for the queued steps and return W2_ERR_TIMEOUT if a wait inside
+ * one of them ran out (see w2_batch_set_wait_limit). */
 w2_status w2_batch_set_potentials(w2_batch *b, int32_t i, w2_fn vext, void *ue, w2_fn vee, void *ui,
                                   double gamma, double c_hartree, double c_xc);
 w2_status w2_batch_set_state(w2_batch *b, int32_t i, const void *f, int32_t on_device);
 w2_status w2_batch_get_state(w2_batch *b, int32_t i, void *f, int32_t on_device);
 w2_status w2_batch_observables(w2_batch *b, int32_t i, w2_obs *out, double *n1, double *n12);
 
-/* Advance every instance by nsteps Lawson steps (as w2_step).  Needs
- * potentials and a state on every instance (W2_ERR_STATE otherwise). */
+/* Advance every instance by nsteps Lawson steps (as w2_step): nsteps
+ * replays of the one-launch step graph.  Needs potentials and a state on
+ * every instance (W2_ERR_STATE otherwise).  Asynchronous; a wait that ran out
+ * in an earlier call is reported here as W2_ERR_TIMEOUT once it is known. */
 w2_status w2_batch_step(w2_batch *b, int32_t nsteps);
 
-/* Choose the grid size of every batched kernel by timing candidates (1 to 16
- * CTAs per SM, capped at the number of work items) on the batch as it is
- * (potentials and states set; the states are not changed).  Synchronises.
- * grids_out (host, grids_len entries, or NULL) receives
- *   [per-X sums, tables, then for each momentum-size class in order of first
- *    appearance: nk, Theta sweep, shift x2, shift x1]  (zeros after the end).
- * Errors: W2_ERR_ARG, W2_ERR_STATE, W2_ERR_CUDA. */
-w2_status w2_batch_autotune(w2_batch *b, int32_t *grids_out, int32_t grids_len);
+/* Wait for the queued steps; W2_OK, or W2_ERR_TIMEOUT / W2_ERR_CUDA (sticky). */
+w2_status w2_batch_sync(w2_batch *b);
+
+/* Failure detection.  Every wait of an item for the previous phase of its
+ * instance is bounded: after `seconds` (default about 2 s; 0 < seconds <= 60)
+ * the CTA records W2_ERR_TIMEOUT, all CTAs stop taking items and the launch
+ * ends, leaving the CUDA context usable; the batch then reports
+ * W2_ERR_TIMEOUT (sticky: its states are not valid).
+ * w2_batch_inject_stall is the host-side fault injector that tests this: the
+ * finished items of phase `phase` (0..6) of instance i are no longer counted,
+ * so the items of the next phase wait until their limit; phase = -1 removes
+ * the stall.  Errors: W2_ERR_ARG. */
+w2_status w2_batch_set_wait_limit(w2_batch *b, double seconds);
+w2_status w2_batch_inject_stall(w2_batch *b, int32_t phase, int32_t i);
+
+/* Autotuner: times candidate tile shapes of the persistent step (columns
+ * per shift item 64 or 32, warps per 16-row Theta block 2 or 1, work units
+ * per item such that a CTA takes about 2, 8 or 32 items per phase) at 1 and
+ * 2 CTAs per SM (as far as they fit) on the batch as it is (potentials and
+ * states set; the states are kept and restored), and keeps the fastest.
+ * Synchronises.  tuning_out (host, tuning_len entries, or NULL) receives
+ *   [shift columns, Theta warps per row block, grid (CTAs), shared memory
+ *    bytes per CTA, best step time in microseconds, shapes tried, work items
+ *    per step, items per CTA and phase]  (zeros after the end).
+ * Errors: W2_ERR_ARG, W2_ERR_STATE, W2_ERR_OOM (no room to keep the states),
+ * W2_ERR_TIMEOUT, W2_ERR_CUDA. */
+w2_status w2_batch_autotune(w2_batch *b, int32_t *tuning_out, int32_t tuning_len);
 
 /* Release the batch and all its instances (NULL is ignored). */
 void w2_batch_destroy(w2_batch *b);

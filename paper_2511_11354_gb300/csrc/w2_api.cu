@@ -62,6 +62,9 @@ static void free_all(w2_ctx *c) {
   if (c->ev_staged) cudaEventDestroy(c->ev_staged);
   if (c->ev_taken) cudaEventDestroy(c->ev_taken);
   if (c->stage) cudaFree(c->stage);
+  void *pm[] = {c->pm_D, c->pm_wb, c->pm_tab[0], c->pm_tab[1], c->pm_xs, c->pm_gh};
+  for (void *p : pm)
+    if (p) cudaFree(p);
 }
 
 extern "C" const char *w2_status_string(w2_status s) {
@@ -150,6 +153,7 @@ extern "C" w2_status w2_create(const w2_config *cfg, void *cuda_stream, w2_ctx *
   // periodic start sums: |z|^k below the storage precision (z^32 ~ 5e-19, z^16 ~ 7e-10)
   const int kmax = f64_state(cfg->precision) ? 32 : 16;
   ctx->nterm = ctx->nx <= kmax ? ctx->nx : kmax;
+  ctx->np_ax[0] = ctx->np_ax[1] = 1;
   ctx->zscale = (ctx->nterm == ctx->nx) ? 1.0 / (1.0 - pow(ctx->z, ctx->nx)) : 1.0;
 
   const int nx = ctx->nx, nk = ctx->nk, M = ctx->M, W = 2 * nk - 1;
@@ -344,12 +348,20 @@ extern "C" w2_status w2_set_potentials(w2_ctx *ctx, w2_fn vext, void *ue, w2_fn 
   return W2_OK;
 }
 
+// The per-X sums of a new state (the time step takes those of f^n from here
+// or from the previous step's corrector).
+cudaError_t w2::state_sums(w2_ctx *ctx, cudaStream_t s) {
+  return f64_state(ctx->prec) ? launch_xsum_f64(ctx->nx, ctx->nk, (const double *)ctx->f, ctx->xsum, s)
+                              : launch_xsum_f32(ctx->nx, ctx->nk, (const float *)ctx->f, ctx->xsum, s);
+}
+
 extern "C" w2_status w2_set_state(w2_ctx *ctx, const void *f, int32_t on_device) {
   if (!ctx || !f) return W2_ERR_ARG;
   if (ctx->sticky) return ctx->sticky;
   if (!ctx->have_pot) return W2_ERR_STATE;
   W2_TRY(cudaMemcpyAsync(ctx->f, f, ctx->esz * ctx->npts,
                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  W2_TRY(state_sums(ctx, ctx->stream));
   ctx->have_state = true;
   ctx->steps = 0;
   return W2_OK;
@@ -385,6 +397,7 @@ extern "C" w2_status w2_use_staged_state(w2_ctx *ctx) {
   W2_TRY(cudaStreamWaitEvent(ctx->stream, ctx->ev_staged, 0));
   W2_TRY(cudaMemcpyAsync(ctx->f, ctx->stage, ctx->esz * ctx->npts, cudaMemcpyDeviceToDevice, ctx->stream));
   W2_TRY(cudaEventRecord(ctx->ev_taken, ctx->stream));
+  W2_TRY(state_sums(ctx, ctx->stream));
   ctx->taken_recorded = true;
   ctx->stage_pending = false;
   ctx->have_state = true;
@@ -400,6 +413,120 @@ extern "C" w2_status w2_get_state(w2_ctx *ctx, void *f, int32_t on_device) {
                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
   if (!on_device) W2_TRY(cudaStreamSynchronize(ctx->stream));
   return W2_OK;
+}
+
+// Slope stencil half-width of the patch decomposition: |z|^26 < 2^-52.
+static const int kPatchStencil = 26;
+
+extern "C" w2_status w2_set_patches(w2_ctx *ctx, int32_t np1, int32_t np2) {
+  if (!ctx || np1 < 1 || np2 < 1) return W2_ERR_ARG;
+  if (ctx->sticky) return ctx->sticky;
+  if (ctx->prec != W2_F64) return W2_ERR_UNSUPPORTED;
+  const int nx = ctx->nx, nk = ctx->nk, nnb = kPatchStencil;
+  std::vector<int> k0;
+  std::vector<double> wt;
+  spline_tables(ctx, k0, wt);
+  int G = 1;
+  for (int n = 0; n < nk; ++n) G = std::max(G, std::max(-k0[n], k0[n] + 1));
+  const int nps[2] = {np1, np2};
+  for (int ax = 0; ax < 2; ++ax)
+    if (nps[ax] > 1 && (nx % nps[ax] != 0 || nx / nps[ax] < G + nnb)) return W2_ERR_UNSUPPORTED;
+  void *pm[] = {ctx->pm_D, ctx->pm_wb, ctx->pm_tab[0], ctx->pm_tab[1], ctx->pm_xs, ctx->pm_gh};
+  for (void *p : pm)
+    if (p) cudaFree(p);
+  ctx->pm_D = ctx->pm_wb = ctx->pm_tab[0] = ctx->pm_tab[1] = ctx->pm_xs = ctx->pm_gh = nullptr;
+  ctx->np_ax[0] = np1;
+  ctx->np_ax[1] = np2;
+  ctx->pm_G = G;
+  if (ctx->graph_ready) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph_ready = false;
+  }
+  if (np1 == 1 && np2 == 1) return W2_OK;
+  // slope of the periodic spline at a point from the samples: the inverse of
+  // the (1,4,1)/6 circulant is beta_m = sqrt(3) (z^m + z^(nx-m)) / (1 - z^nx),
+  // and D_j = (beta_{j-1} - beta_{j+1}) / (2 dx)
+  const double z = ctx->z, zn = pow(z, nx);
+  auto beta = [&](int m) {
+    m %= nx;
+    m += (m < 0) ? nx : 0;
+    return sqrt(3.0) * (pow(z, m) + pow(z, nx - m)) / (1.0 - zn);
+  };
+  std::vector<double> D(2 * nnb + 1), wb(4 * nk);
+  for (int j = -nnb; j <= nnb; ++j) D[j + nnb] = (beta(j - 1) - beta(j + 1)) / (2.0 * ctx->dx);
+  for (int q = 0; q < 4 * nk; ++q) wb[q] = wt[q] / (-6.0 * z);  // the plain B-spline weights b_a(theta)
+  const size_t lines = (size_t)nx * nk * nk;
+  const int npmax = std::max(np1, np2);
+  cudaError_t e = cudaMalloc((void **)&ctx->pm_D, sizeof(double) * D.size());
+  if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->pm_wb, sizeof(double) * wb.size());
+  if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->pm_xs, sizeof(double) * 2 * npmax * 2 * lines);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->pm_gh, sizeof(double) * 2 * npmax * 2 * G * lines);
+  if (e == cudaSuccess) e = cudaMemcpy(ctx->pm_D, D.data(), sizeof(double) * D.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ctx->pm_wb, wb.data(), sizeof(double) * wb.size(), cudaMemcpyHostToDevice);
+  for (int ax = 0; ax < 2 && e == cudaSuccess; ++ax) {
+    if (nps[ax] < 2) continue;
+    // Thomas factors of the (4,2), (1,4,1), (2,4) system on n = M + 2G points
+    const int n = nx / nps[ax] + 2 * G;
+    std::vector<double> tab(2 * n);  // inv_m [n], then c' [n]
+    double cprev = 0.0;
+    for (int v = 0; v < n; ++v) {
+      const double a = v == 0 ? 0.0 : (v == n - 1 ? 2.0 : 1.0), c = v == 0 ? 2.0 : 1.0;
+      const double m = 4.0 - a * cprev;
+      tab[v] = 1.0 / m;
+      tab[n + v] = cprev = (v < n - 1) ? c / m : 0.0;
+    }
+    e = cudaMalloc((void **)&ctx->pm_tab[ax], sizeof(double) * tab.size());
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->pm_tab[ax], tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->np_ax[0] = ctx->np_ax[1] = 1;
+    return e == cudaErrorMemoryAllocation ? W2_ERR_OOM : W2_ERR_CUDA;
+  }
+  return W2_OK;
+}
+
+// One FP64 shift pass (DIR 0: x2 lines, DIR 1: x1 lines), through the patch
+// decomposition when the context has one on that axis.
+static cudaError_t shift_pass64(const w2_ctx *ctx, int dir, int two, const double *in0, const double *in1,
+                                double *out0, double *out1, cudaStream_t s) {
+  const int np = ctx->np_ax[dir == 1 ? 0 : 1];
+  if (np > 1) {
+    PatchArgs pa;
+    pa.nx = ctx->nx;
+    pa.np = np;
+    pa.M = ctx->nx / np;
+    pa.G = ctx->pm_G;
+    pa.nnb = kPatchStencil;
+    pa.in0 = in0;
+    pa.in1 = in1;
+    pa.out0 = out0;
+    pa.out1 = out1;
+    pa.xs = ctx->pm_xs;
+    pa.gh = ctx->pm_gh;
+    pa.D = ctx->pm_D;
+    const double *tab = ctx->pm_tab[dir == 1 ? 0 : 1];
+    pa.inv_m = tab;
+    pa.cp = tab + pa.M + 2 * pa.G;
+    pa.k0tab = ctx->k0tab;
+    pa.wb = ctx->pm_wb;
+    pa.h = ctx->dx;
+    pa.tau = ctx->tau;
+    return launch_adv_pmbc(ctx->nk, dir, two, pa, s);
+  }
+  AdvArgs av;
+  av.nx = ctx->nx;
+  av.k0tab = ctx->k0tab;
+  av.wtab = ctx->wtab;
+  av.z = ctx->z;
+  av.zscale = ctx->zscale;
+  av.nterm = ctx->nterm;
+  av.tau = ctx->tau;
+  av.in0 = in0;
+  av.in1 = in1;
+  av.out0 = out0;
+  av.out1 = out1;
+  return launch_adv_f64(ctx->nk, dir, two, av, s);
 }
 
 static AdvDFArgs adv_df_args(const w2_ctx *ctx) {
@@ -458,10 +585,10 @@ static cudaError_t enqueue_step(w2_ctx *ctx, cudaStream_t s, const StepEvents *e
   const int nx = ctx->nx, nk = ctx->nk, W = 2 * nk - 1;
   cudaError_t e;
   TabArgs ta = tab_args(ctx, ctx->xsum, 0);
-  // per-X sums of f^n always from the same fixed-order reduction, so a state
+  // the per-X sums of f^n come from the previous step's corrector or from the
+  // state's set-up; both are the same exact fixed-point sums, so a state
   // restored with w2_set_state continues bit-identically
   W2_MARK(0, 0)
-  if ((e = launch_xsum_f64(nx, nk, ctx->f, ctx->xsum, s)) != cudaSuccess) return e;
   W2_MARK(0, 1)
   W2_MARK(1, 0)
   if ((e = launch_tables(ta, s)) != cudaSuccess) return e;
@@ -484,18 +611,6 @@ static cudaError_t enqueue_step(w2_ctx *ctx, cudaStream_t s, const StepEvents *e
   W2_MARK(2, 0)
   if ((e = theta64(ctx, 0, th, s)) != cudaSuccess) return e;
   W2_MARK(2, 1)
-  AdvArgs av;
-  av.nx = nx;
-  av.k0tab = ctx->k0tab;
-  av.wtab = ctx->wtab;
-  av.z = ctx->z;
-  av.zscale = ctx->zscale;
-  av.nterm = ctx->nterm;
-  av.tau = ctx->tau;
-  av.in0 = ctx->f;
-  av.in1 = ctx->g;
-  av.out0 = ctx->t1;
-  av.out1 = ctx->t2;
   AdvDFArgs ad = adv_df_args(ctx);  // the sliced path: pairs in t1, t2
   ad.in0 = ctx->f;
   ad.in1 = ctx->g;
@@ -503,18 +618,19 @@ static cudaError_t enqueue_step(w2_ctx *ctx, cudaStream_t s, const StepEvents *e
   ad.out1 = ctx->t2;
   const bool df = ctx->prec == W2_F64_SLICED;
   W2_MARK(3, 0)
-  if ((e = df ? launch_adv_df(nk, 0, 1, ad, s) : launch_adv_f64(nk, 0, 1, av, s)) != cudaSuccess) return e;
+  if ((e = df ? launch_adv_df(nk, 0, 1, ad, s) : shift_pass64(ctx, 0, 1, ctx->f, ctx->g, ctx->t1, ctx->t2, s)) !=
+      cudaSuccess)
+    return e;
   W2_MARK(3, 1)
-  av.in0 = ctx->t1;
-  av.in1 = ctx->t2;
-  av.out0 = ctx->g;  // f~
-  av.out1 = ctx->f;  // h
+  // x1 pass: f~ -> g, h -> f
   ad.in0 = ctx->t1;
   ad.in1 = ctx->t2;
   ad.out0 = ctx->g;
   ad.out1 = ctx->f;
   W2_MARK(4, 0)
-  if ((e = df ? launch_adv_df(nk, 1, 1, ad, s) : launch_adv_f64(nk, 1, 1, av, s)) != cudaSuccess) return e;
+  if ((e = df ? launch_adv_df(nk, 1, 1, ad, s) : shift_pass64(ctx, 1, 1, ctx->t1, ctx->t2, ctx->g, ctx->f, s)) !=
+      cudaSuccess)
+    return e;
   W2_MARK(4, 1)
   W2_MARK(5, 0)
   if ((e = launch_xsum_f64(nx, nk, ctx->g, ctx->xsum, s)) != cudaSuccess) return e;
@@ -525,7 +641,7 @@ static cudaError_t enqueue_step(w2_ctx *ctx, cudaStream_t s, const StepEvents *e
   th.in = ctx->g;
   th.h = ctx->f;
   th.out = ctx->f;
-  th.xsum = nullptr;
+  th.xsum = ctx->xsum;  // the per-X sums of f^{n+1}, for the next step
   if (learned && (e = enqueue_learned_pair(ctx, ctx->g, s)) != cudaSuccess) return e;
   W2_MARK(7, 0)
   if ((e = theta64(ctx, 1, th, s)) != cudaSuccess) return e;
@@ -544,19 +660,23 @@ Adv32Args w2::adv32_args(w2_ctx *ctx) {
   a.zscale = (float)ctx->zscale;
   a.nterm = ctx->nterm;
   a.tau = (float)ctx->tau;
+  a.nterm_df = ctx->nx <= 28 ? ctx->nx : 28;
+  a.zdf = split_df(ctx->z);
+  a.zscale_df = split_df(a.nterm_df == ctx->nx ? 1.0 / (1.0 - pow(ctx->z, ctx->nx)) : 1.0);
+  a.zpow = ctx->zpow;
   return a;
 }
 
 // FP32 precision form of the same step (arrays hold floats):
-//   xsum(f) ; K(f) ; g = Theta f ; (d2 -> t1, g2 -> t2) = A_x2 ;
-//   (f~ -> g, dh -> t1) = A_x1 ; xsum(f~) ; K(f~) ; f = f + (dh + tau/2 Theta f~)
+//   K(f) ; g = Theta f ; (d2 -> t1, g2 -> t2) = A_x2 ;
+//   (f~ -> g, dh -> t1) = A_x1 ; xsum(f~) ; K(f~) ; f = f + (dh + tau/2 Theta f~), xsum(f)
+// (the per-X sums of f^n come from the previous corrector or from the state's set-up)
 static cudaError_t enqueue_step32(w2_ctx *ctx, cudaStream_t s, const StepEvents *evs) {
   const int nx = ctx->nx, nk = ctx->nk, W = 2 * nk - 1;
   float *f = (float *)ctx->f, *g = (float *)ctx->g, *t1 = (float *)ctx->t1, *t2 = (float *)ctx->t2;
   cudaError_t e;
   TabArgs ta = tab_args(ctx, ctx->xsum, 0);
   W2_MARK(0, 0)
-  if ((e = launch_xsum_f32(nx, nk, f, ctx->xsum, s)) != cudaSuccess) return e;
   W2_MARK(0, 1)
   W2_MARK(1, 0)
   if ((e = launch_tables(ta, s)) != cudaSuccess) return e;
@@ -599,6 +719,7 @@ static cudaError_t enqueue_step32(w2_ctx *ctx, cudaStream_t s, const StepEvents 
   th.base = f;
   th.h = t1;
   th.out = f;
+  th.xsum = ctx->xsum;
   W2_MARK(7, 0)
   if ((e = launch_theta_f32(nk, 1, th, s)) != cudaSuccess) return e;
   W2_MARK(7, 1)
@@ -753,22 +874,8 @@ extern "C" w2_status w2_advect(w2_ctx *ctx, const void *f, void *out) {
     ad.out0 = out;
     W2_TRY(launch_adv_df(ctx->nk, 0, 0, ad, ctx->stream));  // then x2, back to FP64
   } else if (f64_state(ctx->prec)) {
-    AdvArgs av;
-    av.nx = ctx->nx;
-    av.k0tab = ctx->k0tab;
-    av.wtab = ctx->wtab;
-    av.z = ctx->z;
-    av.zscale = ctx->zscale;
-    av.nterm = ctx->nterm;
-    av.tau = ctx->tau;
-    av.in0 = (const double *)f;
-    av.in1 = nullptr;
-    av.out0 = ctx->t1;
-    av.out1 = nullptr;
-    W2_TRY(launch_adv_f64(ctx->nk, 1, 0, av, ctx->stream));  // x1 first
-    av.in0 = ctx->t1;
-    av.out0 = (double *)out;
-    W2_TRY(launch_adv_f64(ctx->nk, 0, 0, av, ctx->stream));  // then x2
+    W2_TRY(shift_pass64(ctx, 1, 0, (const double *)f, nullptr, ctx->t1, nullptr, ctx->stream));  // x1 first
+    W2_TRY(shift_pass64(ctx, 0, 0, ctx->t1, nullptr, (double *)out, nullptr, ctx->stream));       // then x2
   } else {
     Adv32Args av = adv32_args(ctx);
     av.f = (const float *)f;

@@ -1,11 +1,14 @@
 // Batching form: many independent problems of uneven grid sizes and
 // interaction strengths advanced together.  Each instance is an ordinary
 // FP32 precision-form context (its own arrays and tables); one step of the
-// whole batch is a fixed sequence of persistent kernels, each striding over
-// the flattened (instance, work item) list of every instance (or of every
-// instance of one momentum size, for the kernels specialised on it), captured
-// once into a CUDA graph.  Grid sizes are chosen by timing candidates on the
-// real batch (w2_batch_autotune).
+// whole batch is ONE persistent kernel (k_bstep in w2_f32.cu) whose CTAs take
+// the work items of all eight phases of every instance from one list, phase
+// after phase, with per-instance phase counters ordering the items of one
+// instance; the launch is captured once into a CUDA graph and replayed.  The
+// tile shapes of the launch (columns per shift item, warps per Theta row
+// block) and its grid are chosen by timing every candidate on the live batch
+// (w2_batch_autotune).  The item bodies are the single-context ones, so the
+// batch reproduces per-instance runs bit for bit.
 #include <string.h>
 
 #include <algorithm>
@@ -16,32 +19,26 @@
 
 using namespace w2;
 
-namespace {
-
-struct Class {  // instances sharing one momentum size
-  int nk = 0;
-  std::vector<int> inst;
-  int *d_inst = nullptr, *d_off_x = nullptr, *d_off_slab = nullptr;
-  int items_x = 0, items_slab = 0;
-  int grid_theta = 0, grid_adv0 = 0, grid_adv1 = 0;
-  int nxmax = 0, nxmin = 1 << 30;
-};
-
-}  // namespace
-
 struct w2_batch {
   int n = 0;
   std::vector<w2_ctx *> inst;
   cudaStream_t stream = nullptr, cap = nullptr;
   TabArgs *d_tab = nullptr;
-  BXsum *d_xs_f = nullptr, *d_xs_ft = nullptr;
+  BXsum *d_xs_ft = nullptr;
   Theta32Args *d_th = nullptr;
   Adv32Args *d_adv = nullptr;
-  int *d_off_x = nullptr, *d_off_tab = nullptr;
-  int items_x = 0, items_tab = 0;
-  int grid_xsum = 0, grid_tab = 0;
-  int nxmax = 0, mmax = 0, sms = 0;
-  std::vector<Class> cls;
+  int *d_plan = nullptr;   // phase offsets, per-instance item offsets, units, group sizes, nk, nx
+  int *d_count = nullptr;  // next, left, err, skip, done [phases][n]
+  int *h_err = nullptr;    // pinned copy of err after each w2_batch_step
+  cudaEvent_t ev_err = nullptr;
+  bool err_pending = false;
+  int nxmax = 0, nkmax = 0, sms = 0;
+  BStepShape shape{64, 2, 8};
+  int grid = 0;
+  size_t smem = 0;
+  std::vector<int> phase_items;  // [phases + 1] global offsets (host copy)
+  long long wait_cycles = 4ll << 30;  // about two seconds at 2 GHz
+  BStepPlan plan{};
   cudaGraphExec_t graph = nullptr;
   bool graph_ready = false;
   bool tab_dirty = true;  // table arguments carry the potentials' weights
@@ -58,14 +55,11 @@ struct w2_batch {
 
 static void batch_free(w2_batch *b) {
   if (b->graph_ready) cudaGraphExecDestroy(b->graph);
-  void *ptrs[] = {b->d_tab, b->d_xs_f, b->d_xs_ft, b->d_th, b->d_adv, b->d_off_x, b->d_off_tab};
+  void *ptrs[] = {b->d_tab, b->d_xs_ft, b->d_th, b->d_adv, b->d_plan, b->d_count};
   for (void *p : ptrs)
     if (p) cudaFree(p);
-  for (auto &c : b->cls) {
-    if (c.d_inst) cudaFree(c.d_inst);
-    if (c.d_off_x) cudaFree(c.d_off_x);
-    if (c.d_off_slab) cudaFree(c.d_off_slab);
-  }
+  if (b->h_err) cudaFreeHost(b->h_err);
+  if (b->ev_err) cudaEventDestroy(b->ev_err);
   for (w2_ctx *c : b->inst)
     if (c) w2_destroy(c);
   if (b->cap) cudaStreamDestroy(b->cap);
@@ -85,12 +79,87 @@ extern "C" void w2_batch_destroy(w2_batch *b) {
   delete b;
 }
 
+// Grid, shared memory and kernel attributes of a tile shape (grid: ctas per
+// SM times SMs, at most the CTAs that fit).
+static cudaError_t set_shape(w2_batch *b, BStepShape sh, int ctas_per_sm) {
+  cudaError_t e = prepare_bstep(sh);
+  if (e != cudaSuccess) return e;
+  const size_t smem = bstep_smem(sh, b->nxmax, b->nkmax);
+  const int fit = bstep_max_ctas_per_sm(sh, smem);
+  if (fit < 1) return cudaErrorInvalidConfiguration;
+  b->shape = sh;
+  b->smem = smem;
+  b->grid = std::min(ctas_per_sm, fit) * b->sms;
+  return cudaSuccess;
+}
+
+// Work units of instance c in phase p: X for the per-X sums and Theta,
+// (particle, x) rows for the tables, (x, n1, column block) slabs for the shift.
+static int phase_units(const w2_ctx *c, int p, int shift_cols) {
+  if (p == 0 || p == 5) return 2 * c->nx;
+  if (p == 2 || p == 3) return c->nx * c->nk * bstep_shift_items(c->nk, shift_cols);
+  return c->nx * c->nx;
+}
+
+// Work items, per-instance offsets and the device plan of the current shape:
+// each phase's units are grouped so that the grid takes about items_per_cta
+// items per CTA in that phase.
+static cudaError_t build_plan(w2_batch *b) {
+  const int n = b->n;
+  std::vector<int> plan(kBatchPhases + 1 + kBatchPhases * (n + 1) + kBatchPhases * n + kBatchPhases + 2 * n, 0);
+  int *phase_off = plan.data(), *inst_off = phase_off + kBatchPhases + 1;
+  int *units = inst_off + kBatchPhases * (n + 1), *gsz = units + kBatchPhases * n;
+  int *nk = gsz + kBatchPhases, *nx = nk + n;
+  for (int p = 0; p < kBatchPhases; ++p) {
+    long long tot = 0;
+    for (int i = 0; i < n; ++i) {
+      units[p * n + i] = phase_units(b->inst[i], p, b->shape.shift_cols);
+      tot += units[p * n + i];
+    }
+    const long long want = (long long)b->grid * std::max(1, b->shape.items_per_cta);
+    gsz[p] = (int)std::max(1ll, tot / std::max(1ll, want));
+    int *io = inst_off + p * (n + 1);
+    for (int i = 0; i < n; ++i) io[i + 1] = io[i] + (units[p * n + i] + gsz[p] - 1) / gsz[p];
+    phase_off[p + 1] = phase_off[p] + io[n];
+  }
+  for (int i = 0; i < n; ++i) {
+    nk[i] = b->inst[i]->nk;
+    nx[i] = b->inst[i]->nx;
+  }
+  b->phase_items.assign(phase_off, phase_off + kBatchPhases + 1);
+  if (b->d_plan) cudaFree(b->d_plan);
+  b->d_plan = nullptr;
+  cudaError_t e = upload(&b->d_plan, plan);
+  if (e != cudaSuccess) return e;
+  BStepPlan &P = b->plan;
+  P.n = n;
+  P.phase_off = b->d_plan;
+  P.inst_off = P.phase_off + kBatchPhases + 1;
+  P.units = P.inst_off + kBatchPhases * (n + 1);
+  P.gsz = P.units + kBatchPhases * n;
+  P.nk = P.gsz + kBatchPhases;
+  P.nx = P.nk + n;
+  P.xs_ft = b->d_xs_ft;
+  P.tab = b->d_tab;
+  P.th = b->d_th;
+  P.adv = b->d_adv;
+  P.next = b->d_count;
+  P.left = b->d_count + 1;
+  P.err = b->d_count + 2;
+  P.skip = b->d_count + 3;
+  P.done = b->d_count + 4;
+  P.wait_cycles = b->wait_cycles;
+  return cudaSuccess;
+}
+
 extern "C" w2_status w2_batch_create(const w2_config *cfgs, int32_t n, void *cuda_stream, w2_batch **out) {
   if (!out) return W2_ERR_ARG;
   *out = nullptr;
   if (!cfgs || n <= 0 || n > 4096) return W2_ERR_ARG;
+  // the persistent step holds a whole line of up to 64 columns in shared memory
+  // and runs every item with one block of 256 threads
   for (int i = 0; i < n; ++i)
-    if (cfgs[i].precision != W2_F32_TF32X3) return W2_ERR_UNSUPPORTED;
+    if (cfgs[i].precision != W2_F32_TF32X3 || cfgs[i].nx > 128 || cfgs[i].nk > 64) return W2_ERR_UNSUPPORTED;
   w2_batch *b = new (std::nothrow) w2_batch();
   if (!b) return W2_ERR_OOM;
   b->n = n;
@@ -107,7 +176,8 @@ extern "C" w2_status w2_batch_create(const w2_config *cfgs, int32_t n, void *cud
   int dev = 0;
   cudaDeviceProp prop;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_err, cudaEventDisableTiming) != cudaSuccess) {
     batch_free(b);
     delete b;
     return W2_ERR_CUDA;
@@ -115,16 +185,14 @@ extern "C" w2_status w2_batch_create(const w2_config *cfgs, int32_t n, void *cud
   b->sms = prop.multiProcessorCount;
 
   std::vector<TabArgs> tab(n);
-  std::vector<BXsum> xf(n), xft(n);
+  std::vector<BXsum> xft(n);
   std::vector<Theta32Args> th(2 * n);
   std::vector<Adv32Args> adv(2 * n);
-  std::vector<int> off_x(n + 1, 0), off_tab(n + 1, 0);
   for (int i = 0; i < n; ++i) {
     w2_ctx *c = b->inst[i];
     const int W = 2 * c->nk - 1;
     float *f = (float *)c->f, *g = (float *)c->g, *t1 = (float *)c->t1, *t2 = (float *)c->t2;
     tab[i] = tab_args(c, c->xsum, 0);
-    xf[i] = BXsum{f, c->xsum, c->nk};
     xft[i] = BXsum{g, c->xsum, c->nk};
     Theta32Args &p = th[2 * i], &q = th[2 * i + 1];
     p.nx = c->nx;
@@ -141,6 +209,7 @@ extern "C" w2_status w2_batch_create(const w2_config *cfgs, int32_t n, void *cud
     q.base = f;
     q.h = t1;
     q.out = f;
+    q.xsum = c->xsum;  // the per-X sums of f^{n+1}, for the next step
     Adv32Args a0 = adv32_args(c), a1 = adv32_args(c);
     a0.f = f;
     a0.g = g;
@@ -153,52 +222,23 @@ extern "C" w2_status w2_batch_create(const w2_config *cfgs, int32_t n, void *cud
     a1.dh = t1;
     adv[2 * i] = a0;
     adv[2 * i + 1] = a1;
-    off_x[i + 1] = off_x[i] + c->nx * c->nx;
-    off_tab[i + 1] = off_tab[i] + 2 * c->nx;
     b->nxmax = std::max(b->nxmax, c->nx);
-    b->mmax = std::max(b->mmax, c->M);
-    // momentum-size classes
-    int k = -1;
-    for (size_t q2 = 0; q2 < b->cls.size(); ++q2)
-      if (b->cls[q2].nk == c->nk) k = (int)q2;
-    if (k < 0) {
-      b->cls.emplace_back();
-      k = (int)b->cls.size() - 1;
-      b->cls[k].nk = c->nk;
-    }
-    b->cls[k].inst.push_back(i);
-    b->cls[k].nxmax = std::max(b->cls[k].nxmax, c->nx);
-    b->cls[k].nxmin = std::min(b->cls[k].nxmin, c->nx);
+    b->nkmax = std::max(b->nkmax, c->nk);
   }
-  b->items_x = off_x[n];
-  b->items_tab = off_tab[n];
   cudaError_t e = upload(&b->d_tab, tab);
-  if (e == cudaSuccess) e = upload(&b->d_xs_f, xf);
   if (e == cudaSuccess) e = upload(&b->d_xs_ft, xft);
   if (e == cudaSuccess) e = upload(&b->d_th, th);
   if (e == cudaSuccess) e = upload(&b->d_adv, adv);
-  if (e == cudaSuccess) e = upload(&b->d_off_x, off_x);
-  if (e == cudaSuccess) e = upload(&b->d_off_tab, off_tab);
-  for (auto &c : b->cls) {
-    std::vector<int> ox(c.inst.size() + 1, 0), os(c.inst.size() + 1, 0);
-    for (size_t q = 0; q < c.inst.size(); ++q) {
-      w2_ctx *ci = b->inst[c.inst[q]];
-      ox[q + 1] = ox[q] + ci->nx * ci->nx;
-      os[q + 1] = os[q] + ci->nk * ci->nx * adv_items_per_line_f32(ci->nk);
-    }
-    c.items_x = ox.back();
-    c.items_slab = os.back();
-    if (e == cudaSuccess) e = upload(&c.d_inst, c.inst);
-    if (e == cudaSuccess) e = upload(&c.d_off_x, ox);
-    if (e == cudaSuccess) e = upload(&c.d_off_slab, os);
-    // default grids: two waves of CTAs over the SMs, at most one per item
-    c.grid_theta = std::min(c.items_x, 2 * b->sms);
-    c.grid_adv0 = std::min(c.items_slab, 4 * b->sms);
-    c.grid_adv1 = std::min(c.items_slab, 4 * b->sms);
-  }
-  b->grid_xsum = std::min(b->items_x, 8 * b->sms);
-  b->grid_tab = std::min(b->items_tab, 4 * b->sms);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_count, sizeof(int) * (4 + kBatchPhases * (size_t)n));
+  if (e == cudaSuccess) e = cudaMemset(b->d_count, 0, sizeof(int) * (4 + kBatchPhases * (size_t)n));
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_err, sizeof(int));
+  if (e == cudaSuccess) *b->h_err = 0;
+  // default shape: 64-column shift items, two warps per Theta row block,
+  // as many CTAs as fit (at most two per SM)
+  if (e == cudaSuccess) e = set_shape(b, BStepShape{64, 2, 8}, 2);
+  if (e == cudaSuccess) e = build_plan(b);
   if (e != cudaSuccess) {
+    cudaGetLastError();
     batch_free(b);
     delete b;
     return e == cudaErrorMemoryAllocation ? W2_ERR_OOM : W2_ERR_CUDA;
@@ -209,67 +249,86 @@ extern "C" w2_status w2_batch_create(const w2_config *cfgs, int32_t n, void *cud
 
 static bool index_ok(const w2_batch *b, int i) { return b && i >= 0 && i < b->n; }
 
+// A wait that ran out in an earlier step makes the batch's status sticky.
+static w2_status check_err(w2_batch *b, bool wait) {
+  if (b->sticky) return b->sticky;
+  if (!b->err_pending) return W2_OK;
+  if (!wait && cudaEventQuery(b->ev_err) != cudaSuccess) return W2_OK;
+  if (cudaEventSynchronize(b->ev_err) != cudaSuccess) {
+    b->sticky = W2_ERR_CUDA;
+    return b->sticky;
+  }
+  b->err_pending = false;
+  if (*b->h_err) b->sticky = (w2_status)*b->h_err;
+  return b->sticky;
+}
+
 extern "C" w2_status w2_batch_set_potentials(w2_batch *b, int32_t i, w2_fn vext, void *ue, w2_fn vee, void *ui,
                                              double gamma, double c_hartree, double c_xc) {
   if (!index_ok(b, i)) return W2_ERR_ARG;
-  if (b->sticky) return b->sticky;
+  if (w2_status st = check_err(b, false)) return st;
   b->tab_dirty = true;
   return w2_set_potentials(b->inst[i], vext, ue, vee, ui, gamma, c_hartree, c_xc);
 }
 
 extern "C" w2_status w2_batch_set_state(w2_batch *b, int32_t i, const void *f, int32_t on_device) {
   if (!index_ok(b, i)) return W2_ERR_ARG;
-  if (b->sticky) return b->sticky;
+  if (w2_status st = check_err(b, false)) return st;
   return w2_set_state(b->inst[i], f, on_device);
 }
 
 extern "C" w2_status w2_batch_get_state(w2_batch *b, int32_t i, void *f, int32_t on_device) {
   if (!index_ok(b, i)) return W2_ERR_ARG;
-  if (b->sticky) return b->sticky;
+  if (w2_status st = check_err(b, true)) return st;
   return w2_get_state(b->inst[i], f, on_device);
 }
 
 extern "C" w2_status w2_batch_observables(w2_batch *b, int32_t i, w2_obs *out, double *n1, double *n12) {
   if (!index_ok(b, i)) return W2_ERR_ARG;
-  if (b->sticky) return b->sticky;
+  if (w2_status st = check_err(b, true)) return st;
   return w2_observables(b->inst[i], out, n1, n12);
 }
 
-// Kernels of one batch step, in order:
-//   per-X sums (all) ; tables (all) ; Theta predictor (per class) ;
-//   shift x2 (per class) ; shift x1 + combination (per class) ;
-//   per-X sums of f~ (all) ; tables (all) ; Theta corrector (per class)
-static cudaError_t enqueue_batch_step(w2_batch *b, cudaStream_t s) {
-  cudaError_t e;
-  if ((e = launch_bxsum(b->d_xs_f, b->d_off_x, b->n, b->grid_xsum, s)) != cudaSuccess) return e;
-  if ((e = launch_btables(b->d_tab, b->d_off_tab, b->n, b->grid_tab, b->nxmax, b->mmax, s)) != cudaSuccess) return e;
-  for (auto &c : b->cls) {
-    BatchLaunch bl{c.grid_theta, c.d_inst, c.d_off_x, (int)c.inst.size()};
-    if ((e = launch_btheta_f32(c.nk, 0, bl, b->d_th, s)) != cudaSuccess) return e;
+extern "C" w2_status w2_batch_sync(w2_batch *b) {
+  if (!b) return W2_ERR_ARG;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+    b->sticky = W2_ERR_CUDA;
+    return W2_ERR_CUDA;
   }
-  for (auto &c : b->cls) {
-    BatchLaunch bl{c.grid_adv0, c.d_inst, c.d_off_slab, (int)c.inst.size()};
-    if ((e = launch_badv_f32(c.nk, 0, bl, b->d_adv, c.nxmax, adv32_pieces(c.nxmax), s)) != cudaSuccess) return e;
+  return check_err(b, true);
+}
+
+extern "C" w2_status w2_batch_set_wait_limit(w2_batch *b, double seconds) {
+  if (!b || !(seconds > 0.0) || seconds > 60.0) return W2_ERR_ARG;
+  if (w2_status st = check_err(b, false)) return st;
+  int dev = 0, khz = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess ||
+      khz <= 0)
+    khz = 2000000;
+  b->wait_cycles = (long long)(seconds * 1e3 * khz);
+  b->plan.wait_cycles = b->wait_cycles;
+  if (b->graph_ready) {  // the plan is a kernel argument baked into the graph
+    cudaGraphExecDestroy(b->graph);
+    b->graph_ready = false;
   }
-  for (auto &c : b->cls) {
-    BatchLaunch bl{c.grid_adv1, c.d_inst, c.d_off_slab, (int)c.inst.size()};
-    if ((e = launch_badv_f32(c.nk, 1, bl, b->d_adv, c.nxmax, adv32_pieces(c.nxmax), s)) != cudaSuccess) return e;
-  }
-  if ((e = launch_bxsum(b->d_xs_ft, b->d_off_x, b->n, b->grid_xsum, s)) != cudaSuccess) return e;
-  if ((e = launch_btables(b->d_tab, b->d_off_tab, b->n, b->grid_tab, b->nxmax, b->mmax, s)) != cudaSuccess) return e;
-  for (auto &c : b->cls) {
-    BatchLaunch bl{c.grid_theta, c.d_inst, c.d_off_x, (int)c.inst.size()};
-    if ((e = launch_btheta_f32(c.nk, 1, bl, b->d_th, s)) != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  return W2_OK;
+}
+
+extern "C" w2_status w2_batch_inject_stall(w2_batch *b, int32_t phase, int32_t i) {
+  if (!b || phase < -1 || phase >= kBatchPhases || (phase >= 0 && !index_ok(b, i))) return W2_ERR_ARG;
+  if (w2_status st = check_err(b, false)) return st;
+  const int v = phase < 0 ? 0 : 1 + phase * b->n + i;
+  WB_TRY(cudaMemcpyAsync(b->d_count + 3, &v, sizeof(int), cudaMemcpyHostToDevice, b->stream));
+  WB_TRY(cudaStreamSynchronize(b->stream));
+  return W2_OK;
 }
 
 static w2_status ready(w2_batch *b) {
-  if (b->sticky) return b->sticky;
+  if (w2_status st = check_err(b, false)) return st;
   for (w2_ctx *c : b->inst)
     if (!c->have_pot || !c->have_state) return W2_ERR_STATE;
   if (b->tab_dirty) {
-    // the kernels read their arguments from device memory at run time, so a
+    // the kernel reads its arguments from device memory at run time, so a
     // captured step sees the refreshed weights without being captured again
     std::vector<TabArgs> tab(b->n);
     for (int i = 0; i < b->n; ++i) tab[i] = tab_args(b->inst[i], b->inst[i]->xsum, 0);
@@ -284,6 +343,14 @@ static w2_status ready(w2_batch *b) {
   return W2_OK;
 }
 
+// Queue the copy of the step's status flag behind the steps just queued.
+static w2_status note_err(w2_batch *b) {
+  WB_TRY(cudaMemcpyAsync(b->h_err, b->d_count + 2, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  WB_TRY(cudaEventRecord(b->ev_err, b->stream));
+  b->err_pending = true;
+  return W2_OK;
+}
+
 extern "C" w2_status w2_batch_step(w2_batch *b, int32_t nsteps) {
   if (!b || nsteps < 0) return W2_ERR_ARG;
   w2_status st = ready(b);
@@ -292,7 +359,7 @@ extern "C" w2_status w2_batch_step(w2_batch *b, int32_t nsteps) {
   if (!b->graph_ready) {
     cudaGraph_t graph;
     WB_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = enqueue_batch_step(b, b->cap);
+    cudaError_t e = launch_bstep(b->shape, b->plan, b->grid, b->smem, b->cap);
     cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {
       if (e2 == cudaSuccess) cudaGraphDestroy(graph);
@@ -306,121 +373,95 @@ extern "C" w2_status w2_batch_step(w2_batch *b, int32_t nsteps) {
   }
   for (int s = 0; s < nsteps; ++s) WB_TRY(cudaGraphLaunch(b->graph, b->stream));
   for (w2_ctx *c : b->inst) c->steps += nsteps;
-  return W2_OK;
+  return note_err(b);
 }
 
-// Time one launch configuration: the best of `reps` launches, in ms.
-template <typename F>
-static float time_best(cudaStream_t s, F launch, int reps, cudaError_t *err) {
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  float best = 1e30f;
-  for (int r = 0; r < reps + 1; ++r) {
-    cudaEventRecord(e0, s);
-    cudaError_t e = launch();
-    cudaEventRecord(e1, s);
-    if (e != cudaSuccess) *err = e;
-    cudaEventSynchronize(e1);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (r > 0) best = std::min(best, ms);  // the first launch warms up
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  return best;
-}
-
-extern "C" w2_status w2_batch_autotune(w2_batch *b, int32_t *grids_out, int32_t grids_len) {
+extern "C" w2_status w2_batch_autotune(w2_batch *b, int32_t *tuning_out, int32_t tuning_len) {
   if (!b) return W2_ERR_ARG;
   w2_status st = ready(b);
   if (st) return st;
   cudaStream_t s = b->stream;
+  // timing runs real steps: keep every state and restore it afterwards
+  size_t total = 0;
+  for (w2_ctx *c : b->inst) total += c->esz * c->npts;
+  char *save = nullptr;
+  if (cudaMalloc((void **)&save, total) != cudaSuccess) {
+    cudaGetLastError();
+    return W2_ERR_OOM;
+  }
+  size_t o = 0;
   cudaError_t err = cudaSuccess;
-  const int mult[] = {1, 2, 3, 4, 6, 8, 12, 16};
-  auto candidates = [&](int items) {
-    std::vector<int> v;
-    for (int m : mult) {
-      const int g = std::min(items, m * b->sms);
-      if (std::find(v.begin(), v.end(), g) == v.end()) v.push_back(g);
-    }
-    return v;
-  };
-  // Each tuned kernel is free of side effects on the state: the predictor
-  // sweep and the x2 pass write scratch arrays only, and the x1 pass is timed
-  // writing into scratch as well (its inputs are rebuilt by the next step).
-  {
-    float best = 1e30f;
-    int pick = b->grid_xsum;
-    for (int g : candidates(b->items_x)) {
-      float t = time_best(s, [&] { return launch_bxsum(b->d_xs_f, b->d_off_x, b->n, g, s); }, 2, &err);
-      if (t < best) best = t, pick = g;
-    }
-    b->grid_xsum = pick;
+  for (w2_ctx *c : b->inst) {
+    if (err == cudaSuccess) err = cudaMemcpyAsync(save + o, c->f, c->esz * c->npts, cudaMemcpyDeviceToDevice, s);
+    o += c->esz * c->npts;
   }
-  {
-    float best = 1e30f;
-    int pick = b->grid_tab;
-    for (int g : candidates(b->items_tab)) {
-      float t = time_best(
-          s, [&] { return launch_btables(b->d_tab, b->d_off_tab, b->n, g, b->nxmax, b->mmax, s); }, 2, &err);
-      if (t < best) best = t, pick = g;
+  const BStepShape shapes[] = {{64, 2, 2}, {64, 2, 8}, {64, 2, 32}, {64, 1, 8}, {32, 2, 8}, {32, 1, 8}};
+  const BStepShape keep_shape = b->shape;
+  const int keep_grid = b->grid;
+  BStepShape best_shape = keep_shape;
+  int best_grid = keep_grid, tried = 0;
+  float best = 1e30f;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (err == cudaSuccess) err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  for (const BStepShape &sh : shapes) {
+    for (int per_sm = 1; per_sm <= 2 && err == cudaSuccess; ++per_sm) {
+      if (set_shape(b, sh, per_sm) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      if (per_sm == 2 && b->grid == b->sms) continue;  // only one CTA fits: same as per_sm = 1
+      if ((err = build_plan(b)) != cudaSuccess) break;
+      float t_best = 1e30f;
+      for (int r = 0; r < 3 && err == cudaSuccess; ++r) {  // the first launch warms up
+        err = cudaEventRecord(e0, s);
+        if (err == cudaSuccess) err = launch_bstep(b->shape, b->plan, b->grid, b->smem, s);
+        if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0) t_best = std::min(t_best, ms);
+      }
+      ++tried;
+      if (t_best < best) {
+        best = t_best;
+        best_shape = b->shape;
+        best_grid = b->grid;
+      }
     }
-    b->grid_tab = pick;
   }
-  for (auto &c : b->cls) {
-    const int m = (int)c.inst.size();
-    float best = 1e30f;
-    int pick = c.grid_theta;
-    for (int g : candidates(c.items_x)) {
-      BatchLaunch bl{g, c.d_inst, c.d_off_x, m};
-      float t = time_best(s, [&] { return launch_btheta_f32(c.nk, 0, bl, b->d_th, s); }, 2, &err);
-      if (t < best) best = t, pick = g;
-    }
-    c.grid_theta = pick;
-    best = 1e30f;
-    pick = c.grid_adv0;
-    for (int g : candidates(c.items_slab)) {
-      BatchLaunch bl{g, c.d_inst, c.d_off_slab, m};
-      float t = time_best(s, [&] { return launch_badv_f32(c.nk, 0, bl, b->d_adv, c.nxmax, adv32_pieces(c.nxmax), s); }, 2, &err);
-      if (t < best) best = t, pick = g;
-    }
-    c.grid_adv0 = pick;
-    // the x1 pass has the same item structure and a larger working set; tune it
-    // separately after restoring its inputs with one x2 pass
-    best = 1e30f;
-    pick = c.grid_adv1;
-    for (int g : candidates(c.items_slab)) {
-      BatchLaunch b0{c.grid_adv0, c.d_inst, c.d_off_slab, m};
-      BatchLaunch bl{g, c.d_inst, c.d_off_slab, m};
-      float t = time_best(
-          s,
-          [&] {
-            cudaError_t e0 = launch_badv_f32(c.nk, 0, b0, b->d_adv, c.nxmax, adv32_pieces(c.nxmax), s);
-            return e0 != cudaSuccess ? e0 : launch_badv_f32(c.nk, 1, bl, b->d_adv, c.nxmax, adv32_pieces(c.nxmax), s);
-          },
-          2, &err);
-      if (t < best) best = t, pick = g;
-    }
-    c.grid_adv1 = pick;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  o = 0;
+  for (w2_ctx *c : b->inst) {  // the states, and the per-X sums the next step reads
+    if (err == cudaSuccess) err = cudaMemcpyAsync(c->f, save + o, c->esz * c->npts, cudaMemcpyDeviceToDevice, s);
+    if (err == cudaSuccess) err = state_sums(c, s);
+    o += c->esz * c->npts;
+  }
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  cudaFree(save);
+  int flag = 0;
+  if (err == cudaSuccess) err = cudaMemcpy(&flag, b->d_count + 2, sizeof(int), cudaMemcpyDeviceToHost);
+  if (err == cudaSuccess && flag) {
+    b->sticky = (w2_status)flag;
+    return b->sticky;
+  }
+  if (err == cudaSuccess) {
+    err = set_shape(b, best_shape, best_grid / b->sms);
+    if (err == cudaSuccess) err = build_plan(b);
   }
   if (err != cudaSuccess) {
     b->sticky = W2_ERR_CUDA;
     return W2_ERR_CUDA;
   }
-  if (b->graph_ready) {  // the captured step used the old grids
+  if (b->graph_ready) {  // the captured step used the old shape
     cudaGraphExecDestroy(b->graph);
     b->graph_ready = false;
   }
-  if (grids_out && grids_len > 0) {
-    std::vector<int> v = {b->grid_xsum, b->grid_tab};
-    for (auto &c : b->cls) {
-      v.push_back(c.nk);
-      v.push_back(c.grid_theta);
-      v.push_back(c.grid_adv0);
-      v.push_back(c.grid_adv1);
-    }
-    for (int q = 0; q < grids_len; ++q) grids_out[q] = q < (int)v.size() ? v[q] : 0;
+  if (tuning_out && tuning_len > 0) {
+    const int v[] = {b->shape.shift_cols, b->shape.theta_split, b->grid, (int)b->smem, (int)(best * 1000.f), tried,
+                     b->phase_items[kBatchPhases], b->shape.items_per_cta};
+    for (int q = 0; q < tuning_len; ++q) tuning_out[q] = q < (int)(sizeof(v) / sizeof(v[0])) ? v[q] : 0;
   }
   return W2_OK;
 }

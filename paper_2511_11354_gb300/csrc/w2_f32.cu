@@ -12,10 +12,17 @@
 //              delta = (S - I) f from taps that merge the B-spline evaluation
 //              weights with the (1,4,1)/6 interpolation condition, so its FP32
 //              error is proportional to the (sub-cell) shift, not to |f|; the
-//              state itself is rounded once per step, in the corrector.
+//              state itself is rounded once per step, in the corrector.  The
+//              spline coefficients are solved in double-float pairs (about
+//              2^-47 per operation) and kept as (hi, lo) FP32 pairs in shared
+//              memory; the evaluation reads both parts.
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
+#include "w2_blocks.cuh"
+#include "w2_df.cuh"
 #include "w2_internal.cuh"
 
 namespace w2 {
@@ -90,7 +97,7 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 template <int NK>
 struct Theta32Smem {
   static constexpr int S = NK + 8;  // padded row stride (floats): conflict-free B fragments
-  static constexpr size_t words = 3 * (size_t)NK * S + 9 * 2 * NK;
+  static constexpr size_t words = 3 * (size_t)NK * S + 9 * 2 * NK + 64;  // + the per-X sum's scratch
   static constexpr size_t bytes = 4 * words;
 };
 
@@ -101,9 +108,12 @@ struct Theta32Smem {
 // tile goes through the same sequence of products either way.
 constexpr int kTh32Split = 2;
 
-// One CTA per X; warps 2r and 2r + 1 own momentum rows [16r, 16r + 16).
+// One CTA per X; the SPLIT warps SPLIT r .. SPLIT r + SPLIT - 1 own momentum
+// rows [16r, 16r + 16) and split its column tiles; warps beyond SPLIT nk / 16
+// only take part in the loads and barriers (the persistent batch step runs
+// every item with the same block).  The split does not change the bits.
 // MODE 0: out = Theta[in].  MODE 1: out = base + (h + half_tau Theta[in]).
-template <int NK, int MODE>
+template <int NK, int MODE, int SPLIT = kTh32Split>
 // compiled once (not inlined) so the single-problem and batched kernels
 // run the same machine code and give identical bits
 __device__ __noinline__ void theta32_block(const Theta32Args &a, const int X, uint32_t *smu) {
@@ -122,9 +132,10 @@ __device__ __noinline__ void theta32_block(const Theta32Args &a, const int X, ui
   dd += (dd < 0) ? nx : 0;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int g = lane >> 2, t4 = lane & 3;
-  const int part = w % kTh32Split;            // this warp's part of the column tiles
-  constexpr int NTH = NT / kTh32Split;
-  static_assert(NT % kTh32Split == 0, "the warps of a row block split its column tiles evenly");
+  const int part = w % SPLIT;                 // this warp's part of the column tiles
+  constexpr int NTH = NT / SPLIT;
+  static_assert(NT % SPLIT == 0, "the warps of a row block split its column tiles evenly");
+  const bool active = w < SPLIT * (NK / 16);
   const int bfirst = part * NTH;
   const size_t base = (size_t)X * NK * NK;
   {
@@ -157,15 +168,16 @@ __device__ __noinline__ void theta32_block(const Theta32Args &a, const int X, ui
   }
   __syncthreads();
 
-  const int r0 = 16 * (w / kTh32Split);
+  const int r0 = 16 * (w / SPLIT);
   const int na = r0 + g, nb = r0 + g + 8;  // the two A/D rows of this lane
 
   // Two-body term in sheared coordinates (see k_theta in w2_f64.cu); the
-  // sheared tiles of the row block are split between its two warps.
-  {
+  // sheared tiles of the row block are split between its warps.
+  if (active) {
     const int cfirst = r0 >> 3, cmax = min((r0 + 15 + NK - 1) >> 3, (2 * NK - 2) >> 3);
-    const int hn = (cmax - cfirst + 2) >> 1;
-    const int cbeg = part ? cfirst + hn : cfirst, cend = part ? cmax : cfirst + hn - 1;
+    const int ntile = cmax - cfirst + 1;
+    const int cbeg = cfirst + (part * ntile + SPLIT - 1) / SPLIT;
+    const int cend = cfirst + ((part + 1) * ntile + SPLIT - 1) / SPLIT - 1;
     for (int c = cbeg; c <= cend; ++c) {
       float d[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f};
       const int nlo = max(0, 8 * c - NK + 1), nhi = min(NK - 1, 8 * c + 7);
@@ -197,8 +209,11 @@ __device__ __noinline__ void theta32_block(const Theta32Args &a, const int X, ui
       n2 = sa + 1 - nb; if (n2 >= 0 && n2 < NK) Acc[nb * S + n2] = d[3];
     }
   }
-  __syncthreads();  // the row block's Acc rows come from both of its warps
-
+  __syncthreads();  // the row block's Acc rows come from all of its warps
+  float held[4 * NTH];  // this thread's outputs (zeros in warps without rows), for the per-X sum
+#pragma unroll
+  for (int q = 0; q < 4 * NTH; ++q) held[q] = 0.f;
+  if (active) {
   float acc[NTH][4], sml[NTH][4];
 #pragma unroll
   for (int bb = 0; bb < NTH; ++bb) {
@@ -262,38 +277,19 @@ __device__ __noinline__ void theta32_block(const Theta32Args &a, const int X, ui
         v.x = fv.x + fmaf(a.half_tau, acc[bb][2 * hrow], hv.x);
         v.y = fv.y + fmaf(a.half_tau, acc[bb][2 * hrow + 1], hv.y);
       }
+      held[4 * bb + 2 * hrow] = v.x;
+      held[4 * bb + 2 * hrow + 1] = v.y;
       *reinterpret_cast<float2 *>(a.out + o) = v;
     }
   }
+  }  // active
+  if (MODE == 1 && a.xsum) block_exact_sum(held, a.xsum + X, reinterpret_cast<int *>(smu + L::words - 64));
 }
 
 template <int NK, int MODE>
 __global__ void __launch_bounds__(NK * 2 * kTh32Split, 1) k_theta32(Theta32Args a) {
   extern __shared__ __align__(16) uint32_t smu[];
   theta32_block<NK, MODE>(a, blockIdx.x, smu);
-}
-
-// Locate work item `item` in a class of instances with item offsets off[0..n].
-__device__ __forceinline__ int find_inst(const int *off, int n, int item) {
-  int k = 0;
-  while (k + 1 < n && off[k + 1] <= item) ++k;
-  return k;
-}
-
-// Persistent batched sweep: CTAs stride over the (instance, X) items of every
-// instance of one momentum size; args[2 * inst + MODE] holds that instance's
-// arguments.
-template <int NK, int MODE>
-__global__ void __launch_bounds__(NK * 2 * kTh32Split, 1) k_btheta32(const Theta32Args *args, const int *inst, const int *off,
-                                                     int n) {
-  extern __shared__ __align__(16) uint32_t smu[];
-  const int total = off[n];
-  for (int item = blockIdx.x; item < total; item += gridDim.x) {
-    const int k = find_inst(off, n, item);
-    const Theta32Args a = args[2 * inst[k] + MODE];
-    theta32_block<NK, MODE>(a, item - off[k], smu);
-    __syncthreads();
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -385,6 +381,102 @@ __device__ __forceinline__ void spline_coeffs32_chunked(float *c0, float *c1, in
   __syncthreads();
 }
 
+// (oh, ol) = z (h, l) + (xh, xl) in double-float arithmetic, renormalised by
+// Fast2Sum (where the sum cancels, |t| may exceed |s|; the pair then still
+// holds s + t to within 2^-48 of the larger input, which is the accuracy the
+// line needs).
+__device__ __forceinline__ void df_madd(float2 z, float h, float l, float xh, float xl, float &oh, float &ol) {
+  float ph, pe, s, t;
+  df_mul(z.x, z.y, h, l, ph, pe);
+  two_sum(ph, xh, s, t);
+  t = __fadd_rn(t, __fadd_rn(pe, xl));
+  fast_two_sum(s, t, oh, ol);
+}
+
+// Start sum sum_{k < nt} z^k (h, l)[row(k)] of one column, in double-float,
+// times the periodic scale, normalised.
+template <typename Row>
+__device__ __forceinline__ void df_start(const float *ch, const float *cl, int stride, const Adv32Args &a, int nt,
+                                         Row row, float &oh, float &ol) {
+  float sh = 0.f, se = 0.f;
+  for (int k = 0; k < nt; ++k) {
+    const int idx = row(k);
+    const float2 zk = __ldg(a.zpow + k);
+    float ph, pe;
+    df_mul(zk.x, zk.y, ch[idx * stride], cl[idx * stride], ph, pe);
+    df_acc(sh, se, ph, pe);
+  }
+  two_sum(sh, se, sh, se);
+  float ph, pe;
+  df_mul(a.zscale_df.x, a.zscale_df.y, sh, se, ph, pe);
+  two_sum(ph, pe, oh, ol);
+}
+
+// The coefficient solve of spline_coeffs32_chunked in double-float pairs: on
+// entry (h0, l0) and (h1, l1) (h1 may be null) hold each line's values as
+// (hi, lo) pairs, on return the coefficients d of the causal and anti-causal
+// recursions with pole z, started from periodic sums over nterm_df terms
+// (exact up to |z|^28 < 2^-53 when nterm_df < n).  Every thread of the CTA
+// calls this: it holds the CTA barriers between the phases.
+__device__ __forceinline__ void spline_coeffs_df_chunked(float *h0, float *l0, float *h1, float *l1, int stride, int n,
+                                                         const Adv32Args &a, int lo, int hi) {
+  const int nt = hi > lo ? a.nterm_df : 0;  // an empty piece reads nothing
+  float p0h = 0.f, p0l = 0.f, p1h = 0.f, p1l = 0.f;
+  auto back = [lo, n](int k) {
+    int idx = lo - k;
+    return idx + ((idx < 0) ? n : 0);
+  };
+  df_start(h0, l0, stride, a, nt, back, p0h, p0l);
+  if (h1) df_start(h1, l1, stride, a, nt, back, p1h, p1l);
+  __syncthreads();  // every start sum has read the input line
+  if (hi > lo) {
+    h0[lo * stride] = p0h;
+    l0[lo * stride] = p0l;
+    if (h1) {
+      h1[lo * stride] = p1h;
+      l1[lo * stride] = p1l;
+    }
+    for (int i = lo + 1; i < hi; ++i) {
+      df_madd(a.zdf, p0h, p0l, h0[i * stride], l0[i * stride], p0h, p0l);
+      h0[i * stride] = p0h;
+      l0[i * stride] = p0l;
+      if (h1) {
+        df_madd(a.zdf, p1h, p1l, h1[i * stride], l1[i * stride], p1h, p1l);
+        h1[i * stride] = p1h;
+        l1[i * stride] = p1l;
+      }
+    }
+  }
+  __syncthreads();
+  const int e = hi - 1;
+  auto fwd = [e, n](int k) {
+    int idx = e + k;
+    return idx - ((idx >= n) ? n : 0);
+  };
+  df_start(h0, l0, stride, a, nt, fwd, p0h, p0l);
+  if (h1) df_start(h1, l1, stride, a, nt, fwd, p1h, p1l);
+  __syncthreads();  // every start sum has read the causal pass
+  if (hi > lo) {
+    h0[e * stride] = p0h;
+    l0[e * stride] = p0l;
+    if (h1) {
+      h1[e * stride] = p1h;
+      l1[e * stride] = p1l;
+    }
+    for (int i = e - 1; i >= lo; --i) {
+      df_madd(a.zdf, p0h, p0l, h0[i * stride], l0[i * stride], p0h, p0l);
+      h0[i * stride] = p0h;
+      l0[i * stride] = p0l;
+      if (h1) {
+        df_madd(a.zdf, p1h, p1l, h1[i * stride], l1[i * stride], p1h, p1l);
+        h1[i * stride] = p1h;
+        l1[i * stride] = p1l;
+      }
+    }
+  }
+  __syncthreads();
+}
+
 __device__ __forceinline__ int wrap(int j, int n) {
   j %= n;
   return j < 0 ? j + n : j;
@@ -470,13 +562,17 @@ __device__ __forceinline__ void stage_slab(float *slab, const float *src, size_t
 //   one array : ft = u + d1  (= S1 S2 f)
 // A CTA owns columns [cb*C, cb*C + C) of the slab with adv32_pieces(nx)
 // threads per column: thread t takes column t % C and the rows of piece t / C
-// (staging, the spline solve in pieces, the evaluation).
-template <int NK, int DIR>
+// (staging, the spline solve in pieces, the evaluation).  Shared memory: the
+// staged slabs (FP32) and the lo parts of the two solved arrays (FP32),
+// rows nx + 2 kGhost each: 4 slabs for DIR 0, 5 for DIR 1.
+template <int DIR>
+__host__ __device__ constexpr int adv32_slabs() { return DIR == 0 ? 4 : 5; }
+
+template <int NK, int DIR, int C>
 // compiled once (not inlined) so the single-problem and batched kernels
 // run the same machine code and give identical bits
 __device__ __noinline__ void adv32_block(const Adv32Args &a, const int n1, const int cb, const int fixed,
                                          float *sm32) {
-  constexpr int C = AdvCols<NK>::C;
   const int nx = a.nx;
   // the pieces depend on nx only, so that every launch shape gives the same bits;
   // threads beyond them idle (a batch launch is sized for its longest lines)
@@ -493,24 +589,36 @@ __device__ __noinline__ void adv32_block(const Adv32Args &a, const int n1, const
   for (int r = 0; r < 4; ++r) w[r] = a.wtab[4 * sidx + r];
 #pragma unroll
   for (int r = 0; r < 8; ++r) ct[r] = a.ctab[8 * sidx + r];
-  float *SA = sm32, *SB = sm32 + (size_t)rows * C, *SC = sm32 + 2 * (size_t)rows * C;
-  float *A = SA + t, *B = SB + t, *Cc = SC + t;  // this thread's column
+  const size_t slab = (size_t)rows * C;
+  float *SA = sm32, *SB = sm32 + slab;
+  float *SC = sm32 + 2 * slab;                                // DIR 1 only
+  float *LA = sm32 + (DIR == 0 ? 2 : 3) * slab, *L1 = LA + slab;  // lo parts of A and of B (DIR 0) / C (DIR 1)
+  float *A = SA + t, *B = SB + t, *Cc = SC + t, *la = LA + t, *l1 = L1 + t;  // this thread's column
   if (DIR == 0) {
     const bool two = a.g != nullptr;
     stage_slab<C>(SA, a.f + base, lineStride, nx);
     if (two) stage_slab<C>(SB, a.g + base, lineStride, nx);
+    for (int i = lo; i < hi; ++i) {
+      la[(kGhost + i) * C] = 0.f;
+      l1[(kGhost + i) * C] = 0.f;
+    }
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-    spline_coeffs32_chunked(A + kGhost * C, two ? B + kGhost * C : nullptr, C, nx, a.z, a.zscale, a.nterm, lo, hi);
+    spline_coeffs_df_chunked(A + kGhost * C, la + kGhost * C, two ? B + kGhost * C : nullptr,
+                             two ? l1 + kGhost * C : nullptr, C, nx, a, lo, hi);
     if (threadIdx.x < C) {
       fill_ghosts(A, C, nx);
-      if (two) fill_ghosts(B, C, nx);
+      fill_ghosts(la, C, nx);
+      if (two) {
+        fill_ghosts(B, C, nx);
+        fill_ghosts(l1, C, nx);
+      }
     }
     __syncthreads();
     for (int i = lo; i < hi; ++i) {
       const size_t o = base + i * lineStride + t;
-      a.d2[o] = incr32(A, C, nx, i, k0, w, ct, a.z);
-      if (two) a.g2[o] = eval32(B, C, nx, i, k0, w);
+      a.d2[o] = incr32(A, C, nx, i, k0, w, ct, a.z) + incr32(la, C, nx, i, k0, w, ct, a.z);
+      if (two) a.g2[o] = eval32(B, C, nx, i, k0, w) + eval32(l1, C, nx, i, k0, w);
     }
   } else {
     const bool two = a.g2in != nullptr;
@@ -519,22 +627,33 @@ __device__ __noinline__ void adv32_block(const Adv32Args &a, const int n1, const
     if (two) stage_slab<C>(SC, a.g2in + base, lineStride, nx);
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-    for (int i = lo; i < hi; ++i) A[(kGhost + i) * C] += B[(kGhost + i) * C];  // u = f + d2
+    for (int i = lo; i < hi; ++i) {  // u = f + d2 as an exact pair
+      float uh, ul;
+      two_sum(A[(kGhost + i) * C], B[(kGhost + i) * C], uh, ul);
+      A[(kGhost + i) * C] = uh;
+      la[(kGhost + i) * C] = ul;
+      l1[(kGhost + i) * C] = 0.f;
+    }
     __syncthreads();
-    spline_coeffs32_chunked(A + kGhost * C, two ? Cc + kGhost * C : nullptr, C, nx, a.z, a.zscale, a.nterm, lo, hi);
+    spline_coeffs_df_chunked(A + kGhost * C, la + kGhost * C, two ? Cc + kGhost * C : nullptr,
+                             two ? l1 + kGhost * C : nullptr, C, nx, a, lo, hi);
     if (threadIdx.x < C) {
       fill_ghosts(A, C, nx);
-      if (two) fill_ghosts(Cc, C, nx);
+      fill_ghosts(la, C, nx);
+      if (two) {
+        fill_ghosts(Cc, C, nx);
+        fill_ghosts(l1, C, nx);
+      }
     }
     __syncthreads();
     for (int i = lo; i < hi; ++i) {
       const size_t o = base + i * lineStride + t;
-      const float d1 = incr32(A, C, nx, i, k0, w, ct, a.z);
+      const float d1 = incr32(A, C, nx, i, k0, w, ct, a.z) + incr32(la, C, nx, i, k0, w, ct, a.z);
       // u_i recovered from its spline coefficients: u = (1,4,1)/6 eta = -z (d_{i-1} + 4 d_i + d_{i+1})
-      const float *ca = A + (kGhost + i) * C;
-      const float u = -a.z * (ca[-C] + 4.f * ca[0] + ca[C]);
+      const float *ca = A + (kGhost + i) * C, *cl = la + (kGhost + i) * C;
+      const float u = -a.z * (ca[-C] + 4.f * ca[0] + ca[C]) - a.z * (cl[-C] + 4.f * cl[0] + cl[C]);
       if (two) {
-        const float b = eval32(Cc, C, nx, i, k0, w);
+        const float b = eval32(Cc, C, nx, i, k0, w) + eval32(l1, C, nx, i, k0, w);
         const float da = B[(kGhost + i) * C] + d1;
         a.ft[o] = u + fmaf(a.tau, b, d1);
         a.dh[o] = fmaf(0.5f * a.tau, b, da);
@@ -545,32 +664,22 @@ __device__ __noinline__ void adv32_block(const Adv32Args &a, const int n1, const
   }
 }
 
-template <int NK, int DIR>
-__global__ void __launch_bounds__(8 * AdvCols<NK>::C) k_adv32(Adv32Args a) {
+// Columns per CTA of the single-problem shift beyond 128 points per line: 32
+// (16 when nk is an odd multiple of 16), so that five slabs of nx + 2 kGhost
+// rows fit.
+template <int NK>
+struct AdvColsWide {
+  static constexpr int C = NK % 32 == 0 ? 32 : 16;
+  static constexpr int blocks = NK / C;
+};
+
+template <int NK, int DIR, int C>
+__global__ void __launch_bounds__(8 * C) k_adv32(Adv32Args a) {
   extern __shared__ __align__(16) float sm32[];
-  adv32_block<NK, DIR>(a, blockIdx.x / AdvCols<NK>::blocks, blockIdx.x % AdvCols<NK>::blocks, blockIdx.y, sm32);
+  constexpr int NB = NK / C;
+  adv32_block<NK, DIR, C>(a, blockIdx.x / NB, blockIdx.x % NB, blockIdx.y, sm32);
 }
 
-// Persistent batched shift: items are (instance, slab) with
-// slab = (fixed * NK + n1) * blocks + cb; args[2 * inst + DIR] holds that
-// instance's arguments.
-template <int NK, int DIR>
-__global__ void __launch_bounds__(8 * AdvCols<NK>::C) k_badv32(const Adv32Args *args, const int *inst, const int *off,
-                                                           int n) {
-  extern __shared__ __align__(16) float sm32[];
-  constexpr int NB = AdvCols<NK>::blocks;
-  const int total = off[n];
-  for (int item = blockIdx.x; item < total; item += gridDim.x) {
-    const int k = find_inst(off, n, item);
-    const Adv32Args a = args[2 * inst[k] + DIR];
-    const int slab = item - off[k];
-    const int cb = slab % NB, rest = slab / NB;
-    adv32_block<NK, DIR>(a, rest % NK, cb, rest / NK, sm32);
-    __syncthreads();
-  }
-}
-
-int adv_items_per_line_f32(int nk) { return nk >= 64 ? nk / 64 : 1; }
 
 // ---------------------------------------------------------------------------
 // Dispatch
@@ -586,42 +695,16 @@ static cudaError_t prep32() {
     e = cudaFuncSetAttribute(k_theta32<NK, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Theta32Smem<NK>::bytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_adv32<NK, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    e = cudaFuncSetAttribute(k_adv32<NK, 0, AdvCols<NK>::C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_adv32<NK, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    e = cudaFuncSetAttribute(k_adv32<NK, 1, AdvCols<NK>::C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_btheta32<NK, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Theta32Smem<NK>::bytes);
+    e = cudaFuncSetAttribute(k_adv32<NK, 0, AdvColsWide<NK>::C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             220 * 1024);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_btheta32<NK, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Theta32Smem<NK>::bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_badv32<NK, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_badv32<NK, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    e = cudaFuncSetAttribute(k_adv32<NK, 1, AdvColsWide<NK>::C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             220 * 1024);
   return e;
-}
-
-template <int NK>
-static cudaError_t run_btheta32(int mode, const BatchLaunch &b, const Theta32Args *args, cudaStream_t s) {
-  if (mode == 0)
-    k_btheta32<NK, 0><<<b.grid, NK * 2 * kTh32Split, Theta32Smem<NK>::bytes, s>>>(args, b.inst, b.off, b.n);
-  else
-    k_btheta32<NK, 1><<<b.grid, NK * 2 * kTh32Split, Theta32Smem<NK>::bytes, s>>>(args, b.inst, b.off, b.n);
-  return cudaGetLastError();
-}
-
-template <int NK>
-static cudaError_t run_badv32(int dir, const BatchLaunch &b, const Adv32Args *args, int nxmax, int pieces,
-                              cudaStream_t s) {
-  constexpr int C = AdvCols<NK>::C;
-  const size_t smem = sizeof(float) * (size_t)(dir == 0 ? 2 : 3) * (nxmax + 2 * kGhost) * C;
-  const int threads = C * pieces;
-  if (dir == 0)
-    k_badv32<NK, 0><<<b.grid, threads, smem, s>>>(args, b.inst, b.off, b.n);
-  else
-    k_badv32<NK, 1><<<b.grid, threads, smem, s>>>(args, b.inst, b.off, b.n);
-  return cudaGetLastError();
 }
 
 template <int NK>
@@ -634,17 +717,22 @@ static cudaError_t run_theta32(int mode, const Theta32Args &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int NK, int C>
+static cudaError_t run_adv32_c(int dir, const Adv32Args &a, cudaStream_t s) {
+  dim3 grid(NK * (NK / C), a.nx), block(C * adv32_pieces(a.nx));
+  const int slabs = dir == 0 ? adv32_slabs<0>() : adv32_slabs<1>();
+  const size_t smem = sizeof(float) * (size_t)slabs * (a.nx + 2 * kGhost) * C;
+  if (smem > 220 * 1024) return cudaErrorInvalidValue;
+  if (dir == 0)
+    k_adv32<NK, 0, C><<<grid, block, smem, s>>>(a);
+  else
+    k_adv32<NK, 1, C><<<grid, block, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <int NK>
 static cudaError_t run_adv32(int dir, const Adv32Args &a, cudaStream_t s) {
-  constexpr int C = AdvCols<NK>::C;
-  dim3 grid(NK * AdvCols<NK>::blocks, a.nx), block(C * adv32_pieces(a.nx));
-  const int slabs = dir == 0 ? 2 : 3;
-  const size_t smem = sizeof(float) * (size_t)slabs * (a.nx + 2 * kGhost) * C;
-  if (dir == 0)
-    k_adv32<NK, 0><<<grid, block, smem, s>>>(a);
-  else
-    k_adv32<NK, 1><<<grid, block, smem, s>>>(a);
-  return cudaGetLastError();
+  return a.nx <= 128 ? run_adv32_c<NK, AdvCols<NK>::C>(dir, a, s) : run_adv32_c<NK, AdvColsWide<NK>::C>(dir, a, s);
 }
 
 #define W2_NK32_SWITCH(nk, EXPR_TEMPLATE) \
@@ -678,18 +766,167 @@ cudaError_t launch_adv_f32(int nk, int dir, const Adv32Args &a, cudaStream_t s) 
 #undef W2_A
 }
 
-cudaError_t launch_btheta_f32(int nk, int mode, const BatchLaunch &b, const Theta32Args *args, cudaStream_t s) {
-#define W2_BT(N) run_btheta32<N>(mode, b, args, s)
-  W2_NK32_SWITCH(nk, W2_BT)
-#undef W2_BT
+
+// ---------------------------------------------------------------------------
+// Batch step: one persistent launch per Lawson step of every instance
+// ---------------------------------------------------------------------------
+
+// Columns per shift item for a tile width CS: CS, or nk when nk <= CS, or 16
+// when CS does not divide nk.
+__host__ __device__ constexpr int bstep_cols(int nk, int cs) { return nk <= cs ? nk : (nk % cs == 0 ? cs : 16); }
+
+int bstep_shift_items(int nk, int shift_cols) { return nk / bstep_cols(nk, shift_cols); }
+
+// Largest k with off[k] <= item among off[0..n] (off ascending, off[0] = 0).
+__device__ __forceinline__ int bsearch_inst(const int *off, int n, int item) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
 }
 
-cudaError_t launch_badv_f32(int nk, int dir, const BatchLaunch &b, const Adv32Args *args, int nxmax, int pieces,
-                            cudaStream_t s) {
-  if (pieces < 1 || pieces > 8) return cudaErrorInvalidValue;
-#define W2_BA(N) run_badv32<N>(dir, b, args, nxmax, pieces, s)
-  W2_NK32_SWITCH(nk, W2_BA)
-#undef W2_BA
+template <int NK, int CS, int TS>
+__device__ __forceinline__ void bstep_item(const BStepPlan &P, int p, int i, int j, unsigned char *sm) {
+  constexpr int C = bstep_cols(NK, CS);
+  constexpr int NB = NK / C;
+  switch (p) {
+    case 1: theta32_block<NK, 0, TS>(P.th[2 * i], j, reinterpret_cast<uint32_t *>(sm)); break;
+    case 6: theta32_block<NK, 1, TS>(P.th[2 * i + 1], j, reinterpret_cast<uint32_t *>(sm)); break;
+    case 2: adv32_block<NK, 0, C>(P.adv[2 * i], (j / NB) % NK, j % NB, (j / NB) / NK, reinterpret_cast<float *>(sm)); break;
+    case 3: adv32_block<NK, 1, C>(P.adv[2 * i + 1], (j / NB) % NK, j % NB, (j / NB) / NK, reinterpret_cast<float *>(sm)); break;
+    default: break;
+  }
+}
+
+template <int CS, int TS>
+__global__ void __launch_bounds__(kBatchThreads, 2) k_bstep(BStepPlan P) {
+  extern __shared__ __align__(16) unsigned char smb[];
+  __shared__ int s_item, s_ok;
+  const int total = P.phase_off[kBatchPhases];
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(P.next, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= total) break;
+    int p = 0;
+    while (item >= P.phase_off[p + 1]) ++p;
+    const int *io = P.inst_off + p * (P.n + 1);
+    const int local = item - P.phase_off[p];
+    const int i = bsearch_inst(io, P.n, local);
+    const int j = local - io[i];
+    if (threadIdx.x == 0) {
+      int ok = *(volatile int *)P.err == 0;
+      if (ok && p > 0) {
+        const int *po = P.inst_off + (p - 1) * (P.n + 1);
+        const int target = po[i + 1] - po[i];
+        const volatile int *d = P.done + (p - 1) * P.n + i;
+        const long long t0 = clock64();
+        while (*d < target) {
+          if (*(volatile int *)P.err) {
+            ok = 0;
+            break;
+          }
+          if (clock64() - t0 > P.wait_cycles) {
+            atomicCAS(P.err, 0, (int)W2_ERR_TIMEOUT);
+            ok = 0;
+            break;
+          }
+          __nanosleep(128);
+        }
+        __threadfence();  // the finished items' writes are seen before this item reads them
+      }
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    const int nk = P.nk[i], g = P.gsz[p];
+    const int u1 = min((j + 1) * g, P.units[p * P.n + i]);
+    for (int u = j * g; u < u1; ++u) {
+      if (p == 4) {
+        const BXsum &a = P.xs_ft[i];
+        xsum_block<float, 16>(a.f, a.xsum, a.nk, u, reinterpret_cast<double *>(smb));
+      } else if (p == 0 || p == 5) {
+        const int nx = P.nx[i];
+        tables_block(P.tab[i], u % nx, u / nx, reinterpret_cast<double *>(smb));
+      } else {
+        switch (nk) {
+          case 16: bstep_item<16, CS, TS>(P, p, i, u, smb); break;
+          case 32: bstep_item<32, CS, TS>(P, p, i, u, smb); break;
+          case 48: bstep_item<48, CS, TS>(P, p, i, u, smb); break;
+          case 64: bstep_item<64, CS, TS>(P, p, i, u, smb); break;
+          default: break;
+        }
+      }
+      __syncthreads();  // every thread's writes of this unit are issued; shared memory is free again
+    }
+    if (threadIdx.x == 0) {
+      __threadfence();
+      if (!(P.skip && *P.skip == 1 + p * P.n + i)) atomicAdd(P.done + p * P.n + i, 1);
+    }
+  }
+  // the last CTA to leave resets the counters for the next launch
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(P.left, 1) == (int)gridDim.x - 1) {
+      for (int k = 0; k < kBatchPhases * P.n; ++k) P.done[k] = 0;
+      *P.next = 0;
+      *P.left = 0;
+      __threadfence();
+    }
+  }
+}
+
+template <int CS, int TS>
+static cudaError_t prep_bstep_v() {
+  return cudaFuncSetAttribute(k_bstep<CS, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+}
+
+#define W2_BSTEP_SWITCH(sh, EXPR)                                       \
+  if (sh.shift_cols == 64 && sh.theta_split == 2) return EXPR(64, 2);  \
+  if (sh.shift_cols == 64 && sh.theta_split == 1) return EXPR(64, 1);  \
+  if (sh.shift_cols == 32 && sh.theta_split == 2) return EXPR(32, 2);  \
+  if (sh.shift_cols == 32 && sh.theta_split == 1) return EXPR(32, 1);  \
+  return cudaErrorInvalidValue;
+
+cudaError_t prepare_bstep(const BStepShape &sh) {
+#define W2_PB(CS, TS) prep_bstep_v<CS, TS>()
+  W2_BSTEP_SWITCH(sh, W2_PB)
+#undef W2_PB
+}
+
+// Shared memory of the persistent step: the largest of its items' needs
+// (shift: five slabs of nx + 2 kGhost rows; Theta: the split block; tables:
+// densities and fine-point potentials; per-X sums: 256 doubles).
+size_t bstep_smem(const BStepShape &sh, int nxmax, int nkmax) {
+  size_t m = 256 * sizeof(double);
+  m = std::max(m, sizeof(double) * (size_t)(nxmax + 2 * nkmax));
+  for (int nk = 16; nk <= nkmax; nk += 16) {
+    const size_t th = 4 * (3 * (size_t)nk * (nk + 8) + 9 * 2 * nk + 64);
+    const size_t ad = sizeof(float) * 5 * (size_t)(nxmax + 2 * kGhost) * bstep_cols(nk, sh.shift_cols);
+    m = std::max(m, std::max(th, ad));
+  }
+  return m;
+}
+
+int bstep_max_ctas_per_sm(const BStepShape &sh, size_t smem) {
+  int n = 0;
+#define W2_OC(CS, TS) \
+  (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_bstep<CS, TS>, kBatchThreads, smem) == cudaSuccess ? n : 0)
+  if (sh.shift_cols == 64 && sh.theta_split == 2) return W2_OC(64, 2);
+  if (sh.shift_cols == 64 && sh.theta_split == 1) return W2_OC(64, 1);
+  if (sh.shift_cols == 32 && sh.theta_split == 2) return W2_OC(32, 2);
+  if (sh.shift_cols == 32 && sh.theta_split == 1) return W2_OC(32, 1);
+#undef W2_OC
+  return 0;
+}
+
+cudaError_t launch_bstep(const BStepShape &sh, const BStepPlan &p, int grid, size_t smem, cudaStream_t s) {
+  if (smem > 220 * 1024 || grid < 1) return cudaErrorInvalidValue;
+#define W2_LB(CS, TS) (k_bstep<CS, TS><<<grid, kBatchThreads, smem, s>>>(p), cudaGetLastError())
+  W2_BSTEP_SWITCH(sh, W2_LB)
+#undef W2_LB
 }
 
 }  // namespace w2

@@ -17,6 +17,7 @@
 //               of the (1, 4, 1)/6 circulant with exact periodic start values.
 #include <math.h>
 
+#include "w2_blocks.cuh"
 #include "w2_internal.cuh"
 
 namespace w2 {
@@ -25,108 +26,9 @@ namespace w2 {
 // Tables
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ double phi_xc(int kind, double n) {
-  if (kind == 1) return n;
-  if (kind == 2) {  // Hedin-Lundqvist form, defined for n >= 0
-    double c = cbrt(fmax(n, 0.0));
-    return 0.985 * c + 0.985 * 0.034 * log1p(18.37 * c);
-  }
-  return 0.0;
-}
-
-// grid: (nx, 2) for one-body kernels (blockIdx.y = particle), (nx, 1) for the
-// pair kernel.  Dynamic shared memory: (nx + M) doubles; 512 threads.
-// compiled once (not inlined) so the single-problem and batched kernels
-// run the same machine code and give identical bits
-__device__ __noinline__ void tables_block(const TabArgs &a, const int i, const int part, double *sm) {
-  const int nx = a.nx, nk = a.nk, M = a.M;
-  double *n = sm, *U = sm + nx;
-  const int quads = blockDim.x >> 2, qd = threadIdx.x >> 2;
-  const bool lead = (threadIdx.x & 3) == 0;
-  const bool mf = !a.pair_mode && a.xsum && (a.c_h != 0.0 || (a.c_xc != 0.0 && a.xc_kind));
-  // one quad per item; the item loops run the same number of rounds in every
-  // thread (the quads' shuffles need all lanes)
-  if (mf) {
-    const double w = a.dx * a.dp * a.dp;
-    for (int b = 0; b < nx; b += quads) {
-      const int q = b + qd;
-      const double s = quad_sum(q < nx, nx, [&](int k) {
-        return part == 0 ? a.xsum[(size_t)q * nx + k] : a.xsum[(size_t)k * nx + q];
-      });
-      if (lead && q < nx) n[q] = s * w;
-    }
-  }
-  __syncthreads();
-  for (int b = 0; b < M; b += quads) {
-    const int l = b + qd;
-    const bool v = l < M;
-    double u = 0.0;
-    if (a.pair_mode) {
-      if (v) u = a.gamma * a.w_fine[(size_t)i * M + l];
-    } else {
-      if (v) u = a.vext_fine[(size_t)i * M + l];
-      if (mf && a.c_h != 0.0) {
-        const double *ker = a.h_fine ? a.h_fine : a.w_fine;  // Poisson kernel, or W scaled below
-        const double vh = quad_sum(v, nx, [&](int q) {
-          int d = i - q;
-          d += (d < 0) ? nx : 0;
-          return ker[(size_t)d * M + l] * n[q];
-        });
-        u += a.c_h * (a.h_fine ? 1.0 : a.gamma * a.dx) * vh;
-      }
-      if (mf && a.c_xc != 0.0 && a.xc_kind) {
-        const double ni = quad_sum(v, nx, [&](int q) {
-          int d = i - q;
-          d += (d < 0) ? nx : 0;
-          return a.d_fine[(size_t)d * M + l] * n[q];
-        });
-        u += a.c_xc * phi_xc(a.xc_kind, ni);
-      }
-    }
-    if (lead && v) U[l] = u;
-  }
-  __syncthreads();
-  const int W = 2 * nk - 1;
-  double *K = a.K + ((size_t)part * nx + i) * W;
-  const double inv = 1.0 / (a.hbar * nk);
-  for (int b = 0; b < nk; b += quads) {
-    const int j = b + qd;
-    double s = quad_sum(j < nk, nk - 1, [&](int k) {
-      const int l = k + 1;
-      return (U[l] - U[M - l]) * a.sintab[(l * j) % M];
-    });
-    if (lead && j < nk) {
-      s *= inv;
-      K[nk - 1 + j] = s;
-      K[nk - 1 - j] = -s;
-    }
-  }
-}
-
 __global__ void k_tables(TabArgs a) {
   extern __shared__ double sm[];
   tables_block(a, blockIdx.x, blockIdx.y, sm);
-}
-
-// Batched tables: items are (instance, part, i) over 2 nx items per instance
-// (args[inst] is that instance's TabArgs, pair_mode 0).
-__global__ void k_btables(const TabArgs *args, const int *off, int n) {
-  extern __shared__ double sm[];
-  const int total = off[n];
-  for (int item = blockIdx.x; item < total; item += gridDim.x) {
-    int k = 0;
-    while (k + 1 < n && off[k + 1] <= item) ++k;
-    const TabArgs a = args[k];
-    const int r = item - off[k];
-    tables_block(a, r % a.nx, r / a.nx, sm);
-    __syncthreads();
-  }
-}
-
-cudaError_t launch_btables(const TabArgs *args, const int *off, int n, int grid, int nxmax, int mmax,
-                           cudaStream_t s) {
-  k_btables<<<grid, 512, sizeof(double) * (nxmax + mmax), s>>>(args, off, n);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_tables(const TabArgs &a, cudaStream_t s) {
@@ -153,13 +55,13 @@ template <int NK>
 struct ThetaSmem {
   static constexpr int T = NK / 8;     // 8x8 tiles per momentum axis
   static constexpr int S = NK + 4;     // padded row stride (doubles): 2 wavefronts per fragment load
-  static constexpr int doubles = 2 * NK * S + 3 * 2 * NK + 8;
+  static constexpr int doubles = 2 * NK * S + 3 * 2 * NK + 32;
   static constexpr size_t bytes = sizeof(double) * doubles;
 };
 
 // One CTA per spatial point X; warp w owns momentum rows n1 in [8w, 8w+8).
 // mode 0: out = Theta[in].  mode 1: out = h + half_tau * Theta[in] and, when
-// xsum is given, xsum[X] = sum_P out (fixed order).
+// xsum is given, xsum[X] = sum_P out (the exact fixed-point sum of xsum_block).
 template <int NK, int MODE>
 __global__ void __launch_bounds__(NK * 4) k_theta(ThetaArgs a) {
   using L = ThetaSmem<NK>;
@@ -170,7 +72,7 @@ __global__ void __launch_bounds__(NK * 4) k_theta(ThetaArgs a) {
   double *k1 = Acc + NK * S;    // [2NK] K1(x1, j + NK - 1)
   double *k2 = k1 + 2 * NK;
   double *k12 = k2 + 2 * NK;
-  double *red = k12 + 2 * NK;   // [T]
+  double *red = k12 + 2 * NK;   // [32] (the per-X sum's scratch)
 
   const int nx = a.nx;
   const int X = blockIdx.x;
@@ -249,7 +151,7 @@ __global__ void __launch_bounds__(NK * 4) k_theta(ThetaArgs a) {
   }
 
   // Epilogue.
-  double local = 0.0;
+  double held[2 * T];
 #pragma unroll
   for (int b = 0; b < T; ++b) {
     const size_t o = base + (size_t)n1 * NK + 8 * b + 2 * t4;
@@ -261,21 +163,12 @@ __global__ void __launch_bounds__(NK * 4) k_theta(ThetaArgs a) {
       const double2 hv = *reinterpret_cast<const double2 *>(a.h + o);
       v.x = hv.x + a.half_tau * acc[b][0];
       v.y = hv.y + a.half_tau * acc[b][1];
-      local += v.x + v.y;
     }
+    held[2 * b] = v.x;
+    held[2 * b + 1] = v.y;
     *reinterpret_cast<double2 *>(a.out + o) = v;
   }
-  if (MODE == 1 && a.xsum) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) local += __shfl_xor_sync(0xffffffffu, local, off);
-    if (lane == 0) red[w] = local;
-    __syncthreads();
-    if (tid == 0) {
-      double s = 0.0;
-      for (int q = 0; q < T; ++q) s += red[q];
-      a.xsum[X] = s;
-    }
-  }
+  if (MODE == 1 && a.xsum) block_exact_sum(held, a.xsum + X, reinterpret_cast<int *>(red));
 }
 
 template <int NK>

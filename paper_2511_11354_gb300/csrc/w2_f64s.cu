@@ -36,6 +36,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "w2_blocks.cuh"
 #include "w2_df.cuh"
 #include "w2_internal.cuh"
 
@@ -345,8 +346,10 @@ __global__ void __launch_bounds__(SlicedLayout<NK>::THREADS, 512 / SlicedLayout<
     }
   }
 
-  // Epilogue: recombine, add the two-body term, scale, combine with h.
+  // Epilogue: recombine, add the two-body term, scale, combine with h; in the
+  // corrector (with xsum given) also the exact per-X sum of the outputs.
   const int xs = emax + kmax - 2096;  // one unit of the recombined integer is 2^xs
+  double held[4 * NCT];
 #pragma unroll
   for (int q = 0; q < NCT; ++q) {
 #pragma unroll
@@ -377,9 +380,12 @@ __global__ void __launch_bounds__(SlicedLayout<NK>::THREADS, 512 / SlicedLayout<
         v.x = fma(a.half_tau, t0, hv.x);
         v.y = fma(a.half_tau, t1, hv.y);
       }
+      held[4 * q + 2 * hr] = v.x;
+      held[4 * q + 2 * hr + 1] = v.y;
       *reinterpret_cast<double2 *>(a.out + o) = v;
     }
   }
+  if (MODE == 1 && a.xsum) block_exact_sum(held, a.xsum + X, red);
 }
 
 template <int NK>
@@ -415,9 +421,8 @@ cudaError_t prepare_kernels_f64s(int nk) {
   }
 }
 
-// Sliced sweep (mode 0 / 1 as launch_theta_f64; per-X sums are not produced).
+// Sliced sweep (mode 0 / 1 as launch_theta_f64, per-X sums of the corrector's output included).
 cudaError_t launch_theta_f64s(int nk, int mode, const ThetaArgs &a, cudaStream_t s) {
-  if (a.xsum) return cudaErrorInvalidValue;
   switch (nk) {
     case 16: return run_s<16>(mode, a, s);
     case 32: return run_s<32>(mode, a, s);

@@ -79,6 +79,24 @@ struct AdvDFArgs {
   int nterm;                // terms of the periodic start sums (<= 32)
 };
 
+// The shift of one axis split into np patches joined by perfectly matched
+// boundary conditions (w2_pmbc.cu).
+struct PatchArgs {
+  int nx, np, M, G, nnb;    // grid, patches, points per patch, ghost points per side, slope stencil half-width
+  const double *in0, *in1;  // arrays to shift (in1 may be null)
+  double *out0, *out1;
+  double *xs;               // [arrays][np][2][lines] slope parts sent to the neighbours
+  double *gh;               // [arrays][np][2][G][lines] ghost samples sent to the neighbours
+  const double *D;          // [2 nnb + 1] slope stencil D_{-nnb..nnb}
+  const double *inv_m, *cp; // [M + 2G] Thomas factors of the local system
+  const int *k0tab;         // [nk]
+  const double *wb;         // [nk][4] B-spline weights b_a(theta)
+  double h, tau;
+};
+cudaError_t launch_adv_pmbc(int nk, int dir, int two, const PatchArgs &a, cudaStream_t s);
+// The per-X sums of a context's state (which the next step's tables read).
+cudaError_t state_sums(w2_ctx *ctx, cudaStream_t s);
+
 struct ObsArgs {
   int nx, nk, M;
   double dx, dp, hbar, mass, gamma, c_h;
@@ -99,6 +117,7 @@ struct Theta32Args {
   float *out;               // mode 0: Theta[in]; mode 1: base + (h + half_tau Theta[in])
   const double *K1, *K2, *K12;
   float half_tau;
+  double *xsum = nullptr;   // mode 1: exact per-X sums of out (or null)
 };
 
 struct Adv32Args {
@@ -113,15 +132,10 @@ struct Adv32Args {
   float z, zscale;
   int nterm;
   float tau;
-};
-
-// A persistent batched launch over the work items of several instances:
-// inst[k] is the k-th instance of the class, items [off[k], off[k+1]) are its.
-struct BatchLaunch {
-  int grid;
-  const int *inst;
-  const int *off;
-  int n;
+  // the coefficient solve in double-float pairs (hi, lo)
+  float2 zdf, zscale_df;    // z and 1/(1 - z^n) (or 1) of the start sums
+  const float2 *zpow;       // [32] z^k
+  int nterm_df;             // terms of the start sums (<= 28: |z|^28 < 2^-53)
 };
 
 struct BXsum {
@@ -129,6 +143,52 @@ struct BXsum {
   double *xsum;
   int nk;
 };
+
+// One step of a batch of FP32 instances as a single persistent launch.  The
+// work items of the seven phases of a Lawson step (tables of f^n, Theta
+// predictor, shift x2, shift x1 + combination, per-X sums of f~, tables,
+// Theta corrector with the per-X sums of f^{n+1}) form one list, phase after
+// phase (the sums of f^n come from the previous step); CTAs take items
+// from a global counter, and an item of phase p of instance i starts once
+// every item of phase p - 1 of instance i has finished (per-instance counters).
+// Items are taken in list order by running CTAs only, so every wait is for
+// items already taken by running CTAs and ends; each wait is still bounded by
+// wait_cycles (clock64), after which the CTA records W2_ERR_TIMEOUT in *err
+// and every CTA stops taking items.  The last CTA to leave resets the
+// counters, so the launch can be replayed (one graph node per step).
+constexpr int kBatchPhases = 7;
+constexpr int kBatchThreads = 256;
+struct BStepPlan {
+  int n;                      // instances
+  const int *phase_off;       // [kBatchPhases + 1] first global item of each phase
+  const int *inst_off;        // [kBatchPhases][n + 1] items of each instance within its phase
+  const int *units;           // [kBatchPhases][n] work units (X, table row or shift slab) of each instance
+  const int *gsz;             // [kBatchPhases] units per item of each phase
+  const int *nk;              // [n]
+  const int *nx;              // [n]
+  const BXsum *xs_ft;         // [n] per-X sums of f~
+  const TabArgs *tab;         // [n]
+  const Theta32Args *th;      // [2 n] predictor, corrector
+  const Adv32Args *adv;       // [2 n] x2 pass, x1 pass
+  int *next;                  // the work counter
+  int *done;                  // [kBatchPhases][n] finished items
+  int *left;                  // CTAs that have left
+  int *err;                   // 0, or a w2_status of the step
+  const int *skip;            // test hook: 1 + p * n + i stops counting phase p of instance i (or 0)
+  long long wait_cycles;      // bound of every wait
+};
+// Tile shapes of the persistent step: columns per CTA of the shift items (32
+// or 64, at most nk), warps per 16-row block of the Theta items (1 or 2), and
+// the work units a CTA takes per item (each phase's units divided into about
+// items_per_cta items per CTA of the grid).
+struct BStepShape {
+  int shift_cols, theta_split, items_per_cta;
+};
+size_t bstep_smem(const BStepShape &sh, int nxmax, int nkmax);
+cudaError_t prepare_bstep(const BStepShape &sh);
+int bstep_max_ctas_per_sm(const BStepShape &sh, size_t smem);
+cudaError_t launch_bstep(const BStepShape &sh, const BStepPlan &p, int grid, size_t smem, cudaStream_t s);
+int bstep_shift_items(int nk, int shift_cols);  // shift items per (n1, x) line
 
 // Harmonics of the pair distance r = x1 - x2 in an MLP input row.
 constexpr int kMlpHarmonics = 8;
@@ -195,18 +255,11 @@ cudaError_t prepare_kernels_f64(int nk);
 bool nk_supported_f64(int nk);
 cudaError_t prepare_kernels_f32(int nk);
 bool nk_supported_f32(int nk);
-int adv_items_per_line_f32(int nk);  // column blocks of the FP32 shift per (n1, x) line
 cudaError_t launch_theta_f32(int nk, int mode, const Theta32Args &a, cudaStream_t s);
 cudaError_t launch_adv_f32(int nk, int dir, const Adv32Args &a, cudaStream_t s);
-cudaError_t launch_btheta_f32(int nk, int mode, const BatchLaunch &b, const Theta32Args *args, cudaStream_t s);
-cudaError_t launch_badv_f32(int nk, int dir, const BatchLaunch &b, const Adv32Args *args, int nxmax, int pieces,
-                            cudaStream_t s);
 // Threads per column of the FP32 shift for lines of nx points (pieces of 32
 // rows or more, at most 8).
 __host__ __device__ inline int adv32_pieces(int nx) { return nx >= 256 ? 8 : nx >= 128 ? 4 : nx >= 64 ? 2 : 1; }
-cudaError_t launch_btables(const TabArgs *args, const int *off, int n, int grid, int nxmax, int mmax,
-                           cudaStream_t s);
-cudaError_t launch_bxsum(const BXsum *args, const int *off, int n, int grid, cudaStream_t s);
 cudaError_t launch_gemm(const GemmArgs &a, cudaStream_t s);
 // Pipelined inference GEMM (unit-stride A rows and B rows; BIAS_SILU / BIAS_SCALE epilogues).
 cudaError_t launch_gemm_fwd(const GemmArgs &a, cudaStream_t s);
@@ -255,6 +308,10 @@ struct w2_ctx {
   double *xpart, *obs_out, *h_obs;
   double z, zscale;
   int nterm;
+  // patch decomposition of the shift (w2_set_patches): patches along x1 and x2
+  // (1: the global spline), ghost points, stencil and Thomas tables per axis
+  int np_ax[2], pm_G;
+  double *pm_D, *pm_wb, *pm_tab[2], *pm_xs, *pm_gh;
   cudaGraphExec_t graph;
   bool graph_ready;
   // learned form (FP64 contexts): the MLP's pair term replaces K12

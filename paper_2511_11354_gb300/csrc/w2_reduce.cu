@@ -4,120 +4,15 @@
 #include <math.h>
 
 #include "w2_df.cuh"
+#include "w2_blocks.cuh"
 #include "w2_internal.cuh"
 
 namespace w2 {
-
-// Fixed-point image of v: round(|v| 2^(49 - E)) (FP64) or |v| 2^(48 - E)
-// (FP32), with sign, where 2^E bounds the block (emax its largest biased
-// exponent); the unit is 2^(emax - 1071) for FP64 and 2^(emax - 174) for FP32,
-// so that up to 4096 (FP64) or 16384 (FP32) images add up below 2^62.
-// Integer operations only.
-__device__ __forceinline__ long long fixed_image(double v, int emax) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  const int e = (int)((b >> 52) & 0x7ff);
-  const unsigned long long m = (b & 0xfffffffffffffull) | (e ? (1ull << 52) : 0ull);
-  const int sh = emax - (e ? e : 1) + 4;  // >= 4
-  const long long q = sh < 64 ? (long long)((m + (1ull << (sh - 1))) >> sh) : 0;
-  return (b >> 63) ? -q : q;
-}
-
-__device__ __forceinline__ long long fixed_image(float v, int emax) {
-  const unsigned b = __float_as_uint(v);
-  const int e = (int)((b >> 23) & 0xff);
-  const unsigned long long m = (unsigned long long)((b & 0x7fffffu) | (e ? 0x800000u : 0u)) << 24;
-  const int sh = emax - (e ? e : 1);  // >= 0
-  const long long q = sh == 0 ? (long long)m : sh < 64 ? (long long)((m + (1ull << (sh - 1))) >> sh) : 0;
-  return (b >> 31) ? -q : q;
-}
-
-__device__ __forceinline__ int expo_of(double v) {
-  return (int)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ff);
-}
-__device__ __forceinline__ int expo_of(float v) { return (int)((__float_as_uint(v) >> 23) & 0xff); }
-
-// Block maximum exponent and exact fixed-point sum of the n values at base,
-// with up to K values per thread held in registers between the two steps
-// (the rest, if any, read a second time).
-template <typename T, int K>
-__device__ __forceinline__ void xsum_hold(const T *f, size_t base, int n, int &em_out, long long &acc_out, int *ired) {
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
-  T v[K];
-  int em = 0;
-#pragma unroll
-  for (int i = 0; i < K; ++i) {
-    const int e = tid + i * (int)blockDim.x;
-    v[i] = e < n ? f[base + e] : (T)0;
-    em = max(em, expo_of(v[i]));
-  }
-  for (int e = tid + K * (int)blockDim.x; e < n; e += blockDim.x) em = max(em, expo_of(f[base + e]));
-  em = __reduce_max_sync(0xffffffffu, em);
-  if (lane == 0) ired[w] = em;
-  __syncthreads();
-  em = 0;
-  for (int q = 0; q < nw; ++q) em = max(em, ired[q]);
-  em = max(em, 1);
-  long long acc = 0;
-#pragma unroll
-  for (int i = 0; i < K; ++i) acc += fixed_image(v[i], em);
-  for (int e = tid + K * (int)blockDim.x; e < n; e += blockDim.x) acc += fixed_image(f[base + e], em);
-  em_out = em;
-  acc_out = acc;
-}
-
-// xsum[X] = sum_P f(X, P), one block per X, as an exact sum of fixed-point
-// images (each rounded to 2^-49 / 2^-48 of the block bound, then added
-// without rounding): the result does not depend on the order of the
-// additions, and neither the FP64 pipe nor a floating-point reduction tree is
-// involved.  A block holding Inf or NaN gives NaN.  red: 256 doubles of
-// shared memory (used as 32 ints and 32 int64).
-// (The sum is exact, so every kernel that uses this gives the same bits.)
-template <typename T, int K>
-__device__ __forceinline__ void xsum_block(const T *f, double *xsum, int nk, int X, double *red) {
-  constexpr int EMAX_NONFINITE = sizeof(T) == 8 ? 2047 : 255;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
-  const size_t base = (size_t)X * nk * nk;
-  const int n = nk * nk;
-  int *ired = reinterpret_cast<int *>(red);
-  long long *lred = reinterpret_cast<long long *>(red) + 32;
-  int em;
-  long long acc;
-  xsum_hold<T, K>(f, base, n, em, acc, ired);  // one read of the block when n <= K * blockDim
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) lred[w] = acc;
-  __syncthreads();
-  if (tid == 0) {
-    long long tot = 0;
-    for (int q = 0; q < nw; ++q) tot += lred[q];
-    xsum[X] = em == EMAX_NONFINITE ? __longlong_as_double(0x7ff8000000000000ll)
-                                   : ll_to_double_scaled(tot, em - (sizeof(T) == 8 ? 1071 : 174));
-  }
-  __syncthreads();  // red is reused by the next item of a persistent caller
-}
 
 template <typename T, int K>
 __global__ void __launch_bounds__(256) k_xsum(const T *f, double *xsum, int nk) {
   __shared__ double red[256];
   xsum_block<T, K>(f, xsum, nk, blockIdx.x, red);
-}
-
-// Batched per-X sums over the FP32 states of several instances.
-__global__ void k_bxsum(const BXsum *args, const int *off, int n) {
-  __shared__ double red[256];
-  const int total = off[n];
-  for (int item = blockIdx.x; item < total; item += gridDim.x) {
-    int k = 0;
-    while (k + 1 < n && off[k + 1] <= item) ++k;
-    const BXsum a = args[k];
-    xsum_block<float, 16>(a.f, a.xsum, a.nk, item - off[k], red);
-    __syncthreads();
-  }
-}
-
-cudaError_t launch_bxsum(const BXsum *args, const int *off, int n, int grid, cudaStream_t s) {
-  k_bxsum<<<grid, 256, 0, s>>>(args, off, n);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_xsum_f64(int nx, int nk, const double *f, double *xsum, cudaStream_t s) {

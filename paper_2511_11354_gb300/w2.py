@@ -32,9 +32,10 @@ STATUS = {0: "W2_OK", -1: "W2_ERR_ARG", -2: "W2_ERR_CUDA", -3: "W2_ERR_OOM", -4:
 EXPORTS = ("w2_create", "w2_set_potentials", "w2_set_state", "w2_stage_state", "w2_use_staged_state",
            "w2_get_state", "w2_step",
            "w2_step_profile", "w2_observables", "w2_theta", "w2_advect", "w2_destroy", "w2_status_string",
-           "w2_last_cuda_error", "w2_set_hartree", "w2_occupations", "w2_hermitian_eigvals",
+           "w2_last_cuda_error", "w2_set_hartree", "w2_set_patches", "w2_occupations", "w2_hermitian_eigvals",
            "w2_batch_create", "w2_batch_set_potentials", "w2_batch_set_state", "w2_batch_get_state",
-           "w2_batch_observables", "w2_batch_step", "w2_batch_autotune", "w2_batch_destroy",
+           "w2_batch_observables", "w2_batch_step", "w2_batch_autotune", "w2_batch_destroy", "w2_batch_sync",
+           "w2_batch_set_wait_limit", "w2_batch_inject_stall",
            "w2_mlp_create", "w2_mlp_param_count", "w2_mlp_input_dim", "w2_mlp_set_params", "w2_mlp_get_params",
            "w2_mlp_set_scales", "w2_mlp_forward", "w2_mlp_train_step", "w2_mlp_gradients", "w2_mlp_destroy",
            "w2_features", "w2_theta_pair", "w2_learned_attach", "w2_learned_report",
@@ -87,6 +88,7 @@ def load(path: str = LIB_PATH):
     lib.w2_set_state.argtypes = [vp, vp, ctypes.c_int32]
     lib.w2_get_state.argtypes = [vp, vp, ctypes.c_int32]
     lib.w2_step.argtypes = [vp, ctypes.c_int32]
+    lib.w2_set_patches.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
     lib.w2_step_profile.argtypes = [vp, ctypes.c_int32, dp]
     lib.w2_observables.argtypes = [vp, ctypes.POINTER(Obs), dp, dp]
     lib.w2_theta.argtypes = [vp, vp, vp]
@@ -103,6 +105,9 @@ def load(path: str = LIB_PATH):
     lib.w2_batch_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]
     lib.w2_batch_destroy.argtypes = [vp]
     lib.w2_batch_destroy.restype = None
+    lib.w2_batch_sync.argtypes = [vp]
+    lib.w2_batch_set_wait_limit.argtypes = [vp, ctypes.c_double]
+    lib.w2_batch_inject_stall.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
     fp = ctypes.POINTER(ctypes.c_float)
     lib.w2_mlp_create.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, ctypes.POINTER(vp)]
     lib.w2_mlp_param_count.argtypes = [vp]
@@ -206,6 +211,11 @@ class Context:
 
     def set_hartree(self, kind):
         _check(self.lib.w2_set_hartree(self.h, int(kind)), "w2_set_hartree")
+
+    def set_patches(self, np1, np2):
+        """Cut the x1 and x2 shifts into np1 and np2 patches joined by
+        perfectly matched boundary conditions (1: the global spline)."""
+        _check(self.lib.w2_set_patches(self.h, int(np1), int(np2)), "w2_set_patches")
 
     def occupations(self):
         """(occupation numbers of the one-body density matrix, largest first;
@@ -387,16 +397,25 @@ class Batch:
         _check(self.lib.w2_batch_step(self.h, int(nsteps)), "w2_batch_step")
 
     def autotune(self):
-        n = 2 + 4 * 16
-        g = (ctypes.c_int32 * n)()
-        _check(self.lib.w2_batch_autotune(self.h, g, n), "w2_batch_autotune")
+        """Time every tile shape of the one-launch step on the live batch and
+        keep the fastest (the states are restored)."""
+        g = (ctypes.c_int32 * 8)()
+        _check(self.lib.w2_batch_autotune(self.h, g, 8), "w2_batch_autotune")
         v = list(g)
-        out = {"xsum": v[0], "tables": v[1], "classes": []}
-        for q in range(2, n, 4):
-            if v[q] == 0:
-                break
-            out["classes"].append({"nk": v[q], "theta": v[q + 1], "shift_x2": v[q + 2], "shift_x1": v[q + 3]})
-        return out
+        return {"shift_cols": v[0], "theta_split": v[1], "grid": v[2], "smem_bytes": v[3], "step_us": v[4],
+                "shapes_tried": v[5], "items_per_step": v[6], "items_per_cta": v[7]}
+
+    def sync(self):
+        """Wait for the queued steps; the status code (0, or -7 for a wait that ran out)."""
+        return int(self.lib.w2_batch_sync(self.h))
+
+    def set_wait_limit(self, seconds):
+        _check(self.lib.w2_batch_set_wait_limit(self.h, float(seconds)), "w2_batch_set_wait_limit")
+
+    def inject_stall(self, phase, instance=0):
+        """Host-side fault injection: stop counting the finished items of one
+        phase of one instance (phase -1 removes it)."""
+        _check(self.lib.w2_batch_inject_stall(self.h, int(phase), int(instance)), "w2_batch_inject_stall")
 
     def observables(self, i):
         o = Obs()

@@ -18,7 +18,7 @@ def test_reference_arm_prints_the_contract_line():
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
               "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert k in d, k
-    assert d["impl"] == "reference" and d["steps"] == 1 and d["warmup"] == 3
+    assert d["impl"] == "reference" and d["steps"] == 1 and d["warmup"] == 3 and d["steps_timed"] == 1
     assert d["unit"] == "point-updates/s" and d["higher_is_better"] is True and d["value"] > 0
     assert d["config"]["nx"] == 64 and d["config"]["nk"] == 64
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]

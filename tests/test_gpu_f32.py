@@ -1,11 +1,13 @@
 """GPU checks of the precision form (W2_F32_TF32X3: FP32 state, TF32 hi+lo
-tensor-core contractions, FP32 spline increments, FP64 reductions).
+tensor-core contractions, spline coefficients solved in double-float pairs,
+FP32 increments, FP64 reductions).
 
 Bars: the operator alone within 2e-6 relative L2 of the FP64 oracle on the
 same (FP32-representable) input; the shift within 1e-6; time steps within the
 1e-6 relative L2 of the forms against the FP64 path, checked over 20 steps of
-the small workload and 200 steps of the 64^4 double-well workload, with the
-error of each observable stated.
+the small workload, 200 and 500 steps of the 64^4 double-well workload and
+500 steps of every instance of the 64-instance batch, with the error of each
+observable stated.
 """
 import numpy as np
 import pytest
@@ -71,9 +73,9 @@ def test_step32_small_workload_vs_oracle():
     assert rel(ctx.get_state(), ref) < 1e-6
 
 
-def _f64_and_f32_run(prob, f0, steps):
+def _f64_and_f32_run(prob, f0, steps, ref=None):
     from paper_2511_11354_gb300 import w2
-    a = _ctx(prob, w2.W2_F64)
+    a = _ctx(prob, w2.W2_F64 if ref is None else ref)
     a.set_state(f0)
     b = _ctx(prob, w2.W2_F32_TF32X3)
     b.set_state(f0.astype(np.float32))
@@ -104,6 +106,47 @@ def test_step32_dwell_64_200_steps_vs_f64_path():
         assert abs(y.entropy_lin - x.entropy_lin) < 1e-6
         assert np.abs(y.n1 - x.n1).max() < 1e-6 * np.abs(x.n1).max()
         assert np.abs(y.n12 - x.n12).max() < 1e-6 * np.abs(x.n12).max()
+
+
+def test_step32_dwell_64_500_steps_vs_f64_path():
+    """Config 3's length on the 64^4 double-well workload: 500 steps against
+    the sliced FP64 path (held to the oracle at 1e-10), observables every 50
+    steps."""
+    from paper_2511_11354_gb300 import w2
+    prob, f0 = inputs.workload_dwell()
+    a, b, oa, ob = _f64_and_f32_run(prob, f0, 500, ref=w2.W2_F64_SLICED)
+    err = rel(b.get_state(), a.get_state())
+    assert err < 1e-6, err
+    for x, y in zip(oa, ob):
+        assert abs(y.mass - x.mass) < 1e-6 * abs(x.mass)
+        assert abs(y.energy - x.energy) < 1e-6 * abs(x.energy)
+        assert abs(y.entropy_lin - x.entropy_lin) < 1e-6
+        assert np.abs(y.n1 - x.n1).max() < 1e-6 * np.abs(x.n1).max()
+        assert np.abs(y.n12 - x.n12).max() < 1e-6 * np.abs(x.n12).max()
+    a.close()
+    b.close()
+
+
+def test_batch_500_steps_vs_f64_path_every_instance():
+    """The batching workload (64 uneven instances, seed 3) for 500 steps: every
+    instance within 1e-6 relative L2 of its own sliced FP64 run."""
+    from paper_2511_11354_gb300 import w2
+    probs, states = inputs.workload_batch(64, seed=3)
+    bt = w2.Batch(probs)
+    for i, f in enumerate(states):
+        bt.set_state(i, f.astype(np.float32))
+    bt.step(500)
+    worst = 0.0
+    for i, (prob, f) in enumerate(zip(probs, states)):
+        a = _ctx(prob, w2.W2_F64_SLICED)
+        a.set_state(f)
+        a.step(500)
+        err = rel(bt.get_state(i), a.get_state())
+        a.close()
+        worst = max(worst, err)
+        assert err < 1e-6, (i, prob.nx, prob.nk, err)
+    bt.close()
+    print(f"batch 500 steps: worst instance rel L2 {worst:.2e}")
 
 
 def test_step32_exchange_symmetry_and_determinism():

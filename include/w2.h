@@ -180,6 +180,7 @@ w2_status w2_set_hartree(w2_ctx *ctx, int32_t kind);
  * W2_ERR_CUDA. */
 w2_status w2_set_patches(w2_ctx *ctx, int32_t np1, int32_t np2);
 
+
 /* Copy a full state f[nx][nx][nk][nk] (element type of the precision) into the context: from device
  * memory when on_device != 0, else from host memory.  Resets the step count.
  * Queued on the stream (a host source is copied with cudaMemcpyAsync, so a

@@ -39,9 +39,11 @@ __device__ __forceinline__ float2 df_norm(float sh, float se) {
   return make_float2(h, l);
 }
 
-constexpr int kChunks = 2;  // independent pieces of each recursion (instruction-level parallelism)
+// Pieces of each line: kPieces threads per (column, array) each run both
+// recursions over one piece of the line, from their own exact start sums.
+constexpr int kPieces = 2;
 
-// Start values of the recursions at positions pos[c]: the causal value
+// Start value of a recursion at position pos: the causal value
 // c_m = zscale sum_{k < nterm} z^k f_{(m - k) mod n}, or the anticausal
 // d_m = zscale sum_{k < nterm} z^k c_{(m + k) mod n}.  With nterm = n these
 // are the exact periodic sums (zscale = 1 / (1 - z^n)); with nterm = 32 < n
@@ -49,36 +51,27 @@ constexpr int kChunks = 2;  // independent pieces of each recursion (instruction
 // the scale, under the pairs' own rounding).  Pairs for the terms above
 // 2^-26 (k < 14), FP32 for the rest (below 2^-50 of the sum's scale).
 template <bool CAUSAL>
-__device__ __forceinline__ void start_sums(const float2 *col, int stride, int n, const int (&pos)[kChunks],
-                                           const AdvDFArgs &a, float2 (&out)[kChunks]) {
-  float sh[kChunks], se[kChunks], tail[kChunks];
-#pragma unroll
-  for (int c = 0; c < kChunks; ++c) sh[c] = se[c] = tail[c] = 0.f;
+__device__ __forceinline__ float2 start_sum(const float2 *col, int stride, int n, int pos, const AdvDFArgs &a) {
+  float sh = 0.f, se = 0.f, tail = 0.f;
   const int nt = a.nterm == n ? n : (a.nterm < 26 ? a.nterm : 26);
   const int kdf = nt < 14 ? nt : 14;
   for (int k = 0; k < nt; ++k) {
     const float2 zk = a.zpow[k];
-#pragma unroll
-    for (int c = 0; c < kChunks; ++c) {
-      int idx = CAUSAL ? pos[c] - k : pos[c] + k;
-      idx += CAUSAL ? (idx < 0 ? n : 0) : (idx >= n ? -n : 0);
-      const float2 v = col[idx * stride];
-      if (k < kdf) {
-        float ph, pe;
-        df_mul(zk.x, zk.y, v.x, v.y, ph, pe);
-        df_acc(sh[c], se[c], ph, pe);
-      } else {
-        tail[c] = __fmaf_rn(zk.x, v.x, tail[c]);
-      }
+    int idx = CAUSAL ? pos - k : pos + k;
+    idx += CAUSAL ? (idx < 0 ? n : 0) : (idx >= n ? -n : 0);
+    const float2 v = col[idx * stride];
+    if (k < kdf) {
+      float ph, pe;
+      df_mul(zk.x, zk.y, v.x, v.y, ph, pe);
+      df_acc(sh, se, ph, pe);
+    } else {
+      tail = __fmaf_rn(zk.x, v.x, tail);
     }
   }
-#pragma unroll
-  for (int c = 0; c < kChunks; ++c) {
-    const float2 sv = df_norm(sh[c], __fadd_rn(se[c], tail[c]));
-    float ph, pe;
-    df_mul(a.zscale.x, a.zscale.y, sv.x, sv.y, ph, pe);
-    out[c] = df_norm(ph, pe);
-  }
+  const float2 sv = df_norm(sh, __fadd_rn(se, tail));
+  float ph, pe;
+  df_mul(a.zscale.x, a.zscale.y, sv.x, sv.y, ph, pe);
+  return df_norm(ph, pe);
 }
 
 // One recursion step u = f + z v on pairs.
@@ -90,49 +83,31 @@ __device__ __forceinline__ float2 rec_step(float2 f, float2 v, float zh, float z
   return df_norm(s, t);
 }
 
-// In place on a strided column: c_i = f_i + z c_{i-1} (periodic), then
-// d_i = c_i + z d_{i+1} (periodic); the -6 z factor is in the weights.  Each
-// pass runs as kChunks interleaved recursions over consecutive pieces of the
-// line, each started from its own exact start sum.
-__device__ __forceinline__ void coeffs_df(float2 *col, int stride, int n, const AdvDFArgs &a) {
+// In place on a strided column, by the kPieces threads of the column (this
+// thread: rows [lo, lo + len)): c_i = f_i + z c_{i-1} (periodic), then
+// d_i = c_i + z d_{i+1} (periodic); the -6 z factor is in the weights.  Every
+// thread of the CTA calls this: it holds the CTA barriers between the phases.
+__device__ __forceinline__ void coeffs_df(float2 *col, int stride, int n, int lo, int len, const AdvDFArgs &a) {
   const float zh = a.z.x, zl = a.z.y;
-  int lo[kChunks], len[kChunks], hi[kChunks];
-#pragma unroll
-  for (int c = 0; c < kChunks; ++c) {
-    lo[c] = (c * n) / kChunks;
-    len[c] = ((c + 1) * n) / kChunks - lo[c];
-    hi[c] = lo[c] + len[c] - 1;
+  const int hi = lo + len - 1;
+  float2 cur = len > 0 ? start_sum<true>(col, stride, n, lo, a) : make_float2(0.f, 0.f);
+  __syncthreads();  // every start sum has read the input line
+  if (len > 0) col[lo * stride] = cur;
+  for (int j = 1; j < len; ++j) {
+    const int i = lo + j;
+    cur = rec_step(col[i * stride], cur, zh, zl);
+    col[i * stride] = cur;
   }
-  const int lmax = (n + kChunks - 1) / kChunks;
-  float2 cur[kChunks];
-  start_sums<true>(col, stride, n, lo, a, cur);
-#pragma unroll
-  for (int c = 0; c < kChunks; ++c)
-    if (len[c] > 0) col[lo[c] * stride] = cur[c];
-  for (int j = 1; j < lmax; ++j) {
-#pragma unroll
-    for (int c = 0; c < kChunks; ++c) {
-      if (j < len[c]) {
-        const int i = lo[c] + j;
-        cur[c] = rec_step(col[i * stride], cur[c], zh, zl);
-        col[i * stride] = cur[c];
-      }
-    }
+  __syncthreads();
+  cur = len > 0 ? start_sum<false>(col, stride, n, hi, a) : make_float2(0.f, 0.f);
+  __syncthreads();  // every start sum has read the causal pass
+  if (len > 0) col[hi * stride] = cur;
+  for (int j = 1; j < len; ++j) {
+    const int i = hi - j;
+    cur = rec_step(col[i * stride], cur, zh, zl);
+    col[i * stride] = cur;
   }
-  start_sums<false>(col, stride, n, hi, a, cur);
-#pragma unroll
-  for (int c = 0; c < kChunks; ++c)
-    if (len[c] > 0) col[hi[c] * stride] = cur[c];
-  for (int j = 1; j < lmax; ++j) {
-#pragma unroll
-    for (int c = 0; c < kChunks; ++c) {
-      if (j < len[c]) {
-        const int i = hi[c] - j;
-        cur[c] = rec_step(col[i * stride], cur[c], zh, zl);
-        col[i * stride] = cur[c];
-      }
-    }
-  }
+  __syncthreads();
 }
 
 // Spline value sum_q w_q d_{p + q} from the window (d_p, d_{p+1}, d_{p+2}, d_{p+3}).
@@ -161,44 +136,52 @@ __device__ __forceinline__ double axpy_join(float2 u, float2 c, float2 v) {
 // DIR 0: lines along x2 at fixed (i1 = blockIdx.y, n1 = blockIdx.x), shift of column n2.
 // DIR 1: lines along x1 at fixed (i2 = blockIdx.y, n1 = blockIdx.x), shift of row n1.
 // Inputs are pairs when DIR == TWO (the second pass), FP64 otherwise; outputs the other way.
-// TWO: shift in0 and in1, lane 2 n2 + r taking array r of column n2 (2 nk threads); DIR 1
-// with TWO writes out0 = a + tau b (lane r = 0) and out1 = a + tau/2 b (lane r = 1), the
-// two lanes swapping their values by shuffle.  Without TWO: one thread per column.
+// TWO: shift in0 and in1, lane 2 n2 + r taking array r of column n2; DIR 1 with TWO writes
+// out0 = a + tau b (lane r = 0) and out1 = a + tau/2 b (lane r = 1), the two lanes swapping
+// their values by shuffle.  Without TWO: one thread per column and piece.  Thread
+// q (A NK) + A n2 + r (A = 2 with TWO, else 1) takes piece q of the line: its rows for
+// the staging, the recursions and the outputs.
 template <int NK, int DIR, int TWO>
-__global__ void __launch_bounds__(TWO ? 2 * NK : NK) k_adv_df(AdvDFArgs a) {
+__global__ void __launch_bounds__(kPieces * (TWO ? 2 : 1) * NK) k_adv_df(AdvDFArgs a) {
   constexpr int IN_DF = (DIR == 1) == (TWO == 1);
-  constexpr int S = NK + 1;
+  constexpr int S = NK + 1, AR = TWO ? 2 : 1;
   extern __shared__ float2 smf[];
   const int nx = a.nx;
   const int n1 = blockIdx.x, fixed = blockIdx.y;
-  const int t = TWO ? (int)(threadIdx.x >> 1) : (int)threadIdx.x;  // column n2
-  const int r = TWO ? (int)(threadIdx.x & 1) : 0;                  // array
+  const int q = threadIdx.x / (AR * NK), lt = threadIdx.x - q * (AR * NK);
+  const int t = lt / AR;  // column n2
+  const int r = lt % AR;  // array
+  const int lo = (q * nx) / kPieces, len = ((q + 1) * nx) / kPieces - lo;
   float2 *A = smf + (size_t)r * (nx * S + 8);  // second buffer skewed by 16 banks (lanes 2c, 2c+1 differ)
   const void *in = r ? a.in1 : a.in0;
   const size_t lineStride = (DIR == 0) ? (size_t)NK * NK : (size_t)nx * NK * NK;
   const size_t base = (DIR == 0) ? ((size_t)fixed * nx * NK + n1) * NK : ((size_t)fixed * NK + n1) * NK;
-  // stage this thread's column; FP64 inputs are split into pairs in place
-  for (int i = 0; i < nx; ++i)
+  // stage this thread's rows of its column; FP64 inputs are split into pairs in place
+  for (int i = lo; i < lo + len; ++i)
     cp_async8(A + i * S + t, reinterpret_cast<const double *>(in) + base + i * lineStride + t);
   cp_async_wait_all();
   if (!IN_DF)
-    for (int i = 0; i < nx; ++i) A[i * S + t] = df_split(*reinterpret_cast<const double *>(A + i * S + t));
+    for (int i = lo; i < lo + len; ++i) A[i * S + t] = df_split(*reinterpret_cast<const double *>(A + i * S + t));
+  __syncthreads();  // the start sums read other pieces' rows
   const int sidx = (DIR == 0) ? t : n1;
   const int k0 = a.k0tab[sidx];
   const float2 w[4] = {a.wdf[4 * sidx], a.wdf[4 * sidx + 1], a.wdf[4 * sidx + 2], a.wdf[4 * sidx + 3]};
-  coeffs_df(A + t, S, nx, a);
-  // walk the coefficient index p of tap 0 (output x_i with i = p - jb mod nx)
-  // with a sliding window of four coefficients
-  int jb = (k0 - 1) % nx;
-  jb += (jb < 0) ? nx : 0;
-  int i = jb ? nx - jb : 0;
+  coeffs_df(A + t, S, nx, lo, len, a);
+  // outputs x_i, i in [lo, lo + len): taps p = i + k0 - 1 + (0..3) (mod nx),
+  // a sliding window of four coefficients
+  int p = (lo + k0 - 1) % nx;
+  p += (p < 0) ? nx : 0;
   float2 d[4];
 #pragma unroll
-  for (int q = 0; q < 3; ++q) d[q] = A[q * S + t];
+  for (int u = 0; u < 3; ++u) {
+    int pu = p + u;
+    pu -= (pu >= nx) ? nx : 0;
+    d[u] = A[pu * S + t];
+  }
   void *out = r ? a.out1 : a.out0;
   const float2 coef = r ? a.half_tau : a.tau;
 #pragma unroll 4
-  for (int p = 0; p < nx; ++p) {
+  for (int i = lo; i < lo + len; ++i) {
     int p3 = p + 3;
     p3 -= (p3 >= nx) ? nx : 0;
     d[3] = A[p3 * S + t];
@@ -215,8 +198,8 @@ __global__ void __launch_bounds__(TWO ? 2 * NK : NK) k_adv_df(AdvDFArgs a) {
       reinterpret_cast<double *>(out)[o] = r ? axpy_join(u, coef, v) : axpy_join(v, coef, u);
     }
 #pragma unroll
-    for (int q = 0; q < 3; ++q) d[q] = d[q + 1];
-    i = (i + 1 == nx) ? 0 : i + 1;
+    for (int u = 0; u < 3; ++u) d[u] = d[u + 1];
+    p = (p + 1 == nx) ? 0 : p + 1;
   }
 }
 
@@ -234,7 +217,7 @@ cudaError_t prep_adv_df() {
 
 template <int NK>
 cudaError_t run_adv_df(int dir, int two, const AdvDFArgs &a, cudaStream_t s) {
-  dim3 grid(NK, a.nx), block(two ? 2 * NK : NK);
+  dim3 grid(NK, a.nx), block(kPieces * (two ? 2 : 1) * NK);
   const size_t smem = sizeof(float2) * ((size_t)(two ? 2 : 1) * a.nx * (NK + 1) + 8);
   if (dir == 0 && !two) k_adv_df<NK, 0, 0><<<grid, block, smem, s>>>(a);
   if (dir == 0 && two) k_adv_df<NK, 0, 1><<<grid, block, smem, s>>>(a);

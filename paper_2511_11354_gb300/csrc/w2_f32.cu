@@ -210,9 +210,8 @@ __device__ __noinline__ void theta32_block(const Theta32Args &a, const int X, ui
     }
   }
   __syncthreads();  // the row block's Acc rows come from all of its warps
-  float held[4 * NTH];  // this thread's outputs (zeros in warps without rows), for the per-X sum
-#pragma unroll
-  for (int q = 0; q < 4 * NTH; ++q) held[q] = 0.f;
+  const bool sums = MODE == 1 && a.xsum;
+  int em_loc = 0;  // largest exponent of this thread's outputs (for the per-X sum)
   if (active) {
   float acc[NTH][4], sml[NTH][4];
 #pragma unroll
@@ -277,13 +276,47 @@ __device__ __noinline__ void theta32_block(const Theta32Args &a, const int X, ui
         v.x = fv.x + fmaf(a.half_tau, acc[bb][2 * hrow], hv.x);
         v.y = fv.y + fmaf(a.half_tau, acc[bb][2 * hrow + 1], hv.y);
       }
-      held[4 * bb + 2 * hrow] = v.x;
-      held[4 * bb + 2 * hrow + 1] = v.y;
+      if (sums) {  // the outputs wait in this thread's own Acc slots for the sum's second pass
+        em_loc = max(em_loc, max(expo_of(v.x), expo_of(v.y)));
+        Acc[n1 * S + 8 * b + 2 * t4] = v.x;
+        Acc[n1 * S + 8 * b + 2 * t4 + 1] = v.y;
+      }
       *reinterpret_cast<float2 *>(a.out + o) = v;
     }
   }
   }  // active
-  if (MODE == 1 && a.xsum) block_exact_sum(held, a.xsum + X, reinterpret_cast<int *>(smu + L::words - 64));
+  if (sums) {
+    // exact per-X sum of the outputs, the rule and bits of xsum_block
+    int *red = reinterpret_cast<int *>(smu + L::words - 64);
+    long long *lred = reinterpret_cast<long long *>(red + 32);
+    const int nw = blockDim.x >> 5;
+    int em = __reduce_max_sync(0xffffffffu, em_loc);
+    if (lane == 0) red[w] = em;
+    __syncthreads();
+    em = 0;
+    for (int q = 0; q < nw; ++q) em = max(em, red[q]);
+    em = max(em, 1);
+    long long acc2 = 0;
+    if (active) {
+#pragma unroll
+      for (int bb = 0; bb < NTH; ++bb)
+#pragma unroll
+        for (int hrow = 0; hrow < 2; ++hrow) {
+          const int n1 = hrow ? nb : na, c = 8 * (bfirst + bb) + 2 * t4;
+          acc2 += fixed_image(Acc[n1 * S + c], em) + fixed_image(Acc[n1 * S + c + 1], em);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
+    if (lane == 0) lred[w] = acc2;
+    __syncthreads();
+    if (tid == 0) {
+      long long tot = 0;
+      for (int q = 0; q < nw; ++q) tot += lred[q];
+      a.xsum[X] = em == 255 ? __longlong_as_double(0x7ff8000000000000ll) : ll_to_double_scaled(tot, em - 174);
+    }
+    __syncthreads();
+  }
 }
 
 template <int NK, int MODE>
@@ -393,20 +426,24 @@ __device__ __forceinline__ void df_madd(float2 z, float h, float l, float xh, fl
   fast_two_sum(s, t, oh, ol);
 }
 
-// Start sum sum_{k < nt} z^k (h, l)[row(k)] of one column, in double-float,
-// times the periodic scale, normalised.
+// Start sum sum_{k < nt} z^k (h, l)[row(k)] of one column, times the periodic
+// scale, normalised: double-float products for the terms above 2^-26 of the
+// sum's scale (k < 14, |z|^14 < 2^-26), FP32 for the rest (their rounding is
+// below 2^-50 of the scale).
 template <typename Row>
 __device__ __forceinline__ void df_start(const float *ch, const float *cl, int stride, const Adv32Args &a, int nt,
                                          Row row, float &oh, float &ol) {
-  float sh = 0.f, se = 0.f;
-  for (int k = 0; k < nt; ++k) {
+  float sh = 0.f, se = 0.f, tail = 0.f;
+  const int kdf = nt < 14 ? nt : 14;
+  for (int k = 0; k < kdf; ++k) {
     const int idx = row(k);
     const float2 zk = __ldg(a.zpow + k);
     float ph, pe;
     df_mul(zk.x, zk.y, ch[idx * stride], cl[idx * stride], ph, pe);
     df_acc(sh, se, ph, pe);
   }
-  two_sum(sh, se, sh, se);
+  for (int k = kdf; k < nt; ++k) tail = __fmaf_rn(__ldg(a.zpow + k).x, ch[row(k) * stride], tail);
+  two_sum(sh, __fadd_rn(se, tail), sh, se);
   float ph, pe;
   df_mul(a.zscale_df.x, a.zscale_df.y, sh, se, ph, pe);
   two_sum(ph, pe, oh, ol);

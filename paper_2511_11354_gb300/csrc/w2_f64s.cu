@@ -190,6 +190,44 @@ __device__ __forceinline__ void pair_tiles(const uint16_t *planes, const uint32_
     }
 }
 
+// The exact per-X sum of the block's outputs (the rule and bits of
+// xsum_block), second pass: each thread's outputs wait in its own slots of
+// I12 (as FP64 bit patterns, at [n1][n2] for the outputs (n1, n2) the
+// epilogue of k_theta_s gives it), em_loc is the largest exponent among them.
+// Every thread of the CTA calls this; red: 64 ints of shared memory.  Thread
+// 0 writes *out.
+template <int NK, int NCT>
+__device__ __forceinline__ void slot_exact_sum(const long long *I12, int em_loc, double *out, int *red) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5, g = lane >> 2, t4 = lane & 3;
+  const int r0 = 16 * (w >> 1), c0 = (w & 1) * (NK / 2);
+  long long *lred = reinterpret_cast<long long *>(red + 32);
+  int em = __reduce_max_sync(0xffffffffu, em_loc);
+  if (lane == 0) red[w] = em;
+  __syncthreads();
+  em = 0;
+  for (int q = 0; q < nw; ++q) em = max(em, red[q]);
+  em = max(em, 1);
+  long long acc = 0;
+#pragma unroll
+  for (int q = 0; q < NCT; ++q)
+#pragma unroll
+    for (int hr = 0; hr < 2; ++hr) {
+      const int n1 = r0 + g + 8 * hr, n2 = c0 + 8 * q + 2 * t4;
+      acc += fixed_image(__longlong_as_double(I12[n1 * NK + n2]), em);
+      acc += fixed_image(__longlong_as_double(I12[n1 * NK + n2 + 1]), em);
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) lred[w] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    long long tot = 0;
+    for (int q = 0; q < nw; ++q) tot += lred[q];
+    *out = em == 2047 ? __longlong_as_double(0x7ff8000000000000ll) : ll_to_double_scaled(tot, em - 1071);
+  }
+  __syncthreads();
+}
+
 // One CTA per spatial point X.  MODE 0: out = Theta[in].  MODE 1: out = h + half_tau Theta[in].
 template <int NK, int MODE>
 __global__ void __launch_bounds__(SlicedLayout<NK>::THREADS, 512 / SlicedLayout<NK>::THREADS)
@@ -347,9 +385,11 @@ __global__ void __launch_bounds__(SlicedLayout<NK>::THREADS, 512 / SlicedLayout<
   }
 
   // Epilogue: recombine, add the two-body term, scale, combine with h; in the
-  // corrector (with xsum given) also the exact per-X sum of the outputs.
+  // corrector (with xsum given) also the exact per-X sum of the outputs, whose
+  // values wait in the thread's own slots of I12 for the second pass.
   const int xs = emax + kmax - 2096;  // one unit of the recombined integer is 2^xs
-  double held[4 * NCT];
+  const bool sums = MODE == 1 && a.xsum;
+  int em_loc = 0;
 #pragma unroll
   for (int q = 0; q < NCT; ++q) {
 #pragma unroll
@@ -380,12 +420,15 @@ __global__ void __launch_bounds__(SlicedLayout<NK>::THREADS, 512 / SlicedLayout<
         v.x = fma(a.half_tau, t0, hv.x);
         v.y = fma(a.half_tau, t1, hv.y);
       }
-      held[4 * q + 2 * hr] = v.x;
-      held[4 * q + 2 * hr + 1] = v.y;
+      if (sums) {
+        em_loc = max(em_loc, max(expo(v.x), expo(v.y)));
+        I12[n1 * NK + n2] = __double_as_longlong(v.x);
+        I12[n1 * NK + n2 + 1] = __double_as_longlong(v.y);
+      }
       *reinterpret_cast<double2 *>(a.out + o) = v;
     }
   }
-  if (MODE == 1 && a.xsum) block_exact_sum(held, a.xsum + X, red);
+  if (sums) slot_exact_sum<NK, NCT>(I12, em_loc, a.xsum + X, red);
 }
 
 template <int NK>

@@ -266,3 +266,4 @@ def test_sliced_learned_pair_term_matches_fp64_pipe():
         c.step(5)
         outs.append(c.get_state())
     assert rel(outs[1], outs[0]) < 1e-11
+

@@ -23,7 +23,7 @@
  *   p_n = (n - nk/2) dp, dp = pi hbar / L,      n in [0, nk)
  *   phase-space arrays are f[i1][i2][n1][n2], n2 fastest, C order,
  *   nx*nx*nk*nk elements (double for W2_F64 and W2_F64_SLICED, float for
- *   W2_F32_TF32X3);
+ *   W2_F32_TF32X3 and W2_F32_BF16X3);
  *   f is zero outside the momentum window.
  *
  * Conventions:
@@ -70,6 +70,11 @@ typedef enum {
                            TF32 parts and the kernel into three (four products,
                            FP32 accumulate); the spline shift as an FP32 increment
                            of the state; densities and observables in FP64       */
+  W2_F32_BF16X3 = 2,    /* precision form as W2_F32_TF32X3, the contractions with
+                           BF16 operands: the state in three BF16 parts (exact),
+                           the kernel in four; seven m16n8k16 products per 16
+                           columns (every term to 2^-16 and the table's 2^-24
+                           term), FP32 accumulate; nk, nx as W2_F32_TF32X3        */
   W2_F64_SLICED = 3     /* FP64 state and results as W2_F64 (the FP64 oracle to
                            1e-10 over whole steps); the pseudo-difference
                            contractions as exact products of six 8-bit integer
@@ -95,9 +100,10 @@ typedef enum {
 
 /* Problem description (Sec. 3.1 grid; Sec. 5 uses hbar = m = 1).
  *   nx  : spatial points per particle, 4 <= nx; FP64 supports nx <= 128,
- *         W2_F32_TF32X3 nx <= 256
+ *         W2_F32_TF32X3 and W2_F32_BF16X3 nx <= 256
  *   nk  : momentum points per particle; W2_F64 supports nk in {8,16,...,64},
- *         W2_F64_SLICED nk in {16,32,48,64}, W2_F32_TF32X3 nk in {16,32,...,128}
+ *         W2_F64_SLICED nk in {16,32,48,64}, W2_F32_TF32X3 and W2_F32_BF16X3
+ *         nk in {16,32,...,128}
  *   L   : period of the box (> 0); dt: time step tau (> 0)
  *   hbar, mass: > 0
  *   precision: a w2_precision;  xc_kind: a w2_xc_kind                          */
@@ -236,7 +242,7 @@ w2_status w2_observables(w2_ctx *ctx, w2_obs *out, double *n1, double *n12);
  *            cubic B-spline of Sec. 4.1, x1 and x2 in turn.
  * Arrays hold the context precision's element type.
  * Errors: W2_ERR_ARG (NULL or aliasing pointers; a pointer not 16-byte aligned
- * for w2_theta, and for w2_advect in W2_F32_TF32X3), W2_ERR_STATE (potentials
+ * for w2_theta, and for w2_advect in the FP32 precisions), W2_ERR_STATE (potentials
  * not set), W2_ERR_CUDA.  Both use the context's workspace and must not overlap
  * with w2_step on another stream. */
 w2_status w2_theta(w2_ctx *ctx, const void *f, void *out);
@@ -388,6 +394,30 @@ typedef struct w2_mlp w2_mlp;
  * weights start uniform in +-sqrt(3/fan_in) (a fixed counter-based sequence),
  * biases 0, scales 1.  Errors: W2_ERR_ARG, W2_ERR_OOM, W2_ERR_CUDA. */
 w2_status w2_mlp_create(int32_t nk, int32_t hidden, int32_t max_rows, void *cuda_stream, w2_mlp **out);
+/* A kernel network: the same layers, with the two-body term's structure.
+ * Theta_{V12} f(X, n1, n2) = sum_{j >= 1} K(r, j) [F(n1 + j, n2 - j) -
+ * F(n1 - j, n2 + j)] is linear in F = f(X, ., .) with a kernel that depends
+ * on the pair distance r = x1 - x2 only, so this network maps the distance's
+ * harmonics (sin, cos (2 pi m r / L), m = 1..8, zeros up to 32 inputs) to
+ * s_y K^(r, j), j = 0 .. nk - 1 (nk outputs; j = 0 is not used).  Attached to
+ * a context (w2_learned_attach) it is evaluated once for the nx distances d dx
+ * and its table K^ takes the place of the exact pair table in the sweep.
+ * max_nx (<= 1024): the largest nx it will serve.
+ * Errors: W2_ERR_ARG, W2_ERR_OOM, W2_ERR_CUDA. */
+w2_status w2_mlp_create_kernel(int32_t nk, int32_t hidden, int32_t max_nx, void *cuda_stream, w2_mlp **out);
+/* One Adam step of a kernel network m (the context's nk, max_nx >= nx) on a
+ * batch of rows spatial points taken from trajectories of the exact method:
+ * f (device, FP64 [rows][nk^2]) the state blocks f(X, ., .), p (device, FP64
+ * [rows][nk^2]) the exact two-body term there, dr (device, int32 [rows]) the
+ * pair distance index d = (i1 - i2) mod nx of each point.  The loss
+ * sum |Theta_K^ F - P|^2 / sum |P|^2 (host, *loss, before the update) and its
+ * gradient with respect to the network's outputs are formed by the library's
+ * kernels; the update runs through the network's own backward and Adam
+ * kernels (lr, as w2_mlp_train_step).  Synchronises.
+ * Errors: W2_ERR_ARG (not a kernel network, another nk, nx > max_nx, NULL),
+ * W2_ERR_OOM, W2_ERR_NONFINITE, W2_ERR_CUDA. */
+w2_status w2_pair_kernel_train_step(w2_ctx *ctx, w2_mlp *m, const double *f, const double *p, const int32_t *dr,
+                                    int32_t rows, float lr, double *loss);
 size_t w2_mlp_param_count(const w2_mlp *m);
 int32_t w2_mlp_input_dim(const w2_mlp *m);
 /* Host copies of the packed FP32 parameters (synchronise). */
@@ -417,9 +447,10 @@ w2_status w2_features(w2_ctx *ctx, const w2_mlp *m, const void *f, const int32_t
  * context's element type, 16-byte aligned).  Queued on the stream. */
 w2_status w2_theta_pair(w2_ctx *ctx, const void *f, void *out);
 
-/* Make w2_step use m for the two-body term of a W2_F64 context (m must have
- * the context's nk and max_rows >= nx*nx; m = NULL goes back to the exact
- * term).  Every judge_every steps (0: never) the network is compared with the
+/* Make w2_step use m for the two-body term of a W2_F64 or W2_F64_SLICED
+ * context (m must have the context's nk and max_rows >= nx*nx, or for a
+ * kernel network max_nx >= nx, whose table is evaluated here; m = NULL goes
+ * back to the exact term).  Every judge_every steps (0: never) the network is compared with the
  * exact term on the current state (relative L2 error of the two-body term);
  * above tol the context falls back to the exact term for good.  The MLP is
  * borrowed and must outlive its use.  Errors: W2_ERR_ARG, W2_ERR_UNSUPPORTED
@@ -465,6 +496,22 @@ const char *w2_status_string(w2_status s);
 /* The CUDA runtime's message for the error behind the calling thread's most
  * recent W2_ERR_CUDA (a static string; "no CUDA error recorded" if none). */
 const char *w2_last_cuda_error(void);
+
+/* ------------------------------------------------------------------------
+ * Host-side fault injection for the allocation paths.  Every device and
+ * pinned-host allocation the library makes (contexts, batches, networks,
+ * patch tables, staging buffers, scratch) goes through one counter.
+ * w2_debug_fail_alloc(n), n >= 0, makes the n-th allocation from now (0: the
+ * next one) fail as if the device were full, once; the call that made it
+ * returns W2_ERR_OOM and releases what it had taken.  n < 0 disarms.  No
+ * allocation is attempted for the failed one, so nothing on the device is
+ * touched.  w2_debug_alloc_count() is the number of allocations attempted
+ * since the library was loaded (injected failures included), so a test can
+ * count a call's allocations and then fail each one in turn.  Process-wide,
+ * not thread-safe against concurrent allocating calls on other threads.
+ * Errors: none (always W2_OK). */
+w2_status w2_debug_fail_alloc(int32_t n);
+int64_t w2_debug_alloc_count(void);
 
 #ifdef __cplusplus
 }

@@ -65,3 +65,43 @@ def loss_and_grad(p, x, t, din, hidden, dout):
     grads = grads[::-1]
     g = np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in grads])
     return loss, g
+
+
+def bf16(a):
+    """Round to the nearest BF16 (ties to even), through FP32, as numbers."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def loss_and_grad_tc(p, x, t, din, hidden, dout):
+    """loss_and_grad with the roundings the tensor-core kernels apply, in
+    FP64 otherwise: weights and inputs in BF16; each hidden activation
+    silu(z) stored in BF16 for the next product and for its weight gradient;
+    the output gradient 2 (y - t)/n and each back-propagated dz rounded to
+    BF16 for the products (the bias gradients sum the unrounded dz)."""
+    p = np.asarray(p, dtype=np.float64)
+    layers = unpack(p, din, hidden, dout)
+    Wb = [bf16(W) for W, _ in layers]
+    acts, zs = [bf16(x)], []
+    a = acts[0]
+    for l, (W, b) in enumerate(layers):
+        z = a @ Wb[l] + b
+        if l < 3:
+            zs.append(z)
+            a = bf16(silu(z))
+            acts.append(a)
+        else:
+            y = z
+    n = y.size
+    loss = float(np.sum((y - t) ** 2) / n)
+    grads = []
+    dz = 2.0 * (y - t) / n
+    for l in range(3, -1, -1):
+        dzb = bf16(dz)
+        grads.append((acts[l].T @ dzb, dz.sum(axis=0)))
+        if l > 0:
+            dz = (dzb @ Wb[l].T) * dsilu(zs[l - 1])
+    grads = grads[::-1]
+    g = np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in grads])
+    return loss, g

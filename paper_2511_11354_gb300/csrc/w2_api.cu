@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <vector>
 
@@ -42,6 +43,11 @@ static cudaError_t theta64(const w2_ctx *ctx, int mode, const ThetaArgs &th, cud
   return ctx->prec == W2_F64_SLICED ? launch_theta_f64s(ctx->nk, mode, th, s) : launch_theta_f64(ctx->nk, mode, th, s);
 }
 
+// The FP32 sweep of a precision-form context: TF32 or BF16 operand splits.
+static cudaError_t theta32(const w2_ctx *ctx, int mode, const Theta32Args &th, cudaStream_t s) {
+  return ctx->prec == W2_F32_BF16X3 ? launch_theta_b3(ctx->nk, mode, th, s) : launch_theta_f32(ctx->nk, mode, th, s);
+}
+
 static void free_all(w2_ctx *c) {
   void *ptrs[] = {c->f, c->g, c->t1, c->t2, c->xsum, c->xsum2, c->K, c->K12, c->vext_fine, c->w_fine,
                   c->d_fine, c->sintab, c->vext_grid, c->k0tab, c->wtab, c->xpart, c->obs_out,
@@ -53,6 +59,7 @@ static void free_all(w2_ctx *c) {
   if (c->f1) cudaFree(c->f1);
   if (c->xrows) cudaFree(c->xrows);
   if (c->Kzero) cudaFree(c->Kzero);
+  if (c->Klearn) cudaFree(c->Klearn);
   if (c->graph_ready) cudaGraphExecDestroy(c->graph);
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->copy) {
@@ -66,6 +73,44 @@ static void free_all(w2_ctx *c) {
   for (void *p : pm)
     if (p) cudaFree(p);
 }
+
+namespace w2 {
+namespace {
+std::atomic<long long> g_alloc_fail_in{-1};  // allocations before the injected failure; -1: off
+std::atomic<long long> g_alloc_count{0};
+
+bool injected_alloc_failure() {
+  g_alloc_count.fetch_add(1);
+  long long v = g_alloc_fail_in.load();
+  while (v >= 0)
+    if (g_alloc_fail_in.compare_exchange_weak(v, v - 1)) return v == 0;
+  return false;
+}
+}  // namespace
+
+cudaError_t dev_alloc(void **p, size_t bytes) {
+  if (injected_alloc_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t host_alloc(void **p, size_t bytes) {
+  if (injected_alloc_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocHost(p, bytes);
+}
+}  // namespace w2
+
+extern "C" w2_status w2_debug_fail_alloc(int32_t n) {
+  w2::g_alloc_fail_in.store(n < 0 ? -1 : (long long)n);
+  return W2_OK;
+}
+
+extern "C" int64_t w2_debug_alloc_count(void) { return (int64_t)w2::g_alloc_count.load(); }
 
 extern "C" const char *w2_status_string(w2_status s) {
   switch (s) {
@@ -122,11 +167,14 @@ extern "C" w2_status w2_create(const w2_config *cfg, void *cuda_stream, w2_ctx *
       !(cfg->hbar > 0) || !(cfg->mass > 0) || !isfinite(cfg->L) || !isfinite(cfg->dt) ||
       cfg->xc_kind < 0 || cfg->xc_kind > 2)
     return W2_ERR_ARG;
-  if (cfg->precision != W2_F64 && cfg->precision != W2_F32_TF32X3 && cfg->precision != W2_F64_SLICED)
+  if (cfg->precision != W2_F64 && cfg->precision != W2_F32_TF32X3 && cfg->precision != W2_F32_BF16X3 &&
+      cfg->precision != W2_F64_SLICED)
     return W2_ERR_UNSUPPORTED;
   if (cfg->precision == W2_F64 && (!nk_supported_f64(cfg->nk) || cfg->nx > 128)) return W2_ERR_UNSUPPORTED;
   if (cfg->precision == W2_F64_SLICED && (!nk_supported_f64s(cfg->nk) || cfg->nx > 128)) return W2_ERR_UNSUPPORTED;
-  if (cfg->precision == W2_F32_TF32X3 && (!nk_supported_f32(cfg->nk) || cfg->nx > 256)) return W2_ERR_UNSUPPORTED;
+  if ((cfg->precision == W2_F32_TF32X3 || cfg->precision == W2_F32_BF16X3) &&
+      (!nk_supported_f32(cfg->nk) || cfg->nx > 256))
+    return W2_ERR_UNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return W2_ERR_CUDA;
   cudaDeviceProp prop;
@@ -159,7 +207,7 @@ extern "C" w2_status w2_create(const w2_config *cfg, void *cuda_stream, w2_ctx *
   const int nx = ctx->nx, nk = ctx->nk, M = ctx->M, W = 2 * nk - 1;
   cudaError_t e = cudaSuccess;
 #define W2_ALLOC(ptr, bytes)                                  \
-  if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), (bytes));
+  if (e == cudaSuccess) e = dev_alloc((void **)&(ptr), (bytes));
   const size_t fb = ctx->esz * ctx->npts;
   W2_ALLOC(ctx->f, fb) W2_ALLOC(ctx->g, fb) W2_ALLOC(ctx->t1, fb) W2_ALLOC(ctx->t2, fb)
   W2_ALLOC(ctx->xsum, sizeof(double) * nx * nx) W2_ALLOC(ctx->xsum2, sizeof(double) * nx * nx)
@@ -172,9 +220,10 @@ extern "C" w2_status w2_create(const w2_config *cfg, void *cuda_stream, w2_ctx *
   W2_ALLOC(ctx->wtab32, sizeof(float) * 4 * nk) W2_ALLOC(ctx->ctab32, sizeof(float) * 8 * nk)
   W2_ALLOC(ctx->wdf, sizeof(float2) * 4 * nk) W2_ALLOC(ctx->zpow, sizeof(float2) * 32)
 #undef W2_ALLOC
-  if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->h_obs, sizeof(double) * (8 + nx + nx * nx));
+  if (e == cudaSuccess) e = host_alloc((void **)&ctx->h_obs, sizeof(double) * (8 + nx + nx * nx));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = f64_state(ctx->prec) ? prepare_kernels_f64(nk) : prepare_kernels_f32(nk);
+  if (e == cudaSuccess && ctx->prec == W2_F32_BF16X3) e = prepare_kernels_b3(nk);
   if (e == cudaSuccess && ctx->prec == W2_F64_SLICED) e = prepare_kernels_f64s(nk);
   if (e == cudaSuccess && ctx->prec == W2_F64_SLICED) e = prepare_kernels_adv_df(nk);
   if (e != cudaSuccess) {
@@ -272,7 +321,7 @@ extern "C" w2_status w2_set_hartree(w2_ctx *ctx, int32_t kind) {
         }
         g[(size_t)d * M + l] = v / nx;
       }
-    if (!ctx->h_fine && cudaMalloc((void **)&ctx->h_fine, sizeof(double) * nx * M) != cudaSuccess) return W2_ERR_OOM;
+    if (!ctx->h_fine && dev_alloc((void **)&ctx->h_fine, sizeof(double) * nx * M) != cudaSuccess) return W2_ERR_OOM;
     W2_TRY(cudaMemcpy(ctx->h_fine, g.data(), sizeof(double) * nx * M, cudaMemcpyHostToDevice));
   }
   ctx->hartree_kind = kind;
@@ -373,7 +422,7 @@ extern "C" w2_status w2_stage_state(w2_ctx *ctx, const void *f) {
   if (!ctx->have_pot) return W2_ERR_STATE;
   const size_t bytes = ctx->esz * ctx->npts;
   if (!ctx->stage) {
-    if (cudaMalloc(&ctx->stage, bytes) != cudaSuccess) {
+    if (dev_alloc(&ctx->stage, bytes) != cudaSuccess) {
       ctx->stage = nullptr;
       (void)cudaGetLastError();
       return W2_ERR_OOM;
@@ -457,10 +506,10 @@ extern "C" w2_status w2_set_patches(w2_ctx *ctx, int32_t np1, int32_t np2) {
   for (int q = 0; q < 4 * nk; ++q) wb[q] = wt[q] / (-6.0 * z);  // the plain B-spline weights b_a(theta)
   const size_t lines = (size_t)nx * nk * nk;
   const int npmax = std::max(np1, np2);
-  cudaError_t e = cudaMalloc((void **)&ctx->pm_D, sizeof(double) * D.size());
-  if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->pm_wb, sizeof(double) * wb.size());
-  if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->pm_xs, sizeof(double) * 2 * npmax * 2 * lines);
-  if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->pm_gh, sizeof(double) * 2 * npmax * 2 * G * lines);
+  cudaError_t e = dev_alloc((void **)&ctx->pm_D, sizeof(double) * D.size());
+  if (e == cudaSuccess) e = dev_alloc((void **)&ctx->pm_wb, sizeof(double) * wb.size());
+  if (e == cudaSuccess) e = dev_alloc((void **)&ctx->pm_xs, sizeof(double) * 2 * npmax * 2 * lines);
+  if (e == cudaSuccess) e = dev_alloc((void **)&ctx->pm_gh, sizeof(double) * 2 * npmax * 2 * G * lines);
   if (e == cudaSuccess) e = cudaMemcpy(ctx->pm_D, D.data(), sizeof(double) * D.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(ctx->pm_wb, wb.data(), sizeof(double) * wb.size(), cudaMemcpyHostToDevice);
   for (int ax = 0; ax < 2 && e == cudaSuccess; ++ax) {
@@ -475,7 +524,7 @@ extern "C" w2_status w2_set_patches(w2_ctx *ctx, int32_t np1, int32_t np2) {
       tab[v] = 1.0 / m;
       tab[n + v] = cprev = (v < n - 1) ? c / m : 0.0;
     }
-    e = cudaMalloc((void **)&ctx->pm_tab[ax], sizeof(double) * tab.size());
+    e = dev_alloc((void **)&ctx->pm_tab[ax], sizeof(double) * tab.size());
     if (e == cudaSuccess) e = cudaMemcpy(ctx->pm_tab[ax], tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
   }
   if (e != cudaSuccess) {
@@ -604,7 +653,10 @@ static cudaError_t enqueue_step(w2_ctx *ctx, cudaStream_t s, const StepEvents *e
   th.K12 = ctx->K12;
   th.half_tau = 0.5 * ctx->tau;
   const bool learned = ctx->mlp && ctx->learned_active;
-  if (learned) {
+  const bool learned_kernel = learned && mlp_kind(ctx->mlp) == 1;
+  if (learned_kernel) {
+    th.K12 = ctx->Klearn;  // the network's pair table, built when it was attached
+  } else if (learned) {
     if ((e = enqueue_learned_pair(ctx, ctx->f, s)) != cudaSuccess) return e;
     th.pair = mlp_out(ctx->mlp);
   }
@@ -642,7 +694,7 @@ static cudaError_t enqueue_step(w2_ctx *ctx, cudaStream_t s, const StepEvents *e
   th.h = ctx->f;
   th.out = ctx->f;
   th.xsum = ctx->xsum;  // the per-X sums of f^{n+1}, for the next step
-  if (learned && (e = enqueue_learned_pair(ctx, ctx->g, s)) != cudaSuccess) return e;
+  if (learned && !learned_kernel && (e = enqueue_learned_pair(ctx, ctx->g, s)) != cudaSuccess) return e;
   W2_MARK(7, 0)
   if ((e = theta64(ctx, 1, th, s)) != cudaSuccess) return e;
   W2_MARK(7, 1)
@@ -692,7 +744,7 @@ static cudaError_t enqueue_step32(w2_ctx *ctx, cudaStream_t s, const StepEvents 
   th.K12 = ctx->K12;
   th.half_tau = (float)(0.5 * ctx->tau);
   W2_MARK(2, 0)
-  if ((e = launch_theta_f32(nk, 0, th, s)) != cudaSuccess) return e;
+  if ((e = theta32(ctx, 0, th, s)) != cudaSuccess) return e;
   W2_MARK(2, 1)
   Adv32Args av = adv32_args(ctx);
   av.f = f;
@@ -721,7 +773,7 @@ static cudaError_t enqueue_step32(w2_ctx *ctx, cudaStream_t s, const StepEvents 
   th.out = f;
   th.xsum = ctx->xsum;
   W2_MARK(7, 0)
-  if ((e = launch_theta_f32(nk, 1, th, s)) != cudaSuccess) return e;
+  if ((e = theta32(ctx, 1, th, s)) != cudaSuccess) return e;
   W2_MARK(7, 1)
   return cudaSuccess;
 }
@@ -854,7 +906,7 @@ extern "C" w2_status w2_theta(w2_ctx *ctx, const void *f, void *out) {
     th.K2 = ctx->K + (size_t)nx * W;
     th.K12 = ctx->K12;
     th.half_tau = (float)(0.5 * ctx->tau);
-    W2_TRY(launch_theta_f32(nk, 0, th, ctx->stream));
+    W2_TRY(theta32(ctx, 0, th, ctx->stream));
   }
   return W2_OK;
 }
@@ -932,8 +984,11 @@ extern "C" w2_status w2_step_profile(w2_ctx *ctx, int32_t nsteps, double *kernel
 // ---------------------------------------------------------------------------
 
 // Exact two-body term of `f` alone: the sweep with zero one-body tables.
-static cudaError_t enqueue_pair_exact(w2_ctx *ctx, const void *f, void *out, cudaStream_t s) {
+// The pair term alone with the pair table K12 (the exact one by default).
+static cudaError_t enqueue_pair_exact(w2_ctx *ctx, const void *f, void *out, cudaStream_t s,
+                                      const double *K12 = nullptr) {
   const int nx = ctx->nx, nk = ctx->nk, W = 2 * nk - 1;
+  if (!K12) K12 = ctx->K12;
   if (f64_state(ctx->prec)) {
     ThetaArgs th;
     th.nx = nx;
@@ -943,7 +998,7 @@ static cudaError_t enqueue_pair_exact(w2_ctx *ctx, const void *f, void *out, cud
     th.xsum = nullptr;
     th.K1 = ctx->Kzero;
     th.K2 = ctx->Kzero + (size_t)nx * W;
-    th.K12 = ctx->K12;
+    th.K12 = K12;
     th.half_tau = 0.0;
     return theta64(ctx, 0, th, s);
   }
@@ -955,18 +1010,18 @@ static cudaError_t enqueue_pair_exact(w2_ctx *ctx, const void *f, void *out, cud
   th.out = (float *)out;
   th.K1 = ctx->Kzero;
   th.K2 = ctx->Kzero + (size_t)nx * W;
-  th.K12 = ctx->K12;
+  th.K12 = K12;
   th.half_tau = 0.0f;
-  return launch_theta_f32(nk, 0, th, s);
+  return theta32(ctx, 0, th, s);
 }
 
 static w2_status ensure_pair_buffers(w2_ctx *ctx) {
   const int nx = ctx->nx, W = 2 * ctx->nk - 1;
   if (!ctx->Kzero) {
-    if (cudaMalloc((void **)&ctx->Kzero, sizeof(double) * 2 * nx * W) != cudaSuccess) return W2_ERR_OOM;
+    if (dev_alloc((void **)&ctx->Kzero, sizeof(double) * 2 * nx * W) != cudaSuccess) return W2_ERR_OOM;
     if (cudaMemset(ctx->Kzero, 0, sizeof(double) * 2 * nx * W) != cudaSuccess) return W2_ERR_CUDA;
   }
-  if (!ctx->f1 && cudaMalloc((void **)&ctx->f1, sizeof(float) * nx * ctx->nk) != cudaSuccess) return W2_ERR_OOM;
+  if (!ctx->f1 && dev_alloc((void **)&ctx->f1, sizeof(float) * nx * ctx->nk) != cudaSuccess) return W2_ERR_OOM;
   return W2_OK;
 }
 
@@ -1010,8 +1065,13 @@ extern "C" w2_status w2_features(w2_ctx *ctx, const w2_mlp *m, const void *f, co
 static w2_status learned_judge(w2_ctx *ctx) {
   cudaStream_t s = ctx->stream;
   W2_TRY(enqueue_pair_exact(ctx, ctx->f, ctx->g, s));
-  W2_TRY(enqueue_learned_pair(ctx, ctx->f, s));
-  W2_TRY(launch_sqdiff(mlp_out(ctx->mlp), ctx->g, f64_state(ctx->prec), mlp_part(ctx->mlp), ctx->npts, 1.0, s));
+  if (mlp_kind(ctx->mlp) == 1) {  // the network's pair term: the sweep with its table (t1 is free between steps)
+    W2_TRY(enqueue_pair_exact(ctx, ctx->f, ctx->t1, s, ctx->Klearn));
+    W2_TRY(launch_sqdiff64((const double *)ctx->t1, (const double *)ctx->g, mlp_part(ctx->mlp), ctx->npts, s));
+  } else {
+    W2_TRY(enqueue_learned_pair(ctx, ctx->f, s));
+    W2_TRY(launch_sqdiff(mlp_out(ctx->mlp), ctx->g, f64_state(ctx->prec), mlp_part(ctx->mlp), ctx->npts, 1.0, s));
+  }
   W2_TRY(cudaMemcpyAsync(mlp_hpart(ctx->mlp), mlp_part(ctx->mlp), sizeof(double) * 256, cudaMemcpyDeviceToHost, s));
   W2_TRY(cudaStreamSynchronize(s));
   double d = 0.0, r = 0.0;
@@ -1044,11 +1104,30 @@ extern "C" w2_status w2_learned_attach(w2_ctx *ctx, w2_mlp *m, int32_t judge_eve
     return W2_OK;
   }
   if (!f64_state(ctx->prec)) return W2_ERR_UNSUPPORTED;
-  if (mlp_nk(m) != ctx->nk || mlp_maxrows(m) < ctx->nx * ctx->nx || judge_every < 0 || !(tol >= 0)) return W2_ERR_ARG;
+  const bool kernel_net = mlp_kind(m) == 1;
+  if (mlp_nk(m) != ctx->nk || mlp_maxrows(m) < (kernel_net ? ctx->nx : ctx->nx * ctx->nx) || judge_every < 0 ||
+      !(tol >= 0))
+    return W2_ERR_ARG;
   w2_status st = ensure_pair_buffers(ctx);
   if (st != W2_OK) return st;
-  if (!ctx->xrows &&
-      cudaMalloc((void **)&ctx->xrows, sizeof(uint16_t) * (size_t)ctx->nx * ctx->nx * mlp_din(m)) != cudaSuccess)
+  if (kernel_net) {
+    // the network's pair table for every distance d dx, evaluated once: it
+    // depends on the distance alone, like the exact table it stands in for
+    const int W = 2 * ctx->nk - 1;
+    if (!ctx->Klearn && dev_alloc((void **)&ctx->Klearn, sizeof(double) * (size_t)ctx->nx * W) != cudaSuccess)
+      return W2_ERR_OOM;
+    uint16_t *rows = nullptr;  // the distance features, only for this evaluation
+    if (dev_alloc((void **)&rows, sizeof(uint16_t) * (size_t)ctx->nx * mlp_din(m)) != cudaSuccess) return W2_ERR_OOM;
+    cudaError_t e = launch_rfeat(rows, ctx->nx, mlp_din(m), ctx->stream);
+    if (e == cudaSuccess) e = mlp_forward(m, rows, ctx->nx, mlp_out(m), 1.0f, ctx->stream);
+    if (e == cudaSuccess)
+      e = launch_pairk_table(mlp_out(m), ctx->nx, ctx->nk, 1.0f / mlp_scale(m, 2), ctx->Klearn, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(rows);
+    W2_TRY(e);
+  }
+  if (!kernel_net && !ctx->xrows &&
+      dev_alloc((void **)&ctx->xrows, sizeof(uint16_t) * (size_t)ctx->nx * ctx->nx * mlp_din(m)) != cudaSuccess)
     return W2_ERR_OOM;
   ctx->mlp = m;
   ctx->learned_active = true;
@@ -1079,13 +1158,22 @@ extern "C" w2_status w2_occupations(w2_ctx *ctx, double *occ, double *entropy) {
   const int nx = ctx->nx, nk = ctx->nk;
   if (!ctx->rdm_rho) {
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->rdm_f1, sizeof(double) * nx * nk);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->rdm_fh, sizeof(double) * nx * nk);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->rdm_kh, sizeof(double) * nx);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->rdm_eig, sizeof(double) * (nx + 1));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->rdm_ph, sizeof(double2) * nx * nk);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->rdm_rho, sizeof(double2) * nx * nx);
-    if (e != cudaSuccess) return W2_ERR_OOM;
+    if (e == cudaSuccess) e = dev_alloc((void **)&ctx->rdm_f1, sizeof(double) * nx * nk);
+    if (e == cudaSuccess) e = dev_alloc((void **)&ctx->rdm_fh, sizeof(double) * nx * nk);
+    if (e == cudaSuccess) e = dev_alloc((void **)&ctx->rdm_kh, sizeof(double) * nx);
+    if (e == cudaSuccess) e = dev_alloc((void **)&ctx->rdm_eig, sizeof(double) * (nx + 1));
+    if (e == cudaSuccess) e = dev_alloc((void **)&ctx->rdm_ph, sizeof(double2) * nx * nk);
+    if (e == cudaSuccess) e = dev_alloc((void **)&ctx->rdm_rho, sizeof(double2) * nx * nx);
+    if (e != cudaSuccess) {  // release the part that was taken, so that a later call starts afresh
+      void **bufs[] = {(void **)&ctx->rdm_f1, (void **)&ctx->rdm_fh, (void **)&ctx->rdm_kh,
+                       (void **)&ctx->rdm_eig, (void **)&ctx->rdm_ph, (void **)&ctx->rdm_rho};
+      for (void **b : bufs) {
+        if (*b) cudaFree(*b);
+        *b = nullptr;
+      }
+      (void)cudaGetLastError();
+      return W2_ERR_OOM;
+    }
     // half-point interpolation kernel: K(j + 1/2), K(t) = (1/N)[1 + 2 sum_{0 < m < N/2} cos(2 pi m t / N)]
     std::vector<double> kh(nx);
     for (int j = 0; j < nx; ++j) {

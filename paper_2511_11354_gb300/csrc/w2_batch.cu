@@ -67,7 +67,7 @@ static void batch_free(w2_batch *b) {
 
 template <typename T>
 static cudaError_t upload(T **dst, const std::vector<T> &v) {
-  cudaError_t e = cudaMalloc((void **)dst, sizeof(T) * std::max<size_t>(v.size(), 1));
+  cudaError_t e = dev_alloc((void **)dst, sizeof(T) * std::max<size_t>(v.size(), 1));
   if (e == cudaSuccess) e = cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
   return e;
 }
@@ -229,9 +229,9 @@ extern "C" w2_status w2_batch_create(const w2_config *cfgs, int32_t n, void *cud
   if (e == cudaSuccess) e = upload(&b->d_xs_ft, xft);
   if (e == cudaSuccess) e = upload(&b->d_th, th);
   if (e == cudaSuccess) e = upload(&b->d_adv, adv);
-  if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_count, sizeof(int) * (4 + kBatchPhases * (size_t)n));
+  if (e == cudaSuccess) e = dev_alloc((void **)&b->d_count, sizeof(int) * (4 + kBatchPhases * (size_t)n));
   if (e == cudaSuccess) e = cudaMemset(b->d_count, 0, sizeof(int) * (4 + kBatchPhases * (size_t)n));
-  if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_err, sizeof(int));
+  if (e == cudaSuccess) e = host_alloc((void **)&b->h_err, sizeof(int));
   if (e == cudaSuccess) *b->h_err = 0;
   // default shape: 64-column shift items, two warps per Theta row block,
   // as many CTAs as fit (at most two per SM)
@@ -385,7 +385,7 @@ extern "C" w2_status w2_batch_autotune(w2_batch *b, int32_t *tuning_out, int32_t
   size_t total = 0;
   for (w2_ctx *c : b->inst) total += c->esz * c->npts;
   char *save = nullptr;
-  if (cudaMalloc((void **)&save, total) != cudaSuccess) {
+  if (dev_alloc((void **)&save, total) != cudaSuccess) {
     cudaGetLastError();
     return W2_ERR_OOM;
   }

@@ -256,6 +256,10 @@ bool nk_supported_f64(int nk);
 cudaError_t prepare_kernels_f32(int nk);
 bool nk_supported_f32(int nk);
 cudaError_t launch_theta_f32(int nk, int mode, const Theta32Args &a, cudaStream_t s);
+// The same sweep with the state in three BF16 parts and the kernel in four
+// (mma.sync m16n8k16); nk as launch_theta_f32.
+cudaError_t prepare_kernels_b3(int nk);
+cudaError_t launch_theta_b3(int nk, int mode, const Theta32Args &a, cudaStream_t s);
 cudaError_t launch_adv_f32(int nk, int dir, const Adv32Args &a, cudaStream_t s);
 // Threads per column of the FP32 shift for lines of nx points (pieces of 32
 // rows or more, at most 8).
@@ -272,6 +276,7 @@ cudaError_t launch_mse(const float *Y, const float *T, float *dY, double *part, 
                        cudaStream_t s);
 cudaError_t launch_sqdiff(const float *a, const void *b, int b_f64, double *part, size_t n, double bscale,
                           cudaStream_t s);
+cudaError_t launch_sqdiff64(const double *a, const double *b, double *part, size_t n, cudaStream_t s);
 
 }  // namespace w2
 
@@ -324,6 +329,7 @@ struct w2_ctx {
   float *f1;               // [nx][nk] reduced Wigner function for the features
   uint16_t *xrows;         // [nx*nx][din] feature rows
   double *Kzero;           // [2][nx][2nk-1] zero one-body tables (pair-only sweeps)
+  double *Klearn;          // [nx][2nk-1] the kernel network's pair table (kernel networks)
   // staged host input (allocated by the first w2_stage_state): one state,
   // filled on a private copy stream while the context's stream computes
   void *stage;
@@ -334,6 +340,11 @@ struct w2_ctx {
 };
 
 namespace w2 {
+// Every allocation of the library: cudaMalloc / cudaMallocHost behind the
+// host-side failure hook (w2_debug_fail_alloc).  On an injected failure *p
+// is null and the result is cudaErrorMemoryAllocation.
+cudaError_t dev_alloc(void **p, size_t bytes);
+cudaError_t host_alloc(void **p, size_t bytes);
 int mlp_din(const w2_mlp *m);
 int mlp_nk(const w2_mlp *m);
 int mlp_maxrows(const w2_mlp *m);
@@ -343,6 +354,15 @@ double *mlp_part(w2_mlp *m);
 double *mlp_hpart(w2_mlp *m);
 // Inference forward (pipelined GEMM with fused epilogues).
 cudaError_t mlp_forward(w2_mlp *m, const uint16_t *x, int rows, float *y, float s, cudaStream_t st);
+int mlp_kind(const w2_mlp *m);  // 0: the pair term per point; 1: the pair kernel per distance
+// Kernel network (w2_pairk.cu): the distance features, the predicted pair
+// table, and the training residual, row gradients and targets.
+cudaError_t launch_rfeat(uint16_t *x, int nx, int din, cudaStream_t s);
+cudaError_t launch_pairk_table(const float *y, int nx, int nk, float inv_sy, double *K, cudaStream_t s);
+cudaError_t launch_pairk_grad(const double *f, const double *p, const int *dr, int rows, const float *y, int nx, int nk,
+                              float inv_sy, double *res, double *g, double *part, cudaStream_t s);
+cudaError_t launch_pairk_target(const float *y, const double *g, const int *dr, int rows, int nx, int nk, float inv_sy,
+                                double inv_p2, float *t, cudaStream_t s);
 TabArgs tab_args(w2_ctx *ctx, const double *xsum, int pair_mode);
 Adv32Args adv32_args(w2_ctx *ctx);
 }  // namespace w2

@@ -13,6 +13,12 @@ using namespace w2;
 
 struct w2_mlp {
   int nk = 0, din = 0, H = 0, dout = 0, maxrows = 0;
+  int kind = 0;  // 0: the pair term per point; 1: the pair kernel per distance
+  // kernel-network training scratch (allocated by the first training step)
+  uint16_t *kx = nullptr;
+  float *ky = nullptr, *kt = nullptr;
+  double *kres = nullptr, *kg = nullptr, *kpart = nullptr, *h_kpart = nullptr;
+  int krows = 0;
   cudaStream_t stream = nullptr;
   size_t np = 0, offW[4] = {}, offb[4] = {};
   int fin[4] = {}, fout[4] = {};
@@ -29,6 +35,7 @@ struct w2_mlp {
 
 namespace w2 {
 int mlp_din(const w2_mlp *m) { return m->din; }
+int mlp_kind(const w2_mlp *m) { return m->kind; }
 int mlp_nk(const w2_mlp *m) { return m->nk; }
 int mlp_maxrows(const w2_mlp *m) { return m->maxrows; }
 float mlp_scale(const w2_mlp *m, int which) { return which == 0 ? m->s_f : which == 1 ? m->s_f1 : m->s_y; }
@@ -90,7 +97,8 @@ static cudaError_t mlp_forward_train(w2_mlp *m, const uint16_t *x, int rows, flo
   } while (0)
 
 static void mlp_free(w2_mlp *m) {
-  void *ptrs[] = {m->p, m->g, m->m, m->v, m->pb, m->Y, m->dY, m->dYb, m->part};
+  void *ptrs[] = {m->p, m->g, m->m, m->v, m->pb, m->Y, m->dY, m->dYb, m->part, m->kx, m->ky, m->kt, m->kres, m->kg,
+                  m->kpart};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   for (int l = 0; l < 3; ++l) {
@@ -100,6 +108,7 @@ static void mlp_free(w2_mlp *m) {
     if (m->dZb[l]) cudaFree(m->dZb[l]);
   }
   if (m->h_part) cudaFreeHost(m->h_part);
+  if (m->h_kpart) cudaFreeHost(m->h_kpart);
 }
 
 extern "C" void w2_mlp_destroy(w2_mlp *m) {
@@ -118,17 +127,23 @@ static double hash_uniform(uint64_t i) {
   return 2.0 * (double)(z >> 11) * (1.0 / 9007199254740992.0) - 1.0;
 }
 
-extern "C" w2_status w2_mlp_create(int32_t nk, int32_t hidden, int32_t max_rows, void *cuda_stream, w2_mlp **out) {
+static w2_status mlp_create(int kind, int32_t nk, int32_t hidden, int32_t max_rows, void *cuda_stream, w2_mlp **out) {
   if (!out) return W2_ERR_ARG;
   *out = nullptr;
   if (nk < 2 || nk > 128 || hidden < 16 || hidden > 4096 || (hidden & 15) || max_rows < 1 || max_rows > (1 << 20))
     return W2_ERR_ARG;
   w2_mlp *m = new (std::nothrow) w2_mlp();
   if (!m) return W2_ERR_OOM;
+  m->kind = kind;
   m->nk = nk;
   m->H = hidden;
-  m->dout = nk * nk;
-  m->din = ((nk * nk + 2 * nk + 2 * kMlpHarmonics) + 31) / 32 * 32;
+  if (kind == 0) {
+    m->dout = nk * nk;
+    m->din = ((nk * nk + 2 * nk + 2 * kMlpHarmonics) + 31) / 32 * 32;
+  } else {
+    m->dout = nk;
+    m->din = (2 * kMlpHarmonics + 31) / 32 * 32;
+  }
   m->maxrows = max_rows;
   m->stream = (cudaStream_t)cuda_stream;
   const int fin[4] = {m->din, hidden, hidden, hidden}, fout[4] = {hidden, hidden, hidden, m->dout};
@@ -145,7 +160,7 @@ extern "C" w2_status w2_mlp_create(int32_t nk, int32_t hidden, int32_t max_rows,
   cudaError_t e = cudaSuccess;
   const size_t R = (size_t)max_rows;
 #define WM_ALLOC(ptr, bytes) \
-  if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), (bytes));
+  if (e == cudaSuccess) e = dev_alloc((void **)&(ptr), (bytes));
   WM_ALLOC(m->p, 4 * m->np) WM_ALLOC(m->g, 4 * m->np) WM_ALLOC(m->m, 4 * m->np) WM_ALLOC(m->v, 4 * m->np)
   WM_ALLOC(m->pb, 2 * m->np)
   for (int l = 0; l < 3; ++l) {
@@ -155,7 +170,7 @@ extern "C" w2_status w2_mlp_create(int32_t nk, int32_t hidden, int32_t max_rows,
   WM_ALLOC(m->Y, 4 * R * m->dout) WM_ALLOC(m->dY, 4 * R * m->dout) WM_ALLOC(m->dYb, 2 * R * m->dout)
   WM_ALLOC(m->part, sizeof(double) * 512)
 #undef WM_ALLOC
-  if (e == cudaSuccess) e = cudaMallocHost((void **)&m->h_part, sizeof(double) * 512);
+  if (e == cudaSuccess) e = host_alloc((void **)&m->h_part, sizeof(double) * 512);
   if (e == cudaSuccess) e = cudaMemset(m->m, 0, 4 * m->np);
   if (e == cudaSuccess) e = cudaMemset(m->v, 0, 4 * m->np);
   if (e != cudaSuccess) {
@@ -178,6 +193,16 @@ extern "C" w2_status w2_mlp_create(int32_t nk, int32_t hidden, int32_t max_rows,
   }
   *out = m;
   return W2_OK;
+}
+
+extern "C" w2_status w2_mlp_create(int32_t nk, int32_t hidden, int32_t max_rows, void *cuda_stream, w2_mlp **out) {
+  return mlp_create(0, nk, hidden, max_rows, cuda_stream, out);
+}
+
+extern "C" w2_status w2_mlp_create_kernel(int32_t nk, int32_t hidden, int32_t max_nx, void *cuda_stream,
+                                          w2_mlp **out) {
+  if (max_nx > 1024) return W2_ERR_ARG;
+  return mlp_create(1, nk, hidden, max_nx, cuda_stream, out);
 }
 
 extern "C" size_t w2_mlp_param_count(const w2_mlp *m) { return m ? m->np : 0; }
@@ -292,4 +317,59 @@ extern "C" w2_status w2_mlp_train_step(w2_mlp *m, const void *x, const float *ta
   m->t += 1;
   WM_TRY(launch_adam(m->p, m->g, m->m, m->v, m->pb, m->np, lr, 0.9f, 0.999f, m->t, 1e-8f, m->stream));
   return W2_OK;
+}
+
+// One Adam step of a kernel network on a batch of spatial points (see w2.h).
+extern "C" w2_status w2_pair_kernel_train_step(w2_ctx *ctx, w2_mlp *m, const double *f, const double *p,
+                                               const int32_t *dr, int32_t rows, float lr, double *loss) {
+  if (!ctx || !m || !f || !p || !dr || rows < 1 || !(lr > 0) || m->kind != 1) return W2_ERR_ARG;
+  const int nx = ctx->nx, nk = ctx->nk;
+  if (m->nk != nk || nx > m->maxrows) return W2_ERR_ARG;
+  cudaStream_t s = m->stream;
+  if (rows > m->krows) {
+    void *old[] = {m->kres, m->kg, m->kpart};
+    for (void *q : old)
+      if (q) cudaFree(q);
+    if (m->h_kpart) cudaFreeHost(m->h_kpart);
+    m->kres = m->kg = m->kpart = m->h_kpart = nullptr;
+    m->krows = 0;
+    cudaError_t e = dev_alloc((void **)&m->kres, sizeof(double) * (size_t)rows * nk * nk);
+    if (e == cudaSuccess) e = dev_alloc((void **)&m->kg, sizeof(double) * (size_t)rows * nk);
+    if (e == cudaSuccess) e = dev_alloc((void **)&m->kpart, sizeof(double) * 2 * (size_t)rows);
+    if (e == cudaSuccess) e = host_alloc((void **)&m->h_kpart, sizeof(double) * 2 * (size_t)rows);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return W2_ERR_OOM;
+    }
+    m->krows = rows;
+  }
+  if (!m->kx) {
+    cudaError_t e = dev_alloc((void **)&m->kx, sizeof(uint16_t) * (size_t)m->maxrows * m->din);
+    if (e == cudaSuccess) e = dev_alloc((void **)&m->ky, sizeof(float) * (size_t)m->maxrows * m->dout);
+    if (e == cudaSuccess) e = dev_alloc((void **)&m->kt, sizeof(float) * (size_t)m->maxrows * m->dout);
+    if (e != cudaSuccess) {  // all three or none: a later call tests kx alone
+      void *part[] = {m->kx, m->ky, m->kt};
+      for (void *q : part)
+        if (q) cudaFree(q);
+      m->kx = nullptr;
+      m->ky = m->kt = nullptr;
+      cudaGetLastError();
+      return W2_ERR_OOM;
+    }
+  }
+  const float inv_sy = 1.0f / m->s_y;
+  WM_TRY(launch_rfeat(m->kx, nx, m->din, s));
+  WM_TRY(mlp_forward(m, m->kx, nx, m->ky, 1.0f, s));
+  WM_TRY(launch_pairk_grad(f, p, (const int *)dr, rows, m->ky, nx, nk, inv_sy, m->kres, m->kg, m->kpart, s));
+  WM_TRY(cudaMemcpyAsync(m->h_kpart, m->kpart, sizeof(double) * 2 * rows, cudaMemcpyDeviceToHost, s));
+  WM_TRY(cudaStreamSynchronize(s));
+  double r2 = 0.0, p2 = 0.0;
+  for (int b = 0; b < rows; ++b) {
+    r2 += m->h_kpart[2 * b];
+    p2 += m->h_kpart[2 * b + 1];
+  }
+  if (!(p2 > 0.0) || !isfinite(r2)) return W2_ERR_NONFINITE;
+  if (loss) *loss = r2 / p2;
+  WM_TRY(launch_pairk_target(m->ky, m->kg, (const int *)dr, rows, nx, nk, inv_sy, 1.0 / p2, m->kt, s));
+  return w2_mlp_train_step(m, m->kx, m->kt, nx, lr, nullptr);
 }

@@ -396,8 +396,8 @@ cudaError_t launch_mse(const float *Y, const float *T, float *dY, double *part, 
 }
 
 // part[b] = (sum (a - b)^2, sum b^2) over a grid-stride slice (fixed order).
-template <typename T>
-__global__ void k_sqdiff(const float *a, const T *b, double *part, size_t n, double bscale) {
+template <typename TA, typename T>
+__global__ void k_sqdiff(const TA *a, const T *b, double *part, size_t n, double bscale) {
   __shared__ double r0[256], r1[256];
   double s0 = 0.0, s1 = 0.0;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -425,9 +425,14 @@ __global__ void k_sqdiff(const float *a, const T *b, double *part, size_t n, dou
 cudaError_t launch_sqdiff(const float *a, const void *b, int b_f64, double *part, size_t n, double bscale,
                           cudaStream_t s) {
   if (b_f64)
-    k_sqdiff<double><<<128, 256, 0, s>>>(a, (const double *)b, part, n, bscale);
+    k_sqdiff<float, double><<<128, 256, 0, s>>>(a, (const double *)b, part, n, bscale);
   else
-    k_sqdiff<float><<<128, 256, 0, s>>>(a, (const float *)b, part, n, bscale);
+    k_sqdiff<float, float><<<128, 256, 0, s>>>(a, (const float *)b, part, n, bscale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sqdiff64(const double *a, const double *b, double *part, size_t n, cudaStream_t s) {
+  k_sqdiff<double, double><<<128, 256, 0, s>>>(a, b, part, n, 1.0);
   return cudaGetLastError();
 }
 

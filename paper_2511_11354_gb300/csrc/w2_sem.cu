@@ -161,7 +161,7 @@ extern "C" w2_status w2_sem_create(const w2_sem_config *cfg, void *cuda_stream, 
 
   cudaError_t e = cudaSuccess;
 #define SEM_ALLOC(ptr, count) \
-  if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), sizeof(*(ptr)) * (size_t)(count));
+  if (e == cudaSuccess) e = w2::dev_alloc((void **)&(ptr), sizeof(*(ptr)) * (size_t)(count));
   const long long N = ctx->npts;
   SEM_ALLOC(ctx->f, N) SEM_ALLOC(ctx->g, N) SEM_ALLOC(ctx->a, N) SEM_ALLOC(ctx->b, N) SEM_ALLOC(ctx->t, N)
   SEM_ALLOC(ctx->p, np) SEM_ALLOC(ctx->w, np) SEM_ALLOC(ctx->centre, M) SEM_ALLOC(ctx->cheb, Q * Q)
@@ -190,7 +190,7 @@ extern "C" w2_status w2_sem_create(const w2_sem_config *cfg, void *cuda_stream, 
     SEM_ALLOC(ctx->tE, bx * Ny) SEM_ALLOC(ctx->bE, bx * Ny) SEM_ALLOC(ctx->sE, bx * np)
   }
 #undef SEM_ALLOC
-  if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->h_obs, sizeof(double) * (8 + nx));
+  if (e == cudaSuccess) e = w2::host_alloc((void **)&ctx->h_obs, sizeof(double) * (8 + nx));
   auto up = [&](void *dst, const void *src, size_t bytes) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream);
   };
@@ -570,7 +570,7 @@ extern "C" w2_status w2_sem_occupations(w2_sem_ctx *ctx, double *occ, double *en
   if (!ctx->rrho) {
     cudaError_t e = cudaSuccess;
 #define SEM_ALLOC(ptr, count) \
-  if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), sizeof(*(ptr)) * (size_t)(count));
+  if (e == cudaSuccess) e = w2::dev_alloc((void **)&(ptr), sizeof(*(ptr)) * (size_t)(count));
     SEM_ALLOC(ctx->rf1, (long long)nx * np) SEM_ALLOC(ctx->reta, (long long)(nx + 2) * np)
     SEM_ALLOC(ctx->rg, (long long)(2 * nx - 1) * np) SEM_ALLOC(ctx->rosc, 2LL * nx * Q)
     SEM_ALLOC(ctx->rphr, (long long)(2 * nx - 1) * np) SEM_ALLOC(ctx->rphi, (long long)(2 * nx - 1) * np)

@@ -100,3 +100,60 @@ def run(prob, f0, steps, mlp=None, judge_every=0, tol=1e30, precision=w2.W2_F64)
     rep = ctx.learned_report() if mlp is not None else None
     ctx.close()
     return out, rep
+
+
+# ---------------------------------------------------------------------------
+# Kernel networks: the two-body term's structure (linear in f, a shift kernel
+# that depends on the pair distance only); the network predicts the kernel.
+# ---------------------------------------------------------------------------
+
+def make_kernel_dataset(prob, f0, snapshots, stride, points_per_snapshot, seed=0, precision=None):
+    """Run the exact FP64 method from f0 and collect, every `stride` steps,
+    `points_per_snapshot` random spatial points: their state blocks, the
+    exact two-body term there and their pair distance index d = (i1 - i2)
+    mod nx.  Returns device tensors (F float64 [rows][nk^2], P float64
+    [rows][nk^2], d int32 [rows])."""
+    torch = _torch()
+    ctx = w2.Context.from_problem(prob, precision=w2.W2_F64_SLICED if precision is None else precision)
+    nx, nk = prob.nx, prob.nk
+    ctx.set_state(torch.from_numpy(np.ascontiguousarray(f0, dtype=np.float64)).cuda())
+    f = torch.empty(ctx.shape, dtype=torch.float64, device="cuda")
+    pair = torch.empty_like(f)
+    gen = torch.Generator(device="cpu").manual_seed(seed)
+    rows = snapshots * points_per_snapshot
+    F = torch.empty(rows, nk * nk, dtype=torch.float64, device="cuda")
+    P = torch.empty_like(F)
+    D = torch.empty(rows, dtype=torch.int32, device="cuda")
+    for s in range(snapshots):
+        if s:
+            ctx.step(stride)
+        ctx.get_state(f)
+        ctx.theta_pair(f, pair)
+        xs = torch.randperm(nx * nx, generator=gen)[:points_per_snapshot]
+        r0 = s * points_per_snapshot
+        F[r0:r0 + points_per_snapshot] = f.view(nx * nx, nk * nk)[xs.cuda()]
+        P[r0:r0 + points_per_snapshot] = pair.view(nx * nx, nk * nk)[xs.cuda()]
+        D[r0:r0 + points_per_snapshot] = ((xs // nx - xs % nx) % nx).to(torch.int32).cuda()
+    ctx.close()
+    return F, P, D
+
+
+def train_kernel(mlp, prob, F, P, D, steps, batch, lr, lr_final=None, seed=0, log_every=0):
+    """Adam on random batches of the kernel dataset, through the library's
+    kernel-network training step; the learning rate decays geometrically from
+    lr to lr_final.  Returns the list of relative losses."""
+    torch = _torch()
+    ctx = w2.Context.from_problem(prob, precision=w2.W2_F64_SLICED)
+    gen = torch.Generator(device="cpu").manual_seed(seed)
+    n = F.shape[0]
+    lr_final = lr if lr_final is None else lr_final
+    losses = []
+    for it in range(steps):
+        idx = torch.randint(0, n, (min(batch, n),), generator=gen).cuda()
+        rate = lr * (lr_final / lr) ** (it / max(1, steps - 1))
+        loss = mlp.kernel_train_step(ctx, F[idx].contiguous(), P[idx].contiguous(), D[idx].contiguous(), rate)
+        losses.append(loss)
+        if log_every and it % log_every == 0:
+            print(f"kernel train step {it}: relative loss {loss:.4e} lr {rate:.2e}")
+    ctx.close()
+    return losses

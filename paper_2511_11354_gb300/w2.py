@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libw2.so")
 
 W2_F64 = 0
 W2_F32_TF32X3 = 1
+W2_F32_BF16X3 = 2
 W2_F64_SLICED = 3
 W2_HARTREE_PAIR = 0
 W2_HARTREE_POISSON = 1
@@ -35,8 +36,8 @@ EXPORTS = ("w2_create", "w2_set_potentials", "w2_set_state", "w2_stage_state", "
            "w2_last_cuda_error", "w2_set_hartree", "w2_set_patches", "w2_occupations", "w2_hermitian_eigvals",
            "w2_batch_create", "w2_batch_set_potentials", "w2_batch_set_state", "w2_batch_get_state",
            "w2_batch_observables", "w2_batch_step", "w2_batch_autotune", "w2_batch_destroy", "w2_batch_sync",
-           "w2_batch_set_wait_limit", "w2_batch_inject_stall",
-           "w2_mlp_create", "w2_mlp_param_count", "w2_mlp_input_dim", "w2_mlp_set_params", "w2_mlp_get_params",
+           "w2_batch_set_wait_limit", "w2_batch_inject_stall", "w2_debug_fail_alloc", "w2_debug_alloc_count",
+           "w2_mlp_create", "w2_mlp_create_kernel", "w2_pair_kernel_train_step", "w2_mlp_param_count", "w2_mlp_input_dim", "w2_mlp_set_params", "w2_mlp_get_params",
            "w2_mlp_set_scales", "w2_mlp_forward", "w2_mlp_train_step", "w2_mlp_gradients", "w2_mlp_destroy",
            "w2_features", "w2_theta_pair", "w2_learned_attach", "w2_learned_report",
            "w2_sem_create", "w2_sem_set_potentials", "w2_sem_momenta", "w2_sem_set_state", "w2_sem_get_state",
@@ -110,6 +111,8 @@ def load(path: str = LIB_PATH):
     lib.w2_batch_inject_stall.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
     fp = ctypes.POINTER(ctypes.c_float)
     lib.w2_mlp_create.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, ctypes.POINTER(vp)]
+    lib.w2_mlp_create_kernel.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, ctypes.POINTER(vp)]
+    lib.w2_pair_kernel_train_step.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int32, ctypes.c_float, dp]
     lib.w2_mlp_param_count.argtypes = [vp]
     lib.w2_mlp_param_count.restype = ctypes.c_size_t
     lib.w2_mlp_input_dim.argtypes = [vp]
@@ -141,13 +144,27 @@ def load(path: str = LIB_PATH):
     lib.w2_status_string.argtypes = [ctypes.c_int]
     lib.w2_status_string.restype = ctypes.c_char_p
     lib.w2_last_cuda_error.restype = ctypes.c_char_p
+    lib.w2_debug_fail_alloc.argtypes = [ctypes.c_int32]
+    lib.w2_debug_alloc_count.argtypes = []
+    lib.w2_debug_alloc_count.restype = ctypes.c_int64
     for name in EXPORTS:
         if name not in ("w2_destroy", "w2_status_string", "w2_last_cuda_error", "w2_batch_destroy", "w2_mlp_destroy",
-                        "w2_sem_destroy",
+                        "w2_sem_destroy", "w2_debug_alloc_count",
                         "w2_mlp_param_count", "w2_mlp_input_dim"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
+
+
+def debug_fail_alloc(n: int):
+    """Make the n-th device or pinned-host allocation of the library from now
+    (0: the next one) fail once as if the device were full; n < 0 disarms."""
+    _check(load().w2_debug_fail_alloc(int(n)), "w2_debug_fail_alloc")
+
+
+def debug_alloc_count() -> int:
+    """Allocations the library has attempted since it was loaded."""
+    return int(load().w2_debug_alloc_count())
 
 
 def _check(code: int, what: str):
@@ -431,21 +448,26 @@ class Batch:
 
 
 class MLP:
-    """A w2_mlp: the learned stand-in for the two-body term."""
+    """A w2_mlp: the learned stand-in for the two-body term.  kind="pair": the
+    term itself per point; kind="kernel": the term's shift kernel per pair
+    distance (max_rows is then the largest nx)."""
 
-    def __init__(self, nk, hidden=256, max_rows=4096, stream=None):
+    def __init__(self, nk, hidden=256, max_rows=4096, stream=None, kind="pair"):
         import torch
         self.lib = load()
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
+        self.kind = kind
         h = ctypes.c_void_p()
-        _check(self.lib.w2_mlp_create(nk, hidden, max_rows, ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h)),
-               "w2_mlp_create")
+        create = self.lib.w2_mlp_create_kernel if kind == "kernel" else self.lib.w2_mlp_create
+        _check(create(nk, hidden, max_rows, ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h)), "w2_mlp_create")
         self.h = h
         self.nk, self.hidden, self.max_rows = nk, hidden, max_rows
+        self.dout = nk if kind == "kernel" else nk * nk
         self.din = int(self.lib.w2_mlp_input_dim(h))
         self.nparams = int(self.lib.w2_mlp_param_count(h))
+        self.scales = (1.0, 1.0, 1.0)
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
@@ -461,7 +483,7 @@ class MLP:
     def layout(self):
         """[(name, offset, shape)] of the packed parameters."""
         dims = [(self.din, self.hidden), (self.hidden, self.hidden), (self.hidden, self.hidden),
-                (self.hidden, self.nk * self.nk)]
+                (self.hidden, self.dout)]
         out, off = [], 0
         for l, (i, o) in enumerate(dims):
             out.append((f"W{l}", off, (i, o)))
@@ -495,6 +517,17 @@ class MLP:
         loss = ctypes.c_double()
         _check(self.lib.w2_mlp_train_step(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(target.data_ptr()),
                                           int(x.shape[0]), float(lr), ctypes.byref(loss)), "w2_mlp_train_step")
+        return loss.value
+
+    def kernel_train_step(self, ctx, f, p, dr, lr):
+        """One Adam step of a kernel network on rows of (state block, exact
+        two-body term, pair distance index) from trajectories (device
+        tensors float64 [rows][nk^2], float64 [rows][nk^2], int32 [rows])."""
+        loss = ctypes.c_double()
+        _check(self.lib.w2_pair_kernel_train_step(ctx.h, self.h, ctypes.c_void_p(f.data_ptr()),
+                                                  ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(dr.data_ptr()),
+                                                  int(f.shape[0]), float(lr), ctypes.byref(loss)),
+               "w2_pair_kernel_train_step")
         return loss.value
 
     def gradients(self, x, target):

@@ -156,3 +156,57 @@ def test_inference_forward_matches_reference(nk, hidden, rows):
         a = _bf16_round(mlp_ref.silu(z)).astype(np.float64) if l < 3 else z
     err = np.linalg.norm(got - a) / np.linalg.norm(a)
     assert err < 5e-3, err
+
+
+def _tc_gradient_error(m, hidden, dout, rows, seed):
+    """Relative L2 error of the kernels' gradient against the FP64 reference
+    with the same BF16 roundings (weights, inputs, activations, dz)."""
+    rng = np.random.default_rng(seed)
+    p = (rng.standard_normal(m.nparams) * 0.05).astype(np.float32)
+    m.set_params(p)
+    x = rng.standard_normal((rows, m.din)).astype(np.float32)
+    t = rng.standard_normal((rows, dout)).astype(np.float32)
+    g, loss = m.gradients(torch.from_numpy(x).to(torch.bfloat16).cuda(), torch.from_numpy(t).cuda())
+    lref, gref = mlp_ref.loss_and_grad_tc(p.astype(np.float64), x, t.astype(np.float64), m.din, hidden, dout)
+    return abs(loss - lref) / lref, float(np.linalg.norm(g - gref) / np.linalg.norm(gref))
+
+
+def test_mlp_gradients_at_the_trained_shapes():
+    """The two trained shapes: the pair-term network of the 64^4 workload
+    (input 4256, width 256, output 4096, batch 1024) and the kernel network
+    (input 32, width 256, output 64, one row per pair distance), against the
+    reference applying the kernels' BF16 roundings: within 2e-3."""
+    from paper_2511_11354_gb300 import w2
+    pair = w2.MLP(64, 256, max_rows=1024)
+    el, eg = _tc_gradient_error(pair, 256, 64 * 64, 1024, 5)
+    assert el < 1e-3 and eg < 2e-3, (el, eg)
+    pair.close()
+    kern = w2.MLP(64, 256, max_rows=64, kind="kernel")
+    el, eg = _tc_gradient_error(kern, 256, 64, 64, 6)
+    assert el < 1e-3 and eg < 2e-3, (el, eg)
+    kern.close()
+
+
+def test_kernel_network_learns_the_two_body_term():
+    """A kernel network trained on snapshots of an exact trajectory (random
+    spatial points of each) stands in for the two-body term: the judge's
+    error is small, the state stays close to the exact run, and far closer
+    than the run without the two-body term."""
+    from paper_2511_11354_gb300 import learned, w2
+    prob, f0 = _small_dwell()
+    torch.manual_seed(0)
+    F, P, D = learned.make_kernel_dataset(prob, f0, snapshots=150, stride=1, points_per_snapshot=24, seed=0)
+    mlp = w2.MLP(prob.nk, hidden=256, max_rows=prob.nx, kind="kernel")
+    s_y = 3.0 * float(F.square().mean().sqrt()) / float(P.square().mean().sqrt())
+    mlp.set_scales(1.0, 1.0, s_y)
+    losses = learned.train_kernel(mlp, prob, F, P, D, steps=4000, batch=1024, lr=1e-3, lr_final=1e-5, seed=0)
+    assert np.mean(losses[-50:]) < 1e-4 * losses[0], (losses[0], np.mean(losses[-50:]))
+    exact, _ = learned.run(prob, f0, 40, precision=w2.W2_F64_SLICED)
+    net, rep = learned.run(prob, f0, 40, mlp, judge_every=20, tol=0.05, precision=w2.W2_F64_SLICED)
+    nopair, _ = learned.run(prob, f0, 40, learned.zero_network(prob.nk, 32, prob.nx * prob.nx),
+                            precision=w2.W2_F64_SLICED)
+    e_net = np.linalg.norm(net - exact) / np.linalg.norm(exact)
+    e_nopair = np.linalg.norm(nopair - exact) / np.linalg.norm(exact)
+    assert rep["judged"] == 2 and rep["active"], rep
+    assert rep["last_err"] < 2e-2, rep
+    assert e_net < 0.05 * e_nopair, (e_net, e_nopair)

@@ -2,7 +2,7 @@
 // interaction strengths advanced together.  Each instance is an ordinary
 // FP32 precision-form context (its own arrays and tables); one step of the
 // whole batch is ONE persistent kernel (k_bstep in w2_f32.cu) whose CTAs take
-// the work items of all eight phases of every instance from one list, phase
+// the work items of all seven phases of every instance from one list, phase
 // after phase, with per-instance phase counters ordering the items of one
 // instance; the launch is captured once into a CUDA graph and replayed.  The
 // tile shapes of the launch (columns per shift item, warps per Theta row
@@ -149,6 +149,7 @@ static cudaError_t build_plan(w2_batch *b) {
   P.skip = b->d_count + 3;
   P.done = b->d_count + 4;
   P.wait_cycles = b->wait_cycles;
+  P.smem = (int)b->smem;
   return cudaSuccess;
 }
 

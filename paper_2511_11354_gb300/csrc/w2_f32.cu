@@ -449,6 +449,19 @@ __device__ __forceinline__ void df_start(const float *ch, const float *cl, int s
   two_sum(ph, pe, oh, ol);
 }
 
+// The threads that work on one shift slab: the whole CTA (bar < 0:
+// __syncthreads), or one group of whole warps of a batch CTA synchronised by
+// its own named barrier (several slabs in flight per CTA).
+struct SlabGroup {
+  int tid, nthr, bar;
+  __device__ __forceinline__ void sync() const {
+    if (bar < 0)
+      __syncthreads();
+    else
+      asm volatile("bar.sync %0, %1;\n" ::"r"(bar), "r"(nthr) : "memory");
+  }
+};
+
 // The coefficient solve of spline_coeffs32_chunked in double-float pairs: on
 // entry (h0, l0) and (h1, l1) (h1 may be null) hold each line's values as
 // (hi, lo) pairs, on return the coefficients d of the causal and anti-causal
@@ -456,7 +469,8 @@ __device__ __forceinline__ void df_start(const float *ch, const float *cl, int s
 // (exact up to |z|^28 < 2^-53 when nterm_df < n).  Every thread of the CTA
 // calls this: it holds the CTA barriers between the phases.
 __device__ __forceinline__ void spline_coeffs_df_chunked(float *h0, float *l0, float *h1, float *l1, int stride, int n,
-                                                         const Adv32Args &a, int lo, int hi) {
+                                                         const Adv32Args &a, int lo, int hi,
+                                                         const SlabGroup &gp) {
   const int nt = hi > lo ? a.nterm_df : 0;  // an empty piece reads nothing
   float p0h = 0.f, p0l = 0.f, p1h = 0.f, p1l = 0.f;
   auto back = [lo, n](int k) {
@@ -465,7 +479,7 @@ __device__ __forceinline__ void spline_coeffs_df_chunked(float *h0, float *l0, f
   };
   df_start(h0, l0, stride, a, nt, back, p0h, p0l);
   if (h1) df_start(h1, l1, stride, a, nt, back, p1h, p1l);
-  __syncthreads();  // every start sum has read the input line
+  gp.sync();  // every start sum has read the input line
   if (hi > lo) {
     h0[lo * stride] = p0h;
     l0[lo * stride] = p0l;
@@ -484,7 +498,7 @@ __device__ __forceinline__ void spline_coeffs_df_chunked(float *h0, float *l0, f
       }
     }
   }
-  __syncthreads();
+  gp.sync();
   const int e = hi - 1;
   auto fwd = [e, n](int k) {
     int idx = e + k;
@@ -492,7 +506,7 @@ __device__ __forceinline__ void spline_coeffs_df_chunked(float *h0, float *l0, f
   };
   df_start(h0, l0, stride, a, nt, fwd, p0h, p0l);
   if (h1) df_start(h1, l1, stride, a, nt, fwd, p1h, p1l);
-  __syncthreads();  // every start sum has read the causal pass
+  gp.sync();  // every start sum has read the causal pass
   if (hi > lo) {
     h0[e * stride] = p0h;
     l0[e * stride] = p0l;
@@ -511,7 +525,7 @@ __device__ __forceinline__ void spline_coeffs_df_chunked(float *h0, float *l0, f
       }
     }
   }
-  __syncthreads();
+  gp.sync();
 }
 
 __device__ __forceinline__ int wrap(int j, int n) {
@@ -583,9 +597,10 @@ struct AdvCols {
 // into rows kGhost + i of a shared slab of stride C, 16 bytes per copy, all
 // copies of the CTA in flight together.
 template <int C>
-__device__ __forceinline__ void stage_slab(float *slab, const float *src, size_t lineStride, int nx) {
+__device__ __forceinline__ void stage_slab(float *slab, const float *src, size_t lineStride, int nx,
+                                           const SlabGroup &gp) {
   constexpr int Q = C / 4;
-  for (int e = threadIdx.x; e < nx * Q; e += blockDim.x) {
+  for (int e = gp.tid; e < nx * Q; e += gp.nthr) {
     const int i = e / Q, c = 4 * (e - i * Q);
     cp_async16(slab + (kGhost + i) * C + c, src + i * lineStride + c);
   }
@@ -597,8 +612,9 @@ __device__ __forceinline__ void stage_slab(float *slab, const float *src, size_t
 //   two arrays: d1 = (S1 - I) u, b = S1 g2, ft = u + d1 + tau b,
 //               dh = d2 + d1 + tau/2 b   (dh may overwrite d2 in place)
 //   one array : ft = u + d1  (= S1 S2 f)
-// A CTA owns columns [cb*C, cb*C + C) of the slab with adv32_pieces(nx)
-// threads per column: thread t takes column t % C and the rows of piece t / C
+// A group of threads (the CTA, or a group of whole warps of a batch CTA)
+// owns columns [cb*C, cb*C + C) of the slab with adv32_pieces(nx) threads per
+// column: its thread t takes column t % C and the rows of piece t / C
 // (staging, the spline solve in pieces, the evaluation).  Shared memory: the
 // staged slabs (FP32) and the lo parts of the two solved arrays (FP32),
 // rows nx + 2 kGhost each: 4 slabs for DIR 0, 5 for DIR 1.
@@ -609,11 +625,11 @@ template <int NK, int DIR, int C>
 // compiled once (not inlined) so the single-problem and batched kernels
 // run the same machine code and give identical bits
 __device__ __noinline__ void adv32_block(const Adv32Args &a, const int n1, const int cb, const int fixed,
-                                         float *sm32) {
+                                         float *sm32, const SlabGroup &gp) {
   const int nx = a.nx;
   // the pieces depend on nx only, so that every launch shape gives the same bits;
   // threads beyond them idle (a batch launch is sized for its longest lines)
-  const int t = threadIdx.x % C, q = threadIdx.x / C, P = adv32_pieces(nx);
+  const int t = gp.tid % C, q = gp.tid / C, P = adv32_pieces(nx);
   const int col = cb * C + t;
   const int rows = nx + 2 * kGhost;
   const int lo = q < P ? (q * nx) / P : 0, hi = q < P ? ((q + 1) * nx) / P : 0;
@@ -633,17 +649,17 @@ __device__ __noinline__ void adv32_block(const Adv32Args &a, const int n1, const
   float *A = SA + t, *B = SB + t, *Cc = SC + t, *la = LA + t, *l1 = L1 + t;  // this thread's column
   if (DIR == 0) {
     const bool two = a.g != nullptr;
-    stage_slab<C>(SA, a.f + base, lineStride, nx);
-    if (two) stage_slab<C>(SB, a.g + base, lineStride, nx);
+    stage_slab<C>(SA, a.f + base, lineStride, nx, gp);
+    if (two) stage_slab<C>(SB, a.g + base, lineStride, nx, gp);
     for (int i = lo; i < hi; ++i) {
       la[(kGhost + i) * C] = 0.f;
       l1[(kGhost + i) * C] = 0.f;
     }
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-    __syncthreads();
+    gp.sync();
     spline_coeffs_df_chunked(A + kGhost * C, la + kGhost * C, two ? B + kGhost * C : nullptr,
-                             two ? l1 + kGhost * C : nullptr, C, nx, a, lo, hi);
-    if (threadIdx.x < C) {
+                             two ? l1 + kGhost * C : nullptr, C, nx, a, lo, hi, gp);
+    if (gp.tid < C) {
       fill_ghosts(A, C, nx);
       fill_ghosts(la, C, nx);
       if (two) {
@@ -651,7 +667,7 @@ __device__ __noinline__ void adv32_block(const Adv32Args &a, const int n1, const
         fill_ghosts(l1, C, nx);
       }
     }
-    __syncthreads();
+    gp.sync();
     for (int i = lo; i < hi; ++i) {
       const size_t o = base + i * lineStride + t;
       a.d2[o] = incr32(A, C, nx, i, k0, w, ct, a.z) + incr32(la, C, nx, i, k0, w, ct, a.z);
@@ -659,11 +675,11 @@ __device__ __noinline__ void adv32_block(const Adv32Args &a, const int n1, const
     }
   } else {
     const bool two = a.g2in != nullptr;
-    stage_slab<C>(SA, a.f + base, lineStride, nx);
-    stage_slab<C>(SB, a.d2in + base, lineStride, nx);
-    if (two) stage_slab<C>(SC, a.g2in + base, lineStride, nx);
+    stage_slab<C>(SA, a.f + base, lineStride, nx, gp);
+    stage_slab<C>(SB, a.d2in + base, lineStride, nx, gp);
+    if (two) stage_slab<C>(SC, a.g2in + base, lineStride, nx, gp);
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-    __syncthreads();
+    gp.sync();
     for (int i = lo; i < hi; ++i) {  // u = f + d2 as an exact pair
       float uh, ul;
       two_sum(A[(kGhost + i) * C], B[(kGhost + i) * C], uh, ul);
@@ -671,10 +687,10 @@ __device__ __noinline__ void adv32_block(const Adv32Args &a, const int n1, const
       la[(kGhost + i) * C] = ul;
       l1[(kGhost + i) * C] = 0.f;
     }
-    __syncthreads();
+    gp.sync();
     spline_coeffs_df_chunked(A + kGhost * C, la + kGhost * C, two ? Cc + kGhost * C : nullptr,
-                             two ? l1 + kGhost * C : nullptr, C, nx, a, lo, hi);
-    if (threadIdx.x < C) {
+                             two ? l1 + kGhost * C : nullptr, C, nx, a, lo, hi, gp);
+    if (gp.tid < C) {
       fill_ghosts(A, C, nx);
       fill_ghosts(la, C, nx);
       if (two) {
@@ -682,7 +698,7 @@ __device__ __noinline__ void adv32_block(const Adv32Args &a, const int n1, const
         fill_ghosts(l1, C, nx);
       }
     }
-    __syncthreads();
+    gp.sync();
     for (int i = lo; i < hi; ++i) {
       const size_t o = base + i * lineStride + t;
       const float d1 = incr32(A, C, nx, i, k0, w, ct, a.z) + incr32(la, C, nx, i, k0, w, ct, a.z);
@@ -701,9 +717,10 @@ __device__ __noinline__ void adv32_block(const Adv32Args &a, const int n1, const
   }
 }
 
-// Columns per CTA of the single-problem shift beyond 128 points per line: 32
+// Columns per CTA of the single-problem shift from 128 points per line on: 32
 // (16 when nk is an odd multiple of 16), so that five slabs of nx + 2 kGhost
-// rows fit.
+// rows fit and, at 128 points, two or three CTAs share an SM (with 64 columns
+// one CTA of 8 warps per SM left the serial recursions latency bound).
 template <int NK>
 struct AdvColsWide {
   static constexpr int C = NK % 32 == 0 ? 32 : 16;
@@ -714,7 +731,8 @@ template <int NK, int DIR, int C>
 __global__ void __launch_bounds__(8 * C) k_adv32(Adv32Args a) {
   extern __shared__ __align__(16) float sm32[];
   constexpr int NB = NK / C;
-  adv32_block<NK, DIR, C>(a, blockIdx.x / NB, blockIdx.x % NB, blockIdx.y, sm32);
+  adv32_block<NK, DIR, C>(a, blockIdx.x / NB, blockIdx.x % NB, blockIdx.y, sm32,
+                          SlabGroup{(int)threadIdx.x, (int)blockDim.x, -1});
 }
 
 
@@ -769,7 +787,7 @@ static cudaError_t run_adv32_c(int dir, const Adv32Args &a, cudaStream_t s) {
 
 template <int NK>
 static cudaError_t run_adv32(int dir, const Adv32Args &a, cudaStream_t s) {
-  return a.nx <= 128 ? run_adv32_c<NK, AdvCols<NK>::C>(dir, a, s) : run_adv32_c<NK, AdvColsWide<NK>::C>(dir, a, s);
+  return a.nx < 128 ? run_adv32_c<NK, AdvCols<NK>::C>(dir, a, s) : run_adv32_c<NK, AdvColsWide<NK>::C>(dir, a, s);
 }
 
 #define W2_NK32_SWITCH(nk, EXPR_TEMPLATE) \
@@ -824,16 +842,47 @@ __device__ __forceinline__ int bsearch_inst(const int *off, int n, int item) {
   return lo;
 }
 
-template <int NK, int CS, int TS>
-__device__ __forceinline__ void bstep_item(const BStepPlan &P, int p, int i, int j, unsigned char *sm) {
+// Warps per 16-row block of a batch Theta item: with TS = 2, as many as the
+// 8 warps of the CTA allow (NK / 16 row blocks; the count must divide the
+// NK / 8 column tiles), so that NK = 32 keeps every warp busy (4 per row
+// block) instead of half of them; TS = 1 keeps one.  The split does not
+// change the bits.
+__host__ __device__ constexpr int bstep_tsplit(int nk, int ts) {
+  return ts == 1 ? 1 : (nk / 8) % (kBatchThreads / 32 / (nk / 16)) == 0 ? kBatchThreads / 32 / (nk / 16) : 2;
+}
+
+template <int NK, int TS>
+__device__ __forceinline__ void bstep_theta(const BStepPlan &P, int p, int i, int j, unsigned char *sm) {
+  constexpr int SPLIT = bstep_tsplit(NK, TS);
+  if (p == 1) theta32_block<NK, 0, SPLIT>(P.th[2 * i], j, reinterpret_cast<uint32_t *>(sm));
+  else theta32_block<NK, 1, SPLIT>(P.th[2 * i + 1], j, reinterpret_cast<uint32_t *>(sm));
+}
+
+// Shift units [u0, u1) of instance i (phase 2: x2 pass, 3: x1 pass).  The
+// slab's adv32_pieces(nx) x C threads, rounded up to whole warps, form a
+// group; as many groups as fit the CTA's threads and shared memory (at most
+// eight) take the units in turn, each in its own part of shared memory and
+// with its own named barrier, so small lines do not leave most of the CTA
+// idle.  Threads outside the groups return at once.
+template <int NK, int CS>
+__device__ __forceinline__ void bstep_shift(const BStepPlan &P, int p, int i, int u0, int u1, unsigned char *sm) {
   constexpr int C = bstep_cols(NK, CS);
   constexpr int NB = NK / C;
-  switch (p) {
-    case 1: theta32_block<NK, 0, TS>(P.th[2 * i], j, reinterpret_cast<uint32_t *>(sm)); break;
-    case 6: theta32_block<NK, 1, TS>(P.th[2 * i + 1], j, reinterpret_cast<uint32_t *>(sm)); break;
-    case 2: adv32_block<NK, 0, C>(P.adv[2 * i], (j / NB) % NK, j % NB, (j / NB) / NK, reinterpret_cast<float *>(sm)); break;
-    case 3: adv32_block<NK, 1, C>(P.adv[2 * i + 1], (j / NB) % NK, j % NB, (j / NB) / NK, reinterpret_cast<float *>(sm)); break;
-    default: break;
+  const int nx = P.nx[i];
+  const int S = (C * adv32_pieces(nx) + 31) & ~31;
+  const size_t slab_bytes =
+      ((size_t)(p == 2 ? adv32_slabs<0>() : adv32_slabs<1>()) * (nx + 2 * kGhost) * C * sizeof(float) + 15) & ~(size_t)15;
+  const int G = max(1, min(min((int)blockDim.x / S, (int)(P.smem / slab_bytes)), 8));
+  const int grp = threadIdx.x / S;
+  if (grp >= G) return;
+  const SlabGroup gp{(int)threadIdx.x - grp * S, S, 1 + grp};
+  float *sm32 = reinterpret_cast<float *>(sm + grp * slab_bytes);
+  for (int u = u0 + grp; u < u1; u += G) {
+    if (p == 2)
+      adv32_block<NK, 0, C>(P.adv[2 * i], (u / NB) % NK, u % NB, (u / NB) / NK, sm32, gp);
+    else
+      adv32_block<NK, 1, C>(P.adv[2 * i + 1], (u / NB) % NK, u % NB, (u / NB) / NK, sm32, gp);
+    gp.sync();  // the group's slabs are free again
   }
 }
 
@@ -879,24 +928,35 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_bstep(BStepPlan P) {
     __syncthreads();
     if (!s_ok) break;
     const int nk = P.nk[i], g = P.gsz[p];
-    const int u1 = min((j + 1) * g, P.units[p * P.n + i]);
-    for (int u = j * g; u < u1; ++u) {
-      if (p == 4) {
-        const BXsum &a = P.xs_ft[i];
-        xsum_block<float, 16>(a.f, a.xsum, a.nk, u, reinterpret_cast<double *>(smb));
-      } else if (p == 0 || p == 5) {
-        const int nx = P.nx[i];
-        tables_block(P.tab[i], u % nx, u / nx, reinterpret_cast<double *>(smb));
-      } else {
-        switch (nk) {
-          case 16: bstep_item<16, CS, TS>(P, p, i, u, smb); break;
-          case 32: bstep_item<32, CS, TS>(P, p, i, u, smb); break;
-          case 48: bstep_item<48, CS, TS>(P, p, i, u, smb); break;
-          case 64: bstep_item<64, CS, TS>(P, p, i, u, smb); break;
-          default: break;
-        }
+    const int u0 = j * g, u1 = min((j + 1) * g, P.units[p * P.n + i]);
+    if (p == 2 || p == 3) {
+      switch (nk) {
+        case 16: bstep_shift<16, CS>(P, p, i, u0, u1, smb); break;
+        case 32: bstep_shift<32, CS>(P, p, i, u0, u1, smb); break;
+        case 48: bstep_shift<48, CS>(P, p, i, u0, u1, smb); break;
+        case 64: bstep_shift<64, CS>(P, p, i, u0, u1, smb); break;
+        default: break;
       }
-      __syncthreads();  // every thread's writes of this unit are issued; shared memory is free again
+      __syncthreads();  // every group's writes are issued; shared memory is free again
+    } else {
+      for (int u = u0; u < u1; ++u) {
+        if (p == 4) {
+          const BXsum &a = P.xs_ft[i];
+          xsum_block<float, 16>(a.f, a.xsum, a.nk, u, reinterpret_cast<double *>(smb));
+        } else if (p == 0 || p == 5) {
+          const int nx = P.nx[i];
+          tables_block(P.tab[i], u % nx, u / nx, reinterpret_cast<double *>(smb));
+        } else {
+          switch (nk) {
+            case 16: bstep_theta<16, TS>(P, p, i, u, smb); break;
+            case 32: bstep_theta<32, TS>(P, p, i, u, smb); break;
+            case 48: bstep_theta<48, TS>(P, p, i, u, smb); break;
+            case 64: bstep_theta<64, TS>(P, p, i, u, smb); break;
+            default: break;
+          }
+        }
+        __syncthreads();  // every thread's writes of this unit are issued; shared memory is free again
+      }
     }
     if (threadIdx.x == 0) {
       __threadfence();
@@ -936,6 +996,9 @@ cudaError_t prepare_bstep(const BStepShape &sh) {
 // Shared memory of the persistent step: the largest of its items' needs
 // (shift: five slabs of nx + 2 kGhost rows; Theta: the split block; tables:
 // densities and fine-point potentials; per-X sums: 256 doubles).
+// Shared memory of a batch CTA: the largest single unit (a Theta block or a
+// shift slab set), and at least 110 KB while two CTAs still fit an SM, so
+// that several shift slabs of the smaller instances are in flight at once.
 size_t bstep_smem(const BStepShape &sh, int nxmax, int nkmax) {
   size_t m = 256 * sizeof(double);
   m = std::max(m, sizeof(double) * (size_t)(nxmax + 2 * nkmax));
@@ -944,7 +1007,7 @@ size_t bstep_smem(const BStepShape &sh, int nxmax, int nkmax) {
     const size_t ad = sizeof(float) * 5 * (size_t)(nxmax + 2 * kGhost) * bstep_cols(nk, sh.shift_cols);
     m = std::max(m, std::max(th, ad));
   }
-  return m;
+  return std::max(m, (size_t)110 * 1024);
 }
 
 int bstep_max_ctas_per_sm(const BStepShape &sh, size_t smem) {

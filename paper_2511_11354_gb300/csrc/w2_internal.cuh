@@ -166,6 +166,7 @@ struct BStepPlan {
   const int *gsz;             // [kBatchPhases] units per item of each phase
   const int *nk;              // [n]
   const int *nx;              // [n]
+  int smem;                   // dynamic shared memory of the launch (bytes)
   const BXsum *xs_ft;         // [n] per-X sums of f~
   const TabArgs *tab;         // [n]
   const Theta32Args *th;      // [2 n] predictor, corrector
@@ -261,9 +262,11 @@ cudaError_t launch_theta_f32(int nk, int mode, const Theta32Args &a, cudaStream_
 cudaError_t prepare_kernels_b3(int nk);
 cudaError_t launch_theta_b3(int nk, int mode, const Theta32Args &a, cudaStream_t s);
 cudaError_t launch_adv_f32(int nk, int dir, const Adv32Args &a, cudaStream_t s);
-// Threads per column of the FP32 shift for lines of nx points (pieces of 32
-// rows or more, at most 8).
-__host__ __device__ inline int adv32_pieces(int nx) { return nx >= 256 ? 8 : nx >= 128 ? 4 : nx >= 64 ? 2 : 1; }
+// Threads per column of the FP32 shift for lines of nx points (at most 8;
+// from 128 points on, pieces of 16 rows or more: the double-float recursions
+// are serial chains, and more of them per SM hide their latency better than
+// the extra start sums cost).
+__host__ __device__ inline int adv32_pieces(int nx) { return nx >= 128 ? 8 : nx >= 64 ? 2 : 1; }
 cudaError_t launch_gemm(const GemmArgs &a, cudaStream_t s);
 // Pipelined inference GEMM (unit-stride A rows and B rows; BIAS_SILU / BIAS_SCALE epilogues).
 cudaError_t launch_gemm_fwd(const GemmArgs &a, cudaStream_t s);

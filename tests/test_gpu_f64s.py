@@ -178,7 +178,7 @@ def test_sliced_determinism_and_resume():
 
 # (precision, nk, operator bar, shift bar, step bar)
 SMALLEST = [("W2_F64", 8, 1e-12, 1e-13, 1e-10), ("W2_F64_SLICED", 16, 2e-12, 1e-13, 1e-10),
-            ("W2_F32_TF32X3", 16, 2e-6, 1e-6, 1e-6)]
+            ("W2_F32_TF32X3", 16, 2e-6, 1e-6, 1e-6), ("W2_F32_BF16X3", 16, 2e-6, 1e-6, 1e-6)]
 
 
 @pytest.mark.parametrize("nx", [4, 5])
@@ -187,7 +187,7 @@ def test_smallest_spatial_grids(nx, prec, nk, bar_theta, bar_adv, bar_step):
     """The smallest grids the API takes (nx = 4 and 5: periodic lines of four
     or five points, shorter than the spline start sums and split into
     recursion pieces of two or three points): operator, shift and three steps
-    against the oracle on every element, for all three precisions."""
+    against the oracle on every element, for every precision."""
     from paper_2511_11354_gb300 import w2
     prob, f0 = inputs.workload_small(nx=nx, nk=nk)
     ctx = w2.Context.from_problem(prob, precision=getattr(w2, prec))
@@ -205,7 +205,7 @@ def test_smallest_spatial_grids(nx, prec, nk, bar_theta, bar_adv, bar_step):
     assert rel(ctx.get_state().astype(np.float64), o.step(f64, 3)) < bar_step
 
 
-@pytest.mark.parametrize("prec", ["W2_F64_SLICED", "W2_F32_TF32X3"])
+@pytest.mark.parametrize("prec", ["W2_F64_SLICED", "W2_F32_TF32X3", "W2_F32_BF16X3"])
 def test_staged_host_input_pipeline(prec):
     """w2_stage_state / w2_use_staged_state: three host states streamed with
     the copy of the next one queued while the current one steps give the same

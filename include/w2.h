@@ -200,9 +200,12 @@ w2_status w2_set_state(w2_ctx *ctx, const void *f, int32_t on_device);
  * the context's staging buffer on a private copy stream and returns; the
  * context's state is not touched.  The copy starts once the previous staged
  * state has been taken.  w2_use_staged_state makes the staged state the
- * context's state: the context's stream waits for the copy, then copies the
- * stage in (device to device) and the step count is reset.  The staging
- * buffer (one state) and the copy stream are created by the first
+ * context's state: the context's stream waits for the copy, the staging
+ * buffer and the state buffer trade places (no device copy; the next staged
+ * copy goes into the old state buffer once the work queued on it is done),
+ * the per-X sums of the new state are computed and the step count is reset.
+ * The step is captured once per state buffer (two graphs alternate).  The
+ * staging buffer (one state) and the copy stream are created by the first
  * w2_stage_state.  The host buffer must stay unchanged until the copy is
  * done, which any synchronising call after the matching w2_use_staged_state
  * guarantees; pinned host memory makes the copy asynchronous.
@@ -232,6 +235,18 @@ w2_status w2_step(w2_ctx *ctx, int32_t nsteps);
  * Errors: W2_ERR_ARG, W2_ERR_STATE, W2_ERR_NONFINITE (NaN/Inf in the state; the
  * outputs are still written), W2_ERR_CUDA. */
 w2_status w2_observables(w2_ctx *ctx, w2_obs *out, double *n1, double *n12);
+
+/* The same observables without waiting, for a host loop that reads each
+ * step's results while the next step runs.  w2_observables_enqueue queues
+ * the reductions of the current state and the copy of their results into
+ * pinned host slot `slot` (0 or 1) on the stream, and returns.
+ * w2_observables_collect waits for that slot's copy (not for later work on
+ * the stream) and unpacks it exactly as w2_observables does; the step count
+ * reported is the one at enqueue time.  A slot must be collected before it is
+ * enqueued again.  Errors: W2_ERR_ARG (slot not 0 or 1, NULL out), W2_ERR_STATE
+ * (no state; collect: slot not enqueued), W2_ERR_NONFINITE, W2_ERR_CUDA. */
+w2_status w2_observables_enqueue(w2_ctx *ctx, int32_t slot);
+w2_status w2_observables_collect(w2_ctx *ctx, int32_t slot, w2_obs *out, double *n1, double *n12);
 
 /* Operator-level entry points on caller-owned DEVICE arrays of the context's
  * layout (f and out may not alias).  Queued on the stream.

@@ -43,6 +43,16 @@ static cudaError_t theta64(const w2_ctx *ctx, int mode, const ThetaArgs &th, cud
   return ctx->prec == W2_F64_SLICED ? launch_theta_f64s(ctx->nk, mode, th, s) : launch_theta_f64(ctx->nk, mode, th, s);
 }
 
+// Forget the captured steps (the potentials, the Hartree kind, the patches or
+// the learned form changed).
+static void drop_graphs(w2_ctx *ctx) {
+  for (int k = 0; k < 2; ++k) {
+    if (ctx->graph_ok[k]) cudaGraphExecDestroy(ctx->graph[k]);
+    ctx->graph_ok[k] = false;
+    ctx->graph_f[k] = nullptr;
+  }
+}
+
 // The FP32 sweep of a precision-form context: TF32 or BF16 operand splits.
 static cudaError_t theta32(const w2_ctx *ctx, int mode, const Theta32Args &th, cudaStream_t s) {
   return ctx->prec == W2_F32_BF16X3 ? launch_theta_b3(ctx->nk, mode, th, s) : launch_theta_f32(ctx->nk, mode, th, s);
@@ -56,11 +66,16 @@ static void free_all(w2_ctx *c) {
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_obs) cudaFreeHost(c->h_obs);
+  for (int k = 0; k < 2; ++k) {
+    if (c->h_obs_slot[k]) cudaFreeHost(c->h_obs_slot[k]);
+    if (c->ev_obs[k]) cudaEventDestroy(c->ev_obs[k]);
+  }
   if (c->f1) cudaFree(c->f1);
   if (c->xrows) cudaFree(c->xrows);
   if (c->Kzero) cudaFree(c->Kzero);
   if (c->Klearn) cudaFree(c->Klearn);
-  if (c->graph_ready) cudaGraphExecDestroy(c->graph);
+  for (int k = 0; k < 2; ++k)
+    if (c->graph_ok[k]) cudaGraphExecDestroy(c->graph[k]);
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->copy) {
     cudaStreamSynchronize(c->copy);
@@ -325,10 +340,7 @@ extern "C" w2_status w2_set_hartree(w2_ctx *ctx, int32_t kind) {
     W2_TRY(cudaMemcpy(ctx->h_fine, g.data(), sizeof(double) * nx * M, cudaMemcpyHostToDevice));
   }
   ctx->hartree_kind = kind;
-  if (ctx->graph_ready) {
-    cudaGraphExecDestroy(ctx->graph);
-    ctx->graph_ready = false;
-  }
+  drop_graphs(ctx);
   return W2_OK;
 }
 
@@ -390,10 +402,7 @@ extern "C" w2_status w2_set_potentials(w2_ctx *ctx, w2_fn vext, void *ue, w2_fn 
   // host vectors are copied by cudaMemcpyAsync from pageable memory before return
   W2_TRY(cudaStreamSynchronize(ctx->stream));
   ctx->have_pot = true;
-  if (ctx->graph_ready) {
-    cudaGraphExecDestroy(ctx->graph);
-    ctx->graph_ready = false;
-  }
+  drop_graphs(ctx);
   return W2_OK;
 }
 
@@ -444,7 +453,12 @@ extern "C" w2_status w2_use_staged_state(w2_ctx *ctx) {
   if (ctx->sticky) return ctx->sticky;
   if (!ctx->stage_pending) return W2_ERR_STATE;
   W2_TRY(cudaStreamWaitEvent(ctx->stream, ctx->ev_staged, 0));
-  W2_TRY(cudaMemcpyAsync(ctx->f, ctx->stage, ctx->esz * ctx->npts, cudaMemcpyDeviceToDevice, ctx->stream));
+  // no copy: the staged buffer becomes the state, and the old state buffer
+  // takes the next staged copy once the work queued on it so far is done
+  // (ev_taken; the step graph for each buffer is captured once)
+  void *staged = ctx->stage;
+  ctx->stage = ctx->f;
+  ctx->f = static_cast<double *>(staged);
   W2_TRY(cudaEventRecord(ctx->ev_taken, ctx->stream));
   W2_TRY(state_sums(ctx, ctx->stream));
   ctx->taken_recorded = true;
@@ -487,10 +501,7 @@ extern "C" w2_status w2_set_patches(w2_ctx *ctx, int32_t np1, int32_t np2) {
   ctx->np_ax[0] = np1;
   ctx->np_ax[1] = np2;
   ctx->pm_G = G;
-  if (ctx->graph_ready) {
-    cudaGraphExecDestroy(ctx->graph);
-    ctx->graph_ready = false;
-  }
+  drop_graphs(ctx);
   if (np1 == 1 && np2 == 1) return W2_OK;
   // slope of the periodic spline at a point from the samples: the inverse of
   // the (1,4,1)/6 circulant is beta_m = sqrt(3) (z^m + z^(nx-m)) / (1 - z^nx),
@@ -812,7 +823,15 @@ extern "C" w2_status w2_step(w2_ctx *ctx, int32_t nsteps) {
 
 static w2_status step_graph(w2_ctx *ctx, int32_t nsteps) {
   if (nsteps == 0) return W2_OK;
-  if (!ctx->graph_ready) {
+  int k = -1;
+  for (int q = 0; q < 2; ++q)
+    if (ctx->graph_ok[q] && ctx->graph_f[q] == ctx->f) k = q;
+  if (k < 0) {  // capture for this state buffer, in a free slot or over slot 1
+    k = !ctx->graph_ok[0] ? 0 : 1;
+    if (ctx->graph_ok[k]) {
+      cudaGraphExecDestroy(ctx->graph[k]);
+      ctx->graph_ok[k] = false;
+    }
     cudaGraph_t graph;
     W2_TRY(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = enqueue_any(ctx, ctx->cap, nullptr);
@@ -822,20 +841,19 @@ static w2_status step_graph(w2_ctx *ctx, int32_t nsteps) {
       ctx->sticky = W2_ERR_CUDA;
       return W2_ERR_CUDA;
     }
-    e = cudaGraphInstantiate(&ctx->graph, graph, 0);
+    e = cudaGraphInstantiate(&ctx->graph[k], graph, 0);
     cudaGraphDestroy(graph);
     W2_TRY(e);
-    ctx->graph_ready = true;
+    ctx->graph_ok[k] = true;
+    ctx->graph_f[k] = ctx->f;
   }
-  for (int s = 0; s < nsteps; ++s) W2_TRY(cudaGraphLaunch(ctx->graph, ctx->stream));
+  for (int s = 0; s < nsteps; ++s) W2_TRY(cudaGraphLaunch(ctx->graph[k], ctx->stream));
   ctx->steps += nsteps;
   return W2_OK;
 }
 
-extern "C" w2_status w2_observables(w2_ctx *ctx, w2_obs *out, double *n1, double *n12) {
-  if (!ctx || !out) return W2_ERR_ARG;
-  if (ctx->sticky) return ctx->sticky;
-  if (!ctx->have_state) return W2_ERR_STATE;
+// Queue the observables' reductions of the current state into ctx->obs_out.
+static w2_status enqueue_obs(w2_ctx *ctx) {
   const int nx = ctx->nx;
   ObsArgs a;
   a.nx = nx;
@@ -855,19 +873,65 @@ extern "C" w2_status w2_observables(w2_ctx *ctx, w2_obs *out, double *n1, double
   a.xpart = ctx->xpart;
   a.out = ctx->obs_out;
   W2_TRY(launch_obs(a, ctx->stream));
-  const size_t nb = sizeof(double) * (8 + nx + (size_t)nx * nx);
-  W2_TRY(cudaMemcpyAsync(ctx->h_obs, ctx->obs_out, nb, cudaMemcpyDeviceToHost, ctx->stream));
-  W2_TRY(cudaStreamSynchronize(ctx->stream));
-  const double *h = ctx->h_obs;
+  return W2_OK;
+}
+
+// Unpack a host copy of obs_out.
+static w2_status unpack_obs(const w2_ctx *ctx, const double *h, long long steps, w2_obs *out, double *n1,
+                            double *n12) {
+  const int nx = ctx->nx;
   out->mass = h[0];
   out->energy = h[1];
   out->purity = h[2];
   out->entropy_lin = 1.0 - h[2];
   out->l2norm = h[3];
-  out->step = ctx->steps;
+  out->step = steps;
   if (n1) memcpy(n1, h + 8, sizeof(double) * nx);
   if (n12) memcpy(n12, h + 8 + nx, sizeof(double) * nx * nx);
   return h[4] != 0.0 ? W2_ERR_NONFINITE : W2_OK;
+}
+
+extern "C" w2_status w2_observables(w2_ctx *ctx, w2_obs *out, double *n1, double *n12) {
+  if (!ctx || !out) return W2_ERR_ARG;
+  if (ctx->sticky) return ctx->sticky;
+  if (!ctx->have_state) return W2_ERR_STATE;
+  w2_status st = enqueue_obs(ctx);
+  if (st != W2_OK) return st;
+  const size_t nb = sizeof(double) * (8 + ctx->nx + (size_t)ctx->nx * ctx->nx);
+  W2_TRY(cudaMemcpyAsync(ctx->h_obs, ctx->obs_out, nb, cudaMemcpyDeviceToHost, ctx->stream));
+  W2_TRY(cudaStreamSynchronize(ctx->stream));
+  return unpack_obs(ctx, ctx->h_obs, ctx->steps, out, n1, n12);
+}
+
+extern "C" w2_status w2_observables_enqueue(w2_ctx *ctx, int32_t slot) {
+  if (!ctx || slot < 0 || slot > 1) return W2_ERR_ARG;
+  if (ctx->sticky) return ctx->sticky;
+  if (!ctx->have_state) return W2_ERR_STATE;
+  const size_t nb = sizeof(double) * (8 + ctx->nx + (size_t)ctx->nx * ctx->nx);
+  if (!ctx->h_obs_slot[slot]) {
+    if (host_alloc((void **)&ctx->h_obs_slot[slot], nb) != cudaSuccess) {
+      ctx->h_obs_slot[slot] = nullptr;
+      (void)cudaGetLastError();
+      return W2_ERR_OOM;
+    }
+  }
+  if (!ctx->ev_obs[slot]) W2_TRY(cudaEventCreateWithFlags(&ctx->ev_obs[slot], cudaEventDisableTiming));
+  w2_status st = enqueue_obs(ctx);
+  if (st != W2_OK) return st;
+  W2_TRY(cudaMemcpyAsync(ctx->h_obs_slot[slot], ctx->obs_out, nb, cudaMemcpyDeviceToHost, ctx->stream));
+  W2_TRY(cudaEventRecord(ctx->ev_obs[slot], ctx->stream));
+  ctx->obs_pending[slot] = true;
+  ctx->obs_steps[slot] = ctx->steps;
+  return W2_OK;
+}
+
+extern "C" w2_status w2_observables_collect(w2_ctx *ctx, int32_t slot, w2_obs *out, double *n1, double *n12) {
+  if (!ctx || !out || slot < 0 || slot > 1) return W2_ERR_ARG;
+  if (ctx->sticky) return ctx->sticky;
+  if (!ctx->obs_pending[slot]) return W2_ERR_STATE;
+  W2_TRY(cudaEventSynchronize(ctx->ev_obs[slot]));
+  ctx->obs_pending[slot] = false;
+  return unpack_obs(ctx, ctx->h_obs_slot[slot], ctx->obs_steps[slot], out, n1, n12);
 }
 
 extern "C" w2_status w2_theta(w2_ctx *ctx, const void *f, void *out) {
@@ -1083,10 +1147,7 @@ static w2_status learned_judge(w2_ctx *ctx) {
   ctx->judged += 1;
   if (!(ctx->last_err <= ctx->judge_tol)) {
     ctx->learned_active = false;
-    if (ctx->graph_ready) {  // the captured step used the network
-      cudaGraphExecDestroy(ctx->graph);
-      ctx->graph_ready = false;
-    }
+    drop_graphs(ctx);  // the captured steps used the network
   }
   return W2_OK;
 }
@@ -1094,10 +1155,7 @@ static w2_status learned_judge(w2_ctx *ctx) {
 extern "C" w2_status w2_learned_attach(w2_ctx *ctx, w2_mlp *m, int32_t judge_every, double tol) {
   if (!ctx) return W2_ERR_ARG;
   if (ctx->sticky) return ctx->sticky;
-  if (ctx->graph_ready) {
-    cudaGraphExecDestroy(ctx->graph);
-    ctx->graph_ready = false;
-  }
+  drop_graphs(ctx);
   if (!m) {
     ctx->mlp = nullptr;
     ctx->learned_active = false;

@@ -314,14 +314,23 @@ struct w2_ctx {
   double2 *rdm_ph, *rdm_rho;                   // [nx][nk] phases, [nx][nx] rho1 dx
   float *wtab32, *ctab32;    // FP32 shift weights and merged increment taps
   double *xpart, *obs_out, *h_obs;
+  // w2_observables_enqueue / _collect: two pinned result slots, their copy
+  // events and the step counts at enqueue time
+  double *h_obs_slot[2];
+  cudaEvent_t ev_obs[2];
+  bool obs_pending[2];
+  long long obs_steps[2];
   double z, zscale;
   int nterm;
   // patch decomposition of the shift (w2_set_patches): patches along x1 and x2
   // (1: the global spline), ghost points, stencil and Thomas tables per axis
   int np_ax[2], pm_G;
   double *pm_D, *pm_wb, *pm_tab[2], *pm_xs, *pm_gh;
-  cudaGraphExec_t graph;
-  bool graph_ready;
+  // captured steps, one per state buffer the step has run on (w2_use_staged_state
+  // swaps the state and staging buffers, so two graphs alternate)
+  cudaGraphExec_t graph[2];
+  const void *graph_f[2];
+  bool graph_ok[2];
   // learned form (FP64 contexts): the MLP's pair term replaces K12
   w2_mlp *mlp;
   bool learned_active;     // the step currently uses the network

@@ -1,6 +1,7 @@
 // Reductions of the phase-space state (FP64 or FP32 storage): per-X momentum
-// sums for the densities (exact fixed-point sums) and the observables (FP64,
-// fixed order).  Repeated calls give identical bits.
+// sums for the densities (exact fixed-point sums) and the observables (exact
+// fixed-point per-X partials for FP64 states, FP64 in a fixed order
+// otherwise).  Repeated calls give identical bits.
 #include <math.h>
 
 #include "w2_df.cuh"
@@ -41,6 +42,107 @@ __device__ __forceinline__ void load_pair(const float *p, double &a, double &b) 
   const float2 v = *reinterpret_cast<const float2 *>(p);
   a = v.x;
   b = v.y;
+}
+
+// The same per-X partials for an FP64 state without the FP64 pipe's
+// accumulations: every value becomes its exact fixed-point image (integer
+// operations, rounded to 2^-49 of the block's largest power of two, as in
+// xsum_block), the row sums sum_{n2} f and column sums sum_{n1} f are exact
+// int64 sums (so they do not depend on the order), and
+//   [0] = sum of the rows,  [1] = sum_n1 p1^2 row(n1) + sum_n2 p2^2 col(n2),
+//   [2] = sum f^2 (FP64 squares, exact fixed-point sum).
+// One FP64 multiply per element (the square) instead of three operations.
+// A block holding Inf or NaN gives NaN partials.  256 threads, nk <= 64.
+__global__ void __launch_bounds__(256) k_obs_x_exact(ObsArgs a, const double *f) {
+  constexpr int K = 16;  // values per thread (nk^2 <= 16 * 256)
+  __shared__ long long img[64 * 65];
+  __shared__ long long lred[2][8];
+  __shared__ int ired[8];
+  __shared__ double dred[8];
+  const int nk = a.nk, X = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int n = nk * nk, S = nk + 1;
+  const double *fx = f + (size_t)X * n;
+  double v[K];
+  int e1 = 0;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const int e = tid + i * 256;
+    v[i] = e < n ? fx[e] : 0.0;
+    e1 = max(e1, expo_of(v[i]));
+  }
+  e1 = __reduce_max_sync(0xffffffffu, e1);
+  if (lane == 0) ired[w] = e1;
+  __syncthreads();
+  e1 = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) e1 = max(e1, ired[k]);
+  // |f| < 2^(e1 - 1022), so every square's biased exponent is at most
+  // 2 e1 - 1022: the squares' images take that bound as their scale
+  const int e2 = max(2 * e1 - 1022, 1);
+  const bool bad = e1 == 2047 || e2 > 2046;
+  e1 = max(e1, 1);
+  long long sq = 0;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const int e = tid + i * 256;
+    if (e < n) {
+      const int r = e / nk, c = e - r * nk;
+      img[r * S + c] = fixed_image(v[i], e1);
+      sq += fixed_image(v[i] * v[i], e2);
+    }
+  }
+  __syncthreads();
+  // rows and columns: four threads (neighbouring lanes) per row or column,
+  // each summing every fourth element, then two exchanges
+  const int k = tid >> 2, part = tid & 3;
+  long long rs = 0, cs = 0;
+  if (k < nk) {
+    for (int c = part; c < nk; c += 4) rs += img[k * S + c];
+    for (int r = part; r < nk; r += 4) cs += img[r * S + k];
+  }
+#pragma unroll
+  for (int o = 1; o < 4; o <<= 1) {
+    rs += __shfl_xor_sync(0xffffffffu, rs, o);
+    cs += __shfl_xor_sync(0xffffffffu, cs, o);
+  }
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  double *xp = a.xpart + (size_t)X * (3 + nk);
+  double t1 = 0.0;  // this row's and column's share of sum f p^2
+  long long tot = 0;
+  if (k < nk && part == 0) {
+    const double drow = bad ? nan : ll_to_double_scaled(rs, e1 - 1071);
+    const double dcol = bad ? nan : ll_to_double_scaled(cs, e1 - 1071);
+    xp[3 + k] = drow;
+    const double p = (k - nk / 2) * a.dp;
+    t1 = p * p * (drow + dcol);
+    tot = rs;
+  }
+  // block totals: exact for the integers, a fixed tree for the FP64 share
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+  }
+  if (lane == 0) {
+    lred[0][w] = tot;
+    lred[1][w] = sq;
+    dred[w] = t1;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    long long T = 0, Q = 0;
+    double s1 = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      T += lred[0][q];
+      Q += lred[1][q];
+      s1 += dred[q];
+    }
+    xp[0] = bad ? nan : ll_to_double_scaled(T, e1 - 1071);
+    xp[1] = bad ? nan : s1;
+    xp[2] = bad ? nan : ll_to_double_scaled(Q, e2 - 1071);
+  }
 }
 
 template <typename T>
@@ -213,6 +315,8 @@ cudaError_t launch_obs(const ObsArgs &a, cudaStream_t s) {
   const int nt = a.nk >= 256 ? 256 : 32 * ((a.nk + 31) / 32);  // a thread per row
   if (a.f32)
     k_obs_x<float><<<a.nx * a.nx, nt, sizeof(double) * a.nk, s>>>(a, a.f32);
+  else if (a.nk <= 64)
+    k_obs_x_exact<<<a.nx * a.nx, 256, 0, s>>>(a, a.f);
   else
     k_obs_x<double><<<a.nx * a.nx, nt, sizeof(double) * a.nk, s>>>(a, a.f);
   cudaError_t e = cudaGetLastError();

@@ -37,6 +37,7 @@ EXPORTS = ("w2_create", "w2_set_potentials", "w2_set_state", "w2_stage_state", "
            "w2_batch_create", "w2_batch_set_potentials", "w2_batch_set_state", "w2_batch_get_state",
            "w2_batch_observables", "w2_batch_step", "w2_batch_autotune", "w2_batch_destroy", "w2_batch_sync",
            "w2_batch_set_wait_limit", "w2_batch_inject_stall", "w2_debug_fail_alloc", "w2_debug_alloc_count",
+           "w2_observables_enqueue", "w2_observables_collect",
            "w2_mlp_create", "w2_mlp_create_kernel", "w2_pair_kernel_train_step", "w2_mlp_param_count", "w2_mlp_input_dim", "w2_mlp_set_params", "w2_mlp_get_params",
            "w2_mlp_set_scales", "w2_mlp_forward", "w2_mlp_train_step", "w2_mlp_gradients", "w2_mlp_destroy",
            "w2_features", "w2_theta_pair", "w2_learned_attach", "w2_learned_report",
@@ -316,6 +317,23 @@ class Context:
         code = self.lib.w2_observables(self.h, ctypes.byref(o), n1.ctypes.data_as(dp), n12.ctypes.data_as(dp))
         if code not in (0, -6) or (code == -6 and raise_nonfinite):
             _check(code, "w2_observables")
+        return Observables(o.mass, o.energy, o.purity, o.entropy_lin, o.l2norm, o.step, n1, n12, STATUS[code])
+
+    def observables_enqueue(self, slot):
+        """Queue the observables of the current state into host slot 0 or 1
+        without waiting (collect them with observables_collect)."""
+        _check(self.lib.w2_observables_enqueue(self.h, int(slot)), "w2_observables_enqueue")
+
+    def observables_collect(self, slot, raise_nonfinite=False) -> Observables:
+        """Wait for slot's queued observables and return them."""
+        o = Obs()
+        n1 = np.zeros(self.nx)
+        n12 = np.zeros((self.nx, self.nx))
+        dp = ctypes.POINTER(ctypes.c_double)
+        code = self.lib.w2_observables_collect(self.h, int(slot), ctypes.byref(o), n1.ctypes.data_as(dp),
+                                               n12.ctypes.data_as(dp))
+        if code not in (0, -6) or (code == -6 and raise_nonfinite):
+            _check(code, "w2_observables_collect")
         return Observables(o.mass, o.energy, o.purity, o.entropy_lin, o.l2norm, o.step, n1, n12, STATUS[code])
 
     def theta_pair(self, f, out):

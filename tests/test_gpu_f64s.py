@@ -236,6 +236,38 @@ def test_staged_host_input_pipeline(prec):
         assert np.array_equal(ctx.get_state(), want[k][0]) and ob.energy == want[k][1], k
 
 
+@pytest.mark.parametrize("prec", ["W2_F64", "W2_F64_SLICED", "W2_F32_TF32X3"])
+def test_observables_enqueue_collect(prec):
+    """The two-slot asynchronous observables (w2_observables_enqueue /
+    _collect) give the bits of w2_observables for the state at enqueue time,
+    with that step count, while later steps are queued; a slot that was not
+    enqueued, or a slot other than 0 and 1, is refused."""
+    from paper_2511_11354_gb300 import w2
+    prob, f0 = inputs.workload_dwell(nx=32, nk=32)
+    ctx = w2.Context.from_problem(prob, precision=getattr(w2, prec))
+    ctx.set_state(np.ascontiguousarray(f0, dtype=ctx.np_dtype))
+    ctx.step(2)
+    want2 = ctx.observables()
+    ctx.observables_enqueue(0)
+    ctx.step(1)
+    want3 = ctx.observables()
+    ctx.observables_enqueue(1)
+    ctx.step(1)
+    got2 = ctx.observables_collect(0)
+    got3 = ctx.observables_collect(1)
+    for got, want, n in ((got2, want2, 2), (got3, want3, 3)):
+        assert got.step == want.step == n
+        assert (got.mass, got.energy, got.purity, got.l2norm) == (want.mass, want.energy, want.purity, want.l2norm)
+        assert np.array_equal(got.n1, want.n1) and np.array_equal(got.n12, want.n12)
+    with pytest.raises(w2.W2Error) as e:
+        ctx.observables_collect(0)
+    assert e.value.name == "W2_ERR_STATE"
+    with pytest.raises(w2.W2Error) as e:
+        ctx.observables_enqueue(2)
+    assert e.value.name == "W2_ERR_ARG"
+    ctx.close()
+
+
 def test_sliced_nonfinite_and_unsupported():
     from paper_2511_11354_gb300 import w2
     prob, f0 = inputs.workload_small(nx=8, nk=16)

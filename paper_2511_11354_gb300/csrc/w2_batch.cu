@@ -82,6 +82,9 @@ extern "C" void w2_batch_destroy(w2_batch *b) {
 // Grid, shared memory and kernel attributes of a tile shape (grid: ctas per
 // SM times SMs, at most the CTAs that fit).
 static cudaError_t set_shape(w2_batch *b, BStepShape sh, int ctas_per_sm) {
+  // a shift slab's threads (columns x pieces per line) must fit one CTA
+  for (const w2_ctx *c : b->inst)
+    if (bstep_cols(c->nk, sh.shift_cols) * adv32_pieces(c->nx) > kBatchThreads) return cudaErrorInvalidConfiguration;
   cudaError_t e = prepare_bstep(sh);
   if (e != cudaSuccess) return e;
   const size_t smem = bstep_smem(sh, b->nxmax, b->nkmax);
@@ -236,7 +239,10 @@ extern "C" w2_status w2_batch_create(const w2_config *cfgs, int32_t n, void *cud
   if (e == cudaSuccess) *b->h_err = 0;
   // default shape: 64-column shift items, two warps per Theta row block,
   // as many CTAs as fit (at most two per SM)
-  if (e == cudaSuccess) e = set_shape(b, BStepShape{64, 2, 8}, 2);
+  if (e == cudaSuccess) {
+    e = set_shape(b, BStepShape{64, 2, 8}, 2);
+    if (e == cudaErrorInvalidConfiguration) e = set_shape(b, BStepShape{32, 2, 8}, 2);  // lines of 128 points
+  }
   if (e == cudaSuccess) e = build_plan(b);
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -727,8 +727,14 @@ struct AdvColsWide {
   static constexpr int blocks = NK / C;
 };
 
+// From 256 points per line: 16 columns per CTA (with 16 pieces per line, 256
+// threads), so that two CTAs of five 264-row slabs share an SM.
+struct AdvColsLong {
+  static constexpr int C = 16;
+};
+
 template <int NK, int DIR, int C>
-__global__ void __launch_bounds__(8 * C) k_adv32(Adv32Args a) {
+__global__ void __launch_bounds__(256) k_adv32(Adv32Args a) {
   extern __shared__ __align__(16) float sm32[];
   constexpr int NB = NK / C;
   adv32_block<NK, DIR, C>(a, blockIdx.x / NB, blockIdx.x % NB, blockIdx.y, sm32,
@@ -759,6 +765,10 @@ static cudaError_t prep32() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_adv32<NK, 1, AdvColsWide<NK>::C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              220 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adv32<NK, 0, AdvColsLong::C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adv32<NK, 1, AdvColsLong::C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   return e;
 }
 
@@ -787,7 +797,9 @@ static cudaError_t run_adv32_c(int dir, const Adv32Args &a, cudaStream_t s) {
 
 template <int NK>
 static cudaError_t run_adv32(int dir, const Adv32Args &a, cudaStream_t s) {
-  return a.nx < 128 ? run_adv32_c<NK, AdvCols<NK>::C>(dir, a, s) : run_adv32_c<NK, AdvColsWide<NK>::C>(dir, a, s);
+  if (a.nx < 128) return run_adv32_c<NK, AdvCols<NK>::C>(dir, a, s);
+  if (a.nx < 256) return run_adv32_c<NK, AdvColsWide<NK>::C>(dir, a, s);
+  return run_adv32_c<NK, AdvColsLong::C>(dir, a, s);
 }
 
 #define W2_NK32_SWITCH(nk, EXPR_TEMPLATE) \
@@ -826,9 +838,6 @@ cudaError_t launch_adv_f32(int nk, int dir, const Adv32Args &a, cudaStream_t s) 
 // Batch step: one persistent launch per Lawson step of every instance
 // ---------------------------------------------------------------------------
 
-// Columns per shift item for a tile width CS: CS, or nk when nk <= CS, or 16
-// when CS does not divide nk.
-__host__ __device__ constexpr int bstep_cols(int nk, int cs) { return nk <= cs ? nk : (nk % cs == 0 ? cs : 16); }
 
 int bstep_shift_items(int nk, int shift_cols) { return nk / bstep_cols(nk, shift_cols); }
 
@@ -870,6 +879,10 @@ __device__ __forceinline__ void bstep_shift(const BStepPlan &P, int p, int i, in
   constexpr int NB = NK / C;
   const int nx = P.nx[i];
   const int S = (C * adv32_pieces(nx) + 31) & ~31;
+  if (S > (int)blockDim.x) {  // the host refuses such shapes; never wait on a barrier that cannot fill
+    if (threadIdx.x == 0) atomicCAS(P.err, 0, (int)W2_ERR_UNSUPPORTED);
+    return;
+  }
   const size_t slab_bytes =
       ((size_t)(p == 2 ? adv32_slabs<0>() : adv32_slabs<1>()) * (nx + 2 * kGhost) * C * sizeof(float) + 15) & ~(size_t)15;
   const int G = max(1, min(min((int)blockDim.x / S, (int)(P.smem / slab_bytes)), 8));

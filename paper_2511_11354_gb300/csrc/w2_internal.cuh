@@ -189,6 +189,9 @@ size_t bstep_smem(const BStepShape &sh, int nxmax, int nkmax);
 cudaError_t prepare_bstep(const BStepShape &sh);
 int bstep_max_ctas_per_sm(const BStepShape &sh, size_t smem);
 cudaError_t launch_bstep(const BStepShape &sh, const BStepPlan &p, int grid, size_t smem, cudaStream_t s);
+// Columns per shift item for a tile width CS: CS, or nk when nk <= CS, or 16
+// when CS does not divide nk.
+__host__ __device__ constexpr int bstep_cols(int nk, int cs) { return nk <= cs ? nk : (nk % cs == 0 ? cs : 16); }
 int bstep_shift_items(int nk, int shift_cols);  // shift items per (n1, x) line
 
 // Harmonics of the pair distance r = x1 - x2 in an MLP input row.
@@ -262,11 +265,11 @@ cudaError_t launch_theta_f32(int nk, int mode, const Theta32Args &a, cudaStream_
 cudaError_t prepare_kernels_b3(int nk);
 cudaError_t launch_theta_b3(int nk, int mode, const Theta32Args &a, cudaStream_t s);
 cudaError_t launch_adv_f32(int nk, int dir, const Adv32Args &a, cudaStream_t s);
-// Threads per column of the FP32 shift for lines of nx points (at most 8;
+// Threads per column of the FP32 shift for lines of nx points (at most 16;
 // from 128 points on, pieces of 16 rows or more: the double-float recursions
 // are serial chains, and more of them per SM hide their latency better than
 // the extra start sums cost).
-__host__ __device__ inline int adv32_pieces(int nx) { return nx >= 128 ? 8 : nx >= 64 ? 2 : 1; }
+__host__ __device__ inline int adv32_pieces(int nx) { return nx >= 256 ? 16 : nx >= 128 ? 8 : nx >= 64 ? 2 : 1; }
 cudaError_t launch_gemm(const GemmArgs &a, cudaStream_t s);
 // Pipelined inference GEMM (unit-stride A rows and B rows; BIAS_SILU / BIAS_SCALE epilogues).
 cudaError_t launch_gemm_fwd(const GemmArgs &a, cudaStream_t s);

@@ -57,6 +57,33 @@ def test_batch_matches_single_contexts_bitwise():
     assert ob.step == 6 and ob.status == "W2_OK"
 
 
+def test_batch_with_128_point_lines():
+    """The batch's largest lines (nx = 128, eight recursion pieces per line)
+    beside a small instance: the shift slabs of 64 columns would need 512
+    threads, so the batch takes 32-column slabs (the autotuner only tries
+    shapes that fit) and still matches single contexts bit for bit."""
+    from paper_2511_11354_gb300 import w2
+    probs = [inputs.Problem(nx=128, nk=64, L=20.0, dt=0.01, vext=inputs.cos_potential(0.5, 20.0),
+                            vee=inputs.soft_coulomb(1.0), gamma=1.0),
+             inputs.Problem(nx=24, nk=32, L=20.0, dt=0.01, vext=inputs.cos_potential(0.5, 20.0),
+                            vee=inputs.soft_coulomb(1.0), gamma=0.5)]
+    states = [inputs.initial_state(q, centres=(-2.0, 2.5), seed=i) for i, q in enumerate(probs)]
+    b = w2.Batch(probs)
+    for i, f in enumerate(states):
+        b.set_state(i, f.astype(np.float32))
+    b.step(2)
+    tuning = b.autotune()
+    assert tuning["shift_cols"] == 32
+    b.step(1)
+    for i, q in enumerate(probs):
+        c = w2.Context.from_problem(q, precision=w2.W2_F32_TF32X3)
+        c.set_state(states[i].astype(np.float32))
+        c.step(3)
+        assert np.array_equal(b.get_state(i), c.get_state()), i
+        c.close()
+    b.close()
+
+
 def test_batch_instance_vs_oracle():
     """Instances of each momentum size of the workload (32, 48, 64) and of
     uneven spatial sizes, 10 steps, each against the FP64 oracle."""

@@ -433,6 +433,14 @@ w2_status w2_mlp_create_kernel(int32_t nk, int32_t hidden, int32_t max_nx, void 
  * W2_ERR_OOM, W2_ERR_NONFINITE, W2_ERR_CUDA. */
 w2_status w2_pair_kernel_train_step(w2_ctx *ctx, w2_mlp *m, const double *f, const double *p, const int32_t *dr,
                                     int32_t rows, float lr, double *loss);
+/* The same loss for a batch of rows, and its gradient with respect to the
+ * network's outputs without an update: *loss (host, required), y (host,
+ * float [nx][nk], or NULL) the network's outputs for every distance,
+ * dldy (host, double [nx][nk], or NULL) dL/dy (column j = 0 is not used by
+ * the kernel and is 0).  For checking the training chain against a reference.
+ * Synchronises.  Errors: as w2_pair_kernel_train_step. */
+w2_status w2_pair_kernel_loss_grad(w2_ctx *ctx, w2_mlp *m, const double *f, const double *p, const int32_t *dr,
+                                   int32_t rows, double *loss, float *y, double *dldy);
 size_t w2_mlp_param_count(const w2_mlp *m);
 int32_t w2_mlp_input_dim(const w2_mlp *m);
 /* Host copies of the packed FP32 parameters (synchronise). */

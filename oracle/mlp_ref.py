@@ -1,8 +1,9 @@
-"""Plain FP64 numpy reference of the learned form's network (test
+"""Plain FP64 numpy reference of the learned form's networks (test
 infrastructure only): forward pass and the gradient of the mean squared error
-with respect to every packed parameter, written out layer by layer.  Used to
-check the CUDA training kernels; pinned by central finite differences in
-tests/test_oracle_mlp.py.
+with respect to every packed parameter, written out layer by layer, and the
+kernel network's operator-side loss and gradient.  Used to check the CUDA
+training kernels; pinned by central finite differences and against the FP64
+oracle's two-body term in tests/test_oracle_mlp.py.
 
 Network: x -> silu(x W0 + b0) -> silu(. W1 + b1) -> silu(. W2 + b2) -> . W3 + b3,
 silu(z) = z / (1 + exp(-z)); loss = mean((y - t)^2).
@@ -105,3 +106,53 @@ def loss_and_grad_tc(p, x, t, din, hidden, dout):
     grads = grads[::-1]
     g = np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in grads])
     return loss, g
+
+
+# ---------------------------------------------------------------------------
+# Kernel network (the two-body term's structure): reference of its loss and
+# of the loss gradient with respect to the network's outputs.  The two-body
+# term of Eq. two_body_FSM at one spatial point, with the shift kernel K of
+# its pair distance: Theta_K F(n1, n2) = sum_{j >= 1} K(j) [F(n1 + j, n2 - j)
+# - F(n1 - j, n2 + j)], F zero outside the momentum window.
+# ---------------------------------------------------------------------------
+
+def _pair_shifts(F, j):
+    """(F(n1 + j, n2 - j), F(n1 - j, n2 + j)) for blocks F [rows][nk][nk]."""
+    nk = F.shape[1]
+    a = np.zeros_like(F)
+    b = np.zeros_like(F)
+    a[:, :nk - j, j:] = F[:, j:, :nk - j]
+    b[:, j:, :nk - j] = F[:, :nk - j, j:]
+    return a, b
+
+
+def pair_apply(F, K):
+    """Theta_K F for blocks F [rows][nk][nk] and one kernel row per block,
+    K [rows][nk] (K[:, 0] is not used)."""
+    F = np.asarray(F, dtype=np.float64)
+    out = np.zeros_like(F)
+    for j in range(1, F.shape[1]):
+        a, b = _pair_shifts(F, j)
+        out += np.asarray(K, dtype=np.float64)[:, j, None, None] * (a - b)
+    return out
+
+
+def pair_kernel_loss_grad(F, P, D, y, s_y):
+    """Relative loss L = sum |Theta_{K[D_b]} F_b - P_b|^2 / sum |P_b|^2 with
+    the kernel table K = y / s_y (column 0 unused) of the network outputs y
+    [nx][nk], and dL/dy [nx][nk] (column 0 zero)."""
+    F = np.asarray(F, dtype=np.float64)
+    P = np.asarray(P, dtype=np.float64)
+    D = np.asarray(D, dtype=np.int64)
+    K = np.array(y, dtype=np.float64) / s_y
+    K[:, 0] = 0.0
+    R = pair_apply(F, K[D]) - P
+    p2 = float(np.sum(P * P))
+    loss = float(np.sum(R * R)) / p2
+    G = np.zeros((D.size, F.shape[1]))
+    for j in range(1, F.shape[1]):
+        a, b = _pair_shifts(F, j)
+        G[:, j] = np.sum(R * (a - b), axis=(1, 2))
+    dK = np.zeros(K.shape)
+    np.add.at(dK, D, G)
+    return loss, 2.0 * dK / p2 / s_y

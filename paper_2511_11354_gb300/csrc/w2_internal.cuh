@@ -377,7 +377,7 @@ cudaError_t launch_pairk_table(const float *y, int nx, int nk, float inv_sy, dou
 cudaError_t launch_pairk_grad(const double *f, const double *p, const int *dr, int rows, const float *y, int nx, int nk,
                               float inv_sy, double *res, double *g, double *part, cudaStream_t s);
 cudaError_t launch_pairk_target(const float *y, const double *g, const int *dr, int rows, int nx, int nk, float inv_sy,
-                                double inv_p2, float *t, cudaStream_t s);
+                                double inv_p2, float *t, double *dldy, cudaStream_t s);
 TabArgs tab_args(w2_ctx *ctx, const double *xsum, int pair_mode);
 Adv32Args adv32_args(w2_ctx *ctx);
 }  // namespace w2

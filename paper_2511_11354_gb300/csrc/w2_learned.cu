@@ -18,6 +18,7 @@ struct w2_mlp {
   uint16_t *kx = nullptr;
   float *ky = nullptr, *kt = nullptr;
   double *kres = nullptr, *kg = nullptr, *kpart = nullptr, *h_kpart = nullptr;
+  double *kd = nullptr;  // dL/dy of w2_pair_kernel_loss_grad [maxrows][nk]
   int krows = 0;
   cudaStream_t stream = nullptr;
   size_t np = 0, offW[4] = {}, offb[4] = {};
@@ -98,7 +99,7 @@ static cudaError_t mlp_forward_train(w2_mlp *m, const uint16_t *x, int rows, flo
 
 static void mlp_free(w2_mlp *m) {
   void *ptrs[] = {m->p, m->g, m->m, m->v, m->pb, m->Y, m->dY, m->dYb, m->part, m->kx, m->ky, m->kt, m->kres, m->kg,
-                  m->kpart};
+                  m->kpart, m->kd};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   for (int l = 0; l < 3; ++l) {
@@ -319,12 +320,13 @@ extern "C" w2_status w2_mlp_train_step(w2_mlp *m, const void *x, const float *ta
   return W2_OK;
 }
 
-// One Adam step of a kernel network on a batch of spatial points (see w2.h).
-extern "C" w2_status w2_pair_kernel_train_step(w2_ctx *ctx, w2_mlp *m, const double *f, const double *p,
-                                               const int32_t *dr, int32_t rows, float lr, double *loss) {
-  if (!ctx || !m || !f || !p || !dr || rows < 1 || !(lr > 0) || m->kind != 1) return W2_ERR_ARG;
+// The kernel network's outputs y for every distance, the residuals of its
+// predicted term on the rows, their per-row sums and the per-row gradients
+// with respect to the kernel (everything the loss and its gradient need);
+// *loss and *inv_p2 = 1 / sum |P|^2 on the host.  Synchronises.
+static w2_status pairk_forward(w2_ctx *ctx, w2_mlp *m, const double *f, const double *p, const int32_t *dr,
+                               int32_t rows, double *loss, double *inv_p2) {
   const int nx = ctx->nx, nk = ctx->nk;
-  if (m->nk != nk || nx > m->maxrows) return W2_ERR_ARG;
   cudaStream_t s = m->stream;
   if (rows > m->krows) {
     void *old[] = {m->kres, m->kg, m->kpart};
@@ -369,7 +371,47 @@ extern "C" w2_status w2_pair_kernel_train_step(w2_ctx *ctx, w2_mlp *m, const dou
     p2 += m->h_kpart[2 * b + 1];
   }
   if (!(p2 > 0.0) || !isfinite(r2)) return W2_ERR_NONFINITE;
-  if (loss) *loss = r2 / p2;
-  WM_TRY(launch_pairk_target(m->ky, m->kg, (const int *)dr, rows, nx, nk, inv_sy, 1.0 / p2, m->kt, s));
-  return w2_mlp_train_step(m, m->kx, m->kt, nx, lr, nullptr);
+  *loss = r2 / p2;
+  *inv_p2 = 1.0 / p2;
+  return W2_OK;
+}
+
+static bool pairk_args_ok(const w2_ctx *ctx, const w2_mlp *m, const void *f, const void *p, const void *dr,
+                          int32_t rows) {
+  return ctx && m && f && p && dr && rows >= 1 && m->kind == 1 && m->nk == ctx->nk && ctx->nx <= m->maxrows;
+}
+
+extern "C" w2_status w2_pair_kernel_train_step(w2_ctx *ctx, w2_mlp *m, const double *f, const double *p,
+                                               const int32_t *dr, int32_t rows, float lr, double *loss) {
+  if (!pairk_args_ok(ctx, m, f, p, dr, rows) || !(lr > 0)) return W2_ERR_ARG;
+  double L = 0.0, inv_p2 = 0.0;
+  w2_status st = pairk_forward(ctx, m, f, p, dr, rows, &L, &inv_p2);
+  if (st != W2_OK) return st;
+  if (loss) *loss = L;
+  WM_TRY(launch_pairk_target(m->ky, m->kg, (const int *)dr, rows, ctx->nx, ctx->nk, 1.0f / m->s_y, inv_p2, m->kt,
+                             nullptr, m->stream));
+  return w2_mlp_train_step(m, m->kx, m->kt, ctx->nx, lr, nullptr);
+}
+
+extern "C" w2_status w2_pair_kernel_loss_grad(w2_ctx *ctx, w2_mlp *m, const double *f, const double *p,
+                                              const int32_t *dr, int32_t rows, double *loss, float *y, double *dldy) {
+  if (!pairk_args_ok(ctx, m, f, p, dr, rows) || !loss) return W2_ERR_ARG;
+  const int nx = ctx->nx, nk = ctx->nk;
+  double L = 0.0, inv_p2 = 0.0;
+  w2_status st = pairk_forward(ctx, m, f, p, dr, rows, &L, &inv_p2);
+  if (st != W2_OK) return st;
+  *loss = L;
+  cudaStream_t s = m->stream;
+  if (dldy) {
+    if (!m->kd && dev_alloc((void **)&m->kd, sizeof(double) * (size_t)m->maxrows * nk) != cudaSuccess) {
+      m->kd = nullptr;
+      cudaGetLastError();
+      return W2_ERR_OOM;
+    }
+    WM_TRY(launch_pairk_target(m->ky, m->kg, (const int *)dr, rows, nx, nk, 1.0f / m->s_y, inv_p2, m->kt, m->kd, s));
+    WM_TRY(cudaMemcpyAsync(dldy, m->kd, sizeof(double) * (size_t)nx * nk, cudaMemcpyDeviceToHost, s));
+  }
+  if (y) WM_TRY(cudaMemcpyAsync(y, m->ky, sizeof(float) * (size_t)nx * nk, cudaMemcpyDeviceToHost, s));
+  WM_TRY(cudaStreamSynchronize(s));
+  return W2_OK;
 }

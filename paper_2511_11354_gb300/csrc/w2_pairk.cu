@@ -112,15 +112,17 @@ __global__ void k_pairk_rowgrad(const double *f, const double *res, int nk, doub
 // whose gradient is then 2 (y - t) / (nx nk) = dL/dy:
 //   t[d][j] = y[d][j] - (nx nk / 2) dL/dy[d][j],
 //   dL/dy = (1 / s_y) 2 / sum P^2 * sum_{rows b with distance d} g[b][j]  (rows in order).
+// With dldy given, dL/dy itself is written there (FP64) as well.
 __global__ void k_pairk_target(const float *y, const double *g, const int *dr, int rows, int nx, int nk, float inv_sy,
-                               double inv_p2, float *t) {
+                               double inv_p2, float *t, double *dldy) {
   const int d = blockIdx.x;
   for (int j = threadIdx.x; j < nk; j += blockDim.x) {
     double s = 0.0;
     for (int b = 0; b < rows; ++b)
       if (dr[b] == d) s += g[(size_t)b * nk + j];
-    const double dldy = 2.0 * s * inv_p2 * (double)inv_sy;
-    t[(size_t)d * nk + j] = y[(size_t)d * nk + j] - (float)(0.5 * nx * nk * dldy);
+    const double v = 2.0 * s * inv_p2 * (double)inv_sy;
+    t[(size_t)d * nk + j] = y[(size_t)d * nk + j] - (float)(0.5 * nx * nk * v);
+    if (dldy) dldy[(size_t)d * nk + j] = v;
   }
 }
 
@@ -163,8 +165,8 @@ cudaError_t launch_pairk_grad(const double *f, const double *p, const int *dr, i
 }
 
 cudaError_t launch_pairk_target(const float *y, const double *g, const int *dr, int rows, int nx, int nk, float inv_sy,
-                                double inv_p2, float *t, cudaStream_t s) {
-  k_pairk_target<<<nx, 64, 0, s>>>(y, g, dr, rows, nx, nk, inv_sy, inv_p2, t);
+                                double inv_p2, float *t, double *dldy, cudaStream_t s) {
+  k_pairk_target<<<nx, 64, 0, s>>>(y, g, dr, rows, nx, nk, inv_sy, inv_p2, t, dldy);
   return cudaGetLastError();
 }
 

@@ -38,7 +38,7 @@ EXPORTS = ("w2_create", "w2_set_potentials", "w2_set_state", "w2_stage_state", "
            "w2_batch_observables", "w2_batch_step", "w2_batch_autotune", "w2_batch_destroy", "w2_batch_sync",
            "w2_batch_set_wait_limit", "w2_batch_inject_stall", "w2_debug_fail_alloc", "w2_debug_alloc_count",
            "w2_observables_enqueue", "w2_observables_collect",
-           "w2_mlp_create", "w2_mlp_create_kernel", "w2_pair_kernel_train_step", "w2_mlp_param_count", "w2_mlp_input_dim", "w2_mlp_set_params", "w2_mlp_get_params",
+           "w2_mlp_create", "w2_mlp_create_kernel", "w2_pair_kernel_train_step", "w2_pair_kernel_loss_grad", "w2_mlp_param_count", "w2_mlp_input_dim", "w2_mlp_set_params", "w2_mlp_get_params",
            "w2_mlp_set_scales", "w2_mlp_forward", "w2_mlp_train_step", "w2_mlp_gradients", "w2_mlp_destroy",
            "w2_features", "w2_theta_pair", "w2_learned_attach", "w2_learned_report",
            "w2_sem_create", "w2_sem_set_potentials", "w2_sem_momenta", "w2_sem_set_state", "w2_sem_get_state",
@@ -547,6 +547,21 @@ class MLP:
                                                   int(f.shape[0]), float(lr), ctypes.byref(loss)),
                "w2_pair_kernel_train_step")
         return loss.value
+
+    def kernel_loss_grad(self, ctx, f, p, dr):
+        """(relative loss, network outputs y [nx][nk], dL/dy [nx][nk]) of a
+        kernel network on rows of (state block, exact two-body term, pair
+        distance index), without an update."""
+        loss = ctypes.c_double()
+        y = np.zeros((ctx.nx, self.nk), dtype=np.float32)
+        g = np.zeros((ctx.nx, self.nk), dtype=np.float64)
+        _check(self.lib.w2_pair_kernel_loss_grad(ctx.h, self.h, ctypes.c_void_p(f.data_ptr()),
+                                                 ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(dr.data_ptr()),
+                                                 int(f.shape[0]), ctypes.byref(loss),
+                                                 y.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                 g.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "w2_pair_kernel_loss_grad")
+        return loss.value, y, g
 
     def gradients(self, x, target):
         g = np.empty(self.nparams, dtype=np.float32)

@@ -187,6 +187,35 @@ def test_mlp_gradients_at_the_trained_shapes():
     kern.close()
 
 
+def test_kernel_network_loss_and_output_gradient_vs_reference():
+    """The operator side of the kernel network's training chain (features,
+    forward, the predicted term's residuals and the gradient of the relative
+    loss with respect to the network outputs) against the FP64 reference of
+    oracle/mlp_ref.py on the same outputs: trajectory rows of the 16^2 x 32^2
+    double well, loss within 1e-12 and dL/dy within 1e-10 relative."""
+    from paper_2511_11354_gb300 import learned, w2
+    prob, f0 = _small_dwell()
+    F, P, D = learned.make_kernel_dataset(prob, f0, snapshots=6, stride=2, points_per_snapshot=20, seed=3)
+    mlp = w2.MLP(prob.nk, hidden=64, max_rows=prob.nx, kind="kernel")
+    s_y = 3.0 * float(F.square().mean().sqrt()) / float(P.square().mean().sqrt())
+    mlp.set_scales(1.0, 1.0, s_y)
+    ctx = w2.Context.from_problem(prob, precision=w2.W2_F64_SLICED)
+    loss, y, g = mlp.kernel_loss_grad(ctx, F, P, D)
+    nk = prob.nk
+    Fh = F.cpu().numpy().reshape(-1, nk, nk)
+    Ph = P.cpu().numpy().reshape(-1, nk, nk)
+    # the kernels scale the outputs by the FP32 reciprocal of s_y
+    s_eff = 1.0 / float(np.float32(1.0) / np.float32(mlp.scales[2]))
+    lref, gref = mlp_ref.pair_kernel_loss_grad(Fh, Ph, D.cpu().numpy(), y.astype(np.float64), s_eff)
+    assert abs(loss - lref) < 1e-12 * lref, (loss, lref)
+    assert np.linalg.norm(g - gref) < 1e-10 * np.linalg.norm(gref), np.linalg.norm(g - gref) / np.linalg.norm(gref)
+    assert np.all(g[:, 0] == 0.0)
+    # the training step reports the same loss before its update
+    assert mlp.kernel_train_step(ctx, F, P, D, 1e-3) == loss
+    ctx.close()
+    mlp.close()
+
+
 def test_kernel_network_learns_the_two_body_term():
     """A kernel network trained on snapshots of an exact trajectory (random
     spatial points of each) stands in for the two-body term: the judge's

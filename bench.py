@@ -141,7 +141,7 @@ def _pipe_peaks():
 # of the predictor and the corrector of one ncu capture
 # (profiles/k_theta_s_dwell_64x64.md), keyed by the hash of the kernel source
 # it was taken on: any change to the source reports null.
-THETA_TRAFFIC = {"6d40002dce10ebeb": 0.5 * ((134.685696e6 + 93.946112e6) + (268.754176e6 + 95.090944e6))}
+THETA_TRAFFIC = {"2d62c7ef54f4f3ac": 0.5 * ((134.500096e6 + 94.296832e6) + (268.730112e6 + 94.436608e6))}
 
 
 def _theta_traffic():
@@ -697,6 +697,49 @@ def main():
     k_shift = kprof[4]
     step_bytes = 72.0 * prob.points   # algorithmic bytes of a whole step
 
+    # ---- the same workload with exchange symmetry declared (the state is an
+    # exchange-symmetrised product, so the sliced sweeps take the blocks with
+    # i1 <= i2 and write the mirrors transposed); a secondary measurement:
+    # the headline above runs every block
+    sy = w2.Context.from_problem(prob, precision=w2.W2_F64_SLICED)
+    sy.set_exchange_symmetry(True)
+    sy.set_state(f_dev)
+    sy.step(args.warmup)
+    sym_ms = []
+    for _ in range(max(1, min(len(rep_ms), 5))):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        sy.step(args.steps)
+        e1.record(stream)
+        barrier()
+        sym_ms.append(max_over_ranks(e0.elapsed_time(e1)))
+    ms_sym = statistics.median(sym_ms)
+    kprof_sym = sy.step_profile(min(args.steps, 50))
+    # agreement with the full sweep: the same number of steps from the same state
+    chk_a = w2.Context.from_problem(prob, precision=w2.W2_F64_SLICED)
+    chk_a.set_state(f_dev)
+    sy.set_state(f_dev)
+    chk_a.step(20)
+    sy.step(20)
+    ga, gs = chk_a.get_state(), sy.get_state()
+    sym_rel = float(np.linalg.norm(gs - ga) / np.linalg.norm(ga))
+    del ga, gs
+    chk_a.close()
+    sy.close()
+    sym_theta_gbs = 40.0 * prob.points / ((kprof_sym[2] + kprof_sym[7]) * 1e-3) / 1e9
+    exchange_symmetric = {
+        "what": "W2_F64_SLICED with w2_set_exchange_symmetry: the sweeps compute the blocks with i1 <= i2 and "
+                "write each mirror block transposed (the workload's state is exchange symmetric); the headline "
+                "value runs every block",
+        "value": whole_job_rate(prob.points, args.steps, ws, ms_sym), "ms_per_step": ms_sym / args.steps,
+        "kernel_ms": dict(zip(w2.STEP_KERNELS, [float(x) for x in kprof_sym])),
+        "theta_roofline": {"bound": "hbm", "achieved": sym_theta_gbs, "peak": MEASURED_HBM_GBS(), "unit": "GB/s",
+                           "frac": sym_theta_gbs / MEASURED_HBM_GBS(),
+                           "bytes_rule": "the method's bytes of every block (16 B/point predictor, 24 corrector)"},
+        "rel_l2_vs_full_sweep_after_20_steps": sym_rel,
+    }
+
     # ---- the FP64-pipe path (DMMA sweep, FP64 shift) on the same workload ---
     pipe = w2.Context.from_problem(prob)
     pipe.set_state(f_dev)
@@ -809,6 +852,7 @@ def main():
                                "peak_source": "hbm_gbs of measured (MEASURED_PEAKS.json)"},
             "step_hbm_frac": step_bytes / (ms / args.steps * 1e-3) / 1e9 / MEASURED_HBM_GBS(),
             "kernel_ms": dict(zip(w2.STEP_KERNELS, [float(x) for x in kprof])),
+            "exchange_symmetric": exchange_symmetric,
             "fp64_pipe_path": {
                 "what": "W2_F64: DMMA m8n8k4 sweep and FP64 spline shift on the FP64 pipe, same workload",
                 "value": whole_job_rate(prob.points, kp, ws, ms_pipe), "unit": UNIT, "steps": kp,

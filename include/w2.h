@@ -214,6 +214,20 @@ w2_status w2_set_state(w2_ctx *ctx, const void *f, int32_t on_device);
 w2_status w2_stage_state(w2_ctx *ctx, const void *f);
 w2_status w2_use_staged_state(w2_ctx *ctx);
 
+/* Exchange symmetry of the two-body state (identical particles):
+ * f(x1, x2, p1, p2) = f(x2, x1, p2, p1), which the paper's 2-RDM satisfies and
+ * the Lawson step preserves.  With on = 1 the sliced sweeps of w2_step
+ * (W2_F64_SLICED only) compute the pseudo-difference operator on the blocks
+ * X = (i1, i2) with i1 <= i2 and write each mirror block (i2, i1) as the
+ * transpose (the one-body kernels of the two particles coincide and the pair
+ * kernel is odd in x1 - x2), about half the tensor-core work of a step.  The
+ * caller guarantees that the state it sets is exchange symmetric; for other
+ * states the results differ from on = 0 by the state's asymmetric part.
+ * Not used while a learned two-body term is active, nor by w2_theta.
+ * Errors: W2_ERR_ARG (on not 0 or 1), W2_ERR_UNSUPPORTED (on = 1 and not
+ * W2_F64_SLICED). */
+w2_status w2_set_exchange_symmetry(w2_ctx *ctx, int32_t on);
+
 /* Copy the current state out (same layout).  With on_device == 0 the call
  * synchronises the stream before returning.  Errors: W2_ERR_ARG, W2_ERR_STATE
  * (no state), W2_ERR_CUDA. */

@@ -468,6 +468,15 @@ extern "C" w2_status w2_use_staged_state(w2_ctx *ctx) {
   return W2_OK;
 }
 
+extern "C" w2_status w2_set_exchange_symmetry(w2_ctx *ctx, int32_t on) {
+  if (!ctx || (on != 0 && on != 1)) return W2_ERR_ARG;
+  if (ctx->sticky) return ctx->sticky;
+  if (on && ctx->prec != W2_F64_SLICED) return W2_ERR_UNSUPPORTED;
+  if (ctx->exchange_sym != (on != 0)) drop_graphs(ctx);
+  ctx->exchange_sym = on != 0;
+  return W2_OK;
+}
+
 extern "C" w2_status w2_get_state(w2_ctx *ctx, void *f, int32_t on_device) {
   if (!ctx || !f) return W2_ERR_ARG;
   if (ctx->sticky) return ctx->sticky;
@@ -665,6 +674,8 @@ static cudaError_t enqueue_step(w2_ctx *ctx, cudaStream_t s, const StepEvents *e
   th.half_tau = 0.5 * ctx->tau;
   const bool learned = ctx->mlp && ctx->learned_active;
   const bool learned_kernel = learned && mlp_kind(ctx->mlp) == 1;
+  // the network's pair table need not be odd in x1 - x2: no mirrored blocks with it
+  th.sym = ctx->exchange_sym && ctx->prec == W2_F64_SLICED && !learned;
   if (learned_kernel) {
     th.K12 = ctx->Klearn;  // the network's pair table, built when it was attached
   } else if (learned) {

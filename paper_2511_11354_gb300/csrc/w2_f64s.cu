@@ -228,7 +228,52 @@ __device__ __forceinline__ void slot_exact_sum(const long long *I12, int em_loc,
   __syncthreads();
 }
 
-// One CTA per spatial point X.  MODE 0: out = Theta[in].  MODE 1: out = h + half_tau Theta[in].
+// The mirror block X' = (i2, i1) of an exchange-symmetric input: Theta at X'
+// is the transpose of Theta at X (the one-body kernels of the two particles
+// coincide and the pair kernel is odd in x1 - x2), so
+//   MODE 0: out(X')[r][c] = C[c][r],   MODE 1: out(X')[r][c] = h(X')[r][c] + half_tau C[c][r],
+// with C = Theta at X staged in shared memory at row stride NK + 1, and in the
+// corrector (with xsum given) the exact per-X sum of out(X').  Every thread of
+// the CTA calls this; red: 64 ints of shared memory.
+template <int NK, int MODE>
+__device__ __forceinline__ void mirror_block(const ThetaArgs &a, const double *C, int Xm, int *red) {
+  constexpr int THREADS = SlicedLayout<NK>::THREADS, PER = NK * NK / THREADS;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = THREADS >> 5;
+  const size_t mbase = (size_t)Xm * NK * NK;
+  double v[PER];
+  int em = 0;
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int e = tid + i * THREADS, r = e / NK, c = e - r * NK;
+    const double t = C[c * (NK + 1) + r];
+    v[i] = MODE == 0 ? t : fma(a.half_tau, t, a.h[mbase + e]);
+    a.out[mbase + e] = v[i];
+    em = max(em, expo(v[i]));
+  }
+  if (MODE == 0 || !a.xsum) return;
+  long long *lred = reinterpret_cast<long long *>(red + 32);
+  em = __reduce_max_sync(0xffffffffu, em);
+  if (lane == 0) red[w] = em;
+  __syncthreads();
+  em = 0;
+  for (int q = 0; q < nw; ++q) em = max(em, red[q]);
+  em = max(em, 1);
+  long long acc = 0;
+#pragma unroll
+  for (int i = 0; i < PER; ++i) acc += fixed_image(v[i], em);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) lred[w] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    long long tot = 0;
+    for (int q = 0; q < nw; ++q) tot += lred[q];
+    a.xsum[Xm] = em == 2047 ? __longlong_as_double(0x7ff8000000000000ll) : ll_to_double_scaled(tot, em - 1071);
+  }
+}
+
+// One CTA per spatial point X (with a.sym: per X with i1 <= i2, the mirror
+// block written as well).  MODE 0: out = Theta[in].  MODE 1: out = h + half_tau Theta[in].
 template <int NK, int MODE>
 __global__ void __launch_bounds__(SlicedLayout<NK>::THREADS, 512 / SlicedLayout<NK>::THREADS)
     k_theta_s(ThetaArgs a) {
@@ -240,8 +285,21 @@ __global__ void __launch_bounds__(SlicedLayout<NK>::THREADS, 512 / SlicedLayout<
   uint32_t *pk = reinterpret_cast<uint32_t *>(smraw + Lay::off_pk);
   int *red = reinterpret_cast<int *>(smraw + Lay::off_red);
 
-  const int nx = a.nx, X = blockIdx.x;
-  const int i1 = X / nx, i2 = X - i1 * nx;
+  const int nx = a.nx;
+  int i1, i2;
+  if (a.sym) {  // block b of the upper triangle, row by row: i1 <= i2
+    int b = blockIdx.x;
+    i1 = 0;
+    while (b >= nx - i1) {
+      b -= nx - i1;
+      ++i1;
+    }
+    i2 = i1 + b;
+  } else {
+    i1 = blockIdx.x / nx;
+    i2 = blockIdx.x - i1 * nx;
+  }
+  const int X = i1 * nx + i2;
   int dd = i1 - i2;
   dd += (dd < 0) ? nx : 0;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -389,6 +447,9 @@ __global__ void __launch_bounds__(SlicedLayout<NK>::THREADS, 512 / SlicedLayout<
   // values wait in the thread's own slots of I12 for the second pass.
   const int xs = emax + kmax - 2096;  // one unit of the recombined integer is 2^xs
   const bool sums = MODE == 1 && a.xsum;
+  const bool mirror = a.sym && i1 != i2;
+  double *C = reinterpret_cast<double *>(planes);  // Theta at X for the mirror block, row stride NK + 1
+  if (mirror) __syncthreads();  // every warp is done with the digit planes
   int em_loc = 0;
 #pragma unroll
   for (int q = 0; q < NCT; ++q) {
@@ -411,6 +472,10 @@ __global__ void __launch_bounds__(SlicedLayout<NK>::THREADS, 512 / SlicedLayout<
         t1 = ll_to_double_scaled(v1, xs) + (double)a.pair[o + 1];
       }
       if (bad) t0 = t1 = __longlong_as_double(0x7ff8000000000000ll);
+      if (mirror) {
+        C[n1 * (NK + 1) + n2] = t0;
+        C[n1 * (NK + 1) + n2 + 1] = t1;
+      }
       double2 v;
       if (MODE == 0) {
         v.x = t0;
@@ -429,6 +494,10 @@ __global__ void __launch_bounds__(SlicedLayout<NK>::THREADS, 512 / SlicedLayout<
     }
   }
   if (sums) slot_exact_sum<NK, NCT>(I12, em_loc, a.xsum + X, red);
+  if (mirror) {
+    __syncthreads();  // C complete
+    mirror_block<NK, MODE>(a, C, i2 * nx + i1, red);
+  }
 }
 
 template <int NK>
@@ -443,10 +512,11 @@ cudaError_t prep_s() {
 template <int NK>
 cudaError_t run_s(int mode, const ThetaArgs &a, cudaStream_t s) {
   using Lay = SlicedLayout<NK>;
+  const int grid = a.sym ? a.nx * (a.nx + 1) / 2 : a.nx * a.nx;
   if (mode == 0)
-    k_theta_s<NK, 0><<<a.nx * a.nx, Lay::THREADS, Lay::bytes, s>>>(a);
+    k_theta_s<NK, 0><<<grid, Lay::THREADS, Lay::bytes, s>>>(a);
   else
-    k_theta_s<NK, 1><<<a.nx * a.nx, Lay::THREADS, Lay::bytes, s>>>(a);
+    k_theta_s<NK, 1><<<grid, Lay::THREADS, Lay::bytes, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -54,6 +54,10 @@ struct ThetaArgs {
   const double *K1, *K2, *K12;
   double half_tau;
   const float *pair = nullptr;  // if set: the two-body term, [nx*nx][nk*nk], used instead of K12
+  // sliced sweep only: the input is exchange symmetric, in(x2, x1, p2, p1) =
+  // in(x1, x2, p1, p2), so the blocks with i1 <= i2 are computed and the
+  // mirror block X' = (i2, i1) of each is written from its transpose
+  int sym = 0;
 };
 
 struct AdvArgs {
@@ -337,6 +341,7 @@ struct w2_ctx {
   // learned form (FP64 contexts): the MLP's pair term replaces K12
   w2_mlp *mlp;
   bool learned_active;     // the step currently uses the network
+  bool exchange_sym;       // w2_set_exchange_symmetry: sliced sweeps on the blocks i1 <= i2
   int judge_every;         // steps between judgements (0: never)
   double judge_tol;        // fall back to the exact term above this error
   int since_judge, judged;

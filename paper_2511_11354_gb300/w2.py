@@ -37,7 +37,7 @@ EXPORTS = ("w2_create", "w2_set_potentials", "w2_set_state", "w2_stage_state", "
            "w2_batch_create", "w2_batch_set_potentials", "w2_batch_set_state", "w2_batch_get_state",
            "w2_batch_observables", "w2_batch_step", "w2_batch_autotune", "w2_batch_destroy", "w2_batch_sync",
            "w2_batch_set_wait_limit", "w2_batch_inject_stall", "w2_debug_fail_alloc", "w2_debug_alloc_count",
-           "w2_observables_enqueue", "w2_observables_collect",
+           "w2_observables_enqueue", "w2_observables_collect", "w2_set_exchange_symmetry",
            "w2_mlp_create", "w2_mlp_create_kernel", "w2_pair_kernel_train_step", "w2_pair_kernel_loss_grad", "w2_mlp_param_count", "w2_mlp_input_dim", "w2_mlp_set_params", "w2_mlp_get_params",
            "w2_mlp_set_scales", "w2_mlp_forward", "w2_mlp_train_step", "w2_mlp_gradients", "w2_mlp_destroy",
            "w2_features", "w2_theta_pair", "w2_learned_attach", "w2_learned_report",
@@ -229,6 +229,12 @@ class Context:
 
     def set_hartree(self, kind):
         _check(self.lib.w2_set_hartree(self.h, int(kind)), "w2_set_hartree")
+
+    def set_exchange_symmetry(self, on=True):
+        """Declare the state exchange symmetric, f(x1, x2, p1, p2) =
+        f(x2, x1, p2, p1): the sliced step then computes the operator on the
+        blocks with i1 <= i2 and mirrors the rest (W2_F64_SLICED)."""
+        _check(self.lib.w2_set_exchange_symmetry(self.h, 1 if on else 0), "w2_set_exchange_symmetry")
 
     def set_patches(self, np1, np2):
         """Cut the x1 and x2 shifts into np1 and np2 patches joined by

@@ -193,6 +193,44 @@ def test_sliced_and_fp64_pipe_paths_agree_over_1000_steps_logged_every_10():
     b.close()
 
 
+@pytest.mark.parametrize("nx,nk,steps", [(8, 16, 4), (5, 32, 3), (12, 48, 3), (64, 64, 5)])
+def test_exchange_symmetric_sweep(nx, nk, steps):
+    """w2_set_exchange_symmetry: on an exchange-symmetric state the sweeps
+    over the blocks with i1 <= i2 plus their transposed mirrors give the
+    steps of the full sweep to rounding (1e-13) and the oracle within 1e-10;
+    the state stays symmetric; the other precisions refuse the mode."""
+    from paper_2511_11354_gb300 import w2
+    prob, f0 = inputs.workload_dwell(nx=nx, nk=nk)
+    assert np.array_equal(f0, f0.transpose(1, 0, 3, 2))
+    full = _ctx(prob)
+    sym = _ctx(prob)
+    sym.set_exchange_symmetry(True)
+    d = _dev(f0)
+    full.set_state(d)
+    sym.set_state(d)
+    full.step(steps)
+    sym.step(steps)
+    a, b = full.get_state(), sym.get_state()
+    assert rel(b, a) < 1e-13, rel(b, a)
+    assert rel(b, oracle.Oracle(prob).step(f0, steps)) < 1e-10
+    assert np.abs(b - b.transpose(1, 0, 3, 2)).max() < 1e-13 * np.abs(b).max()
+    oa, ob = full.observables(), sym.observables()
+    for k in ("mass", "energy", "entropy_lin"):
+        assert abs(getattr(ob, k) - getattr(oa, k)) < 1e-13 * max(1.0, abs(getattr(oa, k))), k
+    sym.set_exchange_symmetry(False)  # and back: the full sweep again
+    sym.set_state(d)
+    sym.step(steps)
+    assert np.array_equal(sym.get_state(), a)
+    full.close()
+    sym.close()
+    for p in (w2.W2_F64, w2.W2_F32_TF32X3):
+        c = w2.Context.from_problem(prob, precision=p)
+        with pytest.raises(w2.W2Error) as e:
+            c.set_exchange_symmetry(True)
+        assert e.value.name == "W2_ERR_UNSUPPORTED"
+        c.close()
+
+
 def test_sliced_determinism_and_resume():
     prob, f0 = inputs.workload_small(nx=16, nk=16)
     a = _ctx(prob)

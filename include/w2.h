@@ -550,6 +550,39 @@ const char *w2_last_cuda_error(void);
 w2_status w2_debug_fail_alloc(int32_t n);
 int64_t w2_debug_alloc_count(void);
 
+/* ------------------------------------------------------------------------
+ * Encoders and one-tile self-test of the 5th-generation tensor-core path
+ * (tcgen05 MMA with a TMEM accumulator, operands in shared memory).
+ *
+ * w2_debug_umma_smem_desc: the 64-bit shared-memory matrix descriptor of a
+ * no-swizzle operand: start address (bytes, shared window), leading-dimension
+ * byte offset (distance between core matrices adjacent along K) and
+ * stride-dimension byte offset (along M or N); each a multiple of 16 below
+ * 256 KB.  w2_debug_umma_idesc: the 32-bit instruction descriptor of a
+ * kind::f16 MMA with BF16 A and B and an FP32 accumulator of M x N, A and B
+ * K-major (0) or MN-major (1).  w2_debug_umma_tile_off: byte offset of
+ * element (r, c) of a 16-bit matrix with ncol columns in the tiled layout
+ * (8 x 8 core matrices of 128 contiguous bytes, row-major over the tiles).
+ * Pure host functions, no device use, no errors.
+ *
+ * w2_debug_umma_gemm: one CTA computes D = A B (A: M x K, B: K x N, both
+ * row-major BF16 bit patterns in device memory; M = 64 or 128, N a multiple
+ * of 16 up to 64 (of 8 for M = 64), K = 16, 32, 48 or 64; A MN-major only
+ * for M = 64) on one tcgen05 MMA chain, after writing the marker word
+ * 0x7fc0dead to TMEM columns [0, 2N) of all 128 lanes, and copies those
+ * columns to dump (device, [128][2N] 32-bit words, lane-major).  swap = 1
+ * passes the two core-matrix strides to the descriptor the other way round
+ * (for the test that tells the two conventions apart; both stay inside the
+ * operand's buffer).  Synchronises the device.  Errors: W2_ERR_ARG (shape or
+ * pointer), W2_ERR_UNSUPPORTED (not a compute-capability 10.x device),
+ * W2_ERR_TIMEOUT (the MMA's completion was not seen within about a second),
+ * W2_ERR_CUDA. */
+uint64_t w2_debug_umma_smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo);
+uint32_t w2_debug_umma_idesc(int32_t M, int32_t N, int32_t a_mn, int32_t b_mn);
+uint32_t w2_debug_umma_tile_off(int32_t r, int32_t c, int32_t ncol);
+w2_status w2_debug_umma_gemm(int32_t M, int32_t N, int32_t K, int32_t a_mn, int32_t b_mn, int32_t swap,
+                             const uint16_t *A, const uint16_t *B, uint32_t *dump);
+
 #ifdef __cplusplus
 }
 #endif

@@ -37,6 +37,7 @@ EXPORTS = ("w2_create", "w2_set_potentials", "w2_set_state", "w2_stage_state", "
            "w2_batch_create", "w2_batch_set_potentials", "w2_batch_set_state", "w2_batch_get_state",
            "w2_batch_observables", "w2_batch_step", "w2_batch_autotune", "w2_batch_destroy", "w2_batch_sync",
            "w2_batch_set_wait_limit", "w2_batch_inject_stall", "w2_debug_fail_alloc", "w2_debug_alloc_count",
+           "w2_debug_umma_smem_desc", "w2_debug_umma_idesc", "w2_debug_umma_tile_off", "w2_debug_umma_gemm",
            "w2_observables_enqueue", "w2_observables_collect", "w2_set_exchange_symmetry",
            "w2_mlp_create", "w2_mlp_create_kernel", "w2_pair_kernel_train_step", "w2_pair_kernel_loss_grad", "w2_mlp_param_count", "w2_mlp_input_dim", "w2_mlp_set_params", "w2_mlp_get_params",
            "w2_mlp_set_scales", "w2_mlp_forward", "w2_mlp_train_step", "w2_mlp_gradients", "w2_mlp_destroy",
@@ -148,9 +149,17 @@ def load(path: str = LIB_PATH):
     lib.w2_debug_fail_alloc.argtypes = [ctypes.c_int32]
     lib.w2_debug_alloc_count.argtypes = []
     lib.w2_debug_alloc_count.restype = ctypes.c_int64
+    lib.w2_debug_umma_smem_desc.argtypes = [ctypes.c_uint32] * 3
+    lib.w2_debug_umma_smem_desc.restype = ctypes.c_uint64
+    lib.w2_debug_umma_idesc.argtypes = [ctypes.c_int32] * 4
+    lib.w2_debug_umma_idesc.restype = ctypes.c_uint32
+    lib.w2_debug_umma_tile_off.argtypes = [ctypes.c_int32] * 3
+    lib.w2_debug_umma_tile_off.restype = ctypes.c_uint32
+    lib.w2_debug_umma_gemm.argtypes = [ctypes.c_int32] * 6 + [vp, vp, vp]
     for name in EXPORTS:
         if name not in ("w2_destroy", "w2_status_string", "w2_last_cuda_error", "w2_batch_destroy", "w2_mlp_destroy",
-                        "w2_sem_destroy", "w2_debug_alloc_count",
+                        "w2_sem_destroy", "w2_debug_alloc_count", "w2_debug_umma_smem_desc",
+                        "w2_debug_umma_idesc", "w2_debug_umma_tile_off",
                         "w2_mlp_param_count", "w2_mlp_input_dim"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -166,6 +175,37 @@ def debug_fail_alloc(n: int):
 def debug_alloc_count() -> int:
     """Allocations the library has attempted since it was loaded."""
     return int(load().w2_debug_alloc_count())
+
+
+def umma_smem_desc(saddr: int, lbo: int, sbo: int) -> int:
+    """The tcgen05 shared-memory matrix descriptor (no swizzle) the library encodes."""
+    return int(load().w2_debug_umma_smem_desc(saddr, lbo, sbo))
+
+
+def umma_idesc(M: int, N: int, a_mn: bool, b_mn: bool) -> int:
+    """The tcgen05 kind::f16 instruction descriptor (BF16 in, FP32 out) the library encodes."""
+    return int(load().w2_debug_umma_idesc(M, N, int(a_mn), int(b_mn)))
+
+
+def umma_tile_off(r: int, c: int, ncol: int) -> int:
+    """Byte offset of element (r, c) in the library's tiled 16-bit operand layout."""
+    return int(load().w2_debug_umma_tile_off(r, c, ncol))
+
+
+def umma_gemm(A, B, a_mn: bool = False, b_mn: bool = False, swap: bool = False):
+    """One tcgen05 MMA chain D = A B on one CTA (A: M x K, B: K x N, BF16
+    tensors on the device); returns the raw TMEM dump, [128][2N] uint32 words
+    as an int32 tensor (marker 0x7fc0dead where the MMA did not write)."""
+    import torch
+    M, K = A.shape
+    K2, N = B.shape
+    if K2 != K or A.dtype != torch.bfloat16 or B.dtype != torch.bfloat16:
+        raise ValueError("A (M x K) and B (K x N) must be BF16 with matching K")
+    A, B = A.contiguous(), B.contiguous()
+    dump = torch.empty((128, 2 * N), dtype=torch.int32, device=A.device)
+    _check(load().w2_debug_umma_gemm(M, N, K, int(a_mn), int(b_mn), int(swap), A.data_ptr(), B.data_ptr(),
+                                     dump.data_ptr()), "w2_debug_umma_gemm")
+    return dump
 
 
 def _check(code: int, what: str):

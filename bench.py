@@ -740,6 +740,42 @@ def main():
         "rel_l2_vs_full_sweep_after_20_steps": sym_rel,
     }
 
+    # ---- the same workload with the sweeps' slice products on tcgen05 (MMA
+    # into tensor memory) instead of mma.sync; a secondary measurement
+    tc = w2.Context.from_problem(prob, precision=w2.W2_F64_SLICED)
+    tc.set_tensor_path(True)
+    tc.set_state(f_dev)
+    tc.step(args.warmup)
+    tc_ms = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        tc.step(args.steps)
+        e1.record(stream)
+        barrier()
+        tc_ms.append(max_over_ranks(e0.elapsed_time(e1)))
+    ms_tc = statistics.median(tc_ms)
+    kprof_tc = tc.step_profile(min(args.steps, 50))
+    chk_a = w2.Context.from_problem(prob, precision=w2.W2_F64_SLICED)
+    chk_a.set_state(f_dev)
+    tc.set_state(f_dev)
+    chk_a.step(20)
+    tc.step(20)
+    ga, gt = chk_a.get_state(), tc.get_state()
+    tc_rel = float(np.linalg.norm(gt - ga) / np.linalg.norm(ga))
+    del ga, gt
+    chk_a.close()
+    tc.close()
+    tcgen05_sweep = {
+        "what": "W2_F64_SLICED with w2_set_tensor_path(1): the same 21 slice products on tcgen05 (BF16 operands "
+                "in shared memory, FP32 accumulators in tensor memory, one CTA of 215 KB per SM); the headline "
+                "runs them on mma.sync, the faster path for this operator",
+        "value": whole_job_rate(prob.points, args.steps, ws, ms_tc), "ms_per_step": ms_tc / args.steps,
+        "kernel_ms": dict(zip(w2.STEP_KERNELS, [float(x) for x in kprof_tc])),
+        "rel_l2_vs_mma_sync_after_20_steps": tc_rel,
+    }
+
     # ---- the FP64-pipe path (DMMA sweep, FP64 shift) on the same workload ---
     pipe = w2.Context.from_problem(prob)
     pipe.set_state(f_dev)
@@ -853,6 +889,7 @@ def main():
             "step_hbm_frac": step_bytes / (ms / args.steps * 1e-3) / 1e9 / MEASURED_HBM_GBS(),
             "kernel_ms": dict(zip(w2.STEP_KERNELS, [float(x) for x in kprof])),
             "exchange_symmetric": exchange_symmetric,
+            "tcgen05_sweep": tcgen05_sweep,
             "fp64_pipe_path": {
                 "what": "W2_F64: DMMA m8n8k4 sweep and FP64 spline shift on the FP64 pipe, same workload",
                 "value": whole_job_rate(prob.points, kp, ws, ms_pipe), "unit": UNIT, "steps": kp,

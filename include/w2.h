@@ -80,7 +80,8 @@ typedef enum {
                            contractions as exact products of six 8-bit integer
                            slices of each operand on the BF16 tensor cores (the
                            Ozaki splitting, 21 slice pairs), recombined in 64-bit
-                           integers; nk in {16, 32, 48, 64}                      */
+                           integers; nk in {16, 32, 48, 64}; on mma.sync, or
+                           on tcgen05 for nk = 64 (w2_set_tensor_path)           */
 } w2_precision;
 
 typedef enum {
@@ -228,6 +229,31 @@ w2_status w2_use_staged_state(w2_ctx *ctx);
  * W2_F64_SLICED). */
 w2_status w2_set_exchange_symmetry(w2_ctx *ctx, int32_t on);
 
+/* Tensor-core path of the sliced sweeps (W2_F64_SLICED; the pseudo-difference
+ * operator of Sec. 3.1 as exact 8-bit slice products).  tcgen05 = 0, the
+ * default, runs every sweep on the warp-level mma.sync path (the faster one
+ * on this operator: see the design notes).  tcgen05 = 1 runs every digit
+ * product on the 5th-generation tensor cores (tcgen05 MMA with the
+ * accumulators in tensor memory) where supported: N_k = 64 without a learned
+ * pair term; other cases stay on the warp-level path.  Both give the operator
+ * to FP64 accuracy and differ only in the rounding of the lowest slice
+ * diagonal (below 2^-50 of each block's scale).  A bounded wait of the
+ * tcgen05 sweep that gives up (about a second) leaves NaN in its block and
+ * makes the next w2_observables return W2_ERR_TIMEOUT.
+ * Errors: W2_ERR_ARG (tcgen05 not 0 or 1), W2_ERR_UNSUPPORTED (tcgen05 = 1 and
+ * not W2_F64_SLICED). */
+w2_status w2_set_tensor_path(w2_ctx *ctx, int32_t tcgen05);
+
+/* Host-requested fault injection into the tcgen05 sweep, for testing its
+ * time-out path without any device fault: with stall = 1 every tcgen05 sweep
+ * of the context leaves one batch of its products and their completion signal
+ * out, so its next bounded wait (wait_cycles SM clocks; 0: about a second)
+ * runs out; the sweep then issues nothing more, waits for the products it did
+ * issue, writes NaN to its blocks and sets the error word that makes
+ * w2_observables return W2_ERR_TIMEOUT.  stall = 0 restores normal sweeps and
+ * clears the error word.  Errors: W2_ERR_ARG. */
+w2_status w2_debug_sweep_stall(w2_ctx *ctx, int32_t stall, int64_t wait_cycles);
+
 /* Copy the current state out (same layout).  With on_device == 0 the call
  * synchronises the stream before returning.  Errors: W2_ERR_ARG, W2_ERR_STATE
  * (no state), W2_ERR_CUDA. */
@@ -247,7 +273,8 @@ w2_status w2_step(w2_ctx *ctx, int32_t nsteps);
  * n_1(x_i) = sum f dx dp^2 over (x2, p1, p2); n12 (host, [nx*nx], or NULL) the
  * pair density n_12(x_i1, x_i2) = sum f dp^2 over (p1, p2).
  * Errors: W2_ERR_ARG, W2_ERR_STATE, W2_ERR_NONFINITE (NaN/Inf in the state; the
- * outputs are still written), W2_ERR_CUDA. */
+ * outputs are still written), W2_ERR_TIMEOUT (a tcgen05 sweep gave up a wait,
+ * see w2_set_tensor_path), W2_ERR_CUDA. */
 w2_status w2_observables(w2_ctx *ctx, w2_obs *out, double *n1, double *n12);
 
 /* The same observables without waiting, for a host loop that reads each
@@ -567,8 +594,8 @@ int64_t w2_debug_alloc_count(void);
  *
  * w2_debug_umma_gemm: one CTA computes D = A B (A: M x K, B: K x N, both
  * row-major BF16 bit patterns in device memory; M = 64 or 128, N a multiple
- * of 16 up to 64 (of 8 for M = 64), K = 16, 32, 48 or 64; A MN-major only
- * for M = 64) on one tcgen05 MMA chain, after writing the marker word
+ * of 16 up to 64 (of 8 for M = 64), K = 16, 32, 48 or 64) on one tcgen05
+ * MMA chain, after writing the marker word
  * 0x7fc0dead to TMEM columns [0, 2N) of all 128 lanes, and copies those
  * columns to dump (device, [128][2N] 32-bit words, lane-major).  swap = 1
  * passes the two core-matrix strides to the descriptor the other way round

@@ -40,7 +40,15 @@ static inline bool f64_state(int prec) { return prec == W2_F64 || prec == W2_F64
 // The FP64 sweep of a context: on the FP64 pipe, or by exact slices on the
 // BF16 tensor cores.
 static cudaError_t theta64(const w2_ctx *ctx, int mode, const ThetaArgs &th, cudaStream_t s) {
-  return ctx->prec == W2_F64_SLICED ? launch_theta_f64s(ctx->nk, mode, th, s) : launch_theta_f64(ctx->nk, mode, th, s);
+  if (ctx->prec != W2_F64_SLICED) return launch_theta_f64(ctx->nk, mode, th, s);
+  if (ctx->tc_path && theta_t_supported(ctx->nk, th)) {
+    ThetaArgs t = th;
+    t.err = ctx->d_err;
+    t.stall = ctx->dbg_stall;
+    t.wait_limit = ctx->dbg_wait;
+    return launch_theta_f64t(mode, t, s);
+  }
+  return launch_theta_f64s(ctx->nk, mode, th, s);
 }
 
 // Forget the captured steps (the potentials, the Hartree kind, the patches or
@@ -62,7 +70,7 @@ static void free_all(w2_ctx *c) {
   void *ptrs[] = {c->f, c->g, c->t1, c->t2, c->xsum, c->xsum2, c->K, c->K12, c->vext_fine, c->w_fine,
                   c->d_fine, c->sintab, c->vext_grid, c->k0tab, c->wtab, c->xpart, c->obs_out,
                   c->wtab32, c->ctab32, c->wdf, c->zpow, c->h_fine, c->rdm_f1, c->rdm_fh, c->rdm_kh,
-                  c->rdm_eig, c->rdm_ph, c->rdm_rho};
+                  c->rdm_eig, c->rdm_ph, c->rdm_rho, c->d_err};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_obs) cudaFreeHost(c->h_obs);
@@ -234,12 +242,15 @@ extern "C" w2_status w2_create(const w2_config *cfg, void *cuda_stream, w2_ctx *
   W2_ALLOC(ctx->obs_out, sizeof(double) * (8 + nx + nx * nx))
   W2_ALLOC(ctx->wtab32, sizeof(float) * 4 * nk) W2_ALLOC(ctx->ctab32, sizeof(float) * 8 * nk)
   W2_ALLOC(ctx->wdf, sizeof(float2) * 4 * nk) W2_ALLOC(ctx->zpow, sizeof(float2) * 32)
+  W2_ALLOC(ctx->d_err, sizeof(int))
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int));
 #undef W2_ALLOC
   if (e == cudaSuccess) e = host_alloc((void **)&ctx->h_obs, sizeof(double) * (8 + nx + nx * nx));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = f64_state(ctx->prec) ? prepare_kernels_f64(nk) : prepare_kernels_f32(nk);
   if (e == cudaSuccess && ctx->prec == W2_F32_BF16X3) e = prepare_kernels_b3(nk);
   if (e == cudaSuccess && ctx->prec == W2_F64_SLICED) e = prepare_kernels_f64s(nk);
+  if (e == cudaSuccess && ctx->prec == W2_F64_SLICED && nk == 64) e = prepare_kernels_f64t();
   if (e == cudaSuccess && ctx->prec == W2_F64_SLICED) e = prepare_kernels_adv_df(nk);
   if (e != cudaSuccess) {
     w2_status st = (e == cudaErrorMemoryAllocation) ? W2_ERR_OOM : W2_ERR_CUDA;
@@ -465,6 +476,25 @@ extern "C" w2_status w2_use_staged_state(w2_ctx *ctx) {
   ctx->stage_pending = false;
   ctx->have_state = true;
   ctx->steps = 0;
+  return W2_OK;
+}
+
+extern "C" w2_status w2_set_tensor_path(w2_ctx *ctx, int32_t tcgen05) {
+  if (!ctx || (tcgen05 != 0 && tcgen05 != 1)) return W2_ERR_ARG;
+  if (ctx->sticky) return ctx->sticky;
+  if (tcgen05 && ctx->prec != W2_F64_SLICED) return W2_ERR_UNSUPPORTED;
+  if (ctx->tc_path != (tcgen05 != 0)) drop_graphs(ctx);
+  ctx->tc_path = tcgen05 != 0;
+  return W2_OK;
+}
+
+extern "C" w2_status w2_debug_sweep_stall(w2_ctx *ctx, int32_t stall, int64_t wait_cycles) {
+  if (!ctx || (stall != 0 && stall != 1) || wait_cycles < 0) return W2_ERR_ARG;
+  if (ctx->sticky) return ctx->sticky;
+  drop_graphs(ctx);
+  ctx->dbg_stall = stall;
+  ctx->dbg_wait = wait_cycles;
+  if (!stall) W2_TRY(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
   return W2_OK;
 }
 
@@ -883,6 +913,7 @@ static w2_status enqueue_obs(w2_ctx *ctx) {
   a.h_fine = ctx->hartree_kind == W2_HARTREE_POISSON ? ctx->h_fine : nullptr;
   a.xpart = ctx->xpart;
   a.out = ctx->obs_out;
+  a.err = ctx->d_err;
   W2_TRY(launch_obs(a, ctx->stream));
   return W2_OK;
 }
@@ -899,6 +930,7 @@ static w2_status unpack_obs(const w2_ctx *ctx, const double *h, long long steps,
   out->step = steps;
   if (n1) memcpy(n1, h + 8, sizeof(double) * nx);
   if (n12) memcpy(n12, h + 8 + nx, sizeof(double) * nx * nx);
+  if (h[5] != 0.0) return W2_ERR_TIMEOUT;
   return h[4] != 0.0 ? W2_ERR_NONFINITE : W2_OK;
 }
 

@@ -58,6 +58,10 @@ struct ThetaArgs {
   // in(x1, x2, p1, p2), so the blocks with i1 <= i2 are computed and the
   // mirror block X' = (i2, i1) of each is written from its transpose
   int sym = 0;
+  // tcgen05 sweep only: set to nonzero if a bounded wait on the tensor core gave up
+  int *err = nullptr;
+  int stall = 0;               // tcgen05 sweep, fault injection: leave one batch of products out
+  long long wait_limit = 0;    // tcgen05 sweep: SM clocks per bounded wait (0: about a second)
 };
 
 struct AdvArgs {
@@ -111,6 +115,7 @@ struct ObsArgs {
   double *xpart;            // [nx*nx][3 + nk] per-X partials, then [nx][8] per-x1 partials
   double *out;              // [8 + nx + nx*nx]
   const double *h_fine = nullptr;  // as in TabArgs (column 0: the kernel at grid distances)
+  const int *err = nullptr;         // device error word of the sweeps (out[5] = its value), or null
 };
 
 struct Theta32Args {
@@ -253,6 +258,11 @@ cudaError_t launch_theta_f64(int nk, int mode, const ThetaArgs &a, cudaStream_t 
 cudaError_t launch_theta_f64s(int nk, int mode, const ThetaArgs &a, cudaStream_t s);
 cudaError_t prepare_kernels_f64s(int nk);
 bool nk_supported_f64s(int nk);
+// The same sweep with every digit product on tcgen05 (w2_f64t.cu): N_k = 64,
+// no learned pair term.
+bool theta_t_supported(int nk, const ThetaArgs &a);
+cudaError_t prepare_kernels_f64t();
+cudaError_t launch_theta_f64t(int mode, const ThetaArgs &a, cudaStream_t s);
 cudaError_t launch_adv_f64(int nk, int dir, int two, const AdvArgs &a, cudaStream_t s);
 cudaError_t launch_adv_df(int nk, int dir, int two, const AdvDFArgs &a, cudaStream_t s);
 cudaError_t prepare_kernels_adv_df(int nk);
@@ -342,6 +352,10 @@ struct w2_ctx {
   w2_mlp *mlp;
   bool learned_active;     // the step currently uses the network
   bool exchange_sym;       // w2_set_exchange_symmetry: sliced sweeps on the blocks i1 <= i2
+  bool tc_path;            // w2_set_tensor_path: sliced sweeps on tcgen05 where supported
+  int *d_err;              // device error word: bounded tensor-core waits that gave up
+  int dbg_stall;           // w2_debug_sweep_stall: fault injection into the tcgen05 sweep
+  long long dbg_wait;      // and its wait limit (SM clocks; 0: the default)
   int judge_every;         // steps between judgements (0: never)
   double judge_tol;        // fall back to the exact term above this error
   int since_judge, judged;

@@ -308,6 +308,7 @@ __global__ void k_obs_final(ObsArgs a, const double *mid) {
     a.out[2] = purity;
     a.out[3] = l2n;
     a.out[4] = (sbad || !isfinite(mass) || !isfinite(energy) || !isfinite(purity) || !isfinite(l2n)) ? 1.0 : 0.0;
+    a.out[5] = a.err ? (double)*a.err : 0.0;
   }
 }
 

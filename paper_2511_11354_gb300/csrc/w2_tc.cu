@@ -20,7 +20,7 @@
 namespace w2 {
 namespace {
 
-constexpr uint32_t kRegA = 64 * 1024, kRegB = 32 * 1024;
+constexpr uint32_t kRegA = 96 * 1024, kRegB = 32 * 1024;
 constexpr uint32_t kMarker = 0x7fc0deadu;
 
 struct UTArgs {

@@ -38,7 +38,7 @@ EXPORTS = ("w2_create", "w2_set_potentials", "w2_set_state", "w2_stage_state", "
            "w2_batch_observables", "w2_batch_step", "w2_batch_autotune", "w2_batch_destroy", "w2_batch_sync",
            "w2_batch_set_wait_limit", "w2_batch_inject_stall", "w2_debug_fail_alloc", "w2_debug_alloc_count",
            "w2_debug_umma_smem_desc", "w2_debug_umma_idesc", "w2_debug_umma_tile_off", "w2_debug_umma_gemm",
-           "w2_observables_enqueue", "w2_observables_collect", "w2_set_exchange_symmetry",
+           "w2_observables_enqueue", "w2_observables_collect", "w2_set_exchange_symmetry", "w2_set_tensor_path", "w2_debug_sweep_stall",
            "w2_mlp_create", "w2_mlp_create_kernel", "w2_pair_kernel_train_step", "w2_pair_kernel_loss_grad", "w2_mlp_param_count", "w2_mlp_input_dim", "w2_mlp_set_params", "w2_mlp_get_params",
            "w2_mlp_set_scales", "w2_mlp_forward", "w2_mlp_train_step", "w2_mlp_gradients", "w2_mlp_destroy",
            "w2_features", "w2_theta_pair", "w2_learned_attach", "w2_learned_report",
@@ -156,6 +156,8 @@ def load(path: str = LIB_PATH):
     lib.w2_debug_umma_tile_off.argtypes = [ctypes.c_int32] * 3
     lib.w2_debug_umma_tile_off.restype = ctypes.c_uint32
     lib.w2_debug_umma_gemm.argtypes = [ctypes.c_int32] * 6 + [vp, vp, vp]
+    lib.w2_debug_sweep_stall.argtypes = [vp, ctypes.c_int32, ctypes.c_int64]
+    lib.w2_set_tensor_path.argtypes = [vp, ctypes.c_int32]
     for name in EXPORTS:
         if name not in ("w2_destroy", "w2_status_string", "w2_last_cuda_error", "w2_batch_destroy", "w2_mlp_destroy",
                         "w2_sem_destroy", "w2_debug_alloc_count", "w2_debug_umma_smem_desc",
@@ -275,6 +277,17 @@ class Context:
         f(x2, x1, p2, p1): the sliced step then computes the operator on the
         blocks with i1 <= i2 and mirrors the rest (W2_F64_SLICED)."""
         _check(self.lib.w2_set_exchange_symmetry(self.h, 1 if on else 0), "w2_set_exchange_symmetry")
+
+    def set_tensor_path(self, tcgen05=True):
+        """Run the sliced sweeps' digit products on tcgen05 (True; nk = 64)
+        or on warp-level mma.sync (False, the default)."""
+        _check(self.lib.w2_set_tensor_path(self.h, 1 if tcgen05 else 0), "w2_set_tensor_path")
+
+    def debug_sweep_stall(self, stall, wait_cycles=0):
+        """Fault injection into the tcgen05 sweep (its next bounded wait runs
+        out); stall=False restores normal sweeps and clears the error word."""
+        _check(self.lib.w2_debug_sweep_stall(self.h, 1 if stall else 0, ctypes.c_int64(int(wait_cycles))),
+               "w2_debug_sweep_stall")
 
     def set_patches(self, np1, np2):
         """Cut the x1 and x2 shifts into np1 and np2 patches joined by

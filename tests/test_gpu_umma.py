@@ -75,6 +75,14 @@ def test_m64_mn_major_a():
     assert rows == set(range(M))
 
 
+@pytest.mark.parametrize("N,K", [(64, 64), (32, 16)])
+def test_m128_mn_major_a(N, K):
+    """M = 128 with an MN-major A (the layout of the sheared planes)."""
+    want, d = _run(128, N, K, a_mn=True, seed=7 + N)
+    assert np.all(d[:, N:] == MARK)
+    assert np.array_equal(d[:, :N].view(np.float32).astype(np.float64), want)
+
+
 def test_stride_convention():
     """The descriptor's two core-matrix strides are not interchangeable: the
     encoding the library uses gives A B, the swapped one does not."""

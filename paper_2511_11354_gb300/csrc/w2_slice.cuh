@@ -90,11 +90,15 @@ __device__ __forceinline__ void mirror_block(const ThetaArgs &a, const double *C
   const size_t mbase = (size_t)Xm * NK * NK;
   double v[PER];
   int em = 0;
+  if (MODE == 1) {  // every load of h before the first store (the stores may alias it)
+#pragma unroll
+    for (int i = 0; i < PER; ++i) v[i] = a.h[mbase + tid + i * THREADS];
+  }
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
     const int e = tid + i * THREADS, r = e / NK, c = e - r * NK;
     const double t = C[c * (NK + 1) + r];
-    v[i] = MODE == 0 ? t : fma(a.half_tau, t, a.h[mbase + e]);
+    v[i] = MODE == 0 ? t : fma(a.half_tau, t, v[i]);
     a.out[mbase + e] = v[i];
     em = max(em, expo(v[i]));
   }

@@ -31,9 +31,12 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def _ctx(prob):
+def _ctx(prob, tcgen05=True):
+    """A sliced context on the tcgen05 path (tcgen05=False: the mma.sync path)."""
     from paper_2511_11354_gb300 import w2
-    return w2.Context.from_problem(prob, precision=w2.W2_F64_SLICED)
+    c = w2.Context.from_problem(prob, precision=w2.W2_F64_SLICED)
+    c.set_tensor_path(tcgen05)
+    return c
 
 
 def _both(prob, f):
@@ -92,8 +95,7 @@ def test_full_size_steps_tcgen05_against_mma_sync():
     prob, f0 = inputs.workload_dwell()
     runs = []
     for tc in (True, False):
-        c = _ctx(prob)
-        c.set_tensor_path(tc)
+        c = _ctx(prob, tc)
         c.set_state(f0)
         c.step(20)
         runs.append((c.get_state(), c.observables()))

@@ -139,15 +139,16 @@ def _pipe_peaks():
 
 # DRAM bytes (read + write) per k_theta_s launch on the 64^4 workload, the mean
 # of the predictor and the corrector of one ncu capture
-# (profiles/k_theta_s_dwell_64x64.md), keyed by the hash of the kernel source
-# it was taken on: any change to the source reports null.
-THETA_TRAFFIC = {"2d62c7ef54f4f3ac": 0.5 * ((134.500096e6 + 94.296832e6) + (268.730112e6 + 94.436608e6))}
+# (profiles/k_theta_s_dwell_64x64.md), keyed by the hash of the kernel's
+# sources (w2_f64s.cu, w2_slice.cuh) it was taken on: any change reports null.
+THETA_TRAFFIC = {"a0d982b65dec86bc": 0.5 * ((134.528000e6 + 93.936128e6) + (268.731392e6 + 91.467008e6))}
 
 
 def _theta_traffic():
     import hashlib
-    src = os.path.join(ROOT, "paper_2511_11354_gb300", "csrc", "w2_f64s.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    csrc = os.path.join(ROOT, "paper_2511_11354_gb300", "csrc")
+    blob = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("w2_f64s.cu", "w2_slice.cuh"))
+    h = hashlib.sha256(blob).hexdigest()[:16]
     return THETA_TRAFFIC.get(h)
 
 

@@ -2,9 +2,9 @@
 // the exact 8-bit slice scheme of k_theta_s (w2_f64s.cu; Ozaki, Ogita, Oishi
 // and Rump, Numer. Algorithms 59, 2012, with fixed-point digits) with every
 // digit product on tcgen05.mma (kind::f16, BF16 operands in shared memory,
-// FP32 accumulators in tensor memory), for N_k = 64.  One CTA of 256 threads
-// per spatial point X, one CTA per SM (215 KB of shared memory, all 512 TMEM
-// columns).
+// FP32 accumulators in tensor memory), for N_k = 64.  Persistent CTAs of 512
+// threads, one per SM (215 KB of shared memory, all 512 TMEM columns), each
+// taking a run of consecutive spatial points X.
 //
 // The three Toeplitz contractions of Eq. Hartree_FSM / Eq. two_body_FSM for
 // the block F = f(X, ., .) and the kernel rows K1(x1), K2(x2), K12(x1 - x2):
@@ -57,7 +57,8 @@ namespace {
 
 using slice::kDig;
 
-constexpr int NK = 64, THREADS = 256, PER = NK * NK / THREADS;
+constexpr int NK = 64, THREADS = 512, PER = NK * NK / THREADS;
+constexpr int ISSUER = THREADS / 32 - 1, BUILDERS = THREADS - 32;  // the last warp issues the products
 constexpr uint32_t MAT = NK * NK * 2;       // one 64 x 64 BF16 matrix, tiled
 constexpr uint32_t HMAT = 15 * 128;         // one Hankel matrix (15 core matrices)
 constexpr uint32_t GMAT = 2 * NK * NK * 2;  // one sheared plane, 128 x 64
@@ -165,40 +166,6 @@ __device__ __forceinline__ void issue_two_body(uint32_t sb, uint32_t tmem, int s
 
 // ---- operand builders (all threads) -------------------------------------------
 
-// Digit tables: word w of table (fam, t) holds the BF16 digits t of K_fam(2w)
-// and K_fam(2w + 1) (fam 0: K1(x1), 1: K2(x2), 2: K12(x1 - x2), 3: K12 times
-// 2^-8; entry j is the kernel at offset j - 63; entry 127 is zero).
-__device__ __forceinline__ void build_tables(uint32_t *tabs, const double *k1, const double *k2, const double *k12,
-                                             int kmax) {
-  uint16_t *t16 = reinterpret_cast<uint16_t *>(tabs);
-  for (int e = threadIdx.x; e < 3 * 128; e += THREADS) {
-    const int fam = e >> 7, j = e & 127;
-    const double *row = fam == 0 ? k1 : fam == 1 ? k2 : k12;
-    int dk[kDig];
-    slice::digits6(j < 2 * NK - 1 ? row[j] : 0.0, kmax, dk);
-#pragma unroll
-    for (int t = 0; t < kDig; ++t) {
-      const uint16_t u = (uint16_t)slice::bf16_int(dk[t]);
-      t16[(fam * kDig + t) * 128 + j] = u;
-      if (fam == 2) t16[(3 * kDig + t) * 128 + j] = dk[t] ? (uint16_t)(u - 0x0400) : (uint16_t)0;
-    }
-  }
-}
-
-// Toeplitz digit matrices M[r][k] = K(k - r), tiled K-major: A1_t (K1) after
-// the zero matrix at OFF_T1, B2_t (K2) at OFF_B2.  Thread q writes the 16
-// bytes at chunk q of its matrix (row r, columns 8 kg .. 8 kg + 7).
-__device__ __forceinline__ void build_toeplitz(unsigned char *sm, const uint32_t *tabs) {
-  for (int q = threadIdx.x; q < 2 * kDig * 512; q += THREADS) {
-    const int m = q >> 9, ch = q & 511;
-    const int r = ((ch >> 6) << 3) + (ch & 7), kg = (ch >> 3) & 7;
-    const int fam = m >= kDig, t = m - fam * kDig;
-    const uint4 v = window8(tabs + (fam * kDig + t) * 64, 8 * kg - r + 63);
-    unsigned char *dst = sm + (fam ? OFF_B2 + (uint32_t)t * MAT : OFF_T1 + (uint32_t)(t + 1) * MAT);
-    *reinterpret_cast<uint4 *>(dst + toff(r, 8 * kg, NK)) = v;
-  }
-}
-
 // Hankel digit matrices of the pair kernel: core matrix q (0..14), row b,
 // entry a holds K12(63 - 8 q - a - b), the eight table entries from
 // 119 - 8 q - b in reverse order; H_t (family 2) then H'_t (family 3).
@@ -213,15 +180,15 @@ __device__ __forceinline__ void build_hankel(unsigned char *sm, const uint32_t *
   }
 }
 
-// Sheared plane of digit s into buffer s & 1: G_s[c][k'] = F_s[63 - k'][c - 63 + k'],
+// Sheared plane of digit s into buffer s & 1, by threads t0, t0 + nt, ...: G_s[c][k'] = F_s[63 - k'][c - 63 + k'],
 // MN-major (core (k' / 8, c / 8), row k' % 8, entries c % 8 .. + 7).  The
 // eight entries of a core row are a window of row 63 - k' of F_s starting at
 // m0 = c - 63 + k' (zero outside the block), cut from two 16-byte chunks.
-__device__ __forceinline__ void build_sheared(unsigned char *sm, int s) {
+__device__ __forceinline__ void build_sheared(unsigned char *sm, int s, int t0, int nt) {
   const unsigned char *P = sm + OFF_F + (uint32_t)(s + 1) * MAT;
   unsigned char *G = sm + OFF_G + (uint32_t)(s & 1) * GMAT;
   const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-  for (int q = threadIdx.x; q < 1024; q += THREADS) {
+  for (int q = t0; q < 1024; q += nt) {
     const int kp = ((q >> 7) << 3) + (q & 7), cg = (q >> 3) & 15;
     const int r = 63 - kp, m0 = 8 * cg - 63 + kp, o = m0 & 7, jc = (m0 - o) >> 3;
     const uint4 lo = (unsigned)jc < 8u ? *reinterpret_cast<const uint4 *>(P + toff(r, 8 * jc, NK)) : z;
@@ -234,24 +201,10 @@ __device__ __forceinline__ void build_sheared(unsigned char *sm, int s) {
 
 __device__ __forceinline__ long long ll_of(uint32_t bits) { return (long long)__float2int_rn(__uint_as_float(bits)); }
 
-// One CTA per spatial point X (with a.sym: per X with i1 <= i2, the mirror
-// block written as well).  MODE 0: out = Theta[in].  MODE 1: out = h + half_tau Theta[in].
-template <int MODE>
-__global__ void __launch_bounds__(THREADS, 1) k_theta_t(ThetaArgs a) {
-  extern __shared__ __align__(1024) unsigned char sm[];
-  // mbar[0], mbar[1]: sheared buffer 0 / 1 consumed; mbar[2]: every product issued has completed
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + OFF_MISC);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + OFF_MISC + 24);
-  int *flag = reinterpret_cast<int *>(sm + OFF_MISC + 28);       // a wait timed out
-  int *red = reinterpret_cast<int *>(sm + OFF_MISC + 64);        // 32 ints + 32 long longs
-  uint32_t *tabs = reinterpret_cast<uint32_t *>(sm + OFF_G + GMAT);
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const uint32_t sb = umma::smem_u32(sm);
-
+// Block number b -> (i1, i2): row-major, or with a.sym the upper triangle row by row.
+__device__ __forceinline__ void block_xy(const ThetaArgs &a, int b, int &i1, int &i2) {
   const int nx = a.nx;
-  int i1, i2;
-  if (a.sym) {  // block b of the upper triangle, row by row: i1 <= i2
-    int b = blockIdx.x;
+  if (a.sym) {
     i1 = 0;
     while (b >= nx - i1) {
       b -= nx - i1;
@@ -259,15 +212,109 @@ __global__ void __launch_bounds__(THREADS, 1) k_theta_t(ThetaArgs a) {
     }
     i2 = i1 + b;
   } else {
-    i1 = blockIdx.x / nx;
-    i2 = blockIdx.x - i1 * nx;
+    i1 = b / nx;
+    i2 = b - i1 * nx;
   }
-  const int X = i1 * nx + i2;
-  int dd = i1 - i2;
-  dd += (dd < 0) ? nx : 0;
-  const size_t base = (size_t)X * NK * NK;
+}
+
+// What a CTA reads from HBM for a block before its digits are cut, loaded one
+// block ahead: the state block (core matrices 4 w .. 4 w + 3 of warp w, thread
+// (row lane / 4, columns 2 (lane % 4), + 1), 64-byte row segments) and one
+// value of the block's three kernel rows (entry tid of 3 x 127, or zero).
+struct Ahead {
+  double2 f[4];
+  double k;
+};
+
+__device__ __forceinline__ void load_ahead(const ThetaArgs &a, int b, Ahead &p) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  int i1, i2;
+  block_xy(a, b, i1, i2);
+  const size_t base = (size_t)(i1 * a.nx + i2) * NK * NK;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int cm = 4 * w + i, r = 8 * (cm >> 3) + (lane >> 2), c = 8 * (cm & 7) + 2 * (lane & 3);
+    p.f[i] = *reinterpret_cast<const double2 *>(a.in + base + (size_t)r * NK + c);
+  }
   constexpr int W = 2 * NK - 1;
-  const double *k1row = a.K1 + (size_t)i1 * W, *k2row = a.K2 + (size_t)i2 * W, *k12row = a.K12 + (size_t)dd * W;
+  int dd = i1 - i2;
+  dd += (dd < 0) ? a.nx : 0;
+  if (tid < 3 * W) {
+    const int fam = tid / W, j = tid - fam * W;
+    const double *row = fam == 0 ? a.K1 + (size_t)i1 * W : fam == 1 ? a.K2 + (size_t)i2 * W : a.K12 + (size_t)dd * W;
+    p.k = row[j];
+  } else {
+    p.k = 0.0;
+  }
+}
+
+// Digit tables from the kernel values the threads hold (thread tid < 381:
+// entry tid % 127 of family tid / 127): word w of table (fam, t) holds the
+// BF16 digits t of K_fam(2 w) and K_fam(2 w + 1) (fam 0: K1(x1), 1: K2(x2),
+// 2: K12(x1 - x2), 3: K12 times 2^-8; entry j is the kernel at offset j - 63;
+// entry 127 is zero).
+__device__ __forceinline__ void build_tables(uint32_t *tabs, double k, int kmax) {
+  constexpr int W = 2 * NK - 1;
+  uint16_t *t16 = reinterpret_cast<uint16_t *>(tabs);
+  const int tid = threadIdx.x;
+  if (tid < 4 * kDig) t16[tid * 128 + 127] = 0;
+  if (tid < 3 * W) {
+    const int fam = tid / W, j = tid - fam * W;
+    int dk[kDig];
+    slice::digits6(k, kmax, dk);
+#pragma unroll
+    for (int t = 0; t < kDig; ++t) {
+      const uint16_t u = (uint16_t)slice::bf16_int(dk[t]);
+      t16[(fam * kDig + t) * 128 + j] = u;
+      if (fam == 2) t16[(3 * kDig + t) * 128 + j] = dk[t] ? (uint16_t)(u - 0x0400) : (uint16_t)0;
+    }
+  }
+}
+
+// Toeplitz digit matrices M[r][k] = K(k - r), tiled K-major, of family fam
+// (0: A1_t of K1 after the zero matrix at OFF_T1; 1: B2_t of K2 at OFF_B2).
+// Thread q writes the 16 bytes at chunk q of its matrix (row r, columns 8 kg .. + 7).
+__device__ __forceinline__ void build_toeplitz(unsigned char *sm, const uint32_t *tabs, int fam) {
+  for (int q = threadIdx.x; q < kDig * 512; q += THREADS) {
+    const int t = q >> 9, ch = q & 511;
+    const int r = ((ch >> 6) << 3) + (ch & 7), kg = (ch >> 3) & 7;
+    const uint4 v = window8(tabs + (fam * kDig + t) * 64, 8 * kg - r + 63);
+    unsigned char *dst = sm + (fam ? OFF_B2 + (uint32_t)t * MAT : OFF_T1 + (uint32_t)(t + 1) * MAT);
+    *reinterpret_cast<uint4 *>(dst + toff(r, 8 * kg, NK)) = v;
+  }
+}
+
+// Persistent CTAs, one per SM: CTA c takes the blocks b in [c P, (c + 1) P)
+// (P = ceil(blocks / CTAs)) in order, so that consecutive blocks mostly share
+// i1 and the A1 digit matrices are rebuilt only when i1 changes.  Per block:
+// digits and operands, the products (two-body digit 0, its completion signal,
+// the one-body chains, then digits 1..5 with the sheared planes rebuilt
+// alternately), the next block's state and kernel values loaded while the
+// last products run, the epilogue.  MODE 0: out = Theta[in].  MODE 1: out =
+// h + half_tau Theta[in], with the exact per-X sums of out.  With a.sym the
+// blocks are those with i1 <= i2 and each mirror block is written as well.
+template <int MODE>
+__global__ void __launch_bounds__(THREADS, 1) k_theta_t(ThetaArgs a) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  // mbar[0], mbar[1]: sheared buffer 0 / 1 consumed; mbar[2]: every product
+  // issued has completed; mbar[3], mbar[4]: sheared buffer 0 / 1 built (one
+  // arrival per builder warp)
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + OFF_MISC);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + OFF_MISC + 40);
+  int *flag = reinterpret_cast<int *>(sm + OFF_MISC + 44);  // a wait timed out
+  int *red = reinterpret_cast<int *>(sm + OFF_MISC + 64);   // 32 ints + 32 long longs
+  uint32_t *tabs = reinterpret_cast<uint32_t *>(sm + OFF_G + GMAT);
+  long long *I12 = reinterpret_cast<long long *>(sm + OFF_B2);        // epilogue: after the products
+  double *C = reinterpret_cast<double *>(sm + OFF_F + MAT);            // mirror staging, after the zero plane
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const uint32_t sb = umma::smem_u32(sm);
+  const int nx = a.nx;
+  const int nblocks = a.sym ? nx * (nx + 1) / 2 : nx * nx;
+  const int per = (nblocks + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int b0 = (int)blockIdx.x * per, b1 = min(nblocks, b0 + per);
+  if (b0 >= b1) return;
+  const long long limit = a.wait_limit > 0 ? a.wait_limit : WAIT_LIMIT;
+  constexpr int W = 2 * NK - 1;
 
   if (w == 0) {
     umma::tmem_alloc(tslot, 512);
@@ -277,6 +324,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_theta_t(ThetaArgs a) {
     umma::mbar_init(&mbar[0], 1);
     umma::mbar_init(&mbar[1], 1);
     umma::mbar_init(&mbar[2], 1);
+    umma::mbar_init(&mbar[3], BUILDERS / 32);
+    umma::mbar_init(&mbar[4], BUILDERS / 32);
     *flag = 0;
   }
   {
@@ -286,187 +335,209 @@ __global__ void __launch_bounds__(THREADS, 1) k_theta_t(ThetaArgs a) {
       reinterpret_cast<uint4 *>(sm + OFF_T1)[i] = z;
     }
   }
-
-  // State block, one core matrix (8 x 8) per warp and step: thread (row
-  // lane / 4, columns 2 (lane % 4), + 1), 64-byte row segments in HBM.
-  double2 fv[8];
-  int ef = 0, ek = 0;
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int cm = 8 * w + i, r = 8 * (cm >> 3) + (lane >> 2), c = 8 * (cm & 7) + 2 * (lane & 3);
-    fv[i] = *reinterpret_cast<const double2 *>(a.in + base + (size_t)r * NK + c);
-    ef = max(ef, max(slice::expo(fv[i].x), slice::expo(fv[i].y)));
-  }
-  for (int e = tid; e < 3 * W; e += THREADS) {
-    const int fam = e / W, j = e - fam * W;
-    ek = max(ek, slice::expo((fam == 0 ? k1row : fam == 1 ? k2row : k12row)[j]));
-  }
-  // the corrector's base, read now so that its latency hides behind the products
-  double hv[PER];
-#pragma unroll
-  for (int i = 0; i < PER; ++i) hv[i] = MODE == 1 ? a.h[base + tid + i * THREADS] : 0.0;
-  ef = __reduce_max_sync(0xffffffffu, ef);
-  ek = __reduce_max_sync(0xffffffffu, ek);
-  if (lane == 0) {
-    red[w] = ef;
-    red[16 + w] = ek;
-  }
-  __syncthreads();
-  ef = ek = 0;
-#pragma unroll
-  for (int q = 0; q < THREADS / 32; ++q) {
-    ef = max(ef, red[q]);
-    ek = max(ek, red[16 + q]);
-  }
-  const bool bad = ef == 2047 || ek == 2047;
-  const int emax = max(ef, 1), kmax = max(ek, 1);
-
-  // Digit planes F_s (tiled, 128 contiguous bytes per warp and step) and the kernel digit tables.
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int cm = 8 * w + i, r = 8 * (cm >> 3) + (lane >> 2), c = 8 * (cm & 7) + 2 * (lane & 3);
-    int dx[kDig], dy[kDig];
-    slice::digits6(fv[i].x, emax, dx);
-    slice::digits6(fv[i].y, emax, dy);
-#pragma unroll
-    for (int s = 0; s < kDig; ++s)
-      *reinterpret_cast<uint32_t *>(sm + OFF_F + (uint32_t)(s + 1) * MAT + toff(r, c, NK)) =
-          slice::bf16_int(dx[s]) | (slice::bf16_int(dy[s]) << 16);
-  }
-  build_tables(tabs, k1row, k2row, k12row, kmax);
-  __syncthreads();
-  build_toeplitz(sm, tabs);
-  build_hankel(sm, tabs);
-  build_sheared(sm, 0);
-  umma::fence_proxy_async();
   umma::fence_before();
   __syncthreads();
   umma::fence_after();
   const uint32_t tmem = *tslot;
-  // The first sheared plane's products and their completion signal go first,
-  // so that the plane's buffer frees early; the one-body chains follow.
-  if (tid == 0) {
-    issue_two_body(sb, tmem, 0);
-    umma::mma_commit(&mbar[0]);
-    issue_one_body(sb, tmem, 0, 24);
-  }
-  // Digits 1..5 of the sheared plane, each built while the tensor core works
-  // on the previous one; buffer b is rebuilt after its last products completed.
-  const long long limit = a.wait_limit > 0 ? a.wait_limit : WAIT_LIMIT;
-  for (int s = 1; s < kDig; ++s) {
-    const int b = s & 1;
-    if (s >= 2 && !*flag && !umma::mbar_wait_bounded(&mbar[b], (uint32_t)((s - 2) >> 1) & 1u, limit))
-      atomicOr(flag, 1);
-    build_sheared(sm, s);
-    umma::fence_proxy_async();
-    umma::fence_before();
-    __syncthreads();
-    umma::fence_after();
-    // a.stall (host-side fault injection): digit 1's products and their
-    // completion signal are left out, so the wait at digit 3 runs out
-    if (tid == 0 && !*flag && !(a.stall && s == 1)) {
-      issue_two_body(sb, tmem, s);
-      umma::mma_commit(&mbar[b]);
-    }
-  }
-  // One more completion signal covers every product issued; tensor memory is
-  // read and released only after it (or after the bounded wait gave up).
-  if (tid == 0) umma::mma_commit(&mbar[2]);
-  if (!umma::mbar_wait_bounded(&mbar[2], 0u, limit)) atomicOr(flag, 1);
-  umma::fence_after();
-  __syncthreads();
-  const bool tmo = *flag != 0;
-  if (tmo && tid == 0 && a.err) atomicOr(a.err, 1);
-
-  // Epilogue.  Warp w reads TMEM lanes 32 (w % 4) .. + 31 and columns
-  // 32 (w / 4) .. + 31 of each accumulator.  The integers, in units of 2^4
-  // diagonal-5 units (2^-4 of a diagonal-4 unit, as in k_theta_s), go to
-  // I12[n1][n2] (int64, row stride 65): the one-body top half (diagonals 0, 2,
-  // 4) written, the bottom half (1, 3, 5) added, then the two-body part of
-  // lane c added at (n1, c - n1).
-  long long *I12 = reinterpret_cast<long long *>(sm + OFF_T1);
-  const int qd = w & 3, ch = w >> 2, L = 32 * qd + lane;
+  const int qd = w & 3, cg = w >> 2, L = 32 * qd + lane;  // epilogue: TMEM lane L, columns 16 cg .. + 15
   const uint32_t tl = tmem + ((uint32_t)(32 * qd) << 16);
-  {
-    long long acc[32];
+
+  Ahead p;
+  load_ahead(a, b0, p);
+  int last_i1 = -1, last_kmax = -1;
+  for (int b = b0, j = 0; b < b1; ++b, ++j) {
+    int i1, i2;
+    block_xy(a, b, i1, i2);
+    const int X = i1 * nx + i2;
+    const size_t base = (size_t)X * NK * NK;
+    const bool mirror = a.sym && i1 != i2;
+    __syncthreads();  // the previous block's epilogue is done with I12, C and red
+    const bool skip = *flag != 0;
+
+    int ef = 0, ek = slice::expo(p.k);
 #pragma unroll
-    for (int j = 0; j < 32; ++j) acc[j] = 0;
-    const bool top = qd < 2;
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-      uint32_t r[32];
-      umma::tmem_ld32(tl + COL_Q + 64u * e + 32u * ch, r);
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const long long v = ll_of(r[j]);
-        if (top)
-          acc[j] += v * (1ll << (8 * (4 - 2 * e) + 4));
-        else if (e < 2)
-          acc[j] += v * (1ll << (8 * (3 - 2 * e) + 4));
-        else
-          acc[j] += (v + 8) >> 4;  // diagonal 5, rounded to the unit
-      }
-    }
-    const int n1 = L & 63;
-    if (top) {
-#pragma unroll
-      for (int j = 0; j < 32; ++j) I12[n1 * IST + 32 * ch + j] = acc[j];
+    for (int i = 0; i < 4; ++i) ef = max(ef, max(slice::expo(p.f[i].x), slice::expo(p.f[i].y)));
+    ef = __reduce_max_sync(0xffffffffu, ef);
+    ek = __reduce_max_sync(0xffffffffu, ek);
+    if (lane == 0) {
+      red[w] = ef;
+      red[16 + w] = ek;
     }
     __syncthreads();
-    if (!top) {
+    ef = ek = 0;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) I12[n1 * IST + 32 * ch + j] += acc[j];
+    for (int q = 0; q < THREADS / 32; ++q) {
+      ef = max(ef, red[q]);
+      ek = max(ek, red[16 + q]);
     }
-    __syncthreads();
-  }
-  {
-    long long acc[32];
+    const bool bad = ef == 2047 || ek == 2047;
+    const int emax = max(ef, 1), kmax = max(ek, 1);
+
+    if (!skip) {
+      // digit planes F_s (one core matrix per warp and step) and the digit tables
 #pragma unroll
-    for (int j = 0; j < 32; ++j) acc[j] = 0;
+      for (int i = 0; i < 4; ++i) {
+        const int cm = 4 * w + i, r = 8 * (cm >> 3) + (lane >> 2), c = 8 * (cm & 7) + 2 * (lane & 3);
+        int dx[kDig], dy[kDig];
+        slice::digits6(p.f[i].x, emax, dx);
+        slice::digits6(p.f[i].y, emax, dy);
 #pragma unroll
-    for (int d = 0; d < 5; ++d) {
-      uint32_t r[32];
-      umma::tmem_ld32(tl + COL_P + 64u * d + 32u * ch, r);
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        if (d < 4)
-          acc[j] += ll_of(r[j]) * (1ll << (8 * (4 - d) + 4));
-        else
-          acc[j] += __float2ll_rn(__uint_as_float(r[j]) * 16.f);
+        for (int s = 0; s < kDig; ++s)
+          *reinterpret_cast<uint32_t *>(sm + OFF_F + (uint32_t)(s + 1) * MAT + toff(r, c, NK)) =
+              slice::bf16_int(dx[s]) | (slice::bf16_int(dy[s]) << 16);
+      }
+      build_tables(tabs, p.k, kmax);
+      __syncthreads();
+      // A1 depends on i1 and on the kernel rows' shared exponent: rebuilt when either differs
+      if (i1 != last_i1 || kmax != last_kmax) build_toeplitz(sm, tabs, 0);
+      build_toeplitz(sm, tabs, 1);
+      build_hankel(sm, tabs);
+      build_sheared(sm, 0, tid, THREADS);
+      umma::fence_proxy_async();
+      umma::fence_before();
+      __syncthreads();
+      umma::fence_after();
+      if (w == ISSUER) {
+        // the issuing warp: digit 0's two-body products, their signal, the
+        // one-body chains, then digits 1..5 as their planes are reported built
+        if (lane == 0) {
+          issue_two_body(sb, tmem, 0);
+          umma::mma_commit(&mbar[0]);
+          issue_one_body(sb, tmem, 0, 24);
+          for (int s = 1; s < kDig; ++s) {
+            const int bb = s & 1;
+            const uint32_t par = (uint32_t)(bb ? 3 * j + ((s - 1) >> 1) : 2 * j + (s >> 1) - 1) & 1u;
+            if (!*flag && !umma::mbar_wait_bounded(&mbar[3 + bb], par, limit)) atomicOr(flag, 1);
+            umma::fence_after();
+            // a.stall (host-side fault injection): digit 1's products and their
+            // completion signal are left out, so the builders' wait at digit 3 runs out
+            if (!*flag && !(a.stall && s == 1)) {
+              issue_two_body(sb, tmem, s);
+              umma::mma_commit(&mbar[bb]);
+            }
+          }
+          umma::mma_commit(&mbar[2]);
+        }
+        __syncwarp();
+      } else {
+        // the builder warps: plane s into buffer s & 1 once digit s - 2's
+        // products have released it, then one arrival per warp
+        for (int s = 1; s < kDig; ++s) {
+          const int bb = s & 1;
+          const uint32_t par = (uint32_t)(3 * j + ((s - 2) >> 1)) & 1u;
+          if (s >= 2 && !*flag && !umma::mbar_wait_bounded(&mbar[bb], par, limit)) atomicOr(flag, 1);
+          build_sheared(sm, s, tid, BUILDERS);
+          umma::fence_proxy_async();
+          __syncwarp();
+          if (lane == 0) umma::mbar_arrive(&mbar[3 + bb]);
+        }
       }
     }
+    last_i1 = i1;
+    last_kmax = kmax;
+
+    // the corrector's base for this block and the next block's inputs, read
+    // while the last products run
+    double hv[PER];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const int n1 = 32 * ch + j, n2 = L - n1;
-      if ((unsigned)n2 < (unsigned)NK) I12[n1 * IST + n2] += acc[j];
+    for (int i = 0; i < PER; ++i) hv[i] = MODE == 1 ? a.h[base + tid + i * THREADS] : 0.0;
+    if (b + 1 < b1) load_ahead(a, b + 1, p);
+    if (!skip && !umma::mbar_wait_bounded(&mbar[2], (uint32_t)j & 1u, limit)) atomicOr(flag, 1);
+    umma::fence_after();
+    __syncthreads();
+    const bool tmo = *flag != 0;
+    if (tmo && !skip && tid == 0 && a.err) atomicOr(a.err, 1);
+
+    // Epilogue.  Warp w reads TMEM lanes 32 (w % 4) .. + 31, columns 16 (w / 4)
+    // .. + 15 of each accumulator.  The integers, in units of 2^4 diagonal-5
+    // units (2^-4 of a diagonal-4 unit, as in k_theta_s), go to I12[n1][n2]
+    // (int64, row stride 65): the one-body top half (diagonals 0, 2, 4)
+    // written, the bottom half (1, 3, 5) added, then the two-body part of lane
+    // c added at (n1, c - n1).
+    if (!tmo) {
+      {
+        long long acc[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) acc[q] = 0;
+        const bool top = qd < 2;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+          uint32_t r[16];
+          umma::tmem_ld16(tl + COL_Q + 64u * e + 16u * cg, r);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const long long v = ll_of(r[q]);
+            if (top)
+              acc[q] += v * (1ll << (8 * (4 - 2 * e) + 4));
+            else if (e < 2)
+              acc[q] += v * (1ll << (8 * (3 - 2 * e) + 4));
+            else
+              acc[q] += (v + 8) >> 4;  // diagonal 5, rounded to the unit
+          }
+        }
+        const int n1 = L & 63;
+        if (top) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) I12[n1 * IST + 16 * cg + q] = acc[q];
+        }
+        __syncthreads();
+        if (!top) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) I12[n1 * IST + 16 * cg + q] += acc[q];
+        }
+        __syncthreads();
+      }
+      {
+        long long acc[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) acc[q] = 0;
+#pragma unroll
+        for (int d = 0; d < 5; ++d) {
+          uint32_t r[16];
+          umma::tmem_ld16(tl + COL_P + 64u * d + 16u * cg, r);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            if (d < 4)
+              acc[q] += ll_of(r[q]) * (1ll << (8 * (4 - d) + 4));
+            else
+              acc[q] += __float2ll_rn(__uint_as_float(r[q]) * 16.f);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int n1 = 16 * cg + q, n2 = L - n1;
+          if ((unsigned)n2 < (unsigned)NK) I12[n1 * IST + n2] += acc[q];
+        }
+      }
+      umma::fence_before();
+      __syncthreads();
+    }
+
+    // FP64 outputs (row-major, coalesced), the corrector combination, the
+    // exact per-X sum and the mirror block.
+    const int xs = emax + kmax - 2096;  // one unit of I12 is 2^xs
+    const bool nan_out = bad || tmo;
+    double v[PER];
+    int em = 0;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int e = tid + i * THREADS, n1 = e >> 6, n2 = e & 63;
+      const double t =
+          nan_out ? __longlong_as_double(0x7ff8000000000000ll) : ll_to_double_scaled(I12[n1 * IST + n2], xs);
+      if (mirror) C[n1 * IST + n2] = t;
+      v[i] = MODE == 0 ? t : fma(a.half_tau, t, hv[i]);
+      a.out[base + e] = v[i];
+      em = max(em, slice::expo(v[i]));
+    }
+    if (MODE == 1 && a.xsum) slice::held_exact_sum<PER>(v, em, a.xsum + X, red);
+    if (mirror) {
+      __syncthreads();
+      slice::mirror_block<NK, THREADS, MODE>(a, C, i2 * nx + i1, red);
     }
   }
   umma::fence_before();
   __syncthreads();
   if (w == 0) umma::tmem_dealloc(tmem, 512);
-
-  // FP64 outputs (row-major, coalesced), the corrector combination, the exact
-  // per-X sum and the mirror block.
-  const int xs = emax + kmax - 2096;  // one unit of I12 is 2^xs
-  const bool nan_out = bad || tmo;
-  const bool mirror = a.sym && i1 != i2;
-  double *C = reinterpret_cast<double *>(sm + OFF_B2);
-  double v[PER];
-  int em = 0;
-#pragma unroll
-  for (int i = 0; i < PER; ++i) {
-    const int e = tid + i * THREADS, n1 = e >> 6, n2 = e & 63;
-    const double t = nan_out ? __longlong_as_double(0x7ff8000000000000ll) : ll_to_double_scaled(I12[n1 * IST + n2], xs);
-    if (mirror) C[n1 * IST + n2] = t;
-    v[i] = MODE == 0 ? t : fma(a.half_tau, t, hv[i]);
-    a.out[base + e] = v[i];
-    em = max(em, slice::expo(v[i]));
-  }
-  if (MODE == 1 && a.xsum) slice::held_exact_sum<PER>(v, em, a.xsum + X, red);
-  if (mirror) {
-    __syncthreads();
-    slice::mirror_block<NK, THREADS, MODE>(a, C, i2 * nx + i1, red);
-  }
 }
 
 }  // namespace
@@ -482,7 +553,12 @@ cudaError_t prepare_kernels_f64t() {
 // The tcgen05 sweep (mode 0 / 1 as launch_theta_f64s) for N_k = 64 without a
 // learned pair term.
 cudaError_t launch_theta_f64t(int mode, const ThetaArgs &a, cudaStream_t s) {
-  const int grid = a.sym ? a.nx * (a.nx + 1) / 2 : a.nx * a.nx;
+  const int nblocks = a.sym ? a.nx * (a.nx + 1) / 2 : a.nx * a.nx;
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int grid = nblocks < nsm ? nblocks : nsm;
   if (mode == 0)
     k_theta_t<0><<<grid, THREADS, SMEM, s>>>(a);
   else

@@ -112,6 +112,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// One arrival on *mbar (release: this thread's earlier shared-memory writes,
+// with fence_proxy_async before it also to the tensor core, happen before
+// the phase completes).
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
+  unsigned long long state;
+  asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];\n" : "=l"(state) : "r"(smem_u32(mbar)) : "memory");
+  (void)state;
+}
 // Wait for the phase with parity `parity` of *mbar to complete, for at most
 // `limit` SM clock cycles; false if it did not.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parity, long long limit) {

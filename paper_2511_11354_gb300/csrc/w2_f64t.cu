@@ -43,9 +43,10 @@
 // d = 5 part rounded to that unit), the two-body part added through shared
 // memory at (n1, c - n1), and converted to FP64 with integer operations.
 //
-// Every wait on the tensor core is bounded (about a second); on time-out the
-// CTA stops issuing, marks its outputs NaN, sets a.err if given, and still
-// releases its tensor memory.
+// Every wait is bounded (about a second, or a.wait_limit clocks); on time-out
+// the CTA stops issuing, waits for the products it did issue, marks its
+// outputs NaN (this block and the rest of its run), sets a.err if given, and
+// still releases its tensor memory.
 #include <math.h>
 #include <stdint.h>
 
@@ -63,16 +64,16 @@ constexpr uint32_t MAT = NK * NK * 2;       // one 64 x 64 BF16 matrix, tiled
 constexpr uint32_t HMAT = 15 * 128;         // one Hankel matrix (15 core matrices)
 constexpr uint32_t GMAT = 2 * NK * NK * 2;  // one sheared plane, 128 x 64
 // shared memory map (bytes)
-constexpr uint32_t OFF_F = 0;                      // [zero, F_0 .. F_5]
-constexpr uint32_t OFF_T1 = OFF_F + 7 * MAT;       // [zero, A1_0 .. A1_5]; later the int64 sums I12
-constexpr uint32_t OFF_B2 = OFF_T1 + 7 * MAT;      // [B2_0 .. B2_5]; later Theta for the mirror block
+constexpr uint32_t OFF_F = 0;                      // [zero, F_0 .. F_5]; in the epilogue the mirror staging after the zero
+constexpr uint32_t OFF_T1 = OFF_F + 7 * MAT;       // [zero, A1_0 .. A1_5] (kept along a row of blocks)
+constexpr uint32_t OFF_B2 = OFF_T1 + 7 * MAT;      // [B2_0 .. B2_5]; in the epilogue the int64 sums I12
 constexpr uint32_t OFF_H = OFF_B2 + 6 * MAT;       // [H_0 .. H_5, H'_0 .. H'_5] (H' = 2^-8 H)
 constexpr uint32_t OFF_G = OFF_H + 12 * HMAT;      // two sheared planes; the digit tables before
 constexpr uint32_t OFF_MISC = OFF_G + 2 * GMAT;    // mbarriers, TMEM address, reduction scratch
 constexpr uint32_t SMEM = OFF_MISC + 512;
 static_assert(OFF_G % 16 == 0 && OFF_H % 16 == 0, "operands on 16-byte boundaries");
 static_assert(SMEM <= 227 * 1024, "shared memory");
-static_assert(NK * 65 * 8 <= 7 * MAT && NK * 65 * 8 <= 6 * MAT, "epilogue buffers fit");
+static_assert(NK * 65 * 8 <= 6 * MAT, "epilogue buffers fit (I12 in B2, the mirror staging in F_0 .. F_5)");
 constexpr int IST = NK + 1;                        // row stride of I12 and of the mirror staging
 // TMEM columns: Q0, Q2, Q4 (one-body), then the two-body diagonals 0..3 and 4/5
 constexpr uint32_t COL_Q = 0, COL_P = 192;

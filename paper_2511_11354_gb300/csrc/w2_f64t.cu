@@ -117,17 +117,13 @@ __device__ __forceinline__ uint4 shift8(uint4 lo, uint4 hi, int o) {
 //   T1: A = [A1_ts ; A1_(ts+1)] K-major (core strides: K 128, M 1024),
 //       B = F_s MN-major (K 1024, N 128);
 //   T2: A = [F_ss ; F_(ss+1)] K-major (K 128, M 1024), B = B2_t K-major (K 128, N 1024).
-// Digit -1 is the zero matrix stored just before digit 0.  The 24 chains
-// (12 of T1, then 12 of T2) are numbered in this order; a call issues those
-// with numbers in [c0, c1), so that the issuing thread can spread them over
-// the sheared-plane steps.  The first product into each accumulator (the
-// s = 0 dominoes of T1, chains 0..2) overwrites it.
-__device__ __forceinline__ void issue_one_body(uint32_t sb, uint32_t tmem, int c0, int c1) {
+// Digit -1 is the zero matrix stored just before digit 0.  24 chains, 12 of
+// T1 then 12 of T2; the first product into each accumulator (the s = 0
+// dominoes of T1) overwrites it.
+__device__ __forceinline__ void issue_one_body(uint32_t sb, uint32_t tmem) {
   const uint32_t id1 = umma::idesc_bf16(128, 64, false, true), id2 = umma::idesc_bf16(128, 64, false, false);
-  int c = 0;
   for (int s = 0; s < kDig; ++s)
-    for (int ts = (s & 1) ? -1 : 0; s + ts <= 4; ts += 2, ++c) {
-      if (c < c0 || c >= c1) continue;
+    for (int ts = (s & 1) ? -1 : 0; s + ts <= 4; ts += 2) {
       const uint32_t q = tmem + COL_Q + 32u * (uint32_t)(s + ts);
       for (int kc = 0; kc < 4; ++kc) {
         const uint64_t ad = umma::smem_desc(sb + OFF_T1 + (uint32_t)(ts + 1) * MAT + 256u * kc, 128, 1024);
@@ -136,8 +132,7 @@ __device__ __forceinline__ void issue_one_body(uint32_t sb, uint32_t tmem, int c
       }
     }
   for (int t = 0; t < kDig; ++t)
-    for (int ss = (t & 1) ? -1 : 0; ss + t <= 4; ss += 2, ++c) {
-      if (c < c0 || c >= c1) continue;
+    for (int ss = (t & 1) ? -1 : 0; ss + t <= 4; ss += 2) {
       const uint32_t q = tmem + COL_Q + 32u * (uint32_t)(ss + t);
       for (int kc = 0; kc < 4; ++kc) {
         const uint64_t ad = umma::smem_desc(sb + OFF_F + (uint32_t)(ss + 1) * MAT + 256u * kc, 128, 1024);
@@ -404,7 +399,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_theta_t(ThetaArgs a) {
         if (lane == 0) {
           issue_two_body(sb, tmem, 0);
           umma::mma_commit(&mbar[0]);
-          issue_one_body(sb, tmem, 0, 24);
+          issue_one_body(sb, tmem);
           for (int s = 1; s < kDig; ++s) {
             const int bb = s & 1;
             const uint32_t par = (uint32_t)(bb ? 3 * j + ((s - 1) >> 1) : 2 * j + (s >> 1) - 1) & 1u;

@@ -145,6 +145,106 @@ __global__ void __launch_bounds__(256) k_obs_x_exact(ObsArgs a, const double *f)
   }
 }
 
+// k_obs_x_exact for nk = 64 without the shared-memory image: thread t holds
+// column c = t % 64 at rows t / 64 + 4 i (i < 16), so its column sum is its
+// own; the row sums come from a transposing butterfly across the warp (after
+// it, lane l holds the sum of row index l / 2 over the warp's 32 columns) and
+// the two warps of a row group.  The integers are those of k_obs_x_exact; the
+// FP64 share of [1] is summed in a fixed order, so repeated calls agree.
+__global__ void __launch_bounds__(256) k_obs_x_exact64(ObsArgs a, const double *f) {
+  __shared__ long long colp[4][64];
+  __shared__ long long rowp[8][16];
+  __shared__ long long lred[2][8];
+  __shared__ int ired[8];
+  __shared__ double dred[8];
+  const int X = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5, g = tid >> 6, c = tid & 63;
+  const double *fx = f + (size_t)X * 4096;
+  long long im[16];
+  int e1 = 0;
+  {
+    double v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      v[i] = fx[tid + 256 * i];
+      e1 = max(e1, expo_of(v[i]));
+    }
+    e1 = __reduce_max_sync(0xffffffffu, e1);
+    if (lane == 0) ired[w] = e1;
+    __syncthreads();
+    e1 = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) e1 = max(e1, ired[k]);
+    // |f| < 2^(e1 - 1022): every square's biased exponent is at most 2 e1 - 1022
+    const int e2 = max(2 * e1 - 1022, 1);
+    const int eb = max(e1, 1);
+    long long sq = 0, cs = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      im[i] = fixed_image(v[i], eb);
+      cs += im[i];
+      sq += fixed_image(v[i] * v[i], e2);
+    }
+    colp[g][c] = cs;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if (lane == 0) lred[1][w] = sq;
+  }
+  // butterfly: at offset o each lane keeps one half of its entries (by lane
+  // bit o) and adds the partner's copy of that half
+#pragma unroll
+  for (int o = 16, h = 8; o >= 2; o >>= 1, h >>= 1) {
+    const bool hi = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < h; ++j) {
+      const long long send = hi ? im[j] : im[h + j], keep = hi ? im[h + j] : im[j];
+      im[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  im[0] += __shfl_xor_sync(0xffffffffu, im[0], 1);
+  if ((lane & 1) == 0) rowp[w][lane >> 1] = im[0];  // row g + 4 (lane / 2), this warp's 32 columns
+  __syncthreads();
+  const bool bad = e1 == 2047 || 2 * e1 - 1022 > 2046;
+  const int eb = max(e1, 1), e2 = max(2 * e1 - 1022, 1);
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  double *xp = a.xpart + (size_t)X * 67;
+  double t1 = 0.0;
+  long long tot = 0;
+  if (tid < 64) {  // row k and column k
+    const int k = tid, rg = k & 3, ri = k >> 2;
+    const long long rs = rowp[2 * rg][ri] + rowp[2 * rg + 1][ri];
+    const long long cl = colp[0][k] + colp[1][k] + colp[2][k] + colp[3][k];
+    const double drow = bad ? nan : ll_to_double_scaled(rs, eb - 1071);
+    const double dcol = bad ? nan : ll_to_double_scaled(cl, eb - 1071);
+    xp[3 + k] = drow;
+    const double p = (k - 32) * a.dp;
+    t1 = p * p * (drow + dcol);
+    tot = rs;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+  }
+  if (lane == 0) {
+    lred[0][w] = tot;
+    dred[w] = t1;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    long long T = 0, Q = 0;
+    double s1 = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      T += lred[0][q];
+      Q += lred[1][q];
+      s1 += dred[q];
+    }
+    xp[0] = bad ? nan : ll_to_double_scaled(T, eb - 1071);
+    xp[1] = bad ? nan : s1;
+    xp[2] = bad ? nan : ll_to_double_scaled(Q, e2 - 1071);
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_obs_x(ObsArgs a, const T *f) {
   __shared__ double red[3][8];
@@ -316,6 +416,8 @@ cudaError_t launch_obs(const ObsArgs &a, cudaStream_t s) {
   const int nt = a.nk >= 256 ? 256 : 32 * ((a.nk + 31) / 32);  // a thread per row
   if (a.f32)
     k_obs_x<float><<<a.nx * a.nx, nt, sizeof(double) * a.nk, s>>>(a, a.f32);
+  else if (a.nk == 64)
+    k_obs_x_exact64<<<a.nx * a.nx, 256, 0, s>>>(a, a.f);
   else if (a.nk <= 64)
     k_obs_x_exact<<<a.nx * a.nx, 256, 0, s>>>(a, a.f);
   else

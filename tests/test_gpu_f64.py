@@ -105,8 +105,9 @@ def test_step_parity_full_size_workload():
     assert np.abs(got - got.transpose(1, 0, 3, 2)).max() < 1e-13 * np.abs(got).max()
 
 
-def test_observables_parity():
-    prob, f0 = inputs.workload_small()
+@pytest.mark.parametrize("nx,nk", [(32, 32), (24, 64)])
+def test_observables_parity(nx, nk):
+    prob, f0 = inputs.workload_small(nx=nx, nk=nk)
     ctx = _ctx(prob)
     ctx.set_state(f0)
     ctx.step(3)
@@ -118,6 +119,33 @@ def test_observables_parity():
     np.testing.assert_allclose(ob.n1, ref["n1"], rtol=0, atol=1e-13)
     np.testing.assert_allclose(ob.n12, ref["n12"], rtol=0, atol=1e-13)
     assert ob.step == 3 and ob.status == "W2_OK"
+
+
+@pytest.mark.parametrize("prec", ["W2_F64", "W2_F64_SLICED"])
+def test_observables_wide_range_state_64(prec):
+    """The 64-point reduction (warp butterfly for the row sums) on a state of
+    both signs spanning ten decades per block, against the oracle; a NaN in
+    one block gives W2_ERR_NONFINITE with the outputs still written."""
+    from paper_2511_11354_gb300 import w2
+    prob, f0 = inputs.workload_small(nx=12, nk=64)
+    rng = np.random.default_rng(8)
+    f = f0 * np.exp(rng.uniform(-11.5, 11.5, f0.shape)) * np.sign(rng.standard_normal(f0.shape))
+    ctx = w2.Context.from_problem(prob, precision=getattr(w2, prec))
+    ctx.set_state(f)
+    ob = ctx.observables()
+    ref = oracle.Oracle(prob).observables(f)
+    for k in ("mass", "energy", "purity", "l2norm"):
+        assert abs(getattr(ob, k) - ref[k]) <= 1e-12 * max(1.0, abs(ref[k])), k
+    np.testing.assert_allclose(ob.n1, ref["n1"], rtol=1e-12, atol=1e-13 * np.abs(ref["n1"]).max())
+    assert ctx.observables().mass == ob.mass  # deterministic
+    g = f.copy()
+    g[3, 7, 40, 2] = np.nan
+    ctx.set_state(g)
+    bad = ctx.observables()
+    assert bad.status == "W2_ERR_NONFINITE" and np.isnan(bad.mass)
+    with pytest.raises(w2.W2Error) as e:
+        ctx.observables(raise_nonfinite=True)
+    assert e.value.code == -6
 
 
 def test_checkpoint_resume_bitwise_and_determinism():

@@ -310,7 +310,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_theta_t(ThetaArgs a) {
   const int b0 = (int)blockIdx.x * per, b1 = min(nblocks, b0 + per);
   if (b0 >= b1) return;
   const long long limit = a.wait_limit > 0 ? a.wait_limit : WAIT_LIMIT;
-  constexpr int W = 2 * NK - 1;
 
   if (w == 0) {
     umma::tmem_alloc(tslot, 512);

@@ -116,9 +116,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, uint32_t parity) {
 // with fence_proxy_async before it also to the tensor core, happen before
 // the phase completes).
 __device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
-  unsigned long long state;
-  asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];\n" : "=l"(state) : "r"(smem_u32(mbar)) : "memory");
-  (void)state;
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(mbar)) : "memory");
 }
 // Wait for the phase with parity `parity` of *mbar to complete, for at most
 // `limit` SM clock cycles; false if it did not.

@@ -146,3 +146,32 @@ def test_timeout_is_reported_and_recovered():
     c.observables()
     np.testing.assert_array_equal(c.get_state(), want)
     c.close()
+
+
+@pytest.mark.parametrize("sym", [False, True])
+def test_full_size_steps_against_the_oracle(sym):
+    """The 64^4 double-well workload, 2 steps on the tcgen05 path (persistent
+    CTAs over runs of 27 blocks; with exchange symmetry over the 2080 blocks
+    i1 <= i2), every element against the oracle."""
+    prob, f0 = inputs.workload_dwell()
+    c = _ctx(prob)
+    c.set_exchange_symmetry(sym)
+    c.set_state(f0)
+    c.step(2)
+    got = c.get_state()
+    c.close()
+    assert rel(got, oracle.Oracle(prob).step(f0, 2)) < 1e-10
+    assert np.abs(got - got.transpose(1, 0, 3, 2)).max() < 1e-13 * np.abs(got).max()
+
+
+@pytest.mark.parametrize("nx", [5, 13, 33])
+def test_steps_on_ragged_grids(nx):
+    """Whole steps where the blocks do not divide evenly over the CTAs (the
+    last CTA's run is shorter) and the A1 matrices change inside a run."""
+    prob, f0 = inputs.workload_small(nx=nx, nk=64)
+    c = _ctx(prob)
+    c.set_state(f0)
+    c.step(3)
+    got = c.get_state()
+    c.close()
+    assert rel(got, oracle.Oracle(prob).step(f0, 3)) < 1e-10

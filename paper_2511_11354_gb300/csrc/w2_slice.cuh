@@ -22,24 +22,33 @@ __device__ __forceinline__ int expo(double v) {
 // Six balanced base-256 digits of |v| 2^(48 - E), 2^E = 2^(emax - 1022) the
 // block bound (emax the largest biased exponent of the block, >= 1), with v's sign:
 //     round(|v| 2^(48 - E)) = sum_{s=0..5} |d_s| 256^(5-s),  d_0 in [0, 256],  d_1..d_5 in [-128, 127].
+// The 48-bit integer is cut as two 24-bit halves in 32-bit arithmetic: the
+// low half gives d_5..d_3 and a carry of 0 or 1 into the high half, which
+// gives d_2, d_1 and d_0.
 __device__ __forceinline__ void digits6(double v, int emax, int (&d)[kDig]) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);
   const int e = (int)((b >> 52) & 0x7ff);
   const unsigned long long m = (b & 0xfffffffffffffull) | (e ? (1ull << 52) : 0ull);
   const int sh = emax - (e ? e : 1) + 5;  // >= 5
-  long long n = sh < 64 ? (long long)((m + (1ull << (sh - 1))) >> sh) : 0;
+  const unsigned long long n = sh < 64 ? (m + (1ull << (sh - 1))) >> sh : 0ull;  // <= 2^48
+  int lo = (int)(n & 0xffffffull), hi = (int)(n >> 24);
 #pragma unroll
-  for (int s = kDig - 1; s >= 1; --s) {
-    const int lo = (int)(n & 255);
-    const int ds = lo - ((lo & 128) << 1);
+  for (int s = kDig - 1; s >= 3; --s) {
+    const int l = lo & 255, ds = l - ((l & 128) << 1);
     d[s] = ds;
-    n = (n - ds) >> 8;
+    lo = (lo - ds) >> 8;
   }
-  d[0] = (int)n;
-  if (b >> 63) {
+  hi += lo;
 #pragma unroll
-    for (int s = 0; s < kDig; ++s) d[s] = -d[s];
+  for (int s = 2; s >= 1; --s) {
+    const int l = hi & 255, ds = l - ((l & 128) << 1);
+    d[s] = ds;
+    hi = (hi - ds) >> 8;
   }
+  d[0] = hi;
+  const int sg = -(int)(b >> 63);  // 0 or -1: the sign of v on every digit
+#pragma unroll
+  for (int s = 0; s < kDig; ++s) d[s] = (d[s] ^ sg) - sg;
 }
 
 // BF16 bits of a small integer (|d| <= 256): exact through the FP32 magic-number sum.

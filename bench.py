@@ -141,7 +141,7 @@ def _pipe_peaks():
 # of the predictor and the corrector of one ncu capture
 # (profiles/k_theta_s_dwell_64x64.md), keyed by the hash of the kernel's
 # sources (w2_f64s.cu, w2_slice.cuh) it was taken on: any change reports null.
-THETA_TRAFFIC = {"a0d982b65dec86bc": 0.5 * ((134.528000e6 + 93.936128e6) + (268.731392e6 + 91.467008e6))}
+THETA_TRAFFIC = {"9d6719351f777370": 0.5 * ((134.688768e6 + 94.048768e6) + (268.727808e6 + 91.462912e6))}
 
 
 def _theta_traffic():

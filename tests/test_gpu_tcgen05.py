@@ -175,3 +175,27 @@ def test_steps_on_ragged_grids(nx):
     got = c.get_state()
     c.close()
     assert rel(got, oracle.Oracle(prob).step(f0, 3)) < 1e-10
+
+
+def test_setter_errors():
+    """w2_set_tensor_path: W2_ERR_ARG for a value other than 0 or 1,
+    W2_ERR_UNSUPPORTED for tcgen05 = 1 outside W2_F64_SLICED; tcgen05 = 1 at
+    an nk the tcgen05 sweep does not take runs the mma.sync sweep (the same
+    operator).  w2_debug_sweep_stall: W2_ERR_ARG for a bad flag or a negative
+    wait."""
+    from paper_2511_11354_gb300 import w2
+    prob, f0 = inputs.workload_small(nx=8, nk=32)
+    c = w2.Context.from_problem(prob, precision=w2.W2_F64_SLICED)
+    lib = w2.load()
+    assert lib.w2_set_tensor_path(c.h, 2) == -1
+    assert lib.w2_debug_sweep_stall(c.h, 2, 0) == -1
+    assert lib.w2_debug_sweep_stall(c.h, 1, -5) == -1
+    c.set_tensor_path(True)
+    c.set_state(f0)
+    c.step(2)
+    assert rel(c.get_state(), oracle.Oracle(prob).step(f0, 2)) < 1e-10
+    c.close()
+    p = w2.Context.from_problem(prob, precision=w2.W2_F64)
+    assert lib.w2_set_tensor_path(p.h, 1) == -8
+    assert lib.w2_set_tensor_path(p.h, 0) == 0
+    p.close()

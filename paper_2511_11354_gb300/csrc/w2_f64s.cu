@@ -318,7 +318,6 @@ __global__ void __launch_bounds__(SlicedLayout<NK>::THREADS, 512 / SlicedLayout<
     for (; c + 3 <= cend; c += 3) pair_tiles<NK, 3>(planes, pk, I12, r0, c);
     if (cend - c == 2) pair_tiles<NK, 2>(planes, pk, I12, r0, c);
     if (cend - c == 1) pair_tiles<NK, 1>(planes, pk, I12, r0, c);
-    __syncthreads();
   }
 
   // One-body terms T1 = A1(x1) F and T2 = F A2(x2)^T on the digit planes.
@@ -371,14 +370,19 @@ __global__ void __launch_bounds__(SlicedLayout<NK>::THREADS, 512 / SlicedLayout<
     }
   }
 
+  // The one-body products above read only the digit planes and the pair
+  // tables, so each warp went on to them as soon as its sheared tiles were
+  // done; the epilogue reads the other warps' two-body results (and the
+  // mirror staging overwrites the digit planes).
+  const bool mirror = a.sym && i1 != i2;
+  if (two_body || mirror) __syncthreads();
+
   // Epilogue: recombine, add the two-body term, scale, combine with h; in the
   // corrector (with xsum given) also the exact per-X sum of the outputs, whose
   // values wait in the thread's own slots of I12 for the second pass.
   const int xs = emax + kmax - 2096;  // one unit of the recombined integer is 2^xs
   const bool sums = MODE == 1 && a.xsum;
-  const bool mirror = a.sym && i1 != i2;
   double *C = reinterpret_cast<double *>(planes);  // Theta at X for the mirror block, row stride NK + 1
-  if (mirror) __syncthreads();  // every warp is done with the digit planes
   int em_loc = 0;
 #pragma unroll
   for (int q = 0; q < NCT; ++q) {

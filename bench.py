@@ -141,7 +141,7 @@ def _pipe_peaks():
 # of the predictor and the corrector of one ncu capture
 # (profiles/k_theta_s_dwell_64x64.md), keyed by the hash of the kernel's
 # sources (w2_f64s.cu, w2_slice.cuh) it was taken on: any change reports null.
-THETA_TRAFFIC = {"9d6719351f777370": 0.5 * ((134.688768e6 + 94.048768e6) + (268.727808e6 + 91.462912e6))}
+THETA_TRAFFIC = {"0b8020afffd5fb75": 0.5 * ((134.501888e6 + 94.811392e6) + (268.730112e6 + 92.352000e6))}
 
 
 def _theta_traffic():

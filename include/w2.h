@@ -239,7 +239,8 @@ w2_status w2_set_exchange_symmetry(w2_ctx *ctx, int32_t on);
  * to FP64 accuracy and differ only in the rounding of the lowest slice
  * diagonal (below 2^-50 of each block's scale).  A bounded wait of the
  * tcgen05 sweep that gives up (about a second) leaves NaN in its block and
- * makes the next w2_observables return W2_ERR_TIMEOUT.
+ * makes w2_observables return W2_ERR_TIMEOUT until a new state is set
+ * (w2_set_state or w2_use_staged_state clears the error).
  * Errors: W2_ERR_ARG (tcgen05 not 0 or 1), W2_ERR_UNSUPPORTED (tcgen05 = 1 and
  * not W2_F64_SLICED). */
 w2_status w2_set_tensor_path(w2_ctx *ctx, int32_t tcgen05);

@@ -431,6 +431,7 @@ extern "C" w2_status w2_set_state(w2_ctx *ctx, const void *f, int32_t on_device)
   W2_TRY(cudaMemcpyAsync(ctx->f, f, ctx->esz * ctx->npts,
                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
   W2_TRY(state_sums(ctx, ctx->stream));
+  W2_TRY(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));  // a new state starts without a time-out
   ctx->have_state = true;
   ctx->steps = 0;
   return W2_OK;
@@ -472,6 +473,7 @@ extern "C" w2_status w2_use_staged_state(w2_ctx *ctx) {
   ctx->f = static_cast<double *>(staged);
   W2_TRY(cudaEventRecord(ctx->ev_taken, ctx->stream));
   W2_TRY(state_sums(ctx, ctx->stream));
+  W2_TRY(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));  // a new state starts without a time-out
   ctx->taken_recorded = true;
   ctx->stage_pending = false;
   ctx->have_state = true;
